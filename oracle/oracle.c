@@ -1,0 +1,551 @@
+/*
+ * oracle.c -- plain, slow, obviously correct CPU reference of the calculus of
+ * Henrio, Kessler and Li (arXiv 1910.11110).  TEST INFRASTRUCTURE ONLY: it is
+ * loaded by tests/, by __graft_entry__.smoke() and by bench.py's cpu_baseline
+ * and reference legs, never by the product path, and it shares no code,
+ * header, table or generator with the CUDA library.
+ *
+ * Everything here steps one operation at a time, in program order, over a
+ * store sigma that maps each variable to its validity pair.  Effects are
+ * applied by unifying the pair with the effect's signature, exactly as the
+ * paper defines them; no transfer table is precomputed.
+ *
+ * Parity pins (tests/test_oracle_*.py): worked examples of Sections 3.1, 3.2,
+ * 3.4 and 4.3; Property Safety and Property Progress; Theorems Subject
+ * reduction / Progress on random well-declared programs; the VectorPU flag
+ * code of Fig. vectorpucoherence; brute-force path enumeration for If/While.
+ * The partial-write projection `pw` and the handling of dropped annotations
+ * are readings, not paper statements, and are pinned only by the per-element
+ * array model of the tests.
+ */
+#include "oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Validity values and status pairs (Section 3.1).                           */
+/* ------------------------------------------------------------------------ */
+enum { I = 0, V = 1 };
+enum { ST_F = 4 };                       /* stuck: no rule applies (Property Progress) */
+enum { K_R = 0, K_W, K_PUSH, K_PULL, K_NOOP, K_PW, K_GT, K_EN,
+       T_IF = 8, T_ELSE = 9, T_WHILE = 10, T_END = 11 };
+
+typedef struct { int local, remote; } pair_t;   /* local = CPU, remote = GPU */
+
+static pair_t decode(int code) { pair_t p = { code & 1, (code >> 1) & 1 }; return p; }
+static int encode(pair_t p) { return p.local | (p.remote << 1); }
+
+/* A term of an effect signature: a constant V or I, or one of the variables
+ * X, Y that are universally quantified in each signature (Section 3.1). */
+typedef struct { int is_var; int v; } term_t;      /* v: V/I, or 0 = X, 1 = Y */
+#define CV { 0, V }
+#define CI { 0, I }
+#define TX { 1, 0 }
+#define TY { 1, 1 }
+typedef struct { term_t pre[2]; term_t post[2]; } effect_t;
+
+/* Section 3.1 effect signatures, in op-byte kind order.  The sixth entry is the
+ * partial-write projection onto an overlapping array: a reading (the paper has
+ * element writes w x[i], Section 3.5); its own side keeps its validity and the
+ * other side becomes invalid. */
+static const effect_t EFFECT[6] = {
+    /* r    : (V,X) |-> (V,X) */ { { CV, TX }, { CV, TX } },
+    /* w    : (X,Y) |-> (V,I) */ { { TX, TY }, { CV, CI } },
+    /* Push : (V,X) |-> (V,V) */ { { CV, TX }, { CV, CV } },
+    /* Pull : (X,V) |-> (V,V) */ { { TX, CV }, { CV, CV } },
+    /* Noop : (X,Y) |-> (X,Y) */ { { TX, TY }, { TX, TY } },
+    /* pw   : (X,Y) |-> (X,I) */ { { TX, TY }, { TX, CI } },
+};
+
+/* Unification of a signature's pre-pattern with a concrete pair: instantiate
+ * X and Y so that both become identical; fail if no instantiation exists
+ * (Section 3.1: an effect applies only through such a unification). */
+static int unify(const term_t pat[2], pair_t s, int bind[2])
+{
+    int val[2] = { s.local, s.remote };
+    bind[0] = bind[1] = -1;
+    for (int k = 0; k < 2; k++) {
+        if (!pat[k].is_var) {
+            if (pat[k].v != val[k]) return 0;
+        } else {
+            int x = pat[k].v;
+            if (bind[x] >= 0 && bind[x] != val[k]) return 0;
+            bind[x] = val[k];
+        }
+    }
+    return 1;
+}
+
+static pair_t instantiate(const term_t pat[2], const int bind[2])
+{
+    pair_t p;
+    p.local = pat[0].is_var ? bind[pat[0].v] : pat[0].v;
+    p.remote = pat[1].is_var ? bind[pat[1].v] : pat[1].v;
+    return p;
+}
+
+/* Rules Effect and Remote Effect of Fig. Opsem.  Returns 0 when stuck. */
+static int effect_step(int kind, int remote, pair_t s, pair_t* out)
+{
+    const effect_t* e = &EFFECT[kind];
+    int bind[2];
+    if (!remote) {
+        /* sigma(x) = (X,Y), E : (X,Y) |-> (Z,T)  gives  (Z,T) */
+        if (!unify(e->pre, s, bind)) return 0;
+        *out = instantiate(e->post, bind);
+    } else {
+        /* sigma(x) = (X,Y), E : (Y,X) |-> (Z,T)  gives  (T,Z) */
+        pair_t swapped = { s.remote, s.local };
+        if (!unify(e->pre, swapped, bind)) return 0;
+        pair_t z = instantiate(e->post, bind);
+        out->local = z.remote;
+        out->remote = z.local;
+    }
+    return 1;
+}
+
+int oracle_apply(int kind, int side, int status)
+{
+    if (status == ST_F) return ST_F;           /* a stuck variable stays stuck */
+    pair_t out;
+    if (!effect_step(kind, side, decode(status), &out)) return ST_F;
+    return encode(out);
+}
+
+/* Conditions of Fig. Opsem: isValid x reads the local flag, remIsValid x the
+ * remote one.  A stuck variable has no pair; its condition is taken as false. */
+static int is_valid_on(int side, int status)
+{
+    if (status == ST_F) return 0;
+    pair_t p = decode(status);
+    return side == 0 ? p.local == V : p.remote == V;
+}
+
+/* The transfer that restores validity on `side` in Fig. sem-AM: the CPU-side
+ * declaration emits Pull, the GPU-side declaration emits Push, both as plain
+ * (non-remote) statements. */
+static int transfer_for(int side, int status)
+{
+    return oracle_apply(side == 0 ? K_PULL : K_PUSH, 0, status);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Trace mode                                                                */
+/* ------------------------------------------------------------------------ */
+static int valid_trace_byte(uint8_t ks) { return (ks & 0xE0) == 0 && (ks & 15) <= K_EN; }
+
+int oracle_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
+                       int32_t n_vars, const uint8_t* init_status,
+                       uint8_t* step_status, uint8_t* final_status,
+                       int32_t* var_first_fault, int64_t* first_fault)
+{
+    if (n_ops < 0 || n_vars < 0 || n_ops > INT32_MAX) return -1;
+    for (int64_t i = 0; i < n_ops; i++) {
+        if (!valid_trace_byte(kind_side[i])) return -1;
+        if (var[i] < 0 || var[i] >= n_vars) return -2;
+        int k = kind_side[i] & 15;
+        if (k == K_GT) {
+            /* a guarded transfer is followed by the check on its guard variable */
+            if (i + 1 >= n_ops || (kind_side[i + 1] & 15) != K_EN ||
+                (kind_side[i + 1] >> 4) != (kind_side[i] >> 4) || var[i + 1] == var[i])
+                return -1;
+        }
+    }
+    uint8_t* st = (uint8_t*)malloc((size_t)(n_vars ? n_vars : 1));
+    if (!st) return -3;
+    for (int32_t v = 0; v < n_vars; v++) {
+        st[v] = init_status ? init_status[v] : (uint8_t)encode((pair_t){ V, I });  /* sigma_0 */
+        if (st[v] > ST_F) { free(st); return -1; }
+        var_first_fault[v] = -1;
+    }
+    int64_t ff = -1;
+    for (int64_t i = 0; i < n_ops; i++) {
+        int k = kind_side[i] & 15, side = kind_side[i] >> 4;
+        int v = var[i];
+        int before = st[v], after;
+        if (k <= K_PW) {
+            after = oracle_apply(k, side, before);
+        } else if (k == K_GT) {
+            /* if (valid_side(guard)) Noop else transfer on the real variable */
+            int guard = st[var[i + 1]];
+            after = is_valid_on(side, guard) ? before : transfer_for(side, before);
+        } else { /* K_EN: the same test on the abstract variable itself */
+            after = is_valid_on(side, before) ? before : transfer_for(side, before);
+        }
+        st[v] = (uint8_t)after;
+        step_status[i] = (uint8_t)after;
+        if (after == ST_F && before != ST_F) {
+            if (var_first_fault[v] < 0) var_first_fault[v] = (int32_t)i;
+            if (ff < 0) ff = i;
+        }
+    }
+    for (int32_t v = 0; v < n_vars; v++) final_status[v] = st[v];
+    *first_fault = ff;
+    free(st);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Relation mode: status sets, If = union of branches, While = closure       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const uint8_t* tok;
+    const int32_t* payload;
+    int32_t n_vars;
+    uint8_t* step_mask;
+    int64_t first_fault;           /* relative token index, -1 none */
+    int depth;
+} prog_ctx;
+
+#define ORACLE_MAX_DEPTH 64
+
+static uint8_t image(int kind, int side, uint8_t mask)
+{
+    uint8_t out = 0;
+    for (int s = 0; s <= ST_F; s++)
+        if (mask & (1u << s)) out |= (uint8_t)(1u << oracle_apply(kind, side, s));
+    return out;
+}
+
+static int eval_seq(prog_ctx* c, int64_t lo, int64_t hi, uint8_t* mask);
+
+static uint8_t* copy_masks(const prog_ctx* c, const uint8_t* m)
+{
+    uint8_t* out = (uint8_t*)malloc((size_t)(c->n_vars ? c->n_vars : 1));
+    if (out) memcpy(out, m, (size_t)c->n_vars);
+    return out;
+}
+
+static int eval_seq(prog_ctx* c, int64_t lo, int64_t hi, uint8_t* mask)
+{
+    if (++c->depth > ORACLE_MAX_DEPTH) return -1;
+    int64_t i = lo;
+    while (i < hi) {
+        int k = c->tok[i] & 15, side = (c->tok[i] >> 4) & 1;
+        if ((c->tok[i] & 0xE0) != 0) return -1;
+        if (k <= K_PW) {
+            int32_t v = c->payload[i];
+            if (v < 0 || v >= c->n_vars) return -2;
+            uint8_t pre = mask[v], post = image(k, side, pre);
+            /* may-fault origin: a possible non-stuck status that gets stuck here */
+            for (int s = 0; s < ST_F; s++)
+                if ((pre & (1u << s)) && oracle_apply(k, side, s) == ST_F) {
+                    if (c->first_fault < 0 || i < c->first_fault) c->first_fault = i;
+                    break;
+                }
+            mask[v] = post;
+            c->step_mask[i] = post;
+            i++;
+        } else if (k == T_IF) {
+            int64_t lt = c->payload[i];
+            int64_t e = i + 1 + lt;                       /* ELSE token */
+            if (lt < 0 || e >= hi || (c->tok[e] & 15) != T_ELSE || side) return -1;
+            int64_t le = c->payload[e];
+            int64_t end = e + 1 + le;                     /* END token */
+            if (le < 0 || end >= hi || (c->tok[end] & 15) != T_END) return -1;
+            /* IF-True / IF-False: both branches start from the same store */
+            uint8_t* m_then = copy_masks(c, mask);
+            uint8_t* m_else = copy_masks(c, mask);
+            if (!m_then || !m_else) { free(m_then); free(m_else); return -3; }
+            int rc = eval_seq(c, i + 1, e, m_then);
+            if (!rc) rc = eval_seq(c, e + 1, end, m_else);
+            if (!rc)
+                for (int32_t v = 0; v < c->n_vars; v++) mask[v] = m_then[v] | m_else[v];
+            free(m_then);
+            free(m_else);
+            if (rc) return rc;
+            c->step_mask[i] = c->step_mask[e] = c->step_mask[end] = 0;
+            i = end + 1;
+        } else if (k == T_WHILE) {
+            int64_t lb = c->payload[i];
+            int64_t end = i + 1 + lb;
+            if (lb < 0 || end >= hi || (c->tok[end] & 15) != T_END || side) return -1;
+            /* While-True / While-False: the set of stores at the loop head is the
+             * least X with X = entry U body(X); the body's step sets are those of
+             * the pass that starts from that fixpoint. */
+            uint8_t* x = copy_masks(c, mask);
+            if (!x) return -3;
+            for (;;) {
+                uint8_t* y = copy_masks(c, x);
+                if (!y) { free(x); return -3; }
+                int rc = eval_seq(c, i + 1, end, y);
+                if (rc) { free(x); free(y); return rc; }
+                int changed = 0;
+                for (int32_t v = 0; v < c->n_vars; v++) {
+                    uint8_t u = x[v] | y[v];
+                    if (u != x[v]) { x[v] = u; changed = 1; }
+                }
+                free(y);
+                if (!changed) break;
+            }
+            memcpy(mask, x, (size_t)c->n_vars);
+            free(x);
+            c->step_mask[i] = c->step_mask[end] = 0;
+            i = end + 1;
+        } else {
+            return -1;      /* ELSE / END without a matching IF / WHILE, or GT / EN */
+        }
+    }
+    c->depth--;
+    return 0;
+}
+
+int oracle_check_program(const uint8_t* tok, const int32_t* payload, int64_t n_tok,
+                         int32_t n_vars, const uint8_t* init_mask,
+                         uint8_t* step_mask, uint8_t* final_mask, int64_t* first_fault)
+{
+    if (n_tok < 0 || n_vars < 0) return -1;
+    prog_ctx c = { tok, payload, n_vars, step_mask, -1, 0 };
+    for (int32_t v = 0; v < n_vars; v++) {
+        final_mask[v] = init_mask ? init_mask[v] : (uint8_t)(1u << encode((pair_t){ V, I }));
+        if (final_mask[v] >> 5) return -1;
+    }
+    int rc = eval_seq(&c, 0, n_tok, final_mask);
+    if (rc) return rc;
+    *first_fault = c.first_fault;
+    return 0;
+}
+
+int oracle_check_batch(const uint8_t* tok, const int32_t* payload, const int64_t* prog_tok_off,
+                       const int32_t* prog_nvars, const int64_t* prog_var_off, int64_t n_progs,
+                       uint8_t* step_mask, uint8_t* final_mask, int64_t* prog_first_fault)
+{
+    if (n_progs < 0 || prog_tok_off[0] != 0 || prog_var_off[0] != 0) return -1;
+    for (int64_t p = 0; p < n_progs; p++) {
+        int64_t t0 = prog_tok_off[p], t1 = prog_tok_off[p + 1];
+        if (t1 < t0 || prog_var_off[p + 1] - prog_var_off[p] != prog_nvars[p]) return -1;
+        int rc = oracle_check_program(tok + t0, payload + t0, t1 - t0, prog_nvars[p], NULL,
+                                      step_mask + t0, final_mask + prog_var_off[p],
+                                      &prog_first_fault[p]);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* VectorPU calls over possibly overlapping arrays                           */
+/* ------------------------------------------------------------------------ */
+static int overlap(int32_t s1, int32_t l1, int32_t s2, int32_t l2)
+{
+    /* half-open intervals [s, s+l) share an element */
+    return (int64_t)s1 < (int64_t)s2 + l2 && (int64_t)s2 < (int64_t)s1 + l1;
+}
+
+static int contains(int32_t s_out, int32_t l_out, int32_t s_in, int32_t l_in)
+{
+    return s_out <= s_in && (int64_t)s_in + l_in <= (int64_t)s_out + l_out;
+}
+
+static int check_intervals(const int32_t* s, const int32_t* l, int32_t n)
+{
+    for (int32_t a = 0; a < n; a++)
+        if (s[a] < 0 || l[a] < 1 || (int64_t)s[a] + l[a] > INT32_MAX) return -1;
+    return 0;
+}
+
+int oracle_overlaps(const int32_t* arr_start, const int32_t* arr_len, int32_t n_arrays,
+                    int64_t* ov_off, int32_t* ov_idx, int64_t ov_cap)
+{
+    if (n_arrays < 0 || check_intervals(arr_start, arr_len, n_arrays)) return -1;
+    int64_t n = 0;
+    ov_off[0] = 0;
+    for (int32_t a = 0; a < n_arrays; a++) {
+        for (int32_t b = 0; b < n_arrays; b++) {
+            if (a == b || !overlap(arr_start[a], arr_len[a], arr_start[b], arr_len[b])) continue;
+            if (n >= ov_cap) return -4;
+            ov_idx[n++] = b;
+        }
+        ov_off[a + 1] = n;
+    }
+    return 0;
+}
+
+enum { M_R = 1, M_W = 2, M_RW = 3, M_DROPPED = 0x80 };
+
+typedef struct {
+    int32_t n_arrays;
+    uint8_t* st;              /* 2A statuses: real 0..A-1, abstract A..2A-1 */
+    int32_t* vff;
+    int64_t ff;
+    uint8_t* out_ks;
+    int32_t* out_var;
+    uint8_t* step;
+    int64_t n, cap;
+} vp_ctx;
+
+/* Record one statement of the translated program and its effect on sigma. */
+static int vp_emit(vp_ctx* c, int kind, int side, int32_t v, int after)
+{
+    if (c->n >= c->cap) return -4;      /* output capacity exceeded */
+    int before = c->st[v];
+    c->st[v] = (uint8_t)after;
+    c->out_ks[c->n] = (uint8_t)(kind | side << 4);
+    c->out_var[c->n] = v;
+    c->step[c->n] = (uint8_t)after;
+    if (after == ST_F && before != ST_F) {
+        if (c->vff[v] < 0) c->vff[v] = (int32_t)c->n;
+        if (c->ff < 0) c->ff = c->n;
+    }
+    c->n++;
+    return 0;
+}
+
+static int vp_op(vp_ctx* c, int kind, int side, int32_t v)
+{
+    return vp_emit(c, kind, side, v, oracle_apply(kind, side, c->st[v]));
+}
+
+/* [[R x#]] and the guard part of [[RW x#]] (Fig. sem-AM):
+ *   if (isValid x#) Noop else (Pull x; Pull x#)          -- CPU side
+ *   if (remIsValid x#) Noop else (Push x; Push x#)       -- GPU side
+ * Both statements are recorded (the GT and EN slots); when the condition holds
+ * they leave their variable unchanged. */
+static int vp_ensure(vp_ctx* c, int side, int32_t x)
+{
+    int32_t xa = c->n_arrays + x;
+    int cond = is_valid_on(side, c->st[xa]);
+    int rc = vp_emit(c, K_GT, side, x, cond ? c->st[x] : transfer_for(side, c->st[x]));
+    if (rc) return rc;
+    return vp_emit(c, K_EN, side, xa, cond ? c->st[xa] : transfer_for(side, c->st[xa]));
+}
+
+static int cmp_i32(const void* a, const void* b)
+{
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+int oracle_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_arrays,
+                    const uint8_t* call_side, const int32_t* call_off, int64_t n_calls,
+                    const int32_t* opnd_array, const uint8_t* opnd_mode, int infer_overlap,
+                    uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap, int64_t* out_n,
+                    int64_t* call_first_op, uint8_t* step_status, uint8_t* final_status,
+                    int32_t* var_first_fault, int64_t* first_fault)
+{
+    if (n_arrays < 0 || n_arrays > (INT32_MAX / 2) || n_calls < 0 || call_off[0] != 0) return -1;
+    if (check_intervals(arr_start, arr_len, n_arrays)) return -1;
+    for (int64_t c = 0; c < n_calls; c++) {
+        if (call_off[c + 1] < call_off[c] || call_side[c] > 1) return -1;
+        for (int32_t k = call_off[c]; k < call_off[c + 1]; k++) {
+            uint8_t m = opnd_mode[k];
+            if ((m & 0x7C) || (m & 3) == 0) return -1;
+            if (opnd_array[k] < 0 || opnd_array[k] >= n_arrays) return -2;
+            for (int32_t j = call_off[c]; j < k; j++)
+                if (opnd_array[j] == opnd_array[k]) return -1;   /* footnote of Section 3.3 */
+        }
+    }
+    /* r_v of Section 4.3: for every array, the arrays that overlap it (ascending) */
+    int64_t* ov_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_arrays + 1));
+    int64_t n_pairs = 0;
+    for (int32_t a = 0; a < n_arrays; a++)
+        for (int32_t b = 0; b < n_arrays; b++)
+            n_pairs += (a != b && overlap(arr_start[a], arr_len[a], arr_start[b], arr_len[b]));
+    int32_t* ov_idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_pairs ? n_pairs : 1));
+    int32_t nv = 2 * n_arrays;
+    vp_ctx c;
+    c.n_arrays = n_arrays;
+    c.st = (uint8_t*)malloc((size_t)(nv ? nv : 1));
+    c.vff = var_first_fault;
+    c.ff = -1;
+    c.out_ks = out_kind_side;
+    c.out_var = out_var;
+    c.step = step_status;
+    c.n = 0;
+    c.cap = out_cap;
+    /* per-array scratch: mode in this call (0 = not an operand), effective
+     * declared mode after O(M), shadow flag, and the list of shadows */
+    uint8_t* opmode = (uint8_t*)calloc((size_t)(n_arrays ? n_arrays : 1), 1);
+    uint8_t* eff = (uint8_t*)calloc((size_t)(n_arrays ? n_arrays : 1), 1);
+    uint8_t* shadow = (uint8_t*)calloc((size_t)(n_arrays ? n_arrays : 1), 1);
+    int32_t* shadow_list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_arrays ? n_arrays : 1));
+    int rc = 0;
+    if (!ov_off || !ov_idx || !c.st || !opmode || !eff || !shadow || !shadow_list) rc = -3;
+    if (!rc) {
+        int rc2 = oracle_overlaps(arr_start, arr_len, n_arrays, ov_off, ov_idx, n_pairs);
+        if (rc2) rc = rc2;
+    }
+    for (int32_t v = 0; v < nv && !rc; v++) {
+        c.st[v] = (uint8_t)encode((pair_t){ V, I });   /* real and abstract start at (V,I) */
+        var_first_fault[v] = -1;
+    }
+    for (int64_t call = 0; call < n_calls && !rc; call++) {
+        int side = call_side[call];
+        int32_t k0 = call_off[call], k1 = call_off[call + 1];
+        int32_t n_shadow = 0;
+        call_first_op[call] = c.n;
+        for (int32_t k = k0; k < k1; k++) {
+            opmode[opnd_array[k]] = opnd_mode[k];
+            eff[opnd_array[k]] = (opnd_mode[k] & M_DROPPED) ? 0 : (opnd_mode[k] & 3);
+        }
+        /* O(M), Table Overlap-ext-tab: the rules read the declared set M only
+         * (not applied recursively, Section 4.3).  A dropped annotation is absent
+         * from M and, being an argument of the call, is neither upgraded nor
+         * shadowed. */
+        if (infer_overlap) {
+            for (int32_t k = k0; k < k1; k++) {
+                int32_t x = opnd_array[k];
+                uint8_t mx = opnd_mode[k];
+                if ((mx & M_DROPPED) || !((mx & 3) & M_W)) continue;   /* x declared W or RW */
+                for (int64_t j = ov_off[x]; j < ov_off[x + 1]; j++) {
+                    int32_t y = ov_idx[j];
+                    if (opmode[y] == 0) {
+                        if (!shadow[y]) { shadow[y] = 1; shadow_list[n_shadow++] = y; }  /* RW y# */
+                    } else if (!(opmode[y] & M_DROPPED)) {
+                        /* RW rule: any y; W rule: only when W y# is not in M */
+                        if ((mx & 3) == M_RW || (opmode[y] & 3) != M_W) eff[y] = M_RW;
+                    }
+                }
+            }
+            qsort(shadow_list, (size_t)n_shadow, sizeof(int32_t), cmp_i32);
+        }
+        /* [[O(M)]] then the body, grouped per operand in argument order (each
+         * statement touches one variable, so per variable this is the paper's
+         * order [[M]]; S) */
+        for (int32_t k = k0; k < k1 && !rc; k++) {
+            int32_t x = opnd_array[k];
+            int mo = opnd_mode[k] & 3;
+            if (!(opnd_mode[k] & M_DROPPED)) {
+                int me = eff[x];
+                if (me == M_R || me == M_RW) rc = vp_ensure(&c, side, x);
+                if (!rc && (me == M_W || me == M_RW)) rc = vp_op(&c, K_W, side, n_arrays + x);
+            }
+            if (!rc && (mo == M_R || mo == M_RW)) rc = vp_op(&c, K_R, side, x);
+            if (!rc && (mo == M_W || mo == M_RW)) rc = vp_op(&c, K_W, side, x);
+        }
+        /* shadow arguments RW(y), ascending array id (Section 4.3) */
+        for (int32_t s = 0; s < n_shadow && !rc; s++) {
+            int32_t y = shadow_list[s];
+            rc = vp_ensure(&c, side, y);
+            if (!rc) rc = vp_op(&c, K_W, side, n_arrays + y);
+        }
+        /* the body's writes also write the shared elements of overlapping arrays:
+         * a wholly covered array is written, a partly covered one keeps its own
+         * side and loses the other (the per-array summary reading) */
+        for (int32_t k = k0; k < k1 && !rc; k++) {
+            int32_t x = opnd_array[k];
+            if (!((opnd_mode[k] & 3) & M_W)) continue;
+            for (int64_t j = ov_off[x]; j < ov_off[x + 1] && !rc; j++) {
+                int32_t y = ov_idx[j];
+                int whole = contains(arr_start[x], arr_len[x], arr_start[y], arr_len[y]);
+                rc = vp_op(&c, whole ? K_W : K_PW, side, y);
+            }
+        }
+        for (int32_t k = k0; k < k1; k++) { opmode[opnd_array[k]] = 0; eff[opnd_array[k]] = 0; }
+        for (int32_t s = 0; s < n_shadow; s++) shadow[shadow_list[s]] = 0;
+    }
+    if (!rc) {
+        call_first_op[n_calls] = c.n;
+        *out_n = c.n;
+        for (int32_t v = 0; v < nv; v++) final_status[v] = c.st[v];
+        *first_fault = c.ff;
+    }
+    free(ov_off);
+    free(ov_idx);
+    free(c.st);
+    free(opmode);
+    free(eff);
+    free(shadow);
+    free(shadow_list);
+    return rc;
+}

@@ -1,0 +1,67 @@
+/*
+ * oracle.h -- plain CPU reference of the access-mode consistency calculus of
+ * Henrio, Kessler and Li, "Leveraging Access Mode Declarations in a Model for
+ * Memory Consistency in Heterogeneous Systems" (arXiv 1910.11110).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py load this library.  The product
+ * path (the CUDA library under paper_1910_11110_gb300/) never links, loads or
+ * calls it, and it shares no code, header or table with that path: the byte
+ * encodings below are restated here on purpose.
+ *
+ * Encodings (inputs and outputs, identical to the product's C ABI):
+ *   status code  = cpuValid | gpuValid << 1, plus 4 = F (stuck, absorbing).
+ *                  The paper's pair is (local, remote) with local = CPU
+ *                  (Section 3.1; data starts in CPU memory, Section 3.2).
+ *   op byte      = kind | side << 4, side 0 = "E x", side 1 = "rem(E x)".
+ *                  kinds: r=0 w=1 Push=2 Pull=3 Noop=4 pw=5 GT=6 EN=7;
+ *                  structure tokens (relation mode): IF=8 ELSE=9 WHILE=10 END=11.
+ *   status mask  = bit k set <=> status code k is possible (relation mode).
+ *
+ * Every function returns 0 on success and a negative code on malformed input
+ * (-1 invalid, -2 id out of range, -3 out of host memory, -4 output capacity
+ * exceeded); outputs are then unspecified.
+ */
+#ifndef AMC_ORACLE_H
+#define AMC_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status code of applying one op (kind 0..5, side 0/1) to status code s.
+ * Section 3.1 effect signatures + Fig. Opsem rules Effect / Remote Effect. */
+int oracle_apply(int kind, int side, int status);
+
+/* Straight-line trace mode (Fig. Opsem, initial store of Section 3.2). */
+int oracle_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
+                       int32_t n_vars, const uint8_t* init_status,
+                       uint8_t* step_status, uint8_t* final_status,
+                       int32_t* var_first_fault, int64_t* first_fault);
+
+/* Relation mode for one structured program (If = union, While = closure). */
+int oracle_check_program(const uint8_t* tok, const int32_t* payload, int64_t n_tok,
+                         int32_t n_vars, const uint8_t* init_mask,
+                         uint8_t* step_mask, uint8_t* final_mask, int64_t* first_fault);
+
+/* Relation mode over a batch of independent programs (CSR layout). */
+int oracle_check_batch(const uint8_t* tok, const int32_t* payload, const int64_t* prog_tok_off,
+                       const int32_t* prog_nvars, const int64_t* prog_var_off, int64_t n_progs,
+                       uint8_t* step_mask, uint8_t* final_mask, int64_t* prog_first_fault);
+
+/* Overlap sets of half-open intervals [start, start+len): CSR, ascending ids. */
+int oracle_overlaps(const int32_t* arr_start, const int32_t* arr_len, int32_t n_arrays,
+                    int64_t* ov_off, int32_t* ov_idx, int64_t ov_cap);
+
+/* VectorPU-annotated calls (Fig. sem-AM, Table Overlap-ext-tab, Section 4.3). */
+int oracle_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_arrays,
+                    const uint8_t* call_side, const int32_t* call_off, int64_t n_calls,
+                    const int32_t* opnd_array, const uint8_t* opnd_mode, int infer_overlap,
+                    uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap, int64_t* out_n,
+                    int64_t* call_first_op, uint8_t* step_status, uint8_t* final_status,
+                    int32_t* var_first_fault, int64_t* first_fault);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
