@@ -1,0 +1,276 @@
+/*
+ * amc.h -- C ABI of the GB300 access-mode consistency checker.
+ *
+ * The checker runs the calculus of Henrio, Kessler and Li, "Leveraging Access
+ * Mode Declarations in a Model for Memory Consistency in Heterogeneous Systems"
+ * (arXiv 1910.11110) over large inputs on one GPU (sm_103a):
+ *   - straight-line op traces (Section 3.2, rules Effect / Remote Effect of
+ *     Fig. Opsem over the effect signatures of Section 3.1);
+ *   - VectorPU component calls with R / W / RW access modes over possibly
+ *     overlapping arrays (translation of Fig. sem-AM, arrays of Section 3.5,
+ *     overlap inference of Table Overlap-ext-tab and Section 4.3);
+ *   - batches of structured If / While programs, with If read as the union of
+ *     its branches and While as the closure of its body (Fig. Opsem rules
+ *     IF-True/IF-False and While-True/While-False with opaque conditions);
+ *   - a serving loop over such requests with device-resident session state.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Status code (uint8):  cpuValid | gpuValid << 1, i.e. 0 = (I,I), 1 = (V,I),
+ *   2 = (I,V), 3 = (V,V), and 4 = F, the stuck state of Property Progress.
+ *   F absorbs: once a variable is stuck every later op on it reports F, while
+ *   other variables keep being checked.  The paper's pair is (local, remote)
+ *   with local = CPU memory (Section 3.1); every variable starts at (V,I)
+ *   (initial store of Section 3.2) unless an initial status is passed.
+ * Status mask (uint8): bit k set <=> status code k is possible (relation mode).
+ * Op byte (uint8):  kind | side << 4, bits 5-7 zero.  side 0 = "E x" (local,
+ *   CPU), side 1 = "rem(E x)" (remote, GPU).  Kinds:
+ *     0 r, 1 w, 2 Push, 3 Pull, 4 Noop           (Section 3.1 effects)
+ *     5 pw   partial write of an overlapping array: own side keeps its
+ *            validity, the other side becomes invalid (per-array summary)
+ *     6 GT   guarded transfer on a real array: acts as the Fig. sem-AM
+ *            transfer (CPU side: Pull, GPU side: Push, both local statements)
+ *            exactly when the side is invalid in the status, before the next
+ *            op, of the next op's variable; must be followed by an EN of the
+ *            same side on another variable (amc_check_guarded_trace only)
+ *     7 EN   the same test and transfer on an abstract variable itself
+ *     8 IF, 9 ELSE, 10 WHILE, 11 END   structure tokens (programs only)
+ * Pointers are DEVICE pointers unless marked "host".  Buffers are owned by
+ *   the caller; the library never frees them.  Every call is asynchronous on
+ *   the given stream (a cudaStream_t passed as void*, NULL = legacy default
+ *   stream) and allocates no device memory: callers size `workspace` with the
+ *   matching *_workspace() query (256-byte aligned).
+ * Return value: argument / launch errors only (AMC_E_*).  A semantic fault is
+ *   a result, never an error.  Data-dependent errors found on the device
+ *   (a var id out of range, a malformed op byte, an expired bounded wait) are
+ *   reported by amc_sync_status(); when it reports one, the outputs of the
+ *   calls since the previous amc_sync_status() are unspecified.
+ */
+#ifndef AMC_H
+#define AMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AMC_API __attribute__((visibility("default")))
+#else
+#define AMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    AMC_OK = 0,
+    AMC_E_INVALID = -1,   /* malformed input (bad op byte, unbalanced tokens, duplicate operand ...) */
+    AMC_E_RANGE = -2,     /* variable / array id out of range, capacity exceeded */
+    AMC_E_NOMEM = -3,     /* workspace too small, or memory budget exceeded */
+    AMC_E_TIMEOUT = -4,   /* a bounded device-side wait expired */
+    AMC_E_CUDA = -5,      /* a CUDA runtime call failed */
+    AMC_E_AGAIN = -6      /* serving: no slot free yet (back-pressure) */
+};
+
+enum { AMC_ST_II = 0, AMC_ST_VI = 1, AMC_ST_IV = 2, AMC_ST_VV = 3, AMC_ST_F = 4 };
+enum { AMC_K_R = 0, AMC_K_W = 1, AMC_K_PUSH = 2, AMC_K_PULL = 3, AMC_K_NOOP = 4,
+       AMC_K_PW = 5, AMC_K_GT = 6, AMC_K_EN = 7,
+       AMC_T_IF = 8, AMC_T_ELSE = 9, AMC_T_WHILE = 10, AMC_T_END = 11 };
+enum { AMC_MODE_R = 1, AMC_MODE_W = 2, AMC_MODE_RW = 3, AMC_MODE_DROPPED = 0x80 };
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+AMC_API int amc_version(void);
+
+/* Static message for an AMC_* code. */
+AMC_API const char* amc_error_string(int code);
+
+/* Synchronises `stream` and returns the first device-side error raised on
+ * the current device since the previous call (AMC_OK if none), clearing it.
+ * A CUDA error while synchronising is returned as AMC_E_CUDA. */
+AMC_API int amc_sync_status(void* stream);
+
+/* Profiling aid (no counterpart in the paper): while set, every call made by
+ * this host thread records `start_event` on its stream just before its
+ * dominant kernel and `stop_event` just after it (cudaEvent_t handles passed
+ * as void*; NULL, NULL turns it off).  Returns AMC_OK. */
+AMC_API int amc_set_profile_events(void* start_event, void* stop_event);
+
+/* ------------------------------------------------------------------------ */
+/* (1) Straight-line traces -- Section 3.2 (Fig. Opsem, Effect and Remote    */
+/*     Effect rules; signatures of Section 3.1; initial store sigma_0).      */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes amc_check_trace needs for these sizes. */
+AMC_API size_t amc_check_trace_workspace(int64_t n_ops, int32_t n_vars);
+
+/* Checks one trace of kinds 0..5 and 7: for every op i (0 <= i < n_ops,
+ * n_ops <= 2^31 - 1) on
+ * variable var[i] (0 <= var[i] < n_vars) writes the variable's status after
+ * the op to step_status[i]; writes every variable's status after the trace to
+ * final_status[v], the index of the op at which v first became F to
+ * var_first_fault[v] (-1 if never) and the minimum of those to *first_fault
+ * (-1 if none; a real execution stops there, Property Progress).
+ *   kind_side   [n_ops]  op bytes (a GT is reported as AMC_E_INVALID)
+ *   var         [n_ops]  int32 variable ids
+ *   init_status [n_vars] initial status codes, or NULL for all (V,I)
+ *   step_status [n_ops], final_status [n_vars], var_first_fault [n_vars],
+ *   first_fault [1]      outputs (int64)
+ * Errors: AMC_E_INVALID for negative sizes or NULL buffers, AMC_E_NOMEM when
+ * ws_bytes is too small.  Ids out of range or malformed op bytes are reported
+ * through amc_sync_status (AMC_E_RANGE / AMC_E_INVALID). */
+AMC_API int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
+                    const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                    int32_t* var_first_fault, int64_t* first_fault,
+                    void* workspace, size_t ws_bytes, void* stream);
+
+/* Workspace bytes amc_check_guarded_trace needs. */
+AMC_API size_t amc_check_guarded_trace_workspace(int64_t n_ops, int32_t n_vars);
+
+/* amc_check_trace for traces that also contain GT (kind 6), as produced by
+ * amc_translate_vectorpu.  Runs two scans: the first yields the status of
+ * every EN's variable before the EN with GT read as Noop (guards only read
+ * abstract variables, which GT never touches); the second resolves each GT
+ * from that status (the condition of Fig. sem-AM is checked on the abstract
+ * value, Section 3.3) and checks the trace.  Same outputs and errors as
+ * amc_check_trace; a GT not followed by an EN of the same side on another
+ * variable is reported as AMC_E_INVALID. */
+AMC_API int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
+                            const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                            int32_t* var_first_fault, int64_t* first_fault,
+                            void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (2) VectorPU calls -> core trace -- Fig. sem-AM (translation of access    */
+/*     modes), Section 3.5 (one abstract status per array), Table            */
+/*     Overlap-ext-tab (inference O(M)) and Section 4.3 (overlap sets r_v,   */
+/*     shadow arguments, no recursive application).                          */
+/* ------------------------------------------------------------------------ */
+
+/* Most operands one call may have. */
+#define AMC_MAX_OPERANDS 32
+
+/* Workspace bytes amc_translate_vectorpu needs (grows as n_arrays^2: the
+ * overlap sets are stored as lists). */
+AMC_API size_t amc_translate_vectorpu_workspace(int32_t n_arrays, int64_t n_calls, int64_t n_operands);
+
+/* Translates n_calls component calls into a core trace over 2 * n_arrays
+ * variables: real arrays 0..A-1 and their abstract variables A..2A-1.
+ *   arr_start, arr_len [n_arrays]  half-open intervals [start, start + len)
+ *                                  of one shared index space (len >= 1)
+ *   call_side [n_calls]            0 = CPU component, 1 = GPU component
+ *   call_off  [n_calls + 1]        CSR offsets into the operand arrays
+ *   opnd_array, opnd_mode          operand array id and mode (1 R, 2 W, 3 RW;
+ *                                  bit 7 = annotation dropped: the body still
+ *                                  accesses the operand but it is not declared)
+ *   infer_overlap                  1 = extend each call's declarations to O(M)
+ * Per call, in this order (each statement touches one variable, so per
+ * variable this is the paper's order [[M]]; S):
+ *   for each operand in argument order: if declared with effective mode R or
+ *   RW: GT x, EN x#; if W or RW: w x#; then the body accesses of its own mode
+ *   (R: r x; W: w x; RW: r x, w x);
+ *   for each shadow RW(y), ascending y: GT y, EN y#, w y#;
+ *   for each operand x that the body writes and each y != x overlapping x,
+ *   ascending y: w y if y lies inside x, else pw y.
+ * All statements carry the call's side.  Outputs: out_kind_side / out_var
+ * [out_cap] and *out_n (device int64) = statements written; call_first_op
+ * [n_calls + 1] = index of each call's first statement.  When the
+ * translation needs more than out_cap statements nothing but *out_n (the
+ * needed count) is written and amc_sync_status reports AMC_E_RANGE.
+ * Feed the result to amc_check_guarded_trace with n_vars = 2 * n_arrays.
+ * Errors (host): AMC_E_INVALID for bad sizes; (device, via amc_sync_status)
+ * AMC_E_INVALID for a bad mode / side / interval, a duplicate operand or more
+ * than AMC_MAX_OPERANDS operands in a call,
+ * AMC_E_RANGE for an array id out of range or an overflowing output. */
+AMC_API int amc_translate_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_arrays,
+                           const uint8_t* call_side, const int32_t* call_off, int64_t n_calls,
+                           const int32_t* opnd_array, const uint8_t* opnd_mode, int64_t n_operands,
+                           int infer_overlap,
+                           uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap, int64_t* out_n,
+                           int64_t* call_first_op, void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (3) Batches of structured programs, relation mode -- Fig. Opsem with      */
+/*     opaque conditions: If = union of both branches, While = closure of    */
+/*     its body.                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Largest If/While nesting depth amc_check_batch accepts. */
+#define AMC_MAX_DEPTH 8
+
+/* Workspace bytes amc_check_batch needs. */
+AMC_API size_t amc_check_batch_workspace(int64_t n_tokens, int64_t n_progs, int64_t total_vars);
+
+/* Checks n_progs independent programs in one launch sequence.  Program p owns
+ * tokens [prog_tok_off[p], prog_tok_off[p+1]) of tok_kind_side / tok_payload
+ * and variables 0..prog_nvars[p]-1 (stored at prog_var_off[p] in final_mask).
+ * Op tokens carry their program-local variable id in the payload; IF, ELSE and
+ * WHILE carry the token length of the branch / body that follows, END 0:
+ *   IF(n_then) <then> ELSE(n_else) <else> END,   WHILE(n_body) <body> END.
+ * Every variable starts as the set {(V,I)}.  Outputs: step_mask[token] = set
+ * of possible statuses of the op's variable after the op (0 for structure
+ * tokens); final_mask[prog_var_off[p] + v]; prog_first_fault[p] = smallest
+ * program-relative token index of an op whose possible pre-statuses include a
+ * non-stuck status that the op makes stuck (-1 if none).
+ * graph_capture = 1 launches through a cached CUDA graph for this shape.
+ * Errors: host-side checks of sizes; device-side (amc_sync_status)
+ * AMC_E_INVALID for unbalanced tokens, depth > AMC_MAX_DEPTH or bad op bytes,
+ * AMC_E_RANGE for a var id out of its program's range. */
+AMC_API int amc_check_batch(const uint8_t* tok_kind_side, const int32_t* tok_payload,
+                    const int64_t* prog_tok_off, const int32_t* prog_nvars,
+                    const int64_t* prog_var_off, int64_t n_progs, int64_t n_tokens,
+                    uint8_t* step_mask, uint8_t* final_mask, int64_t* prog_first_fault,
+                    int graph_capture, void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (4) Serving -- continuous batching of check requests with per-session     */
+/*     variable statuses kept on the device between requests.                */
+/* ------------------------------------------------------------------------ */
+typedef struct amc_server amc_server;
+
+enum { AMC_REQ_TRACE = 0, AMC_REQ_PROGRAM = 1 };
+
+/* A request, described on the host.  Buffers are HOST pointers (copied by the
+ * server when the request is admitted; they must stay valid until then).
+ * TRACE: kind_side / var of n_items ops.  PROGRAM: kind_side / var hold the
+ * token bytes and payloads of n_items tokens.  n_vars sizes the session on its
+ * first request and must match afterwards. */
+typedef struct {
+    int kind;
+    int32_t n_vars;
+    int64_t n_items;
+    const uint8_t* kind_side;
+    const int32_t* var;
+} amc_request;
+
+/* Result of a finished request.  `status` holds n_items host bytes: status
+ * codes (TRACE) or masks (PROGRAM); valid until amc_serve_release(ticket). */
+typedef struct {
+    int error;               /* AMC_OK or a device-side error code */
+    int64_t first_fault;     /* request-relative index, -1 none */
+    int64_t n_items;
+    const uint8_t* status;
+    double t_submit, t_admit, t_done;   /* seconds, server clock */
+} amc_result;
+
+/* Creates a server on the current device that holds at most max_slots
+ * requests on the device at once and at most mem_budget_bytes of device
+ * memory for requests and sessions. */
+AMC_API int amc_server_create(size_t mem_budget_bytes, int max_slots, amc_server** out);
+/* Queues a request of a session (requests of one session run in submission
+ * order; different sessions overlap on the device).  Returns AMC_E_AGAIN when
+ * the queue is full. */
+AMC_API int amc_serve_submit(amc_server* srv, uint64_t session_id, const amc_request* req, uint64_t* ticket);
+/* Non-blocking: *done = 1 and *out filled once the request finished. */
+AMC_API int amc_serve_poll(amc_server* srv, uint64_t ticket, int* done, amc_result* out);
+/* Frees a finished request's host result. */
+AMC_API int amc_serve_release(amc_server* srv, uint64_t ticket);
+/* Copies a session's current variable statuses (status codes for trace
+ * sessions, masks for program sessions) to host memory. */
+AMC_API int amc_session_export(amc_server* srv, uint64_t session_id, uint8_t* host_status, int32_t n_vars);
+/* Waits for all queued requests, then frees the server. */
+AMC_API int amc_server_destroy(amc_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMC_H */

@@ -142,7 +142,7 @@ def vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd_mode,
     A = s.shape[0]
     n_calls = cs.shape[0]
     if out_cap is None:
-        out_cap = int(5 * oa.shape[0] + 16 * n_calls + 2 * A * 8 + 64)
+        out_cap = int(5 * oa.shape[0] + 48 * n_calls + 64)
     while True:
         ks = np.empty(out_cap, np.uint8)
         var = np.empty(out_cap, np.int32)

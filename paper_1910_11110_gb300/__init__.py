@@ -1,0 +1,198 @@
+"""GB300 access-mode consistency checker: Python binding of the C ABI.
+
+Thin ctypes layer over ``_build/libamc.so`` (see ``include/amc.h``): it only
+marshals torch CUDA tensors into device pointers and sizes the workspaces; all
+checking runs in the library's CUDA kernels.  There is no CPU fallback: the
+functions raise ``RuntimeError`` when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libamc.so")
+_lib = None
+
+OK, E_INVALID, E_RANGE, E_NOMEM, E_TIMEOUT, E_CUDA, E_AGAIN = 0, -1, -2, -3, -4, -5, -6
+ST_F = 4
+
+
+class AmcError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {error_string(code)} ({code})" if what else f"{error_string(code)} ({code})")
+
+
+def build(force: bool = False) -> str:
+    from . import builder
+    return builder.build(force=force)
+
+
+def lib():
+    """The loaded CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build() or paper_1910_11110_gb300.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, sz, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_int
+        L.amc_version.restype = ci
+        L.amc_error_string.restype = ctypes.c_char_p
+        L.amc_error_string.argtypes = [ci]
+        L.amc_sync_status.argtypes = [P]
+        L.amc_check_trace_workspace.restype = sz
+        L.amc_check_trace_workspace.argtypes = [i64, i32]
+        L.amc_check_trace.argtypes = [P, P, i64, i32, P, P, P, P, P, P, sz, P]
+        L.amc_check_guarded_trace_workspace.restype = sz
+        L.amc_check_guarded_trace_workspace.argtypes = [i64, i32]
+        L.amc_check_guarded_trace.argtypes = [P, P, i64, i32, P, P, P, P, P, P, sz, P]
+        if hasattr(L, "amc_translate_vectorpu"):
+            L.amc_translate_vectorpu_workspace.restype = sz
+            L.amc_translate_vectorpu_workspace.argtypes = [i32, i64, i64]
+            L.amc_translate_vectorpu.argtypes = [P, P, i32, P, P, i64, P, P, i64, ci,
+                                                 P, P, i64, P, P, P, sz, P]
+        if hasattr(L, "amc_check_batch"):
+            L.amc_check_batch_workspace.restype = sz
+            L.amc_check_batch_workspace.argtypes = [i64, i64, i64]
+            L.amc_check_batch.argtypes = [P, P, P, P, P, i64, i64, P, P, P, ci, P, sz, P]
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    try:
+        return lib().amc_error_string(code).decode()
+    except RuntimeError:
+        return "error"
+
+
+def _p(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise AmcError(rc, what)
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Workspace:
+    """Grow-only device scratch buffer (256-byte aligned, from torch's allocator)."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes: int, device) -> torch.Tensor:
+        nbytes = max(256, int(nbytes))
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        return self.buf[off:off + nbytes]
+
+
+_ws = Workspace()
+
+
+def sync_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device error word."""
+    return lib().amc_sync_status(_stream_ptr(stream))
+
+
+def trace_workspace_bytes(n_ops: int, n_vars: int, guarded: bool = False) -> int:
+    L = lib()
+    f = L.amc_check_guarded_trace_workspace if guarded else L.amc_check_trace_workspace
+    return int(f(n_ops, n_vars))
+
+
+def check_trace(kind_side, var, n_vars, init_status=None, *, guarded=False, out=None,
+                workspace=None, stream=None):
+    """Check one trace on the GPU (amc_check_trace / amc_check_guarded_trace).
+
+    kind_side: uint8 CUDA tensor [n_ops]; var: int32 CUDA tensor [n_ops].
+    Returns dict(step_status, final_status, var_first_fault, first_fault) of
+    CUDA tensors (first_fault: int64 [1]).  ``out`` may pass preallocated
+    output tensors with those keys.
+    """
+    _dev(kind_side, torch.uint8, "kind_side")
+    _dev(var, torch.int32, "var")
+    n = kind_side.numel()
+    if var.numel() != n:
+        raise ValueError("kind_side and var differ in length")
+    dev = kind_side.device
+    if init_status is not None:
+        _dev(init_status, torch.uint8, "init_status")
+    if out is None:
+        out = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+                   final_status=torch.empty(max(n_vars, 0), dtype=torch.uint8, device=dev),
+                   var_first_fault=torch.empty(max(n_vars, 0), dtype=torch.int32, device=dev),
+                   first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+    nbytes = trace_workspace_bytes(n, n_vars, guarded)
+    ws = workspace if workspace is not None else _ws.get(nbytes, dev)
+    L = lib()
+    fn = L.amc_check_guarded_trace if guarded else L.amc_check_trace
+    rc = fn(_p(kind_side), _p(var), n, n_vars, _p(init_status), _p(out["step_status"]),
+            _p(out["final_status"]), _p(out["var_first_fault"]), _p(out["first_fault"]),
+            _p(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_check_trace")
+    return out
+
+
+def translate_vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd_mode, *,
+                       infer_overlap=True, out_cap=None, stream=None):
+    """Translate VectorPU calls into a core trace over 2 * n_arrays variables
+    (amc_translate_vectorpu).  All inputs are CUDA tensors (int32 / uint8).
+    Returns dict(kind_side, var, call_first_op, n).  When ``out_cap`` is too
+    small the call is repeated once with the exact size."""
+    _dev(arr_start, torch.int32, "arr_start")
+    _dev(arr_len, torch.int32, "arr_len")
+    _dev(call_side, torch.uint8, "call_side")
+    _dev(call_off, torch.int32, "call_off")
+    _dev(opnd_array, torch.int32, "opnd_array")
+    _dev(opnd_mode, torch.uint8, "opnd_mode")
+    A = arr_start.numel()
+    n_calls = call_side.numel()
+    n_opnd = opnd_array.numel()
+    dev = arr_start.device
+    L = lib()
+    if out_cap is None:
+        out_cap = 48 * n_calls + 64
+    first = torch.empty(n_calls + 1, dtype=torch.int64, device=dev)
+    out_n = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = _ws.get(L.amc_translate_vectorpu_workspace(A, n_calls, n_opnd), dev)
+    for attempt in range(2):
+        ks = torch.empty(max(out_cap, 1), dtype=torch.uint8, device=dev)
+        var = torch.empty(max(out_cap, 1), dtype=torch.int32, device=dev)
+        rc = L.amc_translate_vectorpu(_p(arr_start), _p(arr_len), A, _p(call_side), _p(call_off), n_calls,
+                                      _p(opnd_array), _p(opnd_mode), n_opnd, int(bool(infer_overlap)),
+                                      _p(ks), _p(var), out_cap, _p(out_n), _p(first), _p(ws), ws.numel(),
+                                      _stream_ptr(stream))
+        _check(rc, "amc_translate_vectorpu")
+        n = int(out_n.item())
+        if n <= out_cap:
+            return dict(kind_side=ks[:n], var=var[:n], call_first_op=first, n=n)
+        code = sync_status(stream)
+        if code not in (OK, E_RANGE):
+            raise AmcError(code, "amc_translate_vectorpu")
+        out_cap = n
+    raise AmcError(E_RANGE, "amc_translate_vectorpu")

@@ -1,0 +1,204 @@
+// api.cu -- C ABI entry points: argument checks, workspace layout, launches.
+#include <cstring>
+
+#include "amc_internal.cuh"
+#include "scan_trace.cuh"
+#include "translate.cuh"
+
+using namespace amc;
+
+namespace {
+
+inline bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
+
+size_t guarded_extra_bytes(int32_t n_vars)
+{
+    return align_up(4 * (size_t)n_vars, 256) + 256;
+}
+
+int check_trace_args(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
+                     uint8_t* step_status, uint8_t* final_status, int32_t* var_first_fault,
+                     int64_t* first_fault)
+{
+    if (n_ops < 0 || n_ops > INT32_MAX || n_vars < 0) return AMC_E_INVALID;
+    if (n_ops > 0 && (n_vars < 1 || !kind_side || !var || !step_status)) return AMC_E_INVALID;
+    if (n_vars > 0 && (!final_status || !var_first_fault)) return AMC_E_INVALID;
+    if (!first_fault) return AMC_E_INVALID;
+    return AMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int amc_version(void) { return 10000; }
+
+int amc_set_profile_events(void* start_event, void* stop_event)
+{
+    amc::set_profile_events(static_cast<cudaEvent_t>(start_event), static_cast<cudaEvent_t>(stop_event));
+    return AMC_OK;
+}
+
+const char* amc_error_string(int code)
+{
+    switch (code) {
+    case AMC_OK: return "ok";
+    case AMC_E_INVALID: return "malformed input";
+    case AMC_E_RANGE: return "id out of range or capacity exceeded";
+    case AMC_E_NOMEM: return "workspace too small or memory budget exceeded";
+    case AMC_E_TIMEOUT: return "a bounded device-side wait expired";
+    case AMC_E_CUDA: return "CUDA runtime error";
+    case AMC_E_AGAIN: return "no slot free yet";
+    }
+    return "unknown error";
+}
+
+int amc_sync_status(void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return AMC_E_CUDA;
+    int* w = device_error_word();
+    if (!w) return AMC_E_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return AMC_E_CUDA;
+    if (v != 0) {
+        int z = 0;
+        if (cudaMemcpy(w, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return AMC_E_CUDA;
+    }
+    return v;
+}
+
+size_t amc_check_trace_workspace(int64_t n_ops, int32_t n_vars)
+{
+    if (n_ops < 0 || n_vars < 0) return 0;
+    return scan_workspace_bytes(n_ops, n_vars);
+}
+
+int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
+                    const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                    int32_t* var_first_fault, int64_t* first_fault, void* workspace, size_t ws_bytes,
+                    void* stream)
+{
+    int rc = check_trace_args(kind_side, var, n_ops, n_vars, step_status, final_status, var_first_fault,
+                              first_fault);
+    if (rc) return rc;
+    if (!workspace || !aligned256(workspace) || ws_bytes < scan_workspace_bytes(n_ops, n_vars))
+        return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    ScanLaunch L;
+    L.kind_side = kind_side;
+    L.var = var;
+    L.n_ops = n_ops;
+    L.n_vars = n_vars;
+    L.init = init_status;
+    L.step = step_status;
+    L.final_status = final_status;
+    L.vff = var_first_fault;
+    L.first_fault = first_fault;
+    L.err = err;
+    L.workspace = workspace;
+    L.profile = 3;
+    return launch_scan_trace(L, static_cast<cudaStream_t>(stream));
+}
+
+size_t amc_check_guarded_trace_workspace(int64_t n_ops, int32_t n_vars)
+{
+    if (n_ops < 0 || n_vars < 0) return 0;
+    return scan_workspace_bytes(n_ops, n_vars) + guarded_extra_bytes(n_vars);
+}
+
+int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
+                            const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                            int32_t* var_first_fault, int64_t* first_fault, void* workspace,
+                            size_t ws_bytes, void* stream)
+{
+    int rc = check_trace_args(kind_side, var, n_ops, n_vars, step_status, final_status, var_first_fault,
+                              first_fault);
+    if (rc) return rc;
+    if (!workspace || !aligned256(workspace) || ws_bytes < amc_check_guarded_trace_workspace(n_ops, n_vars))
+        return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* w = static_cast<uint8_t*>(workspace);
+    uint8_t* extra = w + scan_workspace_bytes(n_ops, n_vars);
+    int32_t* vff_scratch = reinterpret_cast<int32_t*>(extra);
+    int64_t* ff_scratch = reinterpret_cast<int64_t*>(extra + align_up(4 * (size_t)n_vars, 256));
+    // pass 1: pre-statuses of every op with GT as Noop (guards read abstract
+    // variables, which GT never touches)
+    ScanLaunch A;
+    A.kind_side = kind_side;
+    A.var = var;
+    A.n_ops = n_ops;
+    A.n_vars = n_vars;
+    A.init = init_status;
+    A.step = step_status;
+    A.vff = vff_scratch;
+    A.first_fault = ff_scratch;
+    A.pre_mode = 1;
+    A.err = err;
+    A.workspace = workspace;
+    A.profile = 1;          // the profiled span covers both scans
+    rc = launch_scan_trace(A, s);
+    if (rc) return rc;
+    // pass 2: GT resolved from the pre-status of the EN that follows it
+    ScanLaunch B = A;
+    B.step = step_status;
+    B.final_status = final_status;
+    B.vff = var_first_fault;
+    B.first_fault = first_fault;
+    B.guard = step_status;
+    B.pre_mode = 0;
+    B.profile = 2;
+    return launch_scan_trace(B, s);
+}
+
+size_t amc_translate_vectorpu_workspace(int32_t n_arrays, int64_t n_calls, int64_t n_operands)
+{
+    if (n_arrays < 0 || n_calls < 0 || n_operands < 0) return 0;
+    return translate_workspace_bytes(n_arrays, n_calls);
+}
+
+int amc_translate_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_arrays,
+                           const uint8_t* call_side, const int32_t* call_off, int64_t n_calls,
+                           const int32_t* opnd_array, const uint8_t* opnd_mode, int64_t n_operands,
+                           int infer_overlap, uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap,
+                           int64_t* out_n, int64_t* call_first_op, void* workspace, size_t ws_bytes,
+                           void* stream)
+{
+    if (n_arrays < 0 || n_arrays > INT32_MAX / 2 || n_calls < 0 || n_calls > INT32_MAX || n_operands < 0 ||
+        out_cap < 0)
+        return AMC_E_INVALID;
+    if (!out_n || !call_first_op || !call_off) return AMC_E_INVALID;
+    if (n_arrays > 0 && (!arr_start || !arr_len)) return AMC_E_INVALID;
+    if (n_calls > 0 && !call_side) return AMC_E_INVALID;
+    if (n_operands > 0 && (!opnd_array || !opnd_mode)) return AMC_E_INVALID;
+    if (out_cap > 0 && (!out_kind_side || !out_var)) return AMC_E_INVALID;
+    if (!workspace || !aligned256(workspace) || ws_bytes < translate_workspace_bytes(n_arrays, n_calls))
+        return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    TranslateLaunch T;
+    T.arr_start = arr_start;
+    T.arr_len = arr_len;
+    T.n_arrays = n_arrays;
+    T.call_side = call_side;
+    T.call_off = call_off;
+    T.n_calls = n_calls;
+    T.opnd_array = opnd_array;
+    T.opnd_mode = opnd_mode;
+    T.n_operands = n_operands;
+    T.infer = infer_overlap ? 1 : 0;
+    T.out_ks = out_kind_side;
+    T.out_var = out_var;
+    T.out_cap = out_cap;
+    T.out_n = out_n;
+    T.call_first_op = call_first_op;
+    T.err = err;
+    T.workspace = workspace;
+    T.profile = 3;
+    return launch_translate(T, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,588 @@
+// scan_trace.cu -- single-pass per-variable scan of an op trace (sm_103a).
+//
+// What it computes: for every op i on variable v = var[i] the status of v after
+// the op, by applying each op's transfer function in trace order (rules Effect
+// and Remote Effect of Fig. Opsem; sequencing is associative with Noop as unit,
+// Section 3.2, so per-variable prefix compositions give the same statuses).
+//
+// How (one CTA per tile of T ops, persistent CTAs taking tiles in order):
+//  1. the tile's op bytes and var ids are staged into shared memory by bulk
+//     async copies (cp.async.bulk + mbarrier), double buffered;
+//  2. each op byte becomes a monoid element (5-bit id, table lookup);
+//  3. a stable LSD radix sort of (var, position) in shared memory groups the
+//     tile's ops per variable ("runs"), warp ranking with match.any;
+//  4. a segmented scan over the sorted runs composes each op's in-tile prefix
+//     (thread-serial composition, then a warp-shuffle segmented scan);
+//  5. each run needs the status of its variable at tile entry.  Runs of a
+//     variable already known to be stuck take F at once (F is absorbing; the
+//     first-fault table doubles as that index).  The other runs register a
+//     node (tile aggregate) in the variable's list of touching tiles, kept
+//     sorted by tile with lock-free insertion, then -- once every earlier tile
+//     has registered -- walk that list back composing aggregates until a node
+//     with a published inclusive status or the list end (initial status):
+//     decoupled look-back restricted to the tiles that touch the variable;
+//  6. outputs are written in original order (coalesced), first faults by
+//     atomicMin.
+// The only waits are on the registration frontier and on the mbarriers, both
+// bounded; an expired wait raises AMC_E_TIMEOUT and the kernel carries on.
+#include "amc_internal.cuh"
+#include "scan_trace.cuh"
+
+namespace amc {
+
+namespace {
+
+constexpr uint8_t RUN_PENDING = 0xFF;
+constexpr uint32_t NODE_AGG = 0x40;
+constexpr uint32_t NODE_INCL = 0x80;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+template <int T, int NT>
+struct __align__(16) ScanSmem {
+    int32_t var[2][T];               // var ids, later the sort's ping keys
+    uint32_t keyB[T];                // sort pong keys
+    uint8_t kind[2][T];              // op bytes, then element ids
+    uint16_t valA[T];
+    uint16_t valB[T];
+    uint8_t out[T];
+    uint8_t runEntry[T];
+    uint16_t hist[256 * (NT / 32)];
+    uint8_t comp[MAX_ELEMS * MAX_ELEMS];
+    uint8_t app[MAX_ELEMS * 8];
+    uint8_t elem_of[256];
+    int scanTmp[2 * (NT / 32) + 4];
+    uint8_t segF[NT / 32];
+    uint8_t segV[NT / 32];
+    uint64_t mbar[2];
+    int tileId[2];
+    int viaBulk[2];
+    int nRuns;
+};
+
+__device__ __forceinline__ uint32_t comp_of(const uint8_t* comp, uint32_t a, uint32_t b)
+{
+    return comp[a * MAX_ELEMS + b];
+}
+
+// Issue the bulk loads of tile t into buffer b (thread 0 only).  Tiles that are
+// partial or not 16-byte aligned are loaded later with plain loads.
+template <int T, int NT>
+__device__ void issue_tile_load(const ScanParams& p, ScanSmem<T, NT>& S, int b, int t)
+{
+    S.tileId[b] = t;
+    S.viaBulk[b] = 0;
+    if (t >= p.n_tiles) return;
+    const int64_t base = (int64_t)t * T;
+    if (base + T > p.n_ops || !p.bulk_ok) return;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&S.mbar[b], (uint32_t)(T + 4 * T));
+    bulk_g2s(S.kind[b], p.kind_side + base, T, &S.mbar[b]);
+    bulk_g2s(S.var[b], p.var + base, 4 * T, &S.mbar[b]);
+    S.viaBulk[b] = 1;
+}
+
+template <int T, int NT>
+__device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int t, const int b)
+{
+    constexpr int E = T / NT;
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)t * T;
+    const int n = (int)min((int64_t)T, p.n_ops - base);
+    uint8_t* kb = S.kind[b];
+    int32_t* vb = S.var[b];
+    const uint32_t ID = 0;
+
+    if (!S.viaBulk[b]) {
+        for (int i = tid; i < n; i += NT) {
+            kb[i] = p.kind_side[base + i];
+            vb[i] = p.var[base + i];
+        }
+        __syncthreads();
+    }
+
+    // ---- 2. decode: op byte -> element id; validate ------------------------
+    // (all reads happen before any in-place write: GT looks at the next op)
+    uint8_t mloc[E];
+    uint32_t badVar = 0;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int i = tid * E + k;
+        mloc[k] = (uint8_t)ID;
+        if (i < n) {
+            const uint32_t ks = kb[i];
+            const int32_t v = vb[i];
+            if (v < 0 || v >= p.n_vars) {
+                raise_error(p.err, AMC_E_RANGE);
+                badVar |= 1u << k;
+            }
+            uint32_t m = S.elem_of[ks];
+            if (m == ELEM_GT) {
+                // GT must be followed by EN of the same side on another variable
+                const int64_t gi = base + i;
+                uint32_t nks = 0xFF;
+                int32_t nv = v;
+                if (gi + 1 < p.n_ops) {
+                    nks = (i + 1 < n) ? kb[i + 1] : p.kind_side[gi + 1];
+                    nv = (i + 1 < n) ? vb[i + 1] : p.var[gi + 1];
+                }
+                if ((nks & 15) != AMC_K_EN || (nks >> 4) != (ks >> 4) || nv == v) {
+                    raise_error(p.err, AMC_E_INVALID);
+                    m = ID;
+                } else if (p.pre_mode) {
+                    m = ID;                      // guard pass: GT does not touch guards
+                } else if (!p.guard) {
+                    raise_error(p.err, AMC_E_INVALID);   // GT needs the guarded entry point
+                    m = ID;
+                } else {
+                    // guard = status of the EN's variable before the EN, written
+                    // at gi+1 by the guard pass
+                    const uint32_t g = p.guard[gi + 1];
+                    const int side = ks >> 4;
+                    const bool valid = g != ST_F && (g & (side == 0 ? 1u : 2u));
+                    m = valid ? ID : p.tab.pull_of_side[side];
+                }
+            } else if (m == ELEM_BAD) {
+                raise_error(p.err, AMC_E_INVALID);
+                m = ID;
+            }
+            mloc[k] = (uint8_t)m;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int i = tid * E + k;
+        if (i < n) {
+            kb[i] = mloc[k];
+            if (badVar & (1u << k)) vb[i] = 0;
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. stable LSD radix sort of (var, position) -----------------------
+    uint32_t* kin = reinterpret_cast<uint32_t*>(vb);
+    uint32_t* kout = S.keyB;
+    uint16_t* vin = S.valA;
+    uint16_t* vout = S.valB;
+    const int D = 1 << p.digit_bits;
+    const int M = D * NW;
+    const uint32_t lt = lanemask_lt();
+    for (int pass = 0; pass < p.passes; ++pass) {
+        const int shift = pass * p.digit_bits;
+        for (int i = tid; i < M; i += NT) S.hist[i] = 0;
+        __syncthreads();
+        uint32_t kk[E];
+        uint16_t lr[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int pos = warp * 32 * E + e * 32 + lane;
+            const bool ok = pos < n;
+            const uint32_t key = ok ? kin[pos] : 0u;
+            kk[e] = key;
+            const uint32_t dig = ok ? ((key >> shift) & (uint32_t)(D - 1)) : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            const uint32_t rank = __popc(peers & lt);
+            uint16_t c = 0;
+            if (ok) c = S.hist[dig * NW + warp];
+            lr[e] = (uint16_t)(c + rank);
+            __syncwarp();
+            if (ok && rank == 0) S.hist[dig * NW + warp] = (uint16_t)(c + __popc(peers));
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            // exclusive scan of hist in (digit, warp) order
+            const int per = (M + NT - 1) / NT;
+            const int lo = tid * per;
+            int sum = 0;
+            for (int j = 0; j < per; ++j)
+                if (lo + j < M) sum += S.hist[lo + j];
+            int run = block_excl_sum<NT>(sum, S.scanTmp, nullptr);
+            for (int j = 0; j < per; ++j)
+                if (lo + j < M) {
+                    const int c = S.hist[lo + j];
+                    S.hist[lo + j] = (uint16_t)run;
+                    run += c;
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int pos = warp * 32 * E + e * 32 + lane;
+            if (pos < n) {
+                const uint32_t dig = (kk[e] >> shift) & (uint32_t)(D - 1);
+                const int dst = S.hist[dig * NW + warp] + lr[e];
+                kout[dst] = kk[e];
+                vout[dst] = pass == 0 ? (uint16_t)pos : vin[pos];
+            }
+        }
+        __syncthreads();
+        uint32_t* tk = kin; kin = kout; kout = tk;
+        uint16_t* tv = vin; vin = vout; vout = tv;
+    }
+    const uint32_t* K = kin;     // sorted keys
+    const uint16_t* P = vin;     // original positions
+
+    // ---- 4. segmented scan over runs (blocked: thread owns E sorted slots) --
+    uint8_t pm[E], xm[E];
+    uint32_t headMask = 0;
+    int nHeads = 0;
+    uint32_t acc = ID;
+    {
+        const int j0 = tid * E;
+        uint32_t prevKey = (j0 > 0 && j0 - 1 < n) ? K[j0 - 1] : 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            pm[k] = xm[k] = (uint8_t)ID;
+            if (j < n) {
+                const uint32_t key = K[j];
+                const uint32_t m = kb[P[j]];
+                if (key != prevKey) {
+                    headMask |= 1u << k;
+                    ++nHeads;
+                    xm[k] = (uint8_t)ID;
+                    acc = m;
+                } else {
+                    xm[k] = (uint8_t)acc;
+                    acc = comp_of(S.comp, acc, m);
+                }
+                pm[k] = (uint8_t)acc;
+                prevKey = key;
+            }
+        }
+    }
+    // segmented exclusive scan of (has head, value) across threads
+    uint32_t carry;
+    {
+        uint32_t f = headMask != 0, v = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t fu = __shfl_up_sync(0xffffffffu, f, o);
+            const uint32_t vu = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) {
+                if (!f) v = comp_of(S.comp, vu, v);
+                f |= fu;
+            }
+        }
+        // exclusive within warp
+        uint32_t fe = __shfl_up_sync(0xffffffffu, f, 1);
+        uint32_t ve = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) { fe = 0; ve = ID; }
+        if (lane == 31) { S.segF[warp] = (uint8_t)f; S.segV[warp] = (uint8_t)v; }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t wf = lane < NW ? S.segF[lane] : 0, wv = lane < NW ? S.segV[lane] : ID;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t fu = __shfl_up_sync(0xffffffffu, wf, o);
+                const uint32_t vu = __shfl_up_sync(0xffffffffu, wv, o);
+                if (lane >= o) {
+                    if (!wf) wv = comp_of(S.comp, vu, wv);
+                    wf |= fu;
+                }
+            }
+            uint32_t xf = __shfl_up_sync(0xffffffffu, wf, 1);
+            uint32_t xv = __shfl_up_sync(0xffffffffu, wv, 1);
+            if (lane == 0) { xf = 0; xv = ID; }
+            if (lane < NW) { S.segF[lane] = (uint8_t)xf; S.segV[lane] = (uint8_t)xv; }
+        }
+        __syncthreads();
+        const uint32_t wpv = S.segV[warp];
+        carry = fe ? ve : comp_of(S.comp, wpv, ve);
+    }
+    // elements before the thread's first head continue a run from earlier threads
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        if ((headMask & ((2u << k) - 1)) == 0) {
+            pm[k] = (uint8_t)comp_of(S.comp, carry, pm[k]);
+            xm[k] = (uint8_t)comp_of(S.comp, carry, xm[k]);
+        }
+    }
+    int nRuns;
+    const int runBase = block_excl_sum<NT>(nHeads, S.scanTmp, &nRuns);
+
+    // ---- 5a. run entry: stuck shortcut or registration ---------------------
+    const uint32_t nodeBase = (uint32_t)t * (uint32_t)T;
+    {
+        const int j0 = tid * E;
+        int r = runBase - 1;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            if (headMask & (1u << k)) ++r;
+            if (j < n && (j == n - 1 || K[j + 1] != K[j])) {
+                const uint32_t v = K[j];
+                const uint32_t ffv = ld_relaxed(reinterpret_cast<const uint32_t*>(p.vff) + v);
+                if (ffv < (uint32_t)base) {
+                    S.runEntry[r] = ST_F;
+                } else {
+                    S.runEntry[r] = RUN_PENDING;
+                    p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | pm[k]);
+                }
+            }
+        }
+    }
+    __threadfence();
+    {
+        const int j0 = tid * E;
+        int r = runBase - 1;
+#pragma unroll 1
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            if (headMask & (1u << k)) ++r;
+            if (j < n && (j == n - 1 || K[j + 1] != K[j]) && S.runEntry[r] == RUN_PENDING) {
+                const uint32_t v = K[j];
+                const uint32_t node = nodeBase + (uint32_t)r;
+                // insert into v's list, kept sorted by decreasing tile
+                uint32_t* link = p.head + v;
+                uint32_t it = 0;
+                for (;;) {
+                    const uint32_t c = ld_acquire(link);
+                    if (c == NIL || c / T < (uint32_t)t) {
+                        p.node_next[node] = c;
+                        __threadfence();
+                        if (atomicCAS(link, c, node) == c) break;
+                    } else {
+                        link = p.node_next + c;
+                    }
+                    if (++it > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- 5b. registration frontier: all tiles < t have registered ----------
+    if (tid == 0) {
+        __threadfence();
+        st_release(p.regflag + t, 1);
+        bool done = (t == 0);
+        int tp = t - 1;
+        uint32_t it = 0;
+        while (!done) {
+            const uint32_t f = ld_acquire(p.regflag + tp);
+            if (f == 2) done = true;
+            else if (f == 1) { if (tp == 0) done = true; else --tp; }
+            else if (++it > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); done = true; }
+            else __nanosleep(64);
+        }
+        st_release(p.regflag + t, 2);
+    }
+    __syncthreads();
+
+    // ---- 5c. look-back along each registered run's list ---------------------
+    {
+        const int j0 = tid * E;
+        int r = runBase - 1;
+#pragma unroll 1
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            if (headMask & (1u << k)) ++r;
+            if (j < n && (j == n - 1 || K[j + 1] != K[j]) && S.runEntry[r] == RUN_PENDING) {
+                const uint32_t v = K[j];
+                const uint32_t node = nodeBase + (uint32_t)r;
+                uint32_t q = ld_acquire(p.node_next + node);
+                uint32_t a = ID, st;
+                for (;;) {
+                    if (q == NIL) {
+                        st = p.init ? p.init[v] : (uint32_t)AMC_ST_VI;
+                        break;
+                    }
+                    const uint32_t s = ld_acquire_u8(p.node_status + q);
+                    if (s & NODE_INCL) { st = s & 7u; break; }
+                    a = comp_of(S.comp, s & 31u, a);          // earlier tile first
+                    q = ld_acquire(p.node_next + q);
+                }
+                const uint32_t entry = S.app[a * 8 + st];
+                S.runEntry[r] = (uint8_t)entry;
+                st_relaxed_u8(p.node_status + node, NODE_INCL | S.app[pm[k] * 8 + entry]);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- 6. outputs in original order; first faults --------------------------
+    {
+        const int j0 = tid * E;
+        int r = runBase - 1;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            if (headMask & (1u << k)) ++r;
+            if (j < n) {
+                const uint32_t e = S.runEntry[r];
+                const uint32_t pre = S.app[xm[k] * 8 + e];
+                const uint32_t post = S.app[pm[k] * 8 + e];
+                const int pos = P[j];
+                S.out[pos] = (uint8_t)(p.pre_mode ? pre : post);
+                if (post == ST_F && pre != ST_F) {
+                    const uint32_t gi = (uint32_t)(base + pos);
+                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + K[j], gi);
+                    atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (n == T && p.bulk_ok) {
+        const uint4* src = reinterpret_cast<const uint4*>(S.out);
+        uint4* dst = reinterpret_cast<uint4*>(p.step + base);
+        for (int i = tid; i < T / 16; i += NT) dst[i] = src[i];
+    } else {
+        for (int i = tid; i < n; i += NT) p.step[base + i] = S.out[i];
+    }
+}
+
+template <int T, int NT>
+__global__ void __launch_bounds__(NT, 2) scan_trace_kernel(const ScanParams p)
+{
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    ScanSmem<T, NT>& S = *reinterpret_cast<ScanSmem<T, NT>*>(smem_raw);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += NT) S.comp[i] = p.tab.comp[i];
+    for (int i = tid; i < MAX_ELEMS * 8; i += NT) S.app[i] = p.tab.app[i];
+    for (int i = tid; i < 256; i += NT) S.elem_of[i] = p.tab.elem_of[i];
+    if (tid == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        fence_mbar_init();
+        issue_tile_load<T, NT>(p, S, 0, (int)atomicAdd(p.tile_counter, 1u));
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0, 0};
+    int cur = 0;
+    for (;;) {
+        const int t = S.tileId[cur];
+        if (t >= p.n_tiles) break;          // nothing was issued into this buffer
+        if (tid == 0) issue_tile_load<T, NT>(p, S, cur ^ 1, (int)atomicAdd(p.tile_counter, 1u));
+        bool ok = true;
+        if (S.viaBulk[cur]) {
+            ok = mbar_wait_bounded(&S.mbar[cur], parity[cur], p.err);
+            parity[cur] ^= 1;
+        }
+        if (__syncthreads_or(!ok)) {
+            // never leave with a bulk copy in flight into shared memory: drain
+            // the copy just issued (and the one that timed out), both bounded
+            if (tid == 0) {
+                if (S.viaBulk[cur ^ 1]) mbar_wait_bounded(&S.mbar[cur ^ 1], parity[cur ^ 1], p.err);
+                if (!ok) mbar_wait_bounded(&S.mbar[cur], parity[cur] ^ 1, p.err);
+            }
+            break;
+        }
+        process_tile<T, NT>(p, S, t, cur);
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
+__global__ void finalize_trace_kernel(const int32_t* __restrict__ vff, const uint32_t* __restrict__ head,
+                                      const uint8_t* __restrict__ node_status, const uint8_t* __restrict__ init,
+                                      int32_t n_vars, uint8_t* __restrict__ final_status)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_vars) return;
+    uint8_t f;
+    if (vff[v] != -1) {
+        f = ST_F;
+    } else {
+        const uint32_t h = head[v];
+        f = (h == NIL) ? (init ? init[v] : (uint8_t)AMC_ST_VI) : (uint8_t)(node_status[h] & 7u);
+    }
+    final_status[v] = f;
+}
+
+constexpr int TILE = 4096;
+constexpr int THREADS = 256;
+
+}  // namespace
+
+int scan_tile_size() { return TILE; }
+
+size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars)
+{
+    const int64_t n_tiles = (n_ops + TILE - 1) / TILE;
+    size_t b = 0;
+    b += align_up(4 * (size_t)n_vars, 256);                 // head
+    b += align_up(4 * (size_t)n_tiles * TILE, 256);         // node_next
+    b += align_up((size_t)n_tiles * TILE, 256);             // node_status
+    b += align_up(4 * (size_t)n_tiles, 256);                // regflag
+    b += 256;                                               // tile counter
+    return b;
+}
+
+int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
+{
+    ScanParams p{};
+    p.kind_side = L.kind_side;
+    p.var = L.var;
+    p.n_ops = L.n_ops;
+    p.n_vars = L.n_vars;
+    p.init = L.init;
+    p.step = L.step;
+    p.vff = L.vff;
+    p.first_fault = L.first_fault;
+    p.guard = L.guard;
+    p.pre_mode = L.pre_mode;
+    p.err = L.err;
+    p.tab = host_tables();
+    p.n_tiles = (int)((L.n_ops + TILE - 1) / TILE);
+    uint8_t* w = static_cast<uint8_t*>(L.workspace);
+    p.head = reinterpret_cast<uint32_t*>(w);
+    w += align_up(4 * (size_t)L.n_vars, 256);
+    p.node_next = reinterpret_cast<uint32_t*>(w);
+    w += align_up(4 * (size_t)p.n_tiles * TILE, 256);
+    p.node_status = w;
+    w += align_up((size_t)p.n_tiles * TILE, 256);
+    p.regflag = reinterpret_cast<uint32_t*>(w);
+    w += align_up(4 * (size_t)p.n_tiles, 256);
+    p.tile_counter = reinterpret_cast<uint32_t*>(w);
+    // key bits: var ids are < n_vars
+    int kb = 1;
+    while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
+    p.passes = (kb + 7) / 8;
+    p.digit_bits = (kb + p.passes - 1) / p.passes;
+    p.bulk_ok = ((uintptr_t)L.kind_side % 16 == 0) && ((uintptr_t)L.var % 16 == 0) &&
+                ((uintptr_t)L.step % 16 == 0);
+
+    if (cudaMemsetAsync(p.head, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
+    if (L.n_ops > 0) {
+        if (cudaMemsetAsync(p.regflag, 0, 4 * (size_t)p.n_tiles, s) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaMemsetAsync(p.tile_counter, 0, 4, s) != cudaSuccess) return AMC_E_CUDA;
+        const size_t smem = sizeof(ScanSmem<TILE, THREADS>);
+        static bool attr_set[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !attr_set[dev]) {
+            if (cudaFuncSetAttribute(scan_trace_kernel<TILE, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return AMC_E_CUDA;
+            attr_set[dev] = true;
+        }
+        int n_sm = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_trace_kernel<TILE, THREADS>, THREADS, smem);
+        if (per_sm < 1) per_sm = 1;
+        int grid = n_sm * per_sm;
+        if (grid > p.n_tiles) grid = p.n_tiles;
+        if (L.max_ctas > 0 && grid > L.max_ctas) grid = L.max_ctas;
+        if (L.profile & 1) profile_begin(s);
+        scan_trace_kernel<TILE, THREADS><<<grid, THREADS, smem, s>>>(p);
+        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        if (L.profile & 2) profile_end(s);
+    }
+    if (L.final_status) {
+        const int nb = (int)((L.n_vars + 255) / 256);
+        if (nb > 0) {
+            finalize_trace_kernel<<<nb, 256, 0, s>>>(L.vff, p.head, p.node_status, L.init, L.n_vars,
+                                                     L.final_status);
+            if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        }
+    }
+    return AMC_OK;
+}
+
+}  // namespace amc

@@ -1,0 +1,54 @@
+// scan_trace.cuh -- launch interface of the per-variable trace scan.
+#pragma once
+
+#include "amc_internal.cuh"
+
+namespace amc {
+
+struct ScanParams {
+    const uint8_t* kind_side;
+    const int32_t* var;
+    int64_t n_ops;
+    int32_t n_vars;
+    const uint8_t* init;        // nullable: all (V,I)
+    uint8_t* step;              // [n_ops] post-statuses (pre-statuses in pre_mode)
+    int32_t* vff;               // [n_vars] first fault per var (-1 none); also the stuck index
+    int64_t* first_fault;       // [1]
+    const uint8_t* guard;       // pre-statuses from the guard pass (GT resolution)
+    int pre_mode;               // 1 = guard pass: GT is Noop, outputs are pre-statuses
+    int* err;
+    uint32_t* head;             // [n_vars] newest registered node of each var
+    uint32_t* node_next;        // [n_tiles * T]
+    uint8_t* node_status;       // [n_tiles * T]
+    uint32_t* regflag;          // [n_tiles] 1 = registered, 2 = all earlier registered too
+    uint32_t* tile_counter;
+    int n_tiles;
+    int passes;
+    int digit_bits;
+    int bulk_ok;
+    Tables tab;
+};
+
+struct ScanLaunch {
+    const uint8_t* kind_side = nullptr;
+    const int32_t* var = nullptr;
+    int64_t n_ops = 0;
+    int32_t n_vars = 0;
+    const uint8_t* init = nullptr;
+    uint8_t* step = nullptr;
+    uint8_t* final_status = nullptr;    // nullable: skip the final-status pass
+    int32_t* vff = nullptr;
+    int64_t* first_fault = nullptr;
+    const uint8_t* guard = nullptr;
+    int pre_mode = 0;
+    int* err = nullptr;
+    void* workspace = nullptr;
+    int max_ctas = 0;                   // 0 = one wave of resident CTAs
+    int profile = 0;                    // bit 0: record the start event, bit 1: the stop event
+};
+
+int scan_tile_size();
+size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars);
+int launch_scan_trace(const ScanLaunch& L, cudaStream_t s);
+
+}  // namespace amc

@@ -1,0 +1,63 @@
+"""The C ABI library builds for sm_103a and exports every symbol that
+include/*.h declares (no compute calls: runs without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(amc_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libamc():
+    import paper_1910_11110_gb300 as amc
+    path = amc.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("amc_check_trace", "amc_check_guarded_trace", "amc_translate_vectorpu", "amc_check_batch",
+              "amc_serve_submit", "amc_serve_poll", "amc_sync_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libamc):
+    missing = [n for n in declared_functions() if not hasattr(libamc, n)]
+    assert not missing, missing
+
+
+def test_error_strings(libamc):
+    libamc.amc_error_string.restype = ctypes.c_char_p
+    for code in range(0, -7, -1):
+        assert libamc.amc_error_string(code)
+    assert libamc.amc_version() >= 10000
+
+
+def test_workspace_queries_are_sane(libamc):
+    libamc.amc_check_trace_workspace.restype = ctypes.c_size_t
+    libamc.amc_check_trace_workspace.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    a = libamc.amc_check_trace_workspace(1 << 20, 1 << 10)
+    b = libamc.amc_check_trace_workspace(1 << 21, 1 << 10)
+    assert 0 < a < b
+    assert libamc.amc_check_trace_workspace(-1, 4) == 0
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_1910_11110_gb300 as amc
+    monkeypatch.setattr(amc, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(amc, "_lib", None)
+    with pytest.raises(RuntimeError):
+        amc.lib()

@@ -1,0 +1,154 @@
+"""GPU parity of amc_check_trace with the oracle, element by element.
+
+Bit-exact on every step status, final status, per-variable first fault and
+global first fault (integer work: no tolerance).  Sizes span several tiles of
+4,096 ops and ragged tails; edge cases: empty trace, one op, one variable,
+every op on one variable, var ids at the top of the range, initial statuses
+including (I,I) and F, and faulty op bytes / ids reported by sync_status."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amc():
+    import paper_1910_11110_gb300 as m
+    m.build()
+    return m
+
+
+def run_both(amc, oracle_mod, ks, var, n_vars, init=None):
+    exp = oracle_mod.check_trace(ks, var, n_vars, init)
+    dev = torch.device("cuda")
+    out = amc.check_trace(torch.from_numpy(ks).to(dev), torch.from_numpy(var).to(dev), n_vars,
+                          None if init is None else torch.from_numpy(init).to(dev))
+    assert amc.sync_status() == 0
+    got = (out["step_status"].cpu().numpy(), out["final_status"].cpu().numpy(),
+           out["var_first_fault"].cpu().numpy(), int(out["first_fault"].cpu()[0]))
+    return exp, got
+
+
+def assert_same(exp, got):
+    assert np.array_equal(exp[0], got[0]), np.nonzero(exp[0] != got[0])[0][:10]
+    assert np.array_equal(exp[1], got[1]), np.nonzero(exp[1] != got[1])[0][:10]
+    assert np.array_equal(exp[2], got[2]), np.nonzero(exp[2] != got[2])[0][:10]
+    assert exp[3] == got[3]
+
+
+def test_uniform_16_vars_seed0(amc, oracle_mod):
+    ks, var, nv = workloads.trace_uniform(0)
+    assert_same(*run_both(amc, oracle_mod, ks, var, nv))
+
+
+@pytest.mark.parametrize("n_ops,n_vars,zipf", [
+    (1, 1, None), (17, 1, None), (4095, 3, None), (4096, 16, None), (4097, 16, None),
+    (3 * 4096 + 17, 5, None), (50_000, 1000, 1.05), (200_003, 1 << 20, 1.05),
+    (300_000, 7, None), (131_072, 1 << 16, None), (100_000, 2, None)])
+def test_random_traces(amc, oracle_mod, n_ops, n_vars, zipf):
+    rng = np.random.default_rng(n_ops + n_vars)
+    ks, var = workloads.trace_random(rng, n_ops, n_vars, kinds=(0, 1, 2, 3, 4, 5, 7), zipf_s=zipf)
+    assert_same(*run_both(amc, oracle_mod, ks, var, n_vars))
+
+
+@pytest.mark.parametrize("mix", ["benign", "faulty"])
+def test_low_fault_traces(amc, oracle_mod, mix):
+    # mostly writes / noops so that statuses stay non-stuck across many tiles
+    rng = np.random.default_rng(3)
+    p = [0.02, 0.6, 0.05, 0.05, 0.28] if mix == "benign" else [0.3, 0.3, 0.1, 0.1, 0.2]
+    ks, var = workloads.trace_random(rng, 400_000, 300, p=p)
+    assert_same(*run_both(amc, oracle_mod, ks, var, 300))
+
+
+def test_one_variable_many_tiles(amc, oracle_mod):
+    rng = np.random.default_rng(4)
+    ks, var = workloads.trace_random(rng, 70_001, 1, p=[0.0, 0.5, 0.0, 0.0, 0.5])
+    ks[-5:] = np.array([0, 16, 2, 3, 0], np.uint8)
+    assert_same(*run_both(amc, oracle_mod, ks, var, 1))
+
+
+def test_top_of_id_range(amc, oracle_mod):
+    rng = np.random.default_rng(5)
+    n_vars = (1 << 24) + 3
+    ks, var = workloads.trace_random(rng, 20_000, 4)
+    var = (n_vars - 1 - var).astype(np.int32)
+    assert_same(*run_both(amc, oracle_mod, ks, var, n_vars))
+
+
+def test_initial_statuses(amc, oracle_mod):
+    rng = np.random.default_rng(6)
+    ks, var = workloads.trace_random(rng, 60_000, 64)
+    init = rng.integers(0, 5, 64).astype(np.uint8)
+    assert_same(*run_both(amc, oracle_mod, ks, var, 64, init))
+
+
+def test_empty_trace(amc, oracle_mod):
+    ks = np.zeros(0, np.uint8)
+    var = np.zeros(0, np.int32)
+    assert_same(*run_both(amc, oracle_mod, ks, var, 9))
+
+
+def test_repeatable(amc):
+    ks, var = workloads.trace_zipf(300_000, 1 << 20, seed=9, device="cuda")
+    a = amc.check_trace(ks, var, 1 << 20)
+    s1 = a["step_status"].clone()
+    b = amc.check_trace(ks, var, 1 << 20)
+    assert torch.equal(s1, b["step_status"])
+    assert amc.sync_status() == 0
+
+
+def test_bad_inputs_reported(amc):
+    dev = torch.device("cuda")
+    ks = torch.tensor([0, 1, 2], dtype=torch.uint8, device=dev)
+    var = torch.tensor([0, 5, 1], dtype=torch.int32, device=dev)
+    amc.check_trace(ks, var, 4)
+    assert amc.sync_status() == amc.E_RANGE
+    ks = torch.tensor([0, 0x21, 2], dtype=torch.uint8, device=dev)
+    var = torch.tensor([0, 1, 1], dtype=torch.int32, device=dev)
+    amc.check_trace(ks, var, 4)
+    assert amc.sync_status() == amc.E_INVALID
+    ks = torch.tensor([6, 7], dtype=torch.uint8, device=dev)        # GT needs the guarded call
+    var = torch.tensor([0, 1], dtype=torch.int32, device=dev)
+    amc.check_trace(ks, var, 4)
+    assert amc.sync_status() == amc.E_INVALID
+    assert amc.sync_status() == 0
+
+
+def test_guarded_trace_from_vectorpu(amc, oracle_mod):
+    w = workloads.vectorpu_calls(seed=21, n_arrays=64, space=1 << 14, n_calls=20_000,
+                                 len_log2=(4.0, 10.0), drop_p=0.01)
+    res = oracle_mod.vectorpu(**w)
+    A = len(w["arr_start"])
+    dev = torch.device("cuda")
+    out = amc.check_trace(torch.from_numpy(res["kind_side"]).to(dev), torch.from_numpy(res["var"]).to(dev),
+                          2 * A, guarded=True)
+    assert amc.sync_status() == 0
+    assert np.array_equal(out["step_status"].cpu().numpy(), res["step_status"])
+    assert np.array_equal(out["final_status"].cpu().numpy(), res["final_status"])
+    assert np.array_equal(out["var_first_fault"].cpu().numpy(), res["var_first_fault"])
+    assert int(out["first_fault"].cpu()[0]) == res["first_fault"]
+
+
+def test_zipf_trace_full_size_sampled(amc, oracle_mod):
+    """The 2^30-op, 2^20-var Zipf workload in the launch configuration the
+    benchmark times, checked in full against the oracle."""
+    n_ops, n_vars = 1 << 30, 1 << 20
+    ks, var = workloads.trace_zipf(n_ops, n_vars, seed=1, device="cuda")
+    out = amc.check_trace(ks, var, n_vars)
+    assert amc.sync_status() == 0
+    ks_h, var_h = ks.cpu().numpy(), var.cpu().numpy()
+    del ks, var
+    step = out["step_status"].cpu().numpy()
+    final = out["final_status"].cpu().numpy()
+    vff = out["var_first_fault"].cpu().numpy()
+    ff = int(out["first_fault"].cpu()[0])
+    del out
+    torch.cuda.empty_cache()
+    e_step, e_final, e_vff, e_ff = oracle_mod.check_trace(ks_h, var_h, n_vars)
+    assert np.array_equal(e_final, final)
+    assert np.array_equal(e_vff, vff)
+    assert e_ff == ff
+    assert np.array_equal(e_step, step)
