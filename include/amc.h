@@ -139,6 +139,31 @@ AMC_API int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var
                             int32_t* var_first_fault, int64_t* first_fault,
                             void* workspace, size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of amc_check_trace (the paper has no counterpart).
+ * For callers that cannot allocate device memory themselves: code that runs
+ * inside a host application whose allocator owns all device memory, plug-ins
+ * that are handed only their inputs and outputs, and latency-critical loops
+ * where an allocation call would synchronise the device.  The caller still
+ * passes inputs and outputs exactly as for amc_check_trace; the scratch comes
+ * from one fixed device array inside this library instead of a workspace.
+ *   - Limits: n_ops <= AMC_NOALLOC_MAX_OPS and n_vars <= AMC_NOALLOC_MAX_VARS;
+ *     larger sizes are rejected with AMC_E_RANGE before any GPU work.
+ *   - The array (AMC_NOALLOC_SCRATCH_BYTES) is held by every GPU that loads
+ *     the library until the process exits.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the array: calls whose GPU work overlaps (other streams,
+ *     other host threads) race on it and give unspecified results.  Each call
+ *     re-initialises what must start at zero, so sequential calls are safe.
+ *   - It calls no cudaMalloc / cudaFree and no allocating library routine.
+ * Same outputs and device-side error reporting as amc_check_trace. */
+#define AMC_NOALLOC_MAX_OPS (1 << 22)
+#define AMC_NOALLOC_MAX_VARS (1 << 20)
+#define AMC_NOALLOC_SCRATCH_BYTES (25u << 20)
+AMC_API int amc_check_trace_noalloc(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
+                                    const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                                    int32_t* var_first_fault, int64_t* first_fault, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* (2) VectorPU calls -> core trace -- Fig. sem-AM (translation of access    */
 /*     modes), Section 3.5 (one abstract status per array), Table            */
