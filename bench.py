@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="trace", choices=["trace", "programs", "vectorpu", "serve"])
+    ap.add_argument("--rates", default="1000,10000,100000")
+    ap.add_argument("--serve-requests", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -339,10 +342,211 @@ def ctypes_ptr(ev):
     return ctypes.c_void_p(ev.cuda_event)
 
 
+def timed(fn, steps, stream):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def base_line(args, value, ms, config, **extra):
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": config}
+    line.update(extra)
+    return line
+
+
+def run_programs(args):
+    """Batched persistent launch (graph replay) vs one launch per program."""
+    import numpy as np
+    import torch
+
+    import paper_1910_11110_gb300 as amc
+    import workloads
+    torch.cuda.set_device(0)
+    amc.build()
+    b = workloads.programs()
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    tok, pay, off, nv = t(b["tok"]), t(b["payload"]), t(b["prog_tok_off"]), t(b["prog_nvars"])
+    vo = torch.zeros(nv.numel() + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(nv.to(torch.int64), 0, out=vo[1:])
+    n_tok = tok.numel()
+    P = nv.numel()
+    out = dict(step_mask=torch.empty(n_tok, dtype=torch.uint8, device=dev),
+               final_mask=torch.empty(int(vo[-1]), dtype=torch.uint8, device=dev),
+               prog_first_fault=torch.empty(P, dtype=torch.int64, device=dev))
+    stream = torch.cuda.Stream()
+    ws = torch.empty(amc.lib().amc_check_batch_workspace(n_tok, P, int(vo[-1])) + 256, dtype=torch.uint8, device=dev)
+    ws = ws[(-ws.data_ptr()) % 256:]
+    with torch.cuda.stream(stream):
+        batched = lambda: amc.check_batch(tok, pay, off, nv, vo, graph_capture=True, out=out, workspace=ws,
+                                          stream=stream)
+        for _ in range(max(3, args.warmup)):
+            batched()
+        assert amc.sync_status(stream) == 0
+        ms_b = timed(batched, args.steps, stream)
+        # plain: one launch per program through the same entry point (no graph)
+        offs = b["prog_tok_off"]
+        L = amc.lib()
+        import ctypes
+        sp = ctypes.c_void_p(stream.cuda_stream)
+        P_ = lambda x: ctypes.c_void_p(x)
+
+        def plain():
+            for i in range(P):
+                t0 = int(offs[i])
+                L.amc_check_batch(P_(tok.data_ptr() + t0), P_(pay.data_ptr() + 4 * t0), P_(off.data_ptr() + 8 * i),
+                                  P_(nv.data_ptr() + 4 * i), P_(vo.data_ptr() + 8 * i), 1, int(offs[i + 1] - t0),
+                                  P_(out["step_mask"].data_ptr()), P_(out["final_mask"].data_ptr()),
+                                  P_(out["prog_first_fault"].data_ptr() + 8 * i), 0, P_(ws.data_ptr()), ws.numel(),
+                                  sp)
+        plain()
+        assert amc.sync_status(stream) == 0
+        ms_p = timed(plain, 1, stream)
+    leaf = int(b["n_leaf"].sum())
+    line = base_line(args, n_tok / (ms_b * 1e-3), ms_b,
+                     {"workload": "programs", "n_progs": P, "tokens": n_tok, "leaf_ops": leaf, "seed": 3,
+                      "mode": "batched persistent launch, CUDA graph replay, longest-first queue"},
+                     plain={"value": n_tok / (ms_p * 1e-3), "ms_per_step": ms_p,
+                            "mode": "one launch per program, same kernel"},
+                     batched_over_plain=ms_p / ms_b, gpu_launches=args.steps * 4)
+    print(json.dumps(line), flush=True)
+
+
+def run_vectorpu(args):
+    """Translation + guarded check of the 2^24-call VectorPU workload."""
+    import numpy as np
+    import torch
+
+    import paper_1910_11110_gb300 as amc
+    import workloads
+    torch.cuda.set_device(0)
+    amc.build()
+    w = workloads.vectorpu_calls(seed=2)
+    dev = torch.device("cuda")
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in w.items()}
+    A = d["arr_start"].numel()
+    stream = torch.cuda.current_stream()
+    tr = amc.translate_vectorpu(d["arr_start"], d["arr_len"], d["call_side"], d["call_off"], d["opnd_array"],
+                                d["opnd_mode"])
+    n = tr["n"]
+    cap = n
+    res = {}
+
+    def step():
+        r = amc.translate_vectorpu(d["arr_start"], d["arr_len"], d["call_side"], d["call_off"], d["opnd_array"],
+                                   d["opnd_mode"], out_cap=cap)
+        res["o"] = amc.check_trace(r["kind_side"], r["var"], 2 * A, guarded=True)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    assert amc.sync_status() == 0
+    ms = timed(step, args.steps, stream)
+    n_calls = d["call_side"].numel()
+    line = base_line(args, n / (ms * 1e-3), ms,
+                     {"workload": "vectorpu_calls", "n_arrays": A, "n_calls": n_calls, "statements": n, "seed": 2},
+                     calls_per_s=n_calls / (ms * 1e-3), gpu_launches=args.steps * 12)
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Open-loop Poisson arrivals into the continuous-batching server."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_1910_11110_gb300 as amc
+    import workloads
+    torch.cuda.set_device(0)
+    amc.build()
+    rng = np.random.default_rng(4)
+    pool_n = 1 << 25
+    pool_ks = ((rng.choice(5, size=pool_n, p=workloads.KIND_MIX)) | (rng.integers(0, 2, pool_n) << 4)).astype(np.uint8)
+    pool_var = rng.integers(0, 1 << 30, pool_n).astype(np.int64)
+    results = {}
+    for rate in [float(x) for x in args.rates.split(",")]:
+        n_req = args.serve_requests
+        arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        # sessions of 1..64 requests over 64..4096 vars, typed by kind
+        sess = []
+        while sum(x[1] for x in sess) < n_req:
+            sess.append((len(sess), int(rng.integers(1, 65)), int(rng.integers(64, 4097)), int(rng.integers(0, 2))))
+        order = np.repeat(np.arange(len(sess)), [x[1] for x in sess])[:n_req]
+        rng.shuffle(order)
+        reqs = []
+        for k, si in enumerate(order):
+            sid, _, nv, kind = sess[si]
+            if kind == 0:
+                n = int(2 ** rng.uniform(10, 24))
+                a = int(rng.integers(0, pool_n - n))
+                reqs.append((sid, kind, nv, ("trace", a, n)))
+            else:
+                reqs.append((sid, kind, nv, ("prog", k)))
+        with amc.Server(mem_budget_bytes=32 << 30, max_slots=32) as srv:
+            tickets = {}
+            lat = []
+            ops = [0]
+            done_flag = [False]
+
+            def poller():
+                while not done_flag[0] or tickets:
+                    for t in list(tickets):
+                        r = srv.poll(t)
+                        if r is not None:
+                            lat.append(r["t_done"] - r["t_submit"])
+                            ops[0] += len(r["status"])
+                            tickets.pop(t)
+                    time.sleep(2e-5)
+
+            th = threading.Thread(target=poller)
+            th.start()
+            t0 = time.perf_counter()
+            for (sid, kind, nv, spec), at in zip(reqs, arr):
+                while time.perf_counter() - t0 < at:
+                    pass
+                if spec[0] == "trace":
+                    _, a, n = spec
+                    ks = pool_ks[a:a + n]
+                    var = (pool_var[a:a + n] % nv).astype(np.int32)
+                else:
+                    b = workloads.programs(1, seed=44, first=spec[1], vars_lo=nv, vars_hi=nv)
+                    ks, var = b["tok"], b["payload"]
+                while (t := srv.submit(sid, kind, nv, ks, var)) is None:
+                    time.sleep(1e-4)
+                tickets[t] = 1
+            done_flag[0] = True
+            th.join()
+            wall = time.perf_counter() - t0
+        lat = np.array(lat) * 1e3
+        results[str(int(rate))] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                   "ops_per_s": ops[0] / wall, "requests": n_req, "wall_s": wall}
+    first = results[list(results)[0]]
+    line = base_line(args, first["ops_per_s"], None,
+                     {"workload": "serve", "rates_req_per_s": args.rates, "requests_per_rate": args.serve_requests,
+                      "slots": 32, "budget_gb": 32, "seed": 4},
+                     serve=results)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "programs":
+        run_programs(args)
+    elif args.workload == "vectorpu":
+        run_vectorpu(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

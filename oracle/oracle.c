@@ -240,10 +240,10 @@ static int eval_seq(prog_ctx* c, int64_t lo, int64_t hi, uint8_t* mask)
         } else if (k == T_IF) {
             int64_t lt = c->payload[i];
             int64_t e = i + 1 + lt;                       /* ELSE token */
-            if (lt < 0 || e >= hi || (c->tok[e] & 15) != T_ELSE || side) return -1;
+            if (lt < 0 || e >= hi || c->tok[e] != T_ELSE || side) return -1;
             int64_t le = c->payload[e];
             int64_t end = e + 1 + le;                     /* END token */
-            if (le < 0 || end >= hi || (c->tok[end] & 15) != T_END) return -1;
+            if (le < 0 || end >= hi || c->tok[end] != T_END) return -1;
             /* IF-True / IF-False: both branches start from the same store */
             uint8_t* m_then = copy_masks(c, mask);
             uint8_t* m_else = copy_masks(c, mask);
@@ -260,7 +260,7 @@ static int eval_seq(prog_ctx* c, int64_t lo, int64_t hi, uint8_t* mask)
         } else if (k == T_WHILE) {
             int64_t lb = c->payload[i];
             int64_t end = i + 1 + lb;
-            if (lb < 0 || end >= hi || (c->tok[end] & 15) != T_END || side) return -1;
+            if (lb < 0 || end >= hi || c->tok[end] != T_END || side) return -1;
             /* While-True / While-False: the set of stores at the loop head is the
              * least X with X = entry U body(X); the body's step sets are those of
              * the pass that starts from that fixpoint. */

@@ -196,3 +196,122 @@ def translate_vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd
             raise AmcError(code, "amc_translate_vectorpu")
         out_cap = n
     raise AmcError(E_RANGE, "amc_translate_vectorpu")
+
+
+def check_batch(tok, payload, prog_tok_off, prog_nvars, prog_var_off=None, *, graph_capture=False, out=None,
+                workspace=None, stream=None):
+    """Relation-mode check of a batch of programs (amc_check_batch).
+
+    tok uint8 [T], payload int32 [T], prog_tok_off int64 [P+1], prog_nvars
+    int32 [P], prog_var_off int64 [P+1] (computed from prog_nvars if None), all
+    CUDA tensors.  Returns dict(step_mask, final_mask, prog_first_fault)."""
+    _dev(tok, torch.uint8, "tok")
+    _dev(payload, torch.int32, "payload")
+    _dev(prog_tok_off, torch.int64, "prog_tok_off")
+    _dev(prog_nvars, torch.int32, "prog_nvars")
+    dev = tok.device
+    P = prog_nvars.numel()
+    if prog_var_off is None:
+        prog_var_off = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(prog_nvars.to(torch.int64), 0, out=prog_var_off[1:])
+    _dev(prog_var_off, torch.int64, "prog_var_off")
+    n_tok = tok.numel()
+    total_vars = int(prog_var_off[-1].item()) if P > 0 else 0
+    if out is None:
+        out = dict(step_mask=torch.empty(n_tok, dtype=torch.uint8, device=dev),
+                   final_mask=torch.empty(total_vars, dtype=torch.uint8, device=dev),
+                   prog_first_fault=torch.empty(P, dtype=torch.int64, device=dev))
+    L = lib()
+    nbytes = L.amc_check_batch_workspace(n_tok, P, total_vars)
+    ws = workspace if workspace is not None else _ws.get(nbytes, dev)
+    rc = L.amc_check_batch(_p(tok), _p(payload), _p(prog_tok_off), _p(prog_nvars), _p(prog_var_off), P, n_tok,
+                           _p(out["step_mask"]), _p(out["final_mask"]), _p(out["prog_first_fault"]),
+                           int(bool(graph_capture)), _p(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_check_batch")
+    return out
+
+
+# --------------------------------------------------------------------------
+# Serving
+# --------------------------------------------------------------------------
+REQ_TRACE, REQ_PROGRAM = 0, 1
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_vars", ctypes.c_int32), ("n_items", ctypes.c_int64),
+                ("kind_side", ctypes.c_void_p), ("var", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("error", ctypes.c_int), ("first_fault", ctypes.c_int64), ("n_items", ctypes.c_int64),
+                ("status", ctypes.c_void_p), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class Server:
+    """Continuous-batching check server (amc_server_create / amc_serve_*).
+
+    Requests are numpy arrays on the host: op bytes (uint8) and var ids
+    (int32) for traces; token bytes and payloads for programs.  A session's
+    variable statuses stay on the device between its requests."""
+
+    def __init__(self, mem_budget_bytes: int = 32 << 30, max_slots: int = 16):
+        import numpy as np  # noqa: F401
+        L = lib()
+        P = ctypes.c_void_p
+        L.amc_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(P)]
+        L.amc_serve_submit.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]
+        L.amc_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_Result)]
+        L.amc_serve_release.argtypes = [P, ctypes.c_uint64]
+        L.amc_session_export.argtypes = [P, ctypes.c_uint64, P, ctypes.c_int32]
+        L.amc_server_destroy.argtypes = [P]
+        self._L = L
+        self._h = P()
+        _check(L.amc_server_create(mem_budget_bytes, max_slots, ctypes.byref(self._h)), "amc_server_create")
+
+    def submit(self, session: int, kind: int, n_vars: int, kind_side, var):
+        """Queue a request; returns its ticket, or None when the server pushes back."""
+        import numpy as np
+        ks = np.ascontiguousarray(kind_side, dtype=np.uint8)
+        v = np.ascontiguousarray(var, dtype=np.int32)
+        req = _Request(kind, n_vars, ks.shape[0], ks.ctypes.data, v.ctypes.data)
+        t = ctypes.c_uint64()
+        rc = self._L.amc_serve_submit(self._h, session, ctypes.byref(req), ctypes.byref(t))
+        if rc == E_AGAIN:
+            return None
+        _check(rc, "amc_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int, release: bool = True):
+        """None while running; else dict(status, first_fault, error, t_submit, t_admit, t_done)."""
+        import numpy as np
+        done = ctypes.c_int()
+        res = _Result()
+        _check(self._L.amc_serve_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(res)), "amc_serve_poll")
+        if not done.value:
+            return None
+        n = res.n_items
+        status = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(res.status)).copy() if n else \
+            np.zeros(0, np.uint8)
+        out = dict(status=status, first_fault=res.first_fault, error=res.error, t_submit=res.t_submit,
+                   t_admit=res.t_admit, t_done=res.t_done)
+        if release:
+            _check(self._L.amc_serve_release(self._h, ticket), "amc_serve_release")
+        return out
+
+    def export(self, session: int, n_vars: int):
+        import numpy as np
+        out = np.empty(n_vars, np.uint8)
+        _check(self._L.amc_session_export(self._h, session, out.ctypes.data, n_vars), "amc_session_export")
+        return out
+
+    def close(self):
+        if self._h:
+            _check(self._L.amc_server_destroy(self._h), "amc_server_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -35,6 +35,15 @@ struct Tables {
 // Host: the tables (built once per process).
 const Tables& host_tables();
 
+// Status-set images for relation mode.  Op index o = kind << 1 | side for
+// kinds 0..5; img[o * 32 + m] = image of the set m; bit m of flt[o] is set when
+// the set m holds a non-stuck status that op o makes stuck.
+struct SetTables {
+    uint8_t img[16 * 32];
+    uint32_t flt[16];
+};
+const SetTables& host_set_tables();
+
 // Host: address of the device-side error word of the current device (first
 // error wins), or nullptr if it could not be resolved.
 int* device_error_word();

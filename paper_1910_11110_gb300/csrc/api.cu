@@ -1,9 +1,14 @@
 // api.cu -- C ABI entry points: argument checks, workspace layout, launches.
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "amc_internal.cuh"
 #include "scan_trace.cuh"
 #include "translate.cuh"
+#include "batch.cuh"
 
 using namespace amc;
 
@@ -25,6 +30,17 @@ int check_trace_args(const uint8_t* kind_side, const int32_t* var, int64_t n_ops
     if (n_vars > 0 && (!final_status || !var_first_fault)) return AMC_E_INVALID;
     if (!first_fault) return AMC_E_INVALID;
     return AMC_OK;
+}
+
+// CUDA graphs of amc_check_batch, one per (device, stream, arguments)
+struct GraphCache {
+    std::mutex mu;
+    std::map<std::vector<uintptr_t>, cudaGraphExec_t> execs;
+};
+GraphCache& graph_cache()
+{
+    static GraphCache* c = new GraphCache();      // never destroyed: graphs live until exit
+    return *c;
 }
 
 }  // namespace
@@ -199,6 +215,74 @@ int amc_translate_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int
     T.workspace = workspace;
     T.profile = 3;
     return launch_translate(T, static_cast<cudaStream_t>(stream));
+}
+
+size_t amc_check_batch_workspace(int64_t n_tokens, int64_t n_progs, int64_t total_vars)
+{
+    if (n_tokens < 0 || n_progs < 0 || total_vars < 0) return 0;
+    return batch_workspace_bytes(n_tokens, n_progs);
+}
+
+int amc_check_batch(const uint8_t* tok_kind_side, const int32_t* tok_payload, const int64_t* prog_tok_off,
+                    const int32_t* prog_nvars, const int64_t* prog_var_off, int64_t n_progs, int64_t n_tokens,
+                    uint8_t* step_mask, uint8_t* final_mask, int64_t* prog_first_fault, int graph_capture,
+                    void* workspace, size_t ws_bytes, void* stream)
+{
+    if (n_progs < 0 || n_tokens < 0 || n_progs > INT32_MAX) return AMC_E_INVALID;
+    if (n_progs > 0 && (!prog_tok_off || !prog_nvars || !prog_var_off || !prog_first_fault || !final_mask))
+        return AMC_E_INVALID;
+    if (n_tokens > 0 && (!tok_kind_side || !tok_payload || !step_mask)) return AMC_E_INVALID;
+    if (!workspace || !aligned256(workspace) || ws_bytes < batch_workspace_bytes(n_tokens, n_progs))
+        return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    BatchLaunch B;
+    B.tok = tok_kind_side;
+    B.payload = tok_payload;
+    B.prog_tok_off = prog_tok_off;
+    B.prog_nvars = prog_nvars;
+    B.prog_var_off = prog_var_off;
+    B.n_progs = n_progs;
+    B.n_tokens = n_tokens;
+    B.step_mask = step_mask;
+    B.final_mask = final_mask;
+    B.prog_first_fault = prog_first_fault;
+    B.err = err;
+    B.workspace = workspace;
+    B.profile = 3;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!graph_capture || s == nullptr) return launch_batch(B, s);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<uintptr_t> key = {(uintptr_t)dev,          (uintptr_t)s,           (uintptr_t)tok_kind_side,
+                                  (uintptr_t)tok_payload,  (uintptr_t)prog_tok_off, (uintptr_t)prog_nvars,
+                                  (uintptr_t)prog_var_off, (uintptr_t)n_progs,      (uintptr_t)n_tokens,
+                                  (uintptr_t)step_mask,    (uintptr_t)final_mask,   (uintptr_t)prog_first_fault,
+                                  (uintptr_t)workspace};
+    GraphCache& gc = graph_cache();
+    std::lock_guard<std::mutex> lock(gc.mu);
+    auto it = gc.execs.find(key);
+    if (it == gc.execs.end()) {
+        B.profile = 0;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return AMC_E_CUDA;
+        const int rc = launch_batch(B, s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess) return AMC_E_CUDA;
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return AMC_E_CUDA;
+        it = gc.execs.emplace(key, ex).first;
+    }
+    profile_begin(s);
+    const cudaError_t le = cudaGraphLaunch(it->second, s);
+    profile_end(s);
+    return le == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 
 }  // extern "C"

@@ -117,6 +117,35 @@ const Tables& host_tables()
 }
 
 namespace {
+SetTables build_sets()
+{
+    SetTables t;
+    memset(&t, 0, sizeof(t));
+    for (int kind = 0; kind <= AMC_K_PW; ++kind)
+        for (int side = 0; side < 2; ++side) {
+            const int o = kind << 1 | side;
+            for (int m = 0; m < 32; ++m) {
+                uint32_t img = 0;
+                for (int s = 0; s < 5; ++s)
+                    if (m & (1 << s)) {
+                        const int r = step(kind, side, s);
+                        img |= 1u << r;
+                        if (s != ST_F && r == ST_F) t.flt[o] |= 1u << m;
+                    }
+                t.img[o * 32 + m] = (uint8_t)img;
+            }
+        }
+    return t;
+}
+}  // namespace
+
+const SetTables& host_set_tables()
+{
+    static SetTables t = build_sets();
+    return t;
+}
+
+namespace {
 thread_local cudaEvent_t t_prof_start = nullptr;
 thread_local cudaEvent_t t_prof_stop = nullptr;
 }  // namespace

@@ -46,6 +46,8 @@ struct __align__(16) ScanSmem {
     uint16_t valB[T];
     uint8_t out[T];
     uint8_t runEntry[T];
+    uint8_t runAgg[T];
+    uint32_t pend[T];                // pending runs: run id | sorted slot << 16
     uint16_t hist[256 * (NT / 32)];
     uint8_t comp[MAX_ELEMS * MAX_ELEMS];
     uint8_t app[MAX_ELEMS * 8];
@@ -56,7 +58,8 @@ struct __align__(16) ScanSmem {
     uint64_t mbar[2];
     int tileId[2];
     int viaBulk[2];
-    int nRuns;
+    int nPend;
+    uint32_t frontVal;
 };
 
 __device__ __forceinline__ uint32_t comp_of(const uint8_t* comp, uint32_t a, uint32_t b)
@@ -224,33 +227,60 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
     const uint32_t* K = kin;     // sorted keys
     const uint16_t* P = vin;     // original positions
 
-    // ---- 4. segmented scan over runs (blocked: thread owns E sorted slots) --
-    uint8_t pm[E], xm[E];
-    uint32_t headMask = 0;
-    int nHeads = 0;
-    uint32_t acc = ID;
+    // ---- 4a. run boundaries; the stuck-shortcut loads are issued here so
+    // that the segmented scan below hides their latency --------------------
+    const int j0 = tid * E;
+    uint32_t keyk[E];
+    uint32_t headMask = 0, lastMask = 0;
     {
-        const int j0 = tid * E;
         uint32_t prevKey = (j0 > 0 && j0 - 1 < n) ? K[j0 - 1] : 0xFFFFFFFFu;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             const int j = j0 + k;
-            pm[k] = xm[k] = (uint8_t)ID;
+            keyk[k] = 0;
             if (j < n) {
-                const uint32_t key = K[j];
-                const uint32_t m = kb[P[j]];
-                if (key != prevKey) {
-                    headMask |= 1u << k;
-                    ++nHeads;
-                    xm[k] = (uint8_t)ID;
-                    acc = m;
-                } else {
-                    xm[k] = (uint8_t)acc;
-                    acc = comp_of(S.comp, acc, m);
-                }
-                pm[k] = (uint8_t)acc;
-                prevKey = key;
+                keyk[k] = K[j];
+                if (keyk[k] != prevKey) headMask |= 1u << k;
+                prevKey = keyk[k];
             }
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            if (j < n) {
+                const uint32_t nk = (j + 1 < n) ? (k + 1 < E ? keyk[(k + 1) % E] : K[j + 1]) : 0xFFFFFFFFu;
+                if (nk != keyk[k]) lastMask |= 1u << k;
+            }
+        }
+    }
+    uint32_t ffv[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        ffv[k] = 0xFFFFFFFFu;
+        if (lastMask & (1u << k)) ffv[k] = __ldcg(reinterpret_cast<const unsigned int*>(p.vff) + keyk[k]);
+    }
+
+    // ---- 4b. segmented scan over runs (blocked: thread owns E sorted slots) --
+    // per-slot prefix (pm) and exclusive prefix (xm), four bytes per word
+    uint32_t pmw[E / 4], xmw[E / 4];
+#define getb(w, k) (((w)[(k) >> 2] >> (8 * ((k) & 3))) & 0xFFu)
+#define setb(w, k, v) ((w)[(k) >> 2] = ((w)[(k) >> 2] & ~(0xFFu << (8 * ((k) & 3)))) | ((uint32_t)(v) << (8 * ((k) & 3))))
+#pragma unroll
+    for (int i = 0; i < E / 4; ++i) pmw[i] = xmw[i] = 0;    // identity is element 0
+    const int nHeads = __popc(headMask);
+    uint32_t acc = ID;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int j = j0 + k;
+        if (j < n) {
+            const uint32_t m = kb[P[j]];
+            if (headMask & (1u << k)) {
+                acc = m;
+            } else {
+                setb(xmw, k, acc);
+                acc = comp_of(S.comp, acc, m);
+            }
+            setb(pmw, k, acc);
         }
     }
     // segmented exclusive scan of (has head, value) across threads
@@ -266,7 +296,6 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
                 f |= fu;
             }
         }
-        // exclusive within warp
         uint32_t fe = __shfl_up_sync(0xffffffffu, f, 1);
         uint32_t ve = __shfl_up_sync(0xffffffffu, v, 1);
         if (lane == 0) { fe = 0; ve = ID; }
@@ -287,141 +316,183 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
             uint32_t xv = __shfl_up_sync(0xffffffffu, wv, 1);
             if (lane == 0) { xf = 0; xv = ID; }
             if (lane < NW) { S.segF[lane] = (uint8_t)xf; S.segV[lane] = (uint8_t)xv; }
+            if (lane == 0) S.nPend = 0;
         }
         __syncthreads();
-        const uint32_t wpv = S.segV[warp];
-        carry = fe ? ve : comp_of(S.comp, wpv, ve);
+        carry = fe ? ve : comp_of(S.comp, S.segV[warp], ve);
     }
     // elements before the thread's first head continue a run from earlier threads
 #pragma unroll
     for (int k = 0; k < E; ++k) {
         if ((headMask & ((2u << k) - 1)) == 0) {
-            pm[k] = (uint8_t)comp_of(S.comp, carry, pm[k]);
-            xm[k] = (uint8_t)comp_of(S.comp, carry, xm[k]);
+            setb(pmw, k, comp_of(S.comp, carry, getb(pmw, k)));
+            setb(xmw, k, comp_of(S.comp, carry, getb(xmw, k)));
         }
     }
-    int nRuns;
-    const int runBase = block_excl_sum<NT>(nHeads, S.scanTmp, &nRuns);
+    const int runBase = block_excl_sum<NT>(nHeads, S.scanTmp, nullptr);
+    auto run_id = [&](int k) { return runBase - 1 + __popc(headMask & ((2u << k) - 1)); };
 
-    // ---- 5a. run entry: stuck shortcut or registration ---------------------
+    // ---- 5a. run entry: stuck shortcut, or a node in the variable's list ----
     const uint32_t nodeBase = (uint32_t)t * (uint32_t)T;
-    {
-        const int j0 = tid * E;
-        int r = runBase - 1;
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int j = j0 + k;
-            if (headMask & (1u << k)) ++r;
-            if (j < n && (j == n - 1 || K[j + 1] != K[j])) {
-                const uint32_t v = K[j];
-                const uint32_t ffv = ld_relaxed(reinterpret_cast<const uint32_t*>(p.vff) + v);
-                if (ffv < (uint32_t)base) {
-                    S.runEntry[r] = ST_F;
-                } else {
-                    S.runEntry[r] = RUN_PENDING;
-                    p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | pm[k]);
-                }
+    for (int k = 0; k < E; ++k) {
+        if (lastMask & (1u << k)) {
+            const int r = run_id(k);
+            if (ffv[k] < (uint32_t)base) {
+                S.runEntry[r] = ST_F;
+            } else {
+                const uint32_t agg = getb(pmw, k);
+                S.runEntry[r] = RUN_PENDING;
+                S.runAgg[r] = (uint8_t)agg;
+                S.pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
+                p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | agg);
             }
         }
     }
-    __threadfence();
-    {
-        const int j0 = tid * E;
-        int r = runBase - 1;
-#pragma unroll 1
-        for (int k = 0; k < E; ++k) {
-            const int j = j0 + k;
-            if (headMask & (1u << k)) ++r;
-            if (j < n && (j == n - 1 || K[j + 1] != K[j]) && S.runEntry[r] == RUN_PENDING) {
-                const uint32_t v = K[j];
-                const uint32_t node = nodeBase + (uint32_t)r;
-                // insert into v's list, kept sorted by decreasing tile
-                uint32_t* link = p.head + v;
-                uint32_t it = 0;
-                for (;;) {
-                    const uint32_t c = ld_acquire(link);
-                    if (c == NIL || c / T < (uint32_t)t) {
-                        p.node_next[node] = c;
-                        __threadfence();
-                        if (atomicCAS(link, c, node) == c) break;
-                    } else {
-                        link = p.node_next + c;
-                    }
-                    if (++it > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
+    __syncthreads();
+    const int nPend = S.nPend;
+    constexpr int PW = 4;                 // pending runs a thread handles in step
+    for (int lo = 0; lo < nPend; lo += NT * PW) {
+        // insert each node into its variable's list (sorted by decreasing
+        // tile): one attempt for PW runs at once, then retries one by one
+        uint32_t c[PW], old[PW], node[PW], var[PW];
+        uint32_t mine = 0, simple = 0;
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            const int i = lo + u * NT + tid;
+            c[u] = NIL;
+            node[u] = var[u] = 0;
+            if (i < nPend) {
+                const uint32_t e = S.pend[i];
+                mine |= 1u << u;
+                node[u] = nodeBase + (e & 0xFFFFu);
+                var[u] = K[e >> 16];
+                c[u] = __ldcg(p.head + var[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PW; ++u)
+            if ((mine & (1u << u)) && (c[u] == NIL || c[u] / T < (uint32_t)t)) {
+                p.node_next[node[u]] = c[u];
+                simple |= 1u << u;
+            }
+        __threadfence();
+#pragma unroll
+        for (int u = 0; u < PW; ++u) old[u] = (simple & (1u << u)) ? atomicCAS(p.head + var[u], c[u], node[u]) : c[u];
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            if (!(mine & (1u << u)) || ((simple & (1u << u)) && old[u] == c[u])) continue;
+            uint32_t* link = p.head + var[u];
+            for (uint32_t it = 0;; ++it) {
+                const uint32_t cc = ld_acquire(link);
+                if (cc == NIL || cc / T < (uint32_t)t) {
+                    p.node_next[node[u]] = cc;
+                    __threadfence();
+                    if (atomicCAS(link, cc, node[u]) == cc) break;
+                } else {
+                    link = p.node_next + cc;
                 }
+                if (it > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
             }
         }
     }
     __syncthreads();
 
-    // ---- 5b. registration frontier: all tiles < t have registered ----------
+    // ---- 5b. registration frontier ------------------------------------------
+    // regflag[t] = 1 once tile t's nodes are all in their lists; *front = F
+    // means every tile < F has registered.  Only tiles that look back (and all
+    // tiles of the guard-resolving pass, whose first input status is read by
+    // the previous tile) wait for the frontier to reach them.
     if (tid == 0) {
         __threadfence();
         st_release(p.regflag + t, 1);
-        bool done = (t == 0);
-        int tp = t - 1;
-        uint32_t it = 0;
-        while (!done) {
-            const uint32_t f = ld_acquire(p.regflag + tp);
-            if (f == 2) done = true;
-            else if (f == 1) { if (tp == 0) done = true; else --tp; }
-            else if (++it > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); done = true; }
-            else __nanosleep(64);
-        }
-        st_release(p.regflag + t, 2);
     }
-    __syncthreads();
-
-    // ---- 5c. look-back along each registered run's list ---------------------
-    {
-        const int j0 = tid * E;
-        int r = runBase - 1;
-#pragma unroll 1
-        for (int k = 0; k < E; ++k) {
-            const int j = j0 + k;
-            if (headMask & (1u << k)) ++r;
-            if (j < n && (j == n - 1 || K[j + 1] != K[j]) && S.runEntry[r] == RUN_PENDING) {
-                const uint32_t v = K[j];
-                const uint32_t node = nodeBase + (uint32_t)r;
-                uint32_t q = ld_acquire(p.node_next + node);
-                uint32_t a = ID, st;
-                for (;;) {
-                    if (q == NIL) {
-                        st = p.init ? p.init[v] : (uint32_t)AMC_ST_VI;
-                        break;
-                    }
-                    const uint32_t s = ld_acquire_u8(p.node_status + q);
-                    if (s & NODE_INCL) { st = s & 7u; break; }
-                    a = comp_of(S.comp, s & 31u, a);          // earlier tile first
-                    q = ld_acquire(p.node_next + q);
-                }
-                const uint32_t entry = S.app[a * 8 + st];
-                S.runEntry[r] = (uint8_t)entry;
-                st_relaxed_u8(p.node_status + node, NODE_INCL | S.app[pm[k] * 8 + entry]);
+    if (nPend > 0 || p.guard) {
+        for (uint32_t it = 0;; ++it) {
+            if (tid == 0) S.frontVal = ld_acquire(p.front);
+            __syncthreads();
+            const uint32_t f0 = S.frontVal;
+            if (f0 >= (uint32_t)t) break;
+            bool all = true;          // check every tile in [front, t) at once
+            for (uint32_t q = f0 + tid; q < (uint32_t)t; q += NT) all &= ld_acquire(p.regflag + q) != 0;
+            if (__syncthreads_and(all)) {
+                if (tid == 0) { __threadfence(); atomicMax(p.front, (uint32_t)t); }
+                break;
             }
+            if (it > SPIN_LIMIT) { if (tid == 0) raise_error(p.err, AMC_E_TIMEOUT); break; }
+            __nanosleep(128);
+        }
+        __threadfence();
+    }
+
+    // ---- 5c. look-back along the lists, PW runs per thread in step -----------
+    for (int lo = 0; lo < nPend; lo += NT * PW) {
+        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW];
+        uint32_t active = 0;
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            const int i = lo + u * NT + tid;
+            a[u] = ID;
+            st[u] = 0;
+            q[u] = NIL;
+            node[u] = var[u] = rr[u] = 0;
+            if (i < nPend) {
+                const uint32_t e = S.pend[i];
+                active |= 1u << u;
+                rr[u] = e & 0xFFFFu;
+                node[u] = nodeBase + rr[u];
+                var[u] = K[e >> 16];
+                q[u] = ld_acquire(p.node_next + node[u]);
+            }
+        }
+        const uint32_t mine = active;
+        for (uint32_t hop = 0; active; ++hop) {
+            uint32_t sv[PW];
+#pragma unroll
+            for (int u = 0; u < PW; ++u)
+                sv[u] = ((active & (1u << u)) && q[u] != NIL) ? ld_acquire_u8(p.node_status + q[u]) : 0u;
+#pragma unroll
+            for (int u = 0; u < PW; ++u) {
+                if (!(active & (1u << u))) continue;
+                if (q[u] == NIL) {
+                    st[u] = p.init ? p.init[var[u]] : (uint32_t)AMC_ST_VI;
+                    active &= ~(1u << u);
+                } else if (sv[u] & NODE_INCL) {
+                    st[u] = sv[u] & 7u;
+                    active &= ~(1u << u);
+                } else {
+                    a[u] = comp_of(S.comp, sv[u] & 31u, a[u]);     // earlier tile first
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PW; ++u)
+                if (active & (1u << u)) q[u] = ld_acquire(p.node_next + q[u]);
+            if (hop > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
+        }
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            if (!(mine & (1u << u))) continue;
+            const uint32_t entry = S.app[a[u] * 8 + st[u]];
+            S.runEntry[rr[u]] = (uint8_t)entry;
+            st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
         }
     }
     __syncthreads();
 
     // ---- 6. outputs in original order; first faults --------------------------
-    {
-        const int j0 = tid * E;
-        int r = runBase - 1;
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int j = j0 + k;
-            if (headMask & (1u << k)) ++r;
-            if (j < n) {
-                const uint32_t e = S.runEntry[r];
-                const uint32_t pre = S.app[xm[k] * 8 + e];
-                const uint32_t post = S.app[pm[k] * 8 + e];
-                const int pos = P[j];
-                S.out[pos] = (uint8_t)(p.pre_mode ? pre : post);
-                if (post == ST_F && pre != ST_F) {
-                    const uint32_t gi = (uint32_t)(base + pos);
-                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + K[j], gi);
-                    atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
-                }
+    for (int k = 0; k < E; ++k) {
+        const int j = j0 + k;
+        if (j < n) {
+            const uint32_t e = S.runEntry[run_id(k)];
+            const uint32_t pre = S.app[getb(xmw, k) * 8 + e];
+            const uint32_t post = S.app[getb(pmw, k) * 8 + e];
+            const int pos = P[j];
+            S.out[pos] = (uint8_t)(p.pre_mode ? pre : post);
+            if (post == ST_F && pre != ST_F) {
+                const uint32_t gi = (uint32_t)(base + pos);
+                atomicMin(reinterpret_cast<uint32_t*>(p.vff) + K[j], gi);
+                atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
             }
         }
     }
@@ -433,6 +504,8 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
     } else {
         for (int i = tid; i < n; i += NT) p.step[base + i] = S.out[i];
     }
+#undef getb
+#undef setb
 }
 
 template <int T, int NT>
@@ -538,6 +611,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.regflag = reinterpret_cast<uint32_t*>(w);
     w += align_up(4 * (size_t)p.n_tiles, 256);
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
+    p.front = p.tile_counter + 1;
     // key bits: var ids are < n_vars
     int kb = 1;
     while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
@@ -551,7 +625,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
     if (L.n_ops > 0) {
         if (cudaMemsetAsync(p.regflag, 0, 4 * (size_t)p.n_tiles, s) != cudaSuccess) return AMC_E_CUDA;
-        if (cudaMemsetAsync(p.tile_counter, 0, 4, s) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaMemsetAsync(p.tile_counter, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
         const size_t smem = sizeof(ScanSmem<TILE, THREADS>);
         static bool attr_set[64] = {};
         int dev = 0;

@@ -1,0 +1,527 @@
+// serve.cu -- continuous batching of check requests on one GPU.
+//
+// A server owns a device memory pool (the budget), max_slots CUDA streams and
+// a worker thread.  Requests are copied at submission and queued.  The worker
+// admits queued requests in arrival order whenever a slot is free, the pool
+// can hold the request's buffers, and the request's session has nothing in
+// flight (a session's requests see each other's statuses, so they run in
+// submission order; different sessions overlap on the device).  Each admitted
+// request runs on its slot's stream: inputs are staged through pinned memory
+// and copied to the device, the trace kernel (or the relation-mode kernel for
+// a program) runs with the session's status table as initial and final status,
+// the per-op results come back to pinned memory, and an event marks the end.
+// The worker polls those events, hands results to amc_serve_poll, and frees
+// the slot and the request's pool space, which may admit the next requests.
+// Session tables stay on the device between requests (status codes for trace
+// sessions, status masks for program sessions).
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "amc_internal.cuh"
+#include "batch.cuh"
+#include "scan_trace.cuh"
+
+using namespace amc;
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over one device allocation (offsets, 256-byte granules).
+class Pool {
+public:
+    bool init(size_t bytes, bool pinned_host)
+    {
+        bytes = align_up(bytes, 256);
+        host_ = pinned_host;
+        const cudaError_t e = host_ ? cudaHostAlloc(&base_, bytes, cudaHostAllocDefault) : cudaMalloc(&base_, bytes);
+        if (e != cudaSuccess) {
+            base_ = nullptr;
+            return false;
+        }
+        size_ = bytes;
+        free_[0] = bytes;
+        return true;
+    }
+    void release()
+    {
+        if (base_) host_ ? cudaFreeHost(base_) : cudaFree(base_);
+        base_ = nullptr;
+    }
+    // returns offset or SIZE_MAX
+    size_t alloc(size_t n)
+    {
+        n = align_up(n ? n : 256, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                const size_t off = it->first, sz = it->second;
+                free_.erase(it);
+                if (sz > n) free_[off + n] = sz - n;
+                return off;
+            }
+        }
+        return SIZE_MAX;
+    }
+    void free(size_t off, size_t n)
+    {
+        n = align_up(n ? n : 256, 256);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    uint8_t* ptr(size_t off) const { return static_cast<uint8_t*>(base_) + off; }
+    size_t size() const { return size_; }
+
+private:
+    void* base_ = nullptr;
+    size_t size_ = 0;
+    bool host_ = false;
+    std::map<size_t, size_t> free_;
+};
+
+struct Session {
+    int kind = -1;
+    int32_t n_vars = 0;
+    size_t table_off = SIZE_MAX;     // status codes / masks, n_vars bytes (+ first-fault scratch)
+    bool busy = false;
+    cudaEvent_t last = nullptr;
+};
+
+struct Request {
+    uint64_t ticket = 0, session = 0;
+    int kind = 0;
+    int32_t n_vars = 0;
+    int64_t n = 0;
+    size_t host_off = SIZE_MAX;      // pinned: op bytes [n], ids [4n] at 256-aligned offsets, results [n], small
+    size_t host_bytes = 0;
+    int64_t first_fault = -1;
+    int error = AMC_OK;
+    int state = 0;                   // 0 queued, 1 running, 2 done
+    int slot = -1;
+    size_t off = SIZE_MAX, bytes = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    std::shared_ptr<Request> req;
+};
+
+// pinned layout of a request
+struct HostLayout {
+    size_t ks, var, out, small, total;
+};
+HostLayout host_layout(int64_t n)
+{
+    HostLayout L;
+    L.ks = 0;
+    L.var = align_up((size_t)n, 256);
+    L.out = L.var + align_up(4 * (size_t)n, 256);
+    L.small = L.out + align_up((size_t)n, 256);
+    L.total = L.small + 256;
+    return L;
+}
+
+}  // namespace
+
+struct amc_server {
+    std::mutex mu;
+    std::condition_variable cv;
+    Pool pool;                       // device memory: the budget
+    Pool host;                       // pinned staging of inputs and results
+    cudaStream_t ctl = nullptr;
+    std::vector<Slot> slots;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> reqs;
+    std::map<uint64_t, Session> sessions;
+    uint64_t next_ticket = 1;
+    size_t max_queue = 1 << 20;
+    std::atomic<bool> stop{false};
+    std::thread worker;
+    int device = 0;
+    int* err = nullptr;
+};
+
+namespace {
+
+// Host-side validation of a request (so that device errors cannot occur).
+int validate(const amc_request* r)
+{
+    if (!r || r->n_items < 0 || r->n_vars < 1 || (r->n_items > 0 && (!r->kind_side || !r->var))) return AMC_E_INVALID;
+    if (r->kind != AMC_REQ_TRACE && r->kind != AMC_REQ_PROGRAM) return AMC_E_INVALID;
+    if (r->kind == AMC_REQ_TRACE) {
+        if (r->n_items > INT32_MAX) return AMC_E_RANGE;
+        for (int64_t i = 0; i < r->n_items; ++i) {
+            const uint8_t k = r->kind_side[i];
+            if ((k & 0xE0) || (k & 15) > AMC_K_PW) return AMC_E_INVALID;
+            if (r->var[i] < 0 || r->var[i] >= r->n_vars) return AMC_E_RANGE;
+        }
+        return AMC_OK;
+    }
+    // programs: op tokens in range, constructs balanced and nested within AMC_MAX_DEPTH
+    std::vector<int64_t> ends;
+    std::vector<int> kinds;
+    for (int64_t i = 0; i < r->n_items; ++i) {
+        const uint8_t k = r->kind_side[i];
+        if (k & 0xE0) return AMC_E_INVALID;
+        const int kk = k & 15;
+        if (kk <= AMC_K_PW) {
+            if (r->var[i] < 0 || r->var[i] >= r->n_vars) return AMC_E_RANGE;
+            continue;
+        }
+        if (k & 0x10) return AMC_E_INVALID;
+        if (kk == AMC_T_IF || kk == AMC_T_WHILE) {
+            const int64_t len = r->var[i];
+            if (len < 0 || (int)ends.size() >= AMC_MAX_DEPTH) return AMC_E_INVALID;
+            int64_t end;
+            if (kk == AMC_T_IF) {
+                const int64_t e = i + 1 + len;
+                if (e >= r->n_items || r->kind_side[e] != AMC_T_ELSE || r->var[e] < 0) return AMC_E_INVALID;
+                end = e + 1 + r->var[e];
+            } else {
+                end = i + 1 + len;
+            }
+            if (end >= r->n_items || r->kind_side[end] != AMC_T_END) return AMC_E_INVALID;
+            if (!ends.empty() && end >= ends.back()) return AMC_E_INVALID;
+            ends.push_back(end);
+            kinds.push_back(kk);
+        } else if (kk == AMC_T_ELSE) {
+            if (ends.empty() || kinds.back() != AMC_T_IF) return AMC_E_INVALID;
+        } else if (kk == AMC_T_END) {
+            if (ends.empty() || ends.back() != i) return AMC_E_INVALID;
+            ends.pop_back();
+            kinds.pop_back();
+        } else {
+            return AMC_E_INVALID;
+        }
+    }
+    return ends.empty() ? AMC_OK : AMC_E_INVALID;
+}
+
+size_t request_bytes(const Request& r)
+{
+    const size_t n = (size_t)r.n;
+    size_t b = align_up(n, 256) + align_up(4 * n, 256) + align_up(n, 256) + 512;   // ks, var, out, small
+    if (r.kind == AMC_REQ_TRACE)
+        b += scan_workspace_bytes(r.n, r.n_vars) + align_up(4 * (size_t)r.n_vars, 256);   // + vff
+    else
+        b += batch_workspace_bytes(r.n, 1) + 256;
+    return b;
+}
+
+// Launch an admitted request on its slot (worker thread, lock held).
+int launch(amc_server* s, Slot& sl, Request& r, Session& ses)
+{
+    const size_t n = (size_t)r.n;
+    const HostLayout H = host_layout(r.n);
+    uint8_t* h = s->host.ptr(r.host_off);
+    uint8_t* d = s->pool.ptr(r.off);
+    uint8_t* d_ks = d;
+    int32_t* d_var = reinterpret_cast<int32_t*>(d + align_up(n, 256));
+    uint8_t* d_out = d + align_up(n, 256) + align_up(4 * n, 256);
+    int64_t* d_small = reinterpret_cast<int64_t*>(d_out + align_up(n, 256));
+    uint8_t* d_ws = reinterpret_cast<uint8_t*>(d_small) + 512;
+    uint8_t* table = s->pool.ptr(ses.table_off);
+    cudaStream_t st = sl.stream;
+    if (n) {
+        if (cudaMemcpyAsync(d_ks, h + H.ks, n, cudaMemcpyHostToDevice, st) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaMemcpyAsync(d_var, h + H.var, 4 * n, cudaMemcpyHostToDevice, st) != cudaSuccess) return AMC_E_CUDA;
+    }
+    int64_t* d_ff = d_small;
+    int rc;
+    if (r.kind == AMC_REQ_TRACE) {
+        ScanLaunch L;
+        L.kind_side = d_ks;
+        L.var = d_var;
+        L.n_ops = r.n;
+        L.n_vars = r.n_vars;
+        L.init = table;
+        L.step = d_out;
+        L.final_status = table;           // in place: read and written per variable by one thread
+        L.vff = reinterpret_cast<int32_t*>(d_ws + scan_workspace_bytes(r.n, r.n_vars));
+        L.first_fault = d_ff;
+        L.err = s->err;
+        L.workspace = d_ws;
+        rc = launch_scan_trace(L, st);
+    } else {
+        // one program: token offsets {0, n}, var offsets {0, n_vars}, n_vars
+        int64_t* hs = reinterpret_cast<int64_t*>(h + H.small);
+        hs[1] = 0;
+        hs[2] = (int64_t)r.n;
+        hs[3] = 0;
+        hs[4] = (int64_t)r.n_vars;
+        reinterpret_cast<int32_t*>(hs + 5)[0] = r.n_vars;
+        if (cudaMemcpyAsync(d_small + 1, hs + 1, 5 * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return AMC_E_CUDA;
+        BatchLaunch B;
+        B.tok = d_ks;
+        B.payload = d_var;
+        B.prog_tok_off = d_small + 1;
+        B.prog_var_off = d_small + 3;
+        B.prog_nvars = reinterpret_cast<const int32_t*>(d_small + 5);
+        B.n_progs = 1;
+        B.n_tokens = r.n;
+        B.init_mask = table;
+        B.step_mask = d_out;
+        B.final_mask = table;
+        B.prog_first_fault = d_ff;
+        B.err = s->err;
+        B.workspace = d_ws;
+        B.longest_first = 0;
+        rc = launch_batch(B, st);
+    }
+    if (rc) return rc;
+    if (n && cudaMemcpyAsync(h + H.out, d_out, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemcpyAsync(h + H.small, d_ff, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaEventRecord(sl.done, st) != cudaSuccess) return AMC_E_CUDA;
+    return AMC_OK;
+}
+
+void finish(amc_server* s, Slot& sl)
+{
+    Request& r = *sl.req;
+    memcpy(&r.first_fault, s->host.ptr(r.host_off) + host_layout(r.n).small, 8);
+    r.t_done = now_s();
+    r.state = 2;
+    s->pool.free(r.off, r.bytes);
+    s->sessions[r.session].busy = false;
+    sl.req.reset();
+}
+
+void worker_loop(amc_server* s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    for (;;) {
+        bool progress = false;
+        bool running = false;
+        for (Slot& sl : s->slots) {
+            if (!sl.req) continue;
+            running = true;
+            if (cudaEventQuery(sl.done) == cudaSuccess) {
+                finish(s, sl);
+                progress = true;
+            }
+        }
+        // admission in arrival order; a request waits if its session is busy
+        for (auto it = s->queue.begin(); it != s->queue.end();) {
+            Slot* free_slot = nullptr;
+            for (Slot& sl : s->slots)
+                if (!sl.req) { free_slot = &sl; break; }
+            if (!free_slot) break;
+            Request& r = **it;
+            Session& ses = s->sessions[r.session];
+            if (ses.busy) { ++it; continue; }
+            const size_t off = s->pool.alloc(r.bytes);
+            if (off == SIZE_MAX) break;                     // wait for memory
+            r.off = off;
+            r.t_admit = now_s();
+            r.state = 1;
+            ses.busy = true;
+            free_slot->req = *it;
+            const int rc = launch(s, *free_slot, r, ses);
+            if (rc) {
+                cudaStreamSynchronize(free_slot->stream);
+                r.error = rc;
+                r.t_done = now_s();
+                r.state = 2;
+                s->pool.free(r.off, r.bytes);
+                ses.busy = false;
+                free_slot->req.reset();
+            }
+            it = s->queue.erase(it);
+            progress = true;
+            running = true;
+        }
+        if (s->stop && s->queue.empty() && !running) break;
+        if (!progress) {
+            if (running)
+                s->cv.wait_for(lock, std::chrono::microseconds(20));
+            else
+                s->cv.wait_for(lock, std::chrono::milliseconds(2));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int amc_server_create(size_t mem_budget_bytes, int max_slots, amc_server** out)
+{
+    if (!out || max_slots < 1 || max_slots > 256 || mem_budget_bytes < (1u << 20)) return AMC_E_INVALID;
+    std::unique_ptr<amc_server> s(new amc_server());
+    if (cudaGetDevice(&s->device) != cudaSuccess) return AMC_E_CUDA;
+    s->err = device_error_word();
+    if (!s->err) return AMC_E_CUDA;
+    if (!s->pool.init(mem_budget_bytes, false)) return AMC_E_NOMEM;
+    const size_t host_bytes = mem_budget_bytes < ((size_t)4 << 30) ? mem_budget_bytes : ((size_t)4 << 30);
+    if (!s->host.init(host_bytes, true)) {
+        s->pool.release();
+        return AMC_E_NOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking) != cudaSuccess) return AMC_E_CUDA;
+    s->slots.resize(max_slots);
+    for (Slot& sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) return AMC_E_CUDA;
+    }
+    amc_server* raw = s.release();
+    raw->worker = std::thread(worker_loop, raw);
+    *out = raw;
+    return AMC_OK;
+}
+
+int amc_serve_submit(amc_server* s, uint64_t session_id, const amc_request* req, uint64_t* ticket)
+{
+    if (!s || !ticket) return AMC_E_INVALID;
+    const int v = validate(req);
+    if (v) return v;
+    auto r = std::make_shared<Request>();
+    r->session = session_id;
+    r->kind = req->kind;
+    r->n_vars = req->n_vars;
+    r->n = req->n_items;
+    r->bytes = request_bytes(*r);
+    const HostLayout H = host_layout(r->n);
+    r->host_bytes = H.total;
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (s->queue.size() >= s->max_queue) return AMC_E_AGAIN;
+    Session& ses = s->sessions[session_id];
+    if (ses.kind >= 0 && (ses.kind != req->kind || ses.n_vars != req->n_vars))
+        return AMC_E_INVALID;            // sessions are typed by their first request
+    if (r->bytes + align_up((size_t)req->n_vars, 256) > s->pool.size() || H.total > s->host.size())
+        return AMC_E_NOMEM;
+    r->host_off = s->host.alloc(H.total);
+    if (r->host_off == SIZE_MAX) return AMC_E_AGAIN;        // staging full: back-pressure
+    if (ses.kind < 0) {
+        // first request: the session's table (status codes or masks) lives in the pool
+        const size_t off = s->pool.alloc(align_up((size_t)req->n_vars, 256));
+        if (off == SIZE_MAX) {
+            s->host.free(r->host_off, H.total);
+            return AMC_E_NOMEM;
+        }
+        const uint8_t init = req->kind == AMC_REQ_TRACE ? (uint8_t)AMC_ST_VI : (uint8_t)(1u << AMC_ST_VI);
+        if (cudaMemsetAsync(s->pool.ptr(off), init, (size_t)req->n_vars, s->ctl) != cudaSuccess ||
+            cudaStreamSynchronize(s->ctl) != cudaSuccess)
+            return AMC_E_CUDA;
+        ses.kind = req->kind;
+        ses.n_vars = req->n_vars;
+        ses.table_off = off;
+    }
+    uint8_t* h = s->host.ptr(r->host_off);
+    r->ticket = s->next_ticket++;
+    r->t_submit = now_s();
+    lock.unlock();
+    // stage the inputs in pinned memory outside the lock (the slot is reserved)
+    if (r->n) {
+        memcpy(h + H.ks, req->kind_side, (size_t)r->n);
+        memcpy(h + H.var, req->var, 4 * (size_t)r->n);
+    }
+    lock.lock();
+    s->reqs[r->ticket] = r;
+    s->queue.push_back(r);
+    *ticket = r->ticket;
+    s->cv.notify_one();
+    return AMC_OK;
+}
+
+int amc_serve_poll(amc_server* s, uint64_t ticket, int* done, amc_result* out)
+{
+    if (!s || !done) return AMC_E_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return AMC_E_INVALID;
+    const Request& r = *it->second;
+    *done = r.state == 2;
+    if (*done && out) {
+        out->error = r.error;
+        out->first_fault = r.first_fault;
+        out->n_items = r.n;
+        out->status = s->host.ptr(r.host_off) + host_layout(r.n).out;
+        out->t_submit = r.t_submit;
+        out->t_admit = r.t_admit;
+        out->t_done = r.t_done;
+    }
+    return AMC_OK;
+}
+
+int amc_serve_release(amc_server* s, uint64_t ticket)
+{
+    if (!s) return AMC_E_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end() || it->second->state != 2) return AMC_E_INVALID;
+    s->host.free(it->second->host_off, it->second->host_bytes);
+    s->reqs.erase(it);
+    return AMC_OK;
+}
+
+int amc_session_export(amc_server* s, uint64_t session_id, uint8_t* host_status, int32_t n_vars)
+{
+    if (!s || !host_status) return AMC_E_INVALID;
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            auto it = s->sessions.find(session_id);
+            if (it == s->sessions.end() || it->second.n_vars != n_vars) return AMC_E_INVALID;
+            bool pending = it->second.busy;
+            for (const auto& q : s->queue)
+                if (q->session == session_id) pending = true;
+            if (!pending) {
+                return cudaMemcpy(host_status, s->pool.ptr(it->second.table_off), (size_t)n_vars,
+                                  cudaMemcpyDeviceToHost) == cudaSuccess
+                           ? AMC_OK
+                           : AMC_E_CUDA;
+            }
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int amc_server_destroy(amc_server* s)
+{
+    if (!s) return AMC_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+        s->cv.notify_one();
+    }
+    s->worker.join();
+    for (Slot& sl : s->slots) {
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    for (auto& kv : s->reqs)
+        if (kv.second->host_off != SIZE_MAX) s->host.free(kv.second->host_off, kv.second->host_bytes);
+    if (s->ctl) cudaStreamDestroy(s->ctl);
+    s->pool.release();
+    s->host.release();
+    delete s;
+    return AMC_OK;
+}
+
+}  // extern "C"

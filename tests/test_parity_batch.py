@@ -1,0 +1,85 @@
+"""GPU parity of amc_check_batch (relation mode: If = union, While = closure)
+with the oracle: every step mask, final mask and program first fault is
+bit-exact.  Covers nesting up to the depth limit, empty branches and bodies,
+programs with more variables than the shared-memory table holds, graph replay,
+malformed programs, and the 100,000-program workload."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+IF, ELSE, WHILE, END = 8, 9, 10, 11
+
+
+@pytest.fixture(scope="module")
+def amc():
+    import paper_1910_11110_gb300 as m
+    m.build()
+    return m
+
+
+def run(amc, b, graph=False):
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    out = amc.check_batch(t(b["tok"]), t(b["payload"]), t(b["prog_tok_off"]), t(b["prog_nvars"]),
+                          graph_capture=graph, stream=torch.cuda.current_stream() if graph else None)
+    assert amc.sync_status() == 0
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def compare(amc, oracle_mod, b, graph=False):
+    step, final, pff = oracle_mod.check_batch(b["tok"], b["payload"], b["prog_tok_off"], b["prog_nvars"])
+    got = run(amc, b, graph)
+    assert np.array_equal(got["step_mask"], step), np.nonzero(got["step_mask"] != step)[0][:10]
+    assert np.array_equal(got["final_mask"], final)
+    assert np.array_equal(got["prog_first_fault"], pff)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n_progs=200, seed=41, median=300.0, max_len=5000, vars_lo=2, vars_hi=40),
+    dict(n_progs=300, seed=42, median=200.0, max_len=3000, vars_lo=1, vars_hi=3, p_if=0.2, p_while=0.15),
+    dict(n_progs=50, seed=43, median=2000.0, max_len=20000, vars_lo=64, vars_hi=4096),
+    dict(n_progs=20, seed=44, median=500.0, max_len=4000, vars_lo=5000, vars_hi=9000),
+    dict(n_progs=100, seed=45, median=100.0, max_len=2000, vars_lo=3, vars_hi=8, p_if=0.3, p_while=0.3,
+         max_depth=8, max_branch=6, max_body=6),
+])
+def test_random_batches(amc, oracle_mod, kw):
+    compare(amc, oracle_mod, workloads.programs(**kw))
+
+
+def test_graph_replay_matches(amc, oracle_mod):
+    b = workloads.programs(n_progs=400, seed=46, median=500.0, max_len=8000)
+    compare(amc, oracle_mod, b, graph=True)
+    compare(amc, oracle_mod, b, graph=True)      # second call replays the cached graph
+
+
+def test_edge_programs(amc, oracle_mod):
+    progs = [
+        ([], []),                                                   # empty program
+        ([IF, ELSE, END], [0, 0, 0]),                                # empty branches
+        ([WHILE, END, 1 | 16], [0, 0, 0]),                           # empty body
+        ([WHILE, 1 | 16, 2, END], [2, 0, 0, 0]),                     # closure reaches a fault
+        ([IF, 1, ELSE, 1 | 16, END, 0, 0 | 16], [1, 0, 1, 0, 0, 0, 0]),
+    ]
+    tok = np.array([x for p, _ in progs for x in p], np.uint8)
+    pay = np.array([x for _, q in progs for x in q], np.int32)
+    off = np.concatenate([[0], np.cumsum([len(p) for p, _ in progs])]).astype(np.int64)
+    b = dict(tok=tok, payload=pay, prog_tok_off=off, prog_nvars=np.array([1, 1, 1, 1, 1], np.int32))
+    compare(amc, oracle_mod, b)
+
+
+def test_malformed_reported(amc):
+    dev = torch.device("cuda")
+    t = lambda a, dt: torch.tensor(a, dtype=dt, device=dev)
+    amc.check_batch(t([IF, 0], torch.uint8), t([1, 0], torch.int32), t([0, 2], torch.int64), t([1], torch.int32))
+    assert amc.sync_status() == amc.E_INVALID
+    amc.check_batch(t([0], torch.uint8), t([3], torch.int32), t([0, 1], torch.int64), t([1], torch.int32))
+    assert amc.sync_status() == amc.E_RANGE
+    assert amc.sync_status() == 0
+
+
+def test_programs_workload_full_size(amc, oracle_mod):
+    """100,000 programs, 64-4,096 vars, lognormal lengths (seed 3)."""
+    compare(amc, oracle_mod, workloads.programs())
