@@ -5,25 +5,29 @@
 // and Remote Effect of Fig. Opsem; sequencing is associative with Noop as unit,
 // Section 3.2, so per-variable prefix compositions give the same statuses).
 //
-// How (one CTA per tile of T ops, persistent CTAs taking tiles in order):
+// How (one CTA per tile of T = 4096 ops, persistent CTAs taking tiles in order):
 //  1. the tile's op bytes and var ids are staged into shared memory by bulk
-//     async copies (cp.async.bulk + mbarrier), double buffered;
-//  2. each op byte becomes a monoid element (5-bit id, table lookup);
-//  3. a stable LSD radix sort of (var, position) in shared memory groups the
-//     tile's ops per variable ("runs"), warp ranking with match.any;
+//     async copies (cp.async.bulk + mbarrier);
+//  2. each op byte becomes a monoid element (5-bit id, table lookup) and each
+//     op a packed key (var << 12 | position);
+//  3. a stable LSD radix sort of the keys in shared memory (at most 10 bits
+//     per pass, warp ranking with match.any, per-warp histogram rows) groups
+//     the tile's ops per variable ("runs"); arrays are padded one word per 32
+//     so that each thread's blocked slice is read without bank conflicts;
 //  4. a segmented scan over the sorted runs composes each op's in-tile prefix
 //     (thread-serial composition, then a warp-shuffle segmented scan);
 //  5. each run needs the status of its variable at tile entry.  Runs of a
 //     variable already known to be stuck take F at once (F is absorbing; the
-//     first-fault table doubles as that index).  The other runs register a
-//     node (tile aggregate) in the variable's list of touching tiles, kept
-//     sorted by tile with lock-free insertion, then -- once every earlier tile
-//     has registered -- walk that list back composing aggregates until a node
-//     with a published inclusive status or the list end (initial status):
-//     decoupled look-back restricted to the tiles that touch the variable;
-//  6. outputs are written in original order (coalesced), first faults by
-//     atomicMin.
-// The only waits are on the registration frontier and on the mbarriers, both
+//     first-fault table doubles as that index; its loads are issued before the
+//     scan so the scan hides their latency).  The other runs add a node (the
+//     tile's aggregate) to the variable's list of touching tiles, kept sorted
+//     by tile with lock-free insertion, then -- once every earlier tile has
+//     registered -- walk that list back composing aggregates until a node with
+//     a published inclusive status or the list end (initial status): decoupled
+//     look-back restricted to the tiles that touch the variable;
+//  6. outputs are written in original order (coalesced 16-byte stores), first
+//     faults by atomicMin.
+// The only waits are on the registration frontier and on the mbarrier, both
 // bounded; an expired wait raises AMC_E_TIMEOUT and the kernel carries on.
 #include "amc_internal.cuh"
 #include "scan_trace.cuh"
@@ -32,32 +36,35 @@ namespace amc {
 
 namespace {
 
+constexpr int TILE = 4096;
+constexpr int THREADS = 256;
+constexpr int POS_BITS = 12;                // log2(TILE)
+constexpr int MAX_DIGIT_BITS = 10;
 constexpr uint8_t RUN_PENDING = 0xFF;
 constexpr uint32_t NODE_AGG = 0x40;
 constexpr uint32_t NODE_INCL = 0x80;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
-template <int T, int NT>
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
+template <typename KeyT, int T, int NT>
 struct __align__(16) ScanSmem {
-    int32_t var[2][T];               // var ids, later the sort's ping keys
-    uint32_t keyB[T];                // sort pong keys
-    uint8_t kind[2][T];              // op bytes, then element ids
-    uint16_t valA[T];
-    uint16_t valB[T];
+    KeyT keyA[T + T / 32];           // bulk target of the var ids (first 4T bytes), then sort keys
+    KeyT keyB[T + T / 32];
+    uint8_t kind[T];                 // op bytes, then element ids
     uint8_t out[T];
     uint8_t runEntry[T];
     uint8_t runAgg[T];
-    uint32_t pend[T];                // pending runs: run id | sorted slot << 16
-    uint16_t hist[256 * (NT / 32)];
+    uint16_t hist[(NT / 32) << MAX_DIGIT_BITS];
     uint8_t comp[MAX_ELEMS * MAX_ELEMS];
     uint8_t app[MAX_ELEMS * 8];
     uint8_t elem_of[256];
-    int scanTmp[2 * (NT / 32) + 4];
+    int scanTmp[NT / 32 + 2];
     uint8_t segF[NT / 32];
     uint8_t segV[NT / 32];
-    uint64_t mbar[2];
-    int tileId[2];
-    int viaBulk[2];
+    uint64_t mbar;
+    int tile;
+    int viaBulk;
     int nPend;
     uint32_t frontVal;
 };
@@ -67,58 +74,43 @@ __device__ __forceinline__ uint32_t comp_of(const uint8_t* comp, uint32_t a, uin
     return comp[a * MAX_ELEMS + b];
 }
 
-// Issue the bulk loads of tile t into buffer b (thread 0 only).  Tiles that are
-// partial or not 16-byte aligned are loaded later with plain loads.
-template <int T, int NT>
-__device__ void issue_tile_load(const ScanParams& p, ScanSmem<T, NT>& S, int b, int t)
-{
-    S.tileId[b] = t;
-    S.viaBulk[b] = 0;
-    if (t >= p.n_tiles) return;
-    const int64_t base = (int64_t)t * T;
-    if (base + T > p.n_ops || !p.bulk_ok) return;
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&S.mbar[b], (uint32_t)(T + 4 * T));
-    bulk_g2s(S.kind[b], p.kind_side + base, T, &S.mbar[b]);
-    bulk_g2s(S.var[b], p.var + base, 4 * T, &S.mbar[b]);
-    S.viaBulk[b] = 1;
-}
-
-template <int T, int NT>
-__device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int t, const int b)
+template <typename KeyT, int T, int NT>
+__device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, const int t)
 {
     constexpr int E = T / NT;
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)t * T;
     const int n = (int)min((int64_t)T, p.n_ops - base);
-    uint8_t* kb = S.kind[b];
-    int32_t* vb = S.var[b];
+    uint8_t* kb = S.kind;
+    int32_t* vraw = reinterpret_cast<int32_t*>(S.keyA);
     const uint32_t ID = 0;
 
-    if (!S.viaBulk[b]) {
+    if (!S.viaBulk) {
         for (int i = tid; i < n; i += NT) {
             kb[i] = p.kind_side[base + i];
-            vb[i] = p.var[base + i];
+            vraw[i] = p.var[base + i];
         }
         __syncthreads();
     }
 
-    // ---- 2. decode: op byte -> element id; validate ------------------------
-    // (all reads happen before any in-place write: GT looks at the next op)
+    // ---- 2. decode (striped): element ids and packed keys -------------------
+    // all reads happen before any in-place write: GT looks at the next op
     uint8_t mloc[E];
-    uint32_t badVar = 0;
+    KeyT keyloc[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-        const int i = tid * E + k;
+        const int i = k * NT + tid;
         mloc[k] = (uint8_t)ID;
+        keyloc[k] = 0;
         if (i < n) {
             const uint32_t ks = kb[i];
-            const int32_t v = vb[i];
+            int32_t v = vraw[i];
             if (v < 0 || v >= p.n_vars) {
                 raise_error(p.err, AMC_E_RANGE);
-                badVar |= 1u << k;
+                v = 0;
             }
+            keyloc[k] = ((KeyT)(uint32_t)v << POS_BITS) | (KeyT)i;
             uint32_t m = S.elem_of[ks];
             if (m == ELEM_GT) {
                 // GT must be followed by EN of the same side on another variable
@@ -127,7 +119,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
                 int32_t nv = v;
                 if (gi + 1 < p.n_ops) {
                     nks = (i + 1 < n) ? kb[i + 1] : p.kind_side[gi + 1];
-                    nv = (i + 1 < n) ? vb[i + 1] : p.var[gi + 1];
+                    nv = (i + 1 < n) ? vraw[i + 1] : p.var[gi + 1];
                 }
                 if ((nks & 15) != AMC_K_EN || (nks >> 4) != (ks >> 4) || nv == v) {
                     raise_error(p.err, AMC_E_INVALID);
@@ -155,57 +147,62 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-        const int i = tid * E + k;
+        const int i = k * NT + tid;
         if (i < n) {
             kb[i] = mloc[k];
-            if (badVar & (1u << k)) vb[i] = 0;
+            S.keyB[pad(i)] = keyloc[k];
         }
     }
+    // own histogram row cleared before the first ranking
+    const int D0 = 1 << p.digit_bits;
+    for (int i = lane; i < D0; i += 32) S.hist[warp * D0 + i] = 0;
     __syncthreads();
 
-    // ---- 3. stable LSD radix sort of (var, position) -----------------------
-    uint32_t* kin = reinterpret_cast<uint32_t*>(vb);
-    uint32_t* kout = S.keyB;
-    uint16_t* vin = S.valA;
-    uint16_t* vout = S.valB;
-    const int D = 1 << p.digit_bits;
-    const int M = D * NW;
+    // ---- 3. stable LSD radix sort of the packed keys ------------------------
+    KeyT* kin = S.keyB;
+    KeyT* kout = S.keyA;
     const uint32_t lt = lanemask_lt();
     for (int pass = 0; pass < p.passes; ++pass) {
-        const int shift = pass * p.digit_bits;
-        for (int i = tid; i < M; i += NT) S.hist[i] = 0;
-        __syncthreads();
-        uint32_t kk[E];
+        const int D = 1 << p.digit_bits;
+        const int shift = POS_BITS + pass * p.digit_bits;
+        uint16_t* hrow = S.hist + warp * D;
+        if (pass > 0) {
+            for (int i = lane; i < D; i += 32) hrow[i] = 0;
+            __syncwarp();
+        }
+        KeyT kk[E];
         uint16_t lr[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int pos = warp * 32 * E + e * 32 + lane;
             const bool ok = pos < n;
-            const uint32_t key = ok ? kin[pos] : 0u;
+            const KeyT key = ok ? kin[pad(pos)] : (KeyT)0;
             kk[e] = key;
-            const uint32_t dig = ok ? ((key >> shift) & (uint32_t)(D - 1)) : 0xFFFFFFFFu;
+            const uint32_t dig = ok ? (uint32_t)((key >> shift) & (KeyT)(D - 1)) : 0xFFFFFFFFu;
             const uint32_t peers = __match_any_sync(0xffffffffu, dig);
             const uint32_t rank = __popc(peers & lt);
             uint16_t c = 0;
-            if (ok) c = S.hist[dig * NW + warp];
+            if (ok) c = hrow[dig];
             lr[e] = (uint16_t)(c + rank);
             __syncwarp();
-            if (ok && rank == 0) S.hist[dig * NW + warp] = (uint16_t)(c + __popc(peers));
+            if (ok && rank == 0) hrow[dig] = (uint16_t)(c + __popc(peers));
             __syncwarp();
         }
         __syncthreads();
         {
-            // exclusive scan of hist in (digit, warp) order
-            const int per = (M + NT - 1) / NT;
-            const int lo = tid * per;
+            // exclusive scan of the counts in (digit, warp) order
+            const int per = (D + NT - 1) / NT;
+            const int d0 = tid * per;
             int sum = 0;
-            for (int j = 0; j < per; ++j)
-                if (lo + j < M) sum += S.hist[lo + j];
+            for (int d = d0; d < d0 + per && d < D; ++d)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) sum += S.hist[w * D + d];
             int run = block_excl_sum<NT>(sum, S.scanTmp, nullptr);
-            for (int j = 0; j < per; ++j)
-                if (lo + j < M) {
-                    const int c = S.hist[lo + j];
-                    S.hist[lo + j] = (uint16_t)run;
+            for (int d = d0; d < d0 + per && d < D; ++d)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const int c = S.hist[w * D + d];
+                    S.hist[w * D + d] = (uint16_t)run;
                     run += c;
                 }
         }
@@ -214,57 +211,50 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
         for (int e = 0; e < E; ++e) {
             const int pos = warp * 32 * E + e * 32 + lane;
             if (pos < n) {
-                const uint32_t dig = (kk[e] >> shift) & (uint32_t)(D - 1);
-                const int dst = S.hist[dig * NW + warp] + lr[e];
-                kout[dst] = kk[e];
-                vout[dst] = pass == 0 ? (uint16_t)pos : vin[pos];
+                const uint32_t dig = (uint32_t)((kk[e] >> shift) & (KeyT)(D - 1));
+                kout[pad(hrow[dig] + lr[e])] = kk[e];
             }
         }
         __syncthreads();
-        uint32_t* tk = kin; kin = kout; kout = tk;
-        uint16_t* tv = vin; vin = vout; vout = tv;
+        KeyT* tk = kin;
+        kin = kout;
+        kout = tk;
     }
-    const uint32_t* K = kin;     // sorted keys
-    const uint16_t* P = vin;     // original positions
+    const KeyT* K = kin;                       // sorted keys
+    uint32_t* pend = reinterpret_cast<uint32_t*>(kout);   // the free buffer
+    auto kvar = [&](int j) -> uint32_t { return (uint32_t)(K[pad(j)] >> POS_BITS); };
+    auto kpos = [&](int j) -> int { return (int)(K[pad(j)] & (KeyT)(T - 1)); };
 
     // ---- 4a. run boundaries; the stuck-shortcut loads are issued here so
     // that the segmented scan below hides their latency --------------------
     const int j0 = tid * E;
-    uint32_t keyk[E];
     uint32_t headMask = 0, lastMask = 0;
-    {
-        uint32_t prevKey = (j0 > 0 && j0 - 1 < n) ? K[j0 - 1] : 0xFFFFFFFFu;
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int j = j0 + k;
-            keyk[k] = 0;
-            if (j < n) {
-                keyk[k] = K[j];
-                if (keyk[k] != prevKey) headMask |= 1u << k;
-                prevKey = keyk[k];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int j = j0 + k;
-            if (j < n) {
-                const uint32_t nk = (j + 1 < n) ? (k + 1 < E ? keyk[(k + 1) % E] : K[j + 1]) : 0xFFFFFFFFu;
-                if (nk != keyk[k]) lastMask |= 1u << k;
-            }
-        }
-    }
     uint32_t ffv[E];
+    {
+        uint32_t prev = (j0 > 0 && j0 - 1 < n) ? kvar(j0 - 1) : 0xFFFFFFFFu;
+        uint32_t cur = (j0 < n) ? kvar(j0) : 0xFFFFFFFEu;
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        ffv[k] = 0xFFFFFFFFu;
-        if (lastMask & (1u << k)) ffv[k] = __ldcg(reinterpret_cast<const unsigned int*>(p.vff) + keyk[k]);
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            const uint32_t nxt = (j + 1 < n) ? kvar(j + 1) : 0xFFFFFFFDu;
+            ffv[k] = 0xFFFFFFFFu;
+            if (j < n) {
+                if (cur != prev) headMask |= 1u << k;
+                if (nxt != cur) {
+                    lastMask |= 1u << k;
+                    ffv[k] = __ldcg(reinterpret_cast<const unsigned int*>(p.vff) + cur);
+                }
+            }
+            prev = cur;
+            cur = nxt;
+        }
     }
 
     // ---- 4b. segmented scan over runs (blocked: thread owns E sorted slots) --
     // per-slot prefix (pm) and exclusive prefix (xm), four bytes per word
-    uint32_t pmw[E / 4], xmw[E / 4];
 #define getb(w, k) (((w)[(k) >> 2] >> (8 * ((k) & 3))) & 0xFFu)
 #define setb(w, k, v) ((w)[(k) >> 2] = ((w)[(k) >> 2] & ~(0xFFu << (8 * ((k) & 3)))) | ((uint32_t)(v) << (8 * ((k) & 3))))
+    uint32_t pmw[E / 4], xmw[E / 4];
 #pragma unroll
     for (int i = 0; i < E / 4; ++i) pmw[i] = xmw[i] = 0;    // identity is element 0
     const int nHeads = __popc(headMask);
@@ -273,7 +263,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
     for (int k = 0; k < E; ++k) {
         const int j = j0 + k;
         if (j < n) {
-            const uint32_t m = kb[P[j]];
+            const uint32_t m = kb[kpos(j)];
             if (headMask & (1u << k)) {
                 acc = m;
             } else {
@@ -283,7 +273,6 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
             setb(pmw, k, acc);
         }
     }
-    // segmented exclusive scan of (has head, value) across threads
     uint32_t carry;
     {
         uint32_t f = headMask != 0, v = acc;
@@ -344,7 +333,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
                 const uint32_t agg = getb(pmw, k);
                 S.runEntry[r] = RUN_PENDING;
                 S.runAgg[r] = (uint8_t)agg;
-                S.pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
+                pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
                 p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | agg);
             }
         }
@@ -363,10 +352,10 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
             c[u] = NIL;
             node[u] = var[u] = 0;
             if (i < nPend) {
-                const uint32_t e = S.pend[i];
+                const uint32_t e = pend[i];
                 mine |= 1u << u;
                 node[u] = nodeBase + (e & 0xFFFFu);
-                var[u] = K[e >> 16];
+                var[u] = kvar((int)(e >> 16));
                 c[u] = __ldcg(p.head + var[u]);
             }
         }
@@ -399,13 +388,13 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
     __syncthreads();
 
     // ---- 5b. registration frontier ------------------------------------------
-    // regflag[t] = 1 once tile t's nodes are all in their lists; *front = F
-    // means every tile < F has registered.  Only tiles that look back (and all
-    // tiles of the guard-resolving pass, whose first input status is read by
-    // the previous tile) wait for the frontier to reach them.
+    // bit t of regbits is set once tile t's nodes are all in their lists;
+    // *front = F means every tile < F has registered.  Only tiles that look
+    // back (and all tiles of the guard-resolving pass, whose first input status
+    // is read by the previous tile) wait for the frontier to reach them.
     if (tid == 0) {
         __threadfence();
-        st_release(p.regflag + t, 1);
+        atomicOr(p.regbits + (t >> 5), 1u << (t & 31));
     }
     if (nPend > 0 || p.guard) {
         for (uint32_t it = 0;; ++it) {
@@ -413,14 +402,18 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
             __syncthreads();
             const uint32_t f0 = S.frontVal;
             if (f0 >= (uint32_t)t) break;
-            bool all = true;          // check every tile in [front, t) at once
-            for (uint32_t q = f0 + tid; q < (uint32_t)t; q += NT) all &= ld_acquire(p.regflag + q) != 0;
+            bool all = true;          // every tile in [front, t), 32 per word
+            for (uint32_t w = (f0 >> 5) + tid; w <= ((uint32_t)t - 1) >> 5; w += NT) {
+                const uint32_t lo = max(f0, w << 5), hi = min((uint32_t)t, (w << 5) + 32);
+                const uint32_t need = (hi - lo == 32) ? 0xFFFFFFFFu : (((1u << (hi - lo)) - 1u) << (lo & 31));
+                all &= (__ldcg(p.regbits + w) & need) == need;
+            }
             if (__syncthreads_and(all)) {
                 if (tid == 0) { __threadfence(); atomicMax(p.front, (uint32_t)t); }
                 break;
             }
             if (it > SPIN_LIMIT) { if (tid == 0) raise_error(p.err, AMC_E_TIMEOUT); break; }
-            __nanosleep(128);
+            __nanosleep(256);
         }
         __threadfence();
     }
@@ -437,11 +430,11 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
             q[u] = NIL;
             node[u] = var[u] = rr[u] = 0;
             if (i < nPend) {
-                const uint32_t e = S.pend[i];
+                const uint32_t e = pend[i];
                 active |= 1u << u;
                 rr[u] = e & 0xFFFFu;
                 node[u] = nodeBase + rr[u];
-                var[u] = K[e >> 16];
+                var[u] = kvar((int)(e >> 16));
                 q[u] = ld_acquire(p.node_next + node[u]);
             }
         }
@@ -487,15 +480,17 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
             const uint32_t e = S.runEntry[run_id(k)];
             const uint32_t pre = S.app[getb(xmw, k) * 8 + e];
             const uint32_t post = S.app[getb(pmw, k) * 8 + e];
-            const int pos = P[j];
+            const int pos = kpos(j);
             S.out[pos] = (uint8_t)(p.pre_mode ? pre : post);
             if (post == ST_F && pre != ST_F) {
                 const uint32_t gi = (uint32_t)(base + pos);
-                atomicMin(reinterpret_cast<uint32_t*>(p.vff) + K[j], gi);
+                atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j), gi);
                 atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
             }
         }
     }
+#undef getb
+#undef setb
     __syncthreads();
     if (n == T && p.bulk_ok) {
         const uint4* src = reinterpret_cast<const uint4*>(S.out);
@@ -504,49 +499,55 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<T, NT>& S, const int 
     } else {
         for (int i = tid; i < n; i += NT) p.step[base + i] = S.out[i];
     }
-#undef getb
-#undef setb
 }
 
-template <int T, int NT>
-__global__ void __launch_bounds__(NT, 2) scan_trace_kernel(const ScanParams p)
+template <typename KeyT, int T, int NT>
+__global__ void __launch_bounds__(NT, 3) scan_trace_kernel(const ScanParams p)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    ScanSmem<T, NT>& S = *reinterpret_cast<ScanSmem<T, NT>*>(smem_raw);
+    ScanSmem<KeyT, T, NT>& S = *reinterpret_cast<ScanSmem<KeyT, T, NT>*>(smem_raw);
     const int tid = threadIdx.x;
     for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += NT) S.comp[i] = p.tab.comp[i];
     for (int i = tid; i < MAX_ELEMS * 8; i += NT) S.app[i] = p.tab.app[i];
     for (int i = tid; i < 256; i += NT) S.elem_of[i] = p.tab.elem_of[i];
     if (tid == 0) {
-        mbar_init(&S.mbar[0], 1);
-        mbar_init(&S.mbar[1], 1);
+        mbar_init(&S.mbar, 1);
         fence_mbar_init();
-        issue_tile_load<T, NT>(p, S, 0, (int)atomicAdd(p.tile_counter, 1u));
+        S.tile = (int)atomicAdd(p.tile_counter, 1u);
     }
     __syncthreads();
-    uint32_t parity[2] = {0, 0};
-    int cur = 0;
+    uint32_t parity = 0;
     for (;;) {
-        const int t = S.tileId[cur];
-        if (t >= p.n_tiles) break;          // nothing was issued into this buffer
-        if (tid == 0) issue_tile_load<T, NT>(p, S, cur ^ 1, (int)atomicAdd(p.tile_counter, 1u));
+        const int t = S.tile;
+        if (t >= p.n_tiles) break;
+        uint32_t t_next = 0;
+        if (tid == 0) {
+            // stage the tile (bulk copies for full, aligned tiles), then fetch
+            // the next tile id: its latency hides behind this tile's work
+            const int64_t base = (int64_t)t * T;
+            S.viaBulk = 0;
+            if (base + T <= p.n_ops && p.bulk_ok) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&S.mbar, (uint32_t)(T + 4 * T));
+                bulk_g2s(S.kind, p.kind_side + base, T, &S.mbar);
+                bulk_g2s(S.keyA, p.var + base, 4 * T, &S.mbar);
+                S.viaBulk = 1;
+            }
+            t_next = atomicAdd(p.tile_counter, 1u);
+        }
+        __syncthreads();
         bool ok = true;
-        if (S.viaBulk[cur]) {
-            ok = mbar_wait_bounded(&S.mbar[cur], parity[cur], p.err);
-            parity[cur] ^= 1;
+        if (S.viaBulk) {
+            ok = mbar_wait_bounded(&S.mbar, parity, p.err);
+            parity ^= 1;
         }
         if (__syncthreads_or(!ok)) {
-            // never leave with a bulk copy in flight into shared memory: drain
-            // the copy just issued (and the one that timed out), both bounded
-            if (tid == 0) {
-                if (S.viaBulk[cur ^ 1]) mbar_wait_bounded(&S.mbar[cur ^ 1], parity[cur ^ 1], p.err);
-                if (!ok) mbar_wait_bounded(&S.mbar[cur], parity[cur] ^ 1, p.err);
-            }
+            if (tid == 0) mbar_wait_bounded(&S.mbar, parity ^ 1, p.err);   // drain, bounded
             break;
         }
-        process_tile<T, NT>(p, S, t, cur);
+        process_tile<KeyT, T, NT>(p, S, t);
+        if (tid == 0) S.tile = (int)t_next;
         __syncthreads();
-        cur ^= 1;
     }
 }
 
@@ -566,8 +567,32 @@ __global__ void finalize_trace_kernel(const int32_t* __restrict__ vff, const uin
     final_status[v] = f;
 }
 
-constexpr int TILE = 4096;
-constexpr int THREADS = 256;
+template <typename KeyT>
+int launch_kernel(const ScanParams& p, const ScanLaunch& L, cudaStream_t s)
+{
+    const size_t smem = sizeof(ScanSmem<KeyT, TILE, THREADS>);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(scan_trace_kernel<KeyT, TILE, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return AMC_E_CUDA;
+        attr_set[dev] = true;
+    }
+    int n_sm = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_trace_kernel<KeyT, TILE, THREADS>, THREADS, smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = n_sm * per_sm;
+    if (grid > p.n_tiles) grid = p.n_tiles;
+    if (L.max_ctas > 0 && grid > L.max_ctas) grid = L.max_ctas;
+    if (L.profile & 1) profile_begin(s);
+    scan_trace_kernel<KeyT, TILE, THREADS><<<grid, THREADS, smem, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    if (L.profile & 2) profile_end(s);
+    return AMC_OK;
+}
 
 }  // namespace
 
@@ -580,8 +605,8 @@ size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars)
     b += align_up(4 * (size_t)n_vars, 256);                 // head
     b += align_up(4 * (size_t)n_tiles * TILE, 256);         // node_next
     b += align_up((size_t)n_tiles * TILE, 256);             // node_status
-    b += align_up(4 * (size_t)n_tiles, 256);                // regflag
-    b += 256;                                               // tile counter
+    b += align_up(4 * (size_t)((n_tiles + 31) / 32), 256);  // registration bits
+    b += 256;                                               // tile counter, frontier
     return b;
 }
 
@@ -608,14 +633,15 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     w += align_up(4 * (size_t)p.n_tiles * TILE, 256);
     p.node_status = w;
     w += align_up((size_t)p.n_tiles * TILE, 256);
-    p.regflag = reinterpret_cast<uint32_t*>(w);
-    w += align_up(4 * (size_t)p.n_tiles, 256);
+    p.regbits = reinterpret_cast<uint32_t*>(w);
+    const size_t regbytes = 4 * (size_t)((p.n_tiles + 31) / 32);
+    w += align_up(regbytes, 256);
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
-    // key bits: var ids are < n_vars
+    // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
     int kb = 1;
     while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
-    p.passes = (kb + 7) / 8;
+    p.passes = (kb + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
     p.digit_bits = (kb + p.passes - 1) / p.passes;
     p.bulk_ok = ((uintptr_t)L.kind_side % 16 == 0) && ((uintptr_t)L.var % 16 == 0) &&
                 ((uintptr_t)L.step % 16 == 0);
@@ -624,29 +650,11 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
     if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
     if (L.n_ops > 0) {
-        if (cudaMemsetAsync(p.regflag, 0, 4 * (size_t)p.n_tiles, s) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaMemsetAsync(p.regbits, 0, regbytes, s) != cudaSuccess) return AMC_E_CUDA;
         if (cudaMemsetAsync(p.tile_counter, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
-        const size_t smem = sizeof(ScanSmem<TILE, THREADS>);
-        static bool attr_set[64] = {};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (dev < 64 && !attr_set[dev]) {
-            if (cudaFuncSetAttribute(scan_trace_kernel<TILE, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return AMC_E_CUDA;
-            attr_set[dev] = true;
-        }
-        int n_sm = 0, per_sm = 0;
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_trace_kernel<TILE, THREADS>, THREADS, smem);
-        if (per_sm < 1) per_sm = 1;
-        int grid = n_sm * per_sm;
-        if (grid > p.n_tiles) grid = p.n_tiles;
-        if (L.max_ctas > 0 && grid > L.max_ctas) grid = L.max_ctas;
-        if (L.profile & 1) profile_begin(s);
-        scan_trace_kernel<TILE, THREADS><<<grid, THREADS, smem, s>>>(p);
-        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-        if (L.profile & 2) profile_end(s);
+        // keys pack (var << 12 | position): 32-bit while var ids fit 20 bits
+        const int rc = kb + POS_BITS <= 32 ? launch_kernel<uint32_t>(p, L, s) : launch_kernel<uint64_t>(p, L, s);
+        if (rc) return rc;
     }
     if (L.final_status) {
         const int nb = (int)((L.n_vars + 255) / 256);

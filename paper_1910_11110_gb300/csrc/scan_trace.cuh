@@ -20,7 +20,7 @@ struct ScanParams {
     uint32_t* head;             // [n_vars] newest registered node of each var
     uint32_t* node_next;        // [n_tiles * T]
     uint8_t* node_status;       // [n_tiles * T]
-    uint32_t* regflag;          // [n_tiles] 1 = the tile's nodes are in their lists
+    uint32_t* regbits;          // bit t set: tile t's nodes are in their lists
     uint32_t* tile_counter;
     uint32_t* front;            // every tile < *front has registered
     int n_tiles;
