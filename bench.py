@@ -129,14 +129,28 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ms_local, ops_local, world, device="cuda"):
+    """Whole-job throughput: ops of all ranks over the slowest rank's time.
+    Returns (ops_per_s, max_ms, total_ops)."""
+    import torch
+    ms = max_over_ranks(ms_local, world, device)
+    total = float(ops_local)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total = float(t.item())
+    return total / (ms * 1e-3), ms, total
 
 
 def cpu_baseline(ks_host, var_host, n_vars, budget_s):
@@ -248,10 +262,8 @@ def run_ours(args):
     if amc.sync_status() != 0:
         raise RuntimeError("device error during timed steps")
     ms_total = s_start.elapsed_time(s_stop)
-    ms_total = max_over_ranks(ms_total, world)
-    ms_step = ms_total / args.steps
+    value, ms_step, _ = aggregate(ms_total / args.steps, n_ops, world)
     k_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(k_start, k_stop))
-    value = n_ops * world / (ms_step * 1e-3)
 
     peak, peak_kind = peaks()
     alg_bytes = 6 * n_ops + 5 * n_vars

@@ -95,6 +95,14 @@ AMC_API int amc_sync_status(void* stream);
  * as void*; NULL, NULL turns it off).  Returns AMC_OK. */
 AMC_API int amc_set_profile_events(void* start_event, void* stop_event);
 
+/* Profiling aid (no counterpart in the paper): cycle counters of the trace
+ * scan kernel's phases (0 tile staging, 1 decode and compaction, 2 sort,
+ * 3 segmented scan, 4 run entry and list insertion, 5 registration frontier,
+ * 6 look-back, 7 outputs), summed over CTAs.  enable >= 0 switches counting
+ * on (1) or off (0) for later launches and zeroes the counters; host_out
+ * (8 host uint64, nullable) receives the current counters. */
+AMC_API int amc_debug_scan_phases(int enable, uint64_t* host_out);
+
 /* ------------------------------------------------------------------------ */
 /* (1) Straight-line traces -- Section 3.2 (Fig. Opsem, Effect and Remote    */
 /*     Effect rules; signatures of Section 3.1; initial store sigma_0).      */

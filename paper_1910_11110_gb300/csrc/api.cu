@@ -55,6 +55,11 @@ int amc_set_profile_events(void* start_event, void* stop_event)
     return AMC_OK;
 }
 
+int amc_debug_scan_phases(int enable, uint64_t* host_out)
+{
+    return scan_phase_profile(enable, reinterpret_cast<unsigned long long*>(host_out));
+}
+
 const char* amc_error_string(int code)
 {
     switch (code) {

@@ -56,7 +56,7 @@ __device__ void run_program(const BatchParams& p, int64_t prog, uint8_t* smM, ui
     // frames (identical in every lane): kind (8 = IF, 10 = WHILE) and pass
     // count; construct token, ELSE token and END token
     int fk[AMC_MAX_DEPTH * 2];
-    int64_t fpos[AMC_MAX_DEPTH * 3];
+    int64_t fpos[AMC_MAX_DEPTH * 3] = {};
     int depth = 0;
     int64_t ff = INT64_MAX;
     bool bad = false;

@@ -29,6 +29,8 @@
 //     faults by atomicMin.
 // The only waits are on the registration frontier and on the mbarrier, both
 // bounded; an expired wait raises AMC_E_TIMEOUT and the kernel carries on.
+#include <cstdlib>
+
 #include "amc_internal.cuh"
 #include "scan_trace.cuh"
 
@@ -44,14 +46,26 @@ constexpr uint8_t RUN_PENDING = 0xFF;
 constexpr uint32_t NODE_AGG = 0x40;
 constexpr uint32_t NODE_INCL = 0x80;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
+constexpr int DEFAULT_FB_BITS = 1 << 20;      // shared stuck bitmap: 128 KB
+constexpr int N_PHASES = 8;
+constexpr int RANK_SORT_MAX = 128;             // live ops below which a rank sort replaces the radix passes
+
+}  // namespace
+
+// Cycle counters per phase of the scan kernel (debug aid, summed over CTAs).
+__device__ unsigned long long g_scan_phase_cycles[N_PHASES];
+
+namespace {
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
 
 template <typename KeyT, int T, int NT>
 struct __align__(16) ScanSmem {
-    KeyT keyA[T + T / 32];           // bulk target of the var ids (first 4T bytes), then sort keys
-    KeyT keyB[T + T / 32];
-    uint8_t kind[T];                 // op bytes, then element ids
+    KeyT vbuf[1][T + T / 32];        // bulk target of the var ids (first 4T bytes); after the
+                                     // decode it holds the live ops' packed keys
+    KeyT keyA[T + T / 32];
+    uint8_t kind[1][T];              // op bytes
+    uint8_t mel[T];                  // element ids of live ops
     uint8_t out[T];
     uint8_t runEntry[T];
     uint8_t runAgg[T];
@@ -62,11 +76,14 @@ struct __align__(16) ScanSmem {
     int scanTmp[NT / 32 + 2];
     uint8_t segF[NT / 32];
     uint8_t segV[NT / 32];
-    uint64_t mbar;
-    int tile;
-    int viaBulk;
+    uint16_t cnt[(T / NT) * (NT / 32)];   // live ops per (slot, warp), then their offsets
+    uint64_t mbar[1];
+    int tile[1];
+    int viaBulk[1];
     int nPend;
+    int nLive;
     uint32_t frontVal;
+    // followed (dynamic shared memory) by the stuck bitmap: fbw 32-bit words
 };
 
 __device__ __forceinline__ uint32_t comp_of(const uint8_t* comp, uint32_t a, uint32_t b)
@@ -75,94 +92,200 @@ __device__ __forceinline__ uint32_t comp_of(const uint8_t* comp, uint32_t a, uin
 }
 
 template <typename KeyT, int T, int NT>
-__device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, const int t)
+__device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint32_t* fsm, const int t, const int b,
+                             const uint32_t refresh, long long& last)
 {
+#define PHASE(k)                                                                                 \
+    if (p.phase_on && threadIdx.x == 0) {                                                        \
+        const long long now = clock64();                                                         \
+        atomicAdd(&g_scan_phase_cycles[k], (unsigned long long)(now - last));                     \
+        last = now;                                                                              \
+    }
     constexpr int E = T / NT;
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)t * T;
     const int n = (int)min((int64_t)T, p.n_ops - base);
-    uint8_t* kb = S.kind;
-    int32_t* vraw = reinterpret_cast<int32_t*>(S.keyA);
+    uint8_t* kb = S.kind[b];
+    int32_t* vraw = reinterpret_cast<int32_t*>(S.vbuf[b]);
     const uint32_t ID = 0;
+    const uint32_t lt = lanemask_lt();
 
-    if (!S.viaBulk) {
+    if (!S.viaBulk[b]) {
         for (int i = tid; i < n; i += NT) {
             kb[i] = p.kind_side[base + i];
             vraw[i] = p.var[base + i];
         }
         __syncthreads();
     }
+    // rolling refresh of the shared copy of the stuck bitmap (16 bytes per
+    // thread per tile).  Bits are only ever set, so a stale word is merely
+    // less complete, never wrong.
+    if (p.fbw) {
+        const uint32_t nq = (uint32_t)p.fbw / 4;
+        const uint32_t q = (refresh * NT + tid) % nq;
+        reinterpret_cast<uint4*>(fsm)[q] = __ldcg(reinterpret_cast<const uint4*>(p.fbits) + q);
+    }
 
-    // ---- 2. decode (striped): element ids and packed keys -------------------
-    // all reads happen before any in-place write: GT looks at the next op
-    uint8_t mloc[E];
-    KeyT keyloc[E];
+    // ---- 2. decode: four consecutive ops per thread and step (one 32-bit load
+    // of op bytes, one 16-byte load of ids).  Ops on variables known to be
+    // stuck output F at once; the others ("live") get their element ids and
+    // are compacted in position order.
+    constexpr int G = 4;
+    constexpr int STEPS = E / G;
+    uint32_t liveBits = 0;                 // bit 4k+u: op u of step k is live
+    int excl[STEPS];
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const int i = k * NT + tid;
-        mloc[k] = (uint8_t)ID;
-        keyloc[k] = 0;
-        if (i < n) {
-            const uint32_t ks = kb[i];
-            int32_t v = vraw[i];
-            if (v < 0 || v >= p.n_vars) {
-                raise_error(p.err, AMC_E_RANGE);
-                v = 0;
-            }
-            keyloc[k] = ((KeyT)(uint32_t)v << POS_BITS) | (KeyT)i;
-            uint32_t m = S.elem_of[ks];
-            if (m == ELEM_GT) {
-                // GT must be followed by EN of the same side on another variable
-                const int64_t gi = base + i;
-                uint32_t nks = 0xFF;
-                int32_t nv = v;
-                if (gi + 1 < p.n_ops) {
-                    nks = (i + 1 < n) ? kb[i + 1] : p.kind_side[gi + 1];
-                    nv = (i + 1 < n) ? vraw[i + 1] : p.var[gi + 1];
+    for (int k = 0; k < STEPS; ++k) {
+        const int g = k * NT + tid;
+        const int i0 = g * G;
+        uint32_t cnt = 0;
+        if (i0 < n) {
+            const uint32_t kw = *reinterpret_cast<const uint32_t*>(kb + i0);
+            const int4 vv = *reinterpret_cast<const int4*>(vraw + i0);
+            const int32_t va[G] = {vv.x, vv.y, vv.z, vv.w};
+            uint32_t outw = 0;
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int i = i0 + u;
+                const uint32_t ks = (kw >> (8 * u)) & 0xFFu;
+                uint32_t o = ST_F;
+                if (i < n) {
+                    if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
+                    uint32_t uv = (uint32_t)va[u];
+                    if (va[u] < 0 || va[u] >= p.n_vars) {
+                        raise_error(p.err, AMC_E_RANGE);
+                        uv = 0;
+                    }
+                    bool gt_ok = true;
+                    if ((ks & 15u) == AMC_K_GT) {
+                        // GT must be followed by EN of the same side on another variable
+                        const int64_t gi = base + i;
+                        uint32_t nks = 0xFF;
+                        int32_t nv = (int32_t)uv;
+                        if (gi + 1 < p.n_ops) {
+                            nks = (i + 1 < n) ? kb[i + 1] : p.kind_side[gi + 1];
+                            nv = (i + 1 < n) ? vraw[i + 1] : p.var[gi + 1];
+                        }
+                        gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
+                        if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
+                    }
+                    const bool stuck = uv < (uint32_t)p.fbw * 32u && ((fsm[uv >> 5] >> (uv & 31)) & 1u);
+                    if (!stuck) {
+                        uint32_t m = S.elem_of[ks];
+                        if (m == ELEM_GT) {
+                            if (!gt_ok || p.pre_mode) {
+                                m = ID;                      // guard pass: GT does not touch guards
+                            } else if (!p.guard) {
+                                raise_error(p.err, AMC_E_INVALID);   // GT needs the guarded entry point
+                                m = ID;
+                            } else {
+                                // guard = status of the EN's variable before the EN,
+                                // written at the next position by the guard pass
+                                const uint32_t gs = p.guard[base + i + 1];
+                                const int side = ks >> 4;
+                                const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
+                                m = valid ? ID : p.tab.pull_of_side[side];
+                            }
+                        } else if (m == ELEM_BAD) {
+                            m = ID;
+                        }
+                        S.mel[i] = (uint8_t)m;
+                        liveBits |= 1u << (k * G + u);
+                        ++cnt;
+                        o = 0;                       // written by the live path
+                    }
                 }
-                if ((nks & 15) != AMC_K_EN || (nks >> 4) != (ks >> 4) || nv == v) {
-                    raise_error(p.err, AMC_E_INVALID);
-                    m = ID;
-                } else if (p.pre_mode) {
-                    m = ID;                      // guard pass: GT does not touch guards
-                } else if (!p.guard) {
-                    raise_error(p.err, AMC_E_INVALID);   // GT needs the guarded entry point
-                    m = ID;
-                } else {
-                    // guard = status of the EN's variable before the EN, written
-                    // at gi+1 by the guard pass
-                    const uint32_t g = p.guard[gi + 1];
-                    const int side = ks >> 4;
-                    const bool valid = g != ST_F && (g & (side == 0 ? 1u : 2u));
-                    m = valid ? ID : p.tab.pull_of_side[side];
-                }
-            } else if (m == ELEM_BAD) {
-                raise_error(p.err, AMC_E_INVALID);
-                m = ID;
+                outw |= o << (8 * u);
             }
-            mloc[k] = (uint8_t)m;
+            *reinterpret_cast<uint32_t*>(S.out + i0) = outw;   // stuck before the op: stuck after it
         }
+        const int incl = warp_incl_sum((int)cnt);
+        excl[k] = incl - (int)cnt;
+        if (lane == 31) S.cnt[k * NW + warp] = (uint16_t)incl;
     }
     __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the live counts in (step, warp) = position order
+        constexpr int C = STEPS * NW;
+        constexpr int PER = (C + 31) / 32;
+        int v[PER];
+        int sum = 0;
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const int i = k * NT + tid;
-        if (i < n) {
-            kb[i] = mloc[k];
-            S.keyB[pad(i)] = keyloc[k];
+        for (int u = 0; u < PER; ++u) {
+            const int idx = lane * PER + u;
+            v[u] = idx < C ? S.cnt[idx] : 0;
+            sum += v[u];
+        }
+        const int incl = warp_incl_sum(sum);
+        int run = incl - sum;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int idx = lane * PER + u;
+            if (idx < C) S.cnt[idx] = (uint16_t)run;
+            run += v[u];
+        }
+        if (lane == 31) S.nLive = incl;
+        if (lane == 0) S.nPend = 0;
+    }
+    __syncthreads();
+    if (S.nLive == 0 && !p.guard) {
+        // every op's variable was already stuck: outputs are all F
+        if (tid == 0) {
+            __threadfence();
+            atomicOr(p.regbits + (t >> 5), 1u << (t & 31));
+        }
+        if (n == T && p.bulk_ok) {
+            const uint4* src = reinterpret_cast<const uint4*>(S.out);
+            uint4* dst = reinterpret_cast<uint4*>(p.step + base);
+            for (int i = tid; i < T / 16; i += NT) dst[i] = src[i];
+        } else {
+            for (int i = tid; i < n; i += NT) p.step[base + i] = S.out[i];
+        }
+        return;
+    }
+    KeyT* keyIn = S.keyA;
+#pragma unroll
+    for (int k = 0; k < STEPS; ++k) {
+        if (!((liveBits >> (k * G)) & 0xFu)) continue;
+        const int i0 = (k * NT + tid) * G;
+        int c = S.cnt[k * NW + warp] + excl[k];
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            if (liveBits & (1u << (k * G + u))) {
+                const int i = i0 + u;
+                int32_t v = vraw[i];
+                if (v < 0 || v >= p.n_vars) v = 0;
+                keyIn[pad(c++)] = ((KeyT)(uint32_t)v << POS_BITS) | (KeyT)i;
+            }
         }
     }
+    const int nl = S.nLive;                // live ops: the sort and the scan see only these
     // own histogram row cleared before the first ranking
     const int D0 = 1 << p.digit_bits;
     for (int i = lane; i < D0; i += 32) S.hist[warp * D0 + i] = 0;
     __syncthreads();
+    PHASE(1)
 
     // ---- 3. stable LSD radix sort of the packed keys ------------------------
-    KeyT* kin = S.keyB;
-    KeyT* kout = S.keyA;
-    const uint32_t lt = lanemask_lt();
-    for (int pass = 0; pass < p.passes; ++pass) {
+    KeyT* kin = keyIn;
+    KeyT* kout = S.vbuf[b];
+    const bool rank_sort = nl <= RANK_SORT_MAX;
+    if (nl > 0 && rank_sort) {
+        // few live ops: each key's rank is the number of smaller keys (keys are
+        // unique: they carry the position)
+        if (tid < nl) {
+            const KeyT kj = kin[pad(tid)];
+            int r = 0;
+            for (int i = 0; i < nl; ++i) r += kin[pad(i)] < kj;
+            kout[pad(r)] = kj;
+        }
+        __syncthreads();
+        KeyT* tk = kin;
+        kin = kout;
+        kout = tk;
+    }
+    for (int pass = 0; pass < (nl && !rank_sort ? p.passes : 0); ++pass) {
         const int D = 1 << p.digit_bits;
         const int shift = POS_BITS + pass * p.digit_bits;
         uint16_t* hrow = S.hist + warp * D;
@@ -175,7 +298,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int pos = warp * 32 * E + e * 32 + lane;
-            const bool ok = pos < n;
+            const bool ok = pos < nl;
             const KeyT key = ok ? kin[pad(pos)] : (KeyT)0;
             kk[e] = key;
             const uint32_t dig = ok ? (uint32_t)((key >> shift) & (KeyT)(D - 1)) : 0xFFFFFFFFu;
@@ -210,7 +333,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int pos = warp * 32 * E + e * 32 + lane;
-            if (pos < n) {
+            if (pos < nl) {
                 const uint32_t dig = (uint32_t)((kk[e] >> shift) & (KeyT)(D - 1));
                 kout[pad(hrow[dig] + lr[e])] = kk[e];
             }
@@ -220,6 +343,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
         kin = kout;
         kout = tk;
     }
+    PHASE(2)
     const KeyT* K = kin;                       // sorted keys
     uint32_t* pend = reinterpret_cast<uint32_t*>(kout);   // the free buffer
     auto kvar = [&](int j) -> uint32_t { return (uint32_t)(K[pad(j)] >> POS_BITS); };
@@ -231,14 +355,14 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
     uint32_t headMask = 0, lastMask = 0;
     uint32_t ffv[E];
     {
-        uint32_t prev = (j0 > 0 && j0 - 1 < n) ? kvar(j0 - 1) : 0xFFFFFFFFu;
-        uint32_t cur = (j0 < n) ? kvar(j0) : 0xFFFFFFFEu;
+        uint32_t prev = (j0 > 0 && j0 - 1 < nl) ? kvar(j0 - 1) : 0xFFFFFFFFu;
+        uint32_t cur = (j0 < nl) ? kvar(j0) : 0xFFFFFFFEu;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             const int j = j0 + k;
-            const uint32_t nxt = (j + 1 < n) ? kvar(j + 1) : 0xFFFFFFFDu;
+            const uint32_t nxt = (j + 1 < nl) ? kvar(j + 1) : 0xFFFFFFFDu;
             ffv[k] = 0xFFFFFFFFu;
-            if (j < n) {
+            if (j < nl) {
                 if (cur != prev) headMask |= 1u << k;
                 if (nxt != cur) {
                     lastMask |= 1u << k;
@@ -262,8 +386,8 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
 #pragma unroll
     for (int k = 0; k < E; ++k) {
         const int j = j0 + k;
-        if (j < n) {
-            const uint32_t m = kb[kpos(j)];
+        if (j < nl) {
+            const uint32_t m = S.mel[kpos(j)];
             if (headMask & (1u << k)) {
                 acc = m;
             } else {
@@ -305,7 +429,6 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
             uint32_t xv = __shfl_up_sync(0xffffffffu, wv, 1);
             if (lane == 0) { xf = 0; xv = ID; }
             if (lane < NW) { S.segF[lane] = (uint8_t)xf; S.segV[lane] = (uint8_t)xv; }
-            if (lane == 0) S.nPend = 0;
         }
         __syncthreads();
         carry = fe ? ve : comp_of(S.comp, S.segV[warp], ve);
@@ -320,6 +443,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
     }
     const int runBase = block_excl_sum<NT>(nHeads, S.scanTmp, nullptr);
     auto run_id = [&](int k) { return runBase - 1 + __popc(headMask & ((2u << k) - 1)); };
+    PHASE(3)
 
     // ---- 5a. run entry: stuck shortcut, or a node in the variable's list ----
     const uint32_t nodeBase = (uint32_t)t * (uint32_t)T;
@@ -387,6 +511,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
     }
     __syncthreads();
 
+    PHASE(4)
     // ---- 5b. registration frontier ------------------------------------------
     // bit t of regbits is set once tile t's nodes are all in their lists;
     // *front = F means every tile < F has registered.  Only tiles that look
@@ -418,6 +543,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
         __threadfence();
     }
 
+    PHASE(5)
     // ---- 5c. look-back along the lists, PW runs per thread in step -----------
     for (int lo = 0; lo < nPend; lo += NT * PW) {
         uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW];
@@ -472,11 +598,12 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
     }
     __syncthreads();
 
+    PHASE(6)
     // ---- 6. outputs in original order; first faults --------------------------
 #pragma unroll
     for (int k = 0; k < E; ++k) {
         const int j = j0 + k;
-        if (j < n) {
+        if (j < nl) {
             const uint32_t e = S.runEntry[run_id(k)];
             const uint32_t pre = S.app[getb(xmw, k) * 8 + e];
             const uint32_t post = S.app[getb(pmw, k) * 8 + e];
@@ -484,7 +611,9 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
             S.out[pos] = (uint8_t)(p.pre_mode ? pre : post);
             if (post == ST_F && pre != ST_F) {
                 const uint32_t gi = (uint32_t)(base + pos);
-                atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j), gi);
+                const uint32_t v = kvar(j);
+                atomicMin(reinterpret_cast<uint32_t*>(p.vff) + v, gi);
+                atomicOr(p.fbits + (v >> 5), 1u << (v & 31));
                 atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
             }
         }
@@ -499,6 +628,22 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, cons
     } else {
         for (int i = tid; i < n; i += NT) p.step[base + i] = S.out[i];
     }
+    PHASE(7)
+#undef PHASE
+}
+
+template <typename KeyT, int T, int NT>
+__device__ __forceinline__ void issue_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, int b, int t)
+{
+    const int64_t base = (int64_t)t * T;
+    S.viaBulk[b] = 0;
+    if (t < p.n_tiles && base + T <= p.n_ops && p.bulk_ok) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&S.mbar[b], (uint32_t)(T + 4 * T));
+        bulk_g2s(S.kind[b], p.kind_side + base, T, &S.mbar[b]);
+        bulk_g2s(S.vbuf[b], p.var + base, 4 * T, &S.mbar[b]);
+        S.viaBulk[b] = 1;
+    }
 }
 
 template <typename KeyT, int T, int NT>
@@ -506,47 +651,46 @@ __global__ void __launch_bounds__(NT, 3) scan_trace_kernel(const ScanParams p)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     ScanSmem<KeyT, T, NT>& S = *reinterpret_cast<ScanSmem<KeyT, T, NT>*>(smem_raw);
+    uint32_t* fsm = reinterpret_cast<uint32_t*>(smem_raw + sizeof(ScanSmem<KeyT, T, NT>));
     const int tid = threadIdx.x;
     for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += NT) S.comp[i] = p.tab.comp[i];
     for (int i = tid; i < MAX_ELEMS * 8; i += NT) S.app[i] = p.tab.app[i];
     for (int i = tid; i < 256; i += NT) S.elem_of[i] = p.tab.elem_of[i];
+    for (int i = tid; i < p.fbw; i += NT) fsm[i] = __ldcg(p.fbits + i);
     if (tid == 0) {
-        mbar_init(&S.mbar, 1);
+        mbar_init(&S.mbar[0], 1);
         fence_mbar_init();
-        S.tile = (int)atomicAdd(p.tile_counter, 1u);
     }
-    __syncthreads();
     uint32_t parity = 0;
-    for (;;) {
-        const int t = S.tile;
-        if (t >= p.n_tiles) break;
-        uint32_t t_next = 0;
+    long long last = clock64();
+    // A CTA takes the next tile id only when it starts that tile: every tile
+    // below an id being processed has then started too, so it reaches its
+    // registration within one pre-registration phase (no queued tiles, no
+    // convoys of waits through other CTAs' queues).
+    for (uint32_t iter = 0;; ++iter) {
         if (tid == 0) {
-            // stage the tile (bulk copies for full, aligned tiles), then fetch
-            // the next tile id: its latency hides behind this tile's work
-            const int64_t base = (int64_t)t * T;
-            S.viaBulk = 0;
-            if (base + T <= p.n_ops && p.bulk_ok) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&S.mbar, (uint32_t)(T + 4 * T));
-                bulk_g2s(S.kind, p.kind_side + base, T, &S.mbar);
-                bulk_g2s(S.keyA, p.var + base, 4 * T, &S.mbar);
-                S.viaBulk = 1;
-            }
-            t_next = atomicAdd(p.tile_counter, 1u);
+            const int t = (int)atomicAdd(p.tile_counter, 1u);
+            S.tile[0] = t;
+            issue_tile<KeyT, T, NT>(p, S, 0, t);
         }
         __syncthreads();
+        const int t = S.tile[0];
+        if (t >= p.n_tiles) break;
         bool ok = true;
-        if (S.viaBulk) {
-            ok = mbar_wait_bounded(&S.mbar, parity, p.err);
+        if (S.viaBulk[0]) {
+            ok = mbar_wait_bounded(&S.mbar[0], parity, p.err);
             parity ^= 1;
         }
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) mbar_wait_bounded(&S.mbar, parity ^ 1, p.err);   // drain, bounded
+            if (tid == 0) mbar_wait_bounded(&S.mbar[0], parity ^ 1, p.err);   // drain, bounded
             break;
         }
-        process_tile<KeyT, T, NT>(p, S, t);
-        if (tid == 0) S.tile = (int)t_next;
+        if (p.phase_on && tid == 0) {
+            const long long now = clock64();
+            atomicAdd(&g_scan_phase_cycles[0], (unsigned long long)(now - last));
+            last = now;
+        }
+        process_tile<KeyT, T, NT>(p, S, fsm, t, 0, iter, last);
         __syncthreads();
     }
 }
@@ -568,17 +712,21 @@ __global__ void finalize_trace_kernel(const int32_t* __restrict__ vff, const uin
 }
 
 template <typename KeyT>
-int launch_kernel(const ScanParams& p, const ScanLaunch& L, cudaStream_t s)
+int launch_kernel(ScanParams p, const ScanLaunch& L, cudaStream_t s)
 {
-    const size_t smem = sizeof(ScanSmem<KeyT, TILE, THREADS>);
-    static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !attr_set[dev]) {
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int64_t room = ((int64_t)max_optin - (int64_t)sizeof(ScanSmem<KeyT, TILE, THREADS>) - 1024) / 16 * 4;
+    if (p.fbw > room) p.fbw = room > 0 ? (int)room : 0;          // shared bitmap words (multiple of 4)
+    const size_t smem = sizeof(ScanSmem<KeyT, TILE, THREADS>) + 4 * (size_t)p.fbw;
+    static size_t attr_set[64] = {};
+    if (dev >= 64 || attr_set[dev] < smem) {
         if (cudaFuncSetAttribute(scan_trace_kernel<KeyT, TILE, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return AMC_E_CUDA;
-        attr_set[dev] = true;
+        if (dev < 64) attr_set[dev] = smem;
     }
     int n_sm = 0, per_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -598,6 +746,23 @@ int launch_kernel(const ScanParams& p, const ScanLaunch& L, cudaStream_t s)
 
 int scan_tile_size() { return TILE; }
 
+namespace {
+bool g_phase_on = false;
+}
+
+int scan_phase_profile(int enable, unsigned long long* host_out)
+{
+    if (host_out &&
+        cudaMemcpyFromSymbol(host_out, g_scan_phase_cycles, sizeof(unsigned long long) * N_PHASES) != cudaSuccess)
+        return AMC_E_CUDA;
+    if (enable >= 0) {
+        g_phase_on = enable != 0;
+        unsigned long long z[N_PHASES] = {};
+        if (cudaMemcpyToSymbol(g_scan_phase_cycles, z, sizeof(z)) != cudaSuccess) return AMC_E_CUDA;
+    }
+    return AMC_OK;
+}
+
 size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars)
 {
     const int64_t n_tiles = (n_ops + TILE - 1) / TILE;
@@ -606,6 +771,7 @@ size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars)
     b += align_up(4 * (size_t)n_tiles * TILE, 256);         // node_next
     b += align_up((size_t)n_tiles * TILE, 256);             // node_status
     b += align_up(4 * (size_t)((n_tiles + 31) / 32), 256);  // registration bits
+    b += align_up(16 * (size_t)((n_vars + 127) / 128), 256); // stuck bitmap
     b += 256;                                               // tile counter, frontier
     return b;
 }
@@ -624,6 +790,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.guard = L.guard;
     p.pre_mode = L.pre_mode;
     p.err = L.err;
+    p.phase_on = g_phase_on;
     p.tab = host_tables();
     p.n_tiles = (int)((L.n_ops + TILE - 1) / TILE);
     uint8_t* w = static_cast<uint8_t*>(L.workspace);
@@ -636,6 +803,17 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.regbits = reinterpret_cast<uint32_t*>(w);
     const size_t regbytes = 4 * (size_t)((p.n_tiles + 31) / 32);
     w += align_up(regbytes, 256);
+    p.fbits = reinterpret_cast<uint32_t*>(w);
+    const size_t fbytes = 16 * (size_t)((L.n_vars + 127) / 128);
+    w += align_up(fbytes, 256);
+    {
+        // shared copy of the stuck bitmap: the first fb_max_bits variables
+        const int64_t words = (int64_t)(fbytes / 4);
+        int64_t bits = L.fb_max_bits ? L.fb_max_bits : DEFAULT_FB_BITS;
+        if (const char* e = getenv("AMC_SCAN_FB_BITS")) bits = atoll(e);       // tuning override
+        const int64_t cap = bits > 0 ? bits / 32 : 0;
+        p.fbw = (int)(words < cap ? words : cap);
+    }
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
     // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
@@ -651,6 +829,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
     if (L.n_ops > 0) {
         if (cudaMemsetAsync(p.regbits, 0, regbytes, s) != cudaSuccess) return AMC_E_CUDA;
+        if (fbytes && cudaMemsetAsync(p.fbits, 0, fbytes, s) != cudaSuccess) return AMC_E_CUDA;
         if (cudaMemsetAsync(p.tile_counter, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
         // keys pack (var << 12 | position): 32-bit while var ids fit 20 bits
         const int rc = kb + POS_BITS <= 32 ? launch_kernel<uint32_t>(p, L, s) : launch_kernel<uint64_t>(p, L, s);

@@ -21,12 +21,15 @@ struct ScanParams {
     uint32_t* node_next;        // [n_tiles * T]
     uint8_t* node_status;       // [n_tiles * T]
     uint32_t* regbits;          // bit t set: tile t's nodes are in their lists
+    uint32_t* fbits;            // bit v set: variable v is known to be stuck
+    int fbw;                    // words of fbits copied to shared memory (multiple of 4)
     uint32_t* tile_counter;
     uint32_t* front;            // every tile < *front has registered
     int n_tiles;
     int passes;
     int digit_bits;
     int bulk_ok;
+    int phase_on;               // accumulate per-phase cycle counters
     Tables tab;
 };
 
@@ -46,10 +49,14 @@ struct ScanLaunch {
     void* workspace = nullptr;
     int max_ctas = 0;                   // 0 = one wave of resident CTAs
     int profile = 0;                    // bit 0: record the start event, bit 1: the stop event
+    int fb_max_bits = 0;                // variables covered by the shared stuck bitmap (0 = default)
 };
 
 int scan_tile_size();
 size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars);
 int launch_scan_trace(const ScanLaunch& L, cudaStream_t s);
+// enable >= 0: switch phase counting on/off and zero the counters; host_out
+// (nullable): copy the 8 counters (cycles summed over CTAs).
+int scan_phase_profile(int enable, unsigned long long* host_out);
 
 }  // namespace amc
