@@ -413,10 +413,11 @@ def run_programs(args):
         P_ = lambda x: ctypes.c_void_p(x)
 
         def plain():
+            # one launch per program: the CSR arrays are offset to the
+            # program, token and mask buffers stay whole (absolute offsets)
             for i in range(P):
-                t0 = int(offs[i])
-                L.amc_check_batch(P_(tok.data_ptr() + t0), P_(pay.data_ptr() + 4 * t0), P_(off.data_ptr() + 8 * i),
-                                  P_(nv.data_ptr() + 4 * i), P_(vo.data_ptr() + 8 * i), 1, int(offs[i + 1] - t0),
+                L.amc_check_batch(P_(tok.data_ptr()), P_(pay.data_ptr()), P_(off.data_ptr() + 8 * i),
+                                  P_(nv.data_ptr() + 4 * i), P_(vo.data_ptr() + 8 * i), 1, n_tok,
                                   P_(out["step_mask"].data_ptr()), P_(out["final_mask"].data_ptr()),
                                   P_(out["prog_first_fault"].data_ptr() + 8 * i), 0, P_(ws.data_ptr()), ws.numel(),
                                   sp)

@@ -95,12 +95,13 @@ AMC_API int amc_sync_status(void* stream);
  * as void*; NULL, NULL turns it off).  Returns AMC_OK. */
 AMC_API int amc_set_profile_events(void* start_event, void* stop_event);
 
-/* Profiling aid (no counterpart in the paper): cycle counters of the trace
- * scan kernel's phases (0 tile staging, 1 decode and compaction, 2 sort,
- * 3 segmented scan, 4 run entry and list insertion, 5 registration frontier,
- * 6 look-back, 7 outputs), summed over CTAs.  enable >= 0 switches counting
- * on (1) or off (0) for later launches and zeroes the counters; host_out
- * (8 host uint64, nullable) receives the current counters. */
+/* Profiling aid (no counterpart in the paper): counters of the trace scan
+ * kernel, summed over CTAs: cycles per phase (0 tile staging, 1 decode and
+ * compaction, 2 sort, 3 segmented scan, 4 run entry and list insertion,
+ * 5 registration frontier, 6 look-back, 7 outputs), then 8 tiles, 9 tiles
+ * with live ops, 10 live ops, 11 tiles with runs that look back.  enable >= 0
+ * switches counting on (1) or off (0) for later launches and zeroes the
+ * counters; host_out (12 host uint64, nullable) receives the counters. */
 AMC_API int amc_debug_scan_phases(int enable, uint64_t* host_out);
 
 /* ------------------------------------------------------------------------ */

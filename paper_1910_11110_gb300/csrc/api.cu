@@ -9,6 +9,7 @@
 #include "scan_trace.cuh"
 #include "translate.cuh"
 #include "batch.cuh"
+#include "autotune.cuh"
 
 using namespace amc;
 
@@ -120,7 +121,15 @@ int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
     L.err = err;
     L.workspace = workspace;
     L.profile = 3;
-    return launch_scan_trace(L, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // candidates: stuck bitmap in shared memory (2^20 variables, one CTA per
+    // SM), read through L1 (more CTAs per SM), or none
+    static const int fb[3] = {1 << 20, -2, -1};
+    return autotune_run(shape_key("trace", n_ops, n_vars, 0), 3, 0, s, [&](int i) {
+        ScanLaunch C = L;
+        C.fb_max_bits = fb[i];
+        return launch_scan_trace(C, s);
+    });
 }
 
 size_t amc_check_guarded_trace_workspace(int64_t n_ops, int32_t n_vars)
@@ -161,6 +170,9 @@ int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_
     A.err = err;
     A.workspace = workspace;
     A.profile = 1;          // the profiled span covers both scans
+    static const int fb[3] = {1 << 20, -2, -1};
+    const int pick = autotune_lookup(shape_key("trace", n_ops, n_vars, 0));
+    A.fb_max_bits = fb[pick >= 0 && pick < 3 ? pick : 0];
     rc = launch_scan_trace(A, s);
     if (rc) return rc;
     // pass 2: GT resolved from the pre-status of the EN that follows it
@@ -256,17 +268,37 @@ int amc_check_batch(const uint8_t* tok_kind_side, const int32_t* tok_payload, co
     B.workspace = workspace;
     B.profile = 3;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (!graph_capture || s == nullptr) return launch_batch(B, s);
+    // candidates: longest-first queue or input order, one or two waves of CTAs
+    int n_sm = 0, dev0 = 0;
+    cudaGetDevice(&dev0);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev0);
+    auto shape = [&](BatchLaunch X, int i) {
+        X.longest_first = (i & 1) ? 0 : 1;
+        X.max_ctas = (i & 2) ? n_sm : 0;
+        return X;
+    };
+    const std::string key = shape_key("batch", n_tokens, n_progs, 0);
+    if (!graph_capture || s == nullptr)
+        return autotune_run(key, 4, 0, s, [&](int i) { return launch_batch(shape(B, i), s); });
+    {
+        // tune outside the capture first (no-op when the key is cached)
+        const int rc0 = autotune_lookup(key) >= 0
+                            ? AMC_OK
+                            : autotune_run(key, 4, 0, s, [&](int i) { return launch_batch(shape(B, i), s); });
+        if (rc0) return rc0;
+        const int pick = autotune_lookup(key);
+        B = shape(B, pick >= 0 ? pick : 0);
+    }
     int dev = 0;
     cudaGetDevice(&dev);
-    std::vector<uintptr_t> key = {(uintptr_t)dev,          (uintptr_t)s,           (uintptr_t)tok_kind_side,
+    std::vector<uintptr_t> gkey = {(uintptr_t)dev,          (uintptr_t)s,           (uintptr_t)tok_kind_side,
                                   (uintptr_t)tok_payload,  (uintptr_t)prog_tok_off, (uintptr_t)prog_nvars,
                                   (uintptr_t)prog_var_off, (uintptr_t)n_progs,      (uintptr_t)n_tokens,
                                   (uintptr_t)step_mask,    (uintptr_t)final_mask,   (uintptr_t)prog_first_fault,
                                   (uintptr_t)workspace};
     GraphCache& gc = graph_cache();
     std::lock_guard<std::mutex> lock(gc.mu);
-    auto it = gc.execs.find(key);
+    auto it = gc.execs.find(gkey);
     if (it == gc.execs.end()) {
         B.profile = 0;
         cudaGraph_t g = nullptr;
@@ -282,7 +314,7 @@ int amc_check_batch(const uint8_t* tok_kind_side, const int32_t* tok_payload, co
         const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) return AMC_E_CUDA;
-        it = gc.execs.emplace(key, ex).first;
+        it = gc.execs.emplace(gkey, ex).first;
     }
     profile_begin(s);
     const cudaError_t le = cudaGraphLaunch(it->second, s);

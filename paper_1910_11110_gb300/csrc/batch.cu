@@ -47,7 +47,8 @@ __device__ void run_program(const BatchParams& p, int64_t prog, uint8_t* smM, ui
     const int32_t nv = p.prog_nvars[prog];
     uint8_t* gM = p.final_mask + p.prog_var_off[prog];
     uint8_t* M = SMEM ? smM : gM;
-    if (t1 < t0 || nv < 0 || p.prog_var_off[prog + 1] - p.prog_var_off[prog] != nv) {
+    if (t0 < 0 || t1 < t0 || t1 > p.n_tokens || nv < 0 || p.prog_var_off[prog] < 0 ||
+        p.prog_var_off[prog + 1] - p.prog_var_off[prog] != nv) {
         if (lane == 0) raise_error(p.err, AMC_E_INVALID);
         return;
     }

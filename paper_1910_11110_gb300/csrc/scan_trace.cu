@@ -47,7 +47,7 @@ constexpr uint32_t NODE_AGG = 0x40;
 constexpr uint32_t NODE_INCL = 0x80;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 constexpr int DEFAULT_FB_BITS = 1 << 20;      // shared stuck bitmap: 128 KB
-constexpr int N_PHASES = 8;
+constexpr int N_PHASES = 12;
 constexpr int RANK_SORT_MAX = 128;             // live ops below which a rank sort replaces the radix passes
 
 }  // namespace
@@ -118,13 +118,19 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
         }
         __syncthreads();
     }
+    // L1-cached copy of the stuck bitmap: the two global copies alternate every
+    // 64 tiles of this CTA, so cached lines never get older than that
+    const uint32_t* fbl1 = p.fbits + ((refresh >> 6) & 1u) * (uint32_t)p.fbits_words;
     // rolling refresh of the shared copy of the stuck bitmap (16 bytes per
     // thread per tile).  Bits are only ever set, so a stale word is merely
     // less complete, never wrong.
     if (p.fbw) {
         const uint32_t nq = (uint32_t)p.fbw / 4;
-        const uint32_t q = (refresh * NT + tid) % nq;
-        reinterpret_cast<uint4*>(fsm)[q] = __ldcg(reinterpret_cast<const uint4*>(p.fbits) + q);
+#pragma unroll
+        for (uint32_t r = 0; r < 2; ++r) {
+            const uint32_t q = ((2 * refresh + r) * NT + tid) % nq;
+            reinterpret_cast<uint4*>(fsm)[q] = __ldcg(reinterpret_cast<const uint4*>(p.fbits) + q);
+        }
     }
 
     // ---- 2. decode: four consecutive ops per thread and step (one 32-bit load
@@ -170,7 +176,11 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                         gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
                         if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
                     }
-                    const bool stuck = uv < (uint32_t)p.fbw * 32u && ((fsm[uv >> 5] >> (uv & 31)) & 1u);
+                    bool stuck;
+                    if (p.fb_mode == 2)          // read-only path: cached in L1, one of two copies
+                        stuck = ((__ldg(fbl1 + (uv >> 5)) >> (uv & 31)) & 1u) != 0;
+                    else
+                        stuck = uv < (uint32_t)p.fbw * 32u && ((fsm[uv >> 5] >> (uv & 31)) & 1u);
                     if (!stuck) {
                         uint32_t m = S.elem_of[ks];
                         if (m == ELEM_GT) {
@@ -229,6 +239,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
         if (lane == 0) S.nPend = 0;
     }
     __syncthreads();
+    if (p.phase_on && tid == 0) atomicAdd(&g_scan_phase_cycles[8], 1ull);
     if (S.nLive == 0 && !p.guard) {
         // every op's variable was already stuck: outputs are all F
         if (tid == 0) {
@@ -261,6 +272,10 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
         }
     }
     const int nl = S.nLive;                // live ops: the sort and the scan see only these
+    if (p.phase_on && tid == 0) {
+        atomicAdd(&g_scan_phase_cycles[9], 1ull);
+        atomicAdd(&g_scan_phase_cycles[10], (unsigned long long)nl);
+    }
     // own histogram row cleared before the first ranking
     const int D0 = 1 << p.digit_bits;
     for (int i = lane; i < D0; i += 32) S.hist[warp * D0 + i] = 0;
@@ -453,6 +468,9 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             const int r = run_id(k);
             if (ffv[k] < (uint32_t)base) {
                 S.runEntry[r] = ST_F;
+                // stuck before this tile, hence before every later tile of this CTA
+                const uint32_t v = kvar(j0 + k);
+                if (v < (uint32_t)p.fbw * 32u) atomicOr(fsm + (v >> 5), 1u << (v & 31));
             } else {
                 const uint32_t agg = getb(pmw, k);
                 S.runEntry[r] = RUN_PENDING;
@@ -464,6 +482,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     }
     __syncthreads();
     const int nPend = S.nPend;
+    if (p.phase_on && tid == 0 && nPend) atomicAdd(&g_scan_phase_cycles[11], 1ull);
     constexpr int PW = 4;                 // pending runs a thread handles in step
     for (int lo = 0; lo < nPend; lo += NT * PW) {
         // insert each node into its variable's list (sorted by decreasing
@@ -614,6 +633,8 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 const uint32_t v = kvar(j);
                 atomicMin(reinterpret_cast<uint32_t*>(p.vff) + v, gi);
                 atomicOr(p.fbits + (v >> 5), 1u << (v & 31));
+                atomicOr(p.fbits + p.fbits_words + (v >> 5), 1u << (v & 31));
+                if (v < (uint32_t)p.fbw * 32u) atomicOr(fsm + (v >> 5), 1u << (v & 31));
                 atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
             }
         }
@@ -771,7 +792,7 @@ size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars)
     b += align_up(4 * (size_t)n_tiles * TILE, 256);         // node_next
     b += align_up((size_t)n_tiles * TILE, 256);             // node_status
     b += align_up(4 * (size_t)((n_tiles + 31) / 32), 256);  // registration bits
-    b += align_up(16 * (size_t)((n_vars + 127) / 128), 256); // stuck bitmap
+    b += 2 * align_up(16 * (size_t)((n_vars + 127) / 128), 256); // stuck bitmap, two copies
     b += 256;                                               // tile counter, frontier
     return b;
 }
@@ -804,13 +825,15 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     const size_t regbytes = 4 * (size_t)((p.n_tiles + 31) / 32);
     w += align_up(regbytes, 256);
     p.fbits = reinterpret_cast<uint32_t*>(w);
-    const size_t fbytes = 16 * (size_t)((L.n_vars + 127) / 128);
-    w += align_up(fbytes, 256);
+    const size_t fbytes = 2 * align_up(16 * (size_t)((L.n_vars + 127) / 128), 256);
+    p.fbits_words = (int)(fbytes / 8);
+    w += fbytes;
     {
         // shared copy of the stuck bitmap: the first fb_max_bits variables
         const int64_t words = (int64_t)(fbytes / 4);
         int64_t bits = L.fb_max_bits ? L.fb_max_bits : DEFAULT_FB_BITS;
         if (const char* e = getenv("AMC_SCAN_FB_BITS")) bits = atoll(e);       // tuning override
+        p.fb_mode = bits > 0 ? 1 : (bits == -2 ? 2 : 0);    // -2: L1-cached global copies
         const int64_t cap = bits > 0 ? bits / 32 : 0;
         p.fbw = (int)(words < cap ? words : cap);
     }

@@ -23,6 +23,8 @@ struct ScanParams {
     uint32_t* regbits;          // bit t set: tile t's nodes are in their lists
     uint32_t* fbits;            // bit v set: variable v is known to be stuck
     int fbw;                    // words of fbits copied to shared memory (multiple of 4)
+    int fbits_words;            // words per copy of fbits (two copies)
+    int fb_mode;                // 0 none, 1 shared copy, 2 L1-cached global copies
     uint32_t* tile_counter;
     uint32_t* front;            // every tile < *front has registered
     int n_tiles;
@@ -49,7 +51,8 @@ struct ScanLaunch {
     void* workspace = nullptr;
     int max_ctas = 0;                   // 0 = one wave of resident CTAs
     int profile = 0;                    // bit 0: record the start event, bit 1: the stop event
-    int fb_max_bits = 0;                // variables covered by the shared stuck bitmap (0 = default)
+    int fb_max_bits = 0;                // shared stuck bitmap size in variables (0 = default,
+                                        // -1 = no bitmap, -2 = bitmap read through L1)
 };
 
 int scan_tile_size();

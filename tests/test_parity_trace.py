@@ -152,3 +152,26 @@ def test_zipf_trace_full_size_sampled(amc, oracle_mod):
     assert np.array_equal(e_vff, vff)
     assert e_ff == ff
     assert np.array_equal(e_step, step)
+
+
+def test_autotune_cache_file(tmp_path):
+    """The first call of a shape times the candidate launch shapes and records
+    the choice; outputs are identical whichever candidate runs."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = (
+        "import sys; sys.path.insert(0, '.'); import torch, numpy as np, workloads, oracle;"
+        "import paper_1910_11110_gb300 as amc; amc.build();"
+        "ks, var = workloads.trace_zipf(300_000, 1 << 16, seed=4, device='cuda');"
+        "a = amc.check_trace(ks, var, 1 << 16); b = amc.check_trace(ks, var, 1 << 16);"
+        "assert amc.sync_status() == 0;"
+        "e = oracle.check_trace(ks.cpu().numpy(), var.cpu().numpy(), 1 << 16);"
+        "assert np.array_equal(a['step_status'].cpu().numpy(), e[0]);"
+        "assert torch.equal(a['step_status'], b['step_status'])")
+    env = dict(__import__("os").environ, AMC_AUTOTUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code], cwd=__import__("os").path.dirname(__import__("os").path.dirname(__file__)),
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = cache.read_text().split()
+    assert lines and lines[0].startswith("trace:")
