@@ -69,7 +69,10 @@ struct __align__(16) ScanSmem {
     uint8_t out[T];
     uint8_t runEntry[T];
     uint8_t runAgg[T];
-    uint16_t hist[(NT / 32) << MAX_DIGIT_BITS];
+    union {                          // the radix histogram is free once the keys are sorted
+        uint16_t hist[(NT / 32) << MAX_DIGIT_BITS];
+        uint32_t runHead[T];         // list head of each run's variable, loaded with the scan
+    };
     uint8_t comp[MAX_ELEMS * MAX_ELEMS];
     uint8_t app[MAX_ELEMS * 8];
     uint8_t elem_of[256];
@@ -85,6 +88,10 @@ struct __align__(16) ScanSmem {
     uint32_t frontVal;
     // followed (dynamic shared memory) by the stuck bitmap: fbw 32-bit words
 };
+static_assert(sizeof(uint16_t) * ((THREADS / 32) << MAX_DIGIT_BITS) >= sizeof(uint32_t) * TILE,
+              "run heads must fit in the histogram's space");
+// three CTAs per SM with 32-bit keys (228 KB of shared memory per SM, 1 KB reserved per CTA)
+static_assert(3 * (sizeof(ScanSmem<uint32_t, TILE, THREADS>) + 1024) <= 228 * 1024, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t comp_of(const uint8_t* comp, uint32_t a, uint32_t b)
 {
@@ -141,14 +148,38 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     constexpr int STEPS = E / G;
     uint32_t liveBits = 0;                 // bit 4k+u: op u of step k is live
     int excl[STEPS];
+    // all loads first: op bytes, ids and (L1 mode) bitmap words of every step
+    uint32_t kwa[STEPS];
+    int4 vva[STEPS];
+    uint32_t fwa[STEPS][G];
+#pragma unroll
+    for (int k = 0; k < STEPS; ++k) {
+        const int i0 = (k * NT + tid) * G;
+        kwa[k] = 0;
+        vva[k] = make_int4(0, 0, 0, 0);
+        if (i0 < n) {
+            kwa[k] = *reinterpret_cast<const uint32_t*>(kb + i0);
+            vva[k] = *reinterpret_cast<const int4*>(vraw + i0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < STEPS; ++k) {
+        const int32_t va[G] = {vva[k].x, vva[k].y, vva[k].z, vva[k].w};
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
+            fwa[k][u] = p.fb_mode == 2 ? __ldg(fbl1 + (uv >> 5))
+                                       : (uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : 0u);
+        }
+    }
 #pragma unroll
     for (int k = 0; k < STEPS; ++k) {
         const int g = k * NT + tid;
         const int i0 = g * G;
         uint32_t cnt = 0;
         if (i0 < n) {
-            const uint32_t kw = *reinterpret_cast<const uint32_t*>(kb + i0);
-            const int4 vv = *reinterpret_cast<const int4*>(vraw + i0);
+            const uint32_t kw = kwa[k];
+            const int4 vv = vva[k];
             const int32_t va[G] = {vv.x, vv.y, vv.z, vv.w};
             uint32_t outw = 0;
 #pragma unroll
@@ -176,11 +207,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                         gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
                         if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
                     }
-                    bool stuck;
-                    if (p.fb_mode == 2)          // read-only path: cached in L1, one of two copies
-                        stuck = ((__ldg(fbl1 + (uv >> 5)) >> (uv & 31)) & 1u) != 0;
-                    else
-                        stuck = uv < (uint32_t)p.fbw * 32u && ((fsm[uv >> 5] >> (uv & 31)) & 1u);
+                    const bool stuck = ((fwa[k][u] >> (uv & 31)) & 1u) != 0;
                     if (!stuck) {
                         uint32_t m = S.elem_of[ks];
                         if (m == ELEM_GT) {
@@ -368,7 +395,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     // that the segmented scan below hides their latency --------------------
     const int j0 = tid * E;
     uint32_t headMask = 0, lastMask = 0;
-    uint32_t ffv[E];
+    uint32_t ffv[E], hdv[E];
     {
         uint32_t prev = (j0 > 0 && j0 - 1 < nl) ? kvar(j0 - 1) : 0xFFFFFFFFu;
         uint32_t cur = (j0 < nl) ? kvar(j0) : 0xFFFFFFFEu;
@@ -377,11 +404,13 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             const int j = j0 + k;
             const uint32_t nxt = (j + 1 < nl) ? kvar(j + 1) : 0xFFFFFFFDu;
             ffv[k] = 0xFFFFFFFFu;
+            hdv[k] = NIL;
             if (j < nl) {
                 if (cur != prev) headMask |= 1u << k;
                 if (nxt != cur) {
                     lastMask |= 1u << k;
                     ffv[k] = __ldcg(reinterpret_cast<const unsigned int*>(p.vff) + cur);
+                    hdv[k] = __ldcg(p.head + cur);       // the list head, for the insertion
                 }
             }
             prev = cur;
@@ -475,6 +504,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 const uint32_t agg = getb(pmw, k);
                 S.runEntry[r] = RUN_PENDING;
                 S.runAgg[r] = (uint8_t)agg;
+                S.runHead[r] = hdv[k];
                 pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
                 p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | agg);
             }
@@ -499,7 +529,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 mine |= 1u << u;
                 node[u] = nodeBase + (e & 0xFFFFu);
                 var[u] = kvar((int)(e >> 16));
-                c[u] = __ldcg(p.head + var[u]);
+                c[u] = S.runHead[e & 0xFFFFu];           // prefetched; a stale value fails the CAS
             }
         }
 #pragma unroll
@@ -541,23 +571,30 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
         atomicOr(p.regbits + (t >> 5), 1u << (t & 31));
     }
     if (nPend > 0 || p.guard) {
+        // check every tile in [front, t) at once, 32 per word, starting from the
+        // frontier this CTA last knew (checking more tiles than needed is safe)
+        uint32_t f0 = min(S.frontVal, (uint32_t)t);
         for (uint32_t it = 0;; ++it) {
-            if (tid == 0) S.frontVal = ld_acquire(p.front);
-            __syncthreads();
-            const uint32_t f0 = S.frontVal;
-            if (f0 >= (uint32_t)t) break;
-            bool all = true;          // every tile in [front, t), 32 per word
-            for (uint32_t w = (f0 >> 5) + tid; w <= ((uint32_t)t - 1) >> 5; w += NT) {
+            bool all = true;
+            for (uint32_t w = (f0 >> 5) + tid; f0 < (uint32_t)t && w <= ((uint32_t)t - 1) >> 5; w += NT) {
                 const uint32_t lo = max(f0, w << 5), hi = min((uint32_t)t, (w << 5) + 32);
                 const uint32_t need = (hi - lo == 32) ? 0xFFFFFFFFu : (((1u << (hi - lo)) - 1u) << (lo & 31));
                 all &= (__ldcg(p.regbits + w) & need) == need;
             }
             if (__syncthreads_and(all)) {
-                if (tid == 0) { __threadfence(); atomicMax(p.front, (uint32_t)t); }
+                if (tid == 0) {
+                    __threadfence();
+                    atomicMax(p.front, (uint32_t)t);
+                    S.frontVal = (uint32_t)t;
+                }
                 break;
             }
             if (it > SPIN_LIMIT) { if (tid == 0) raise_error(p.err, AMC_E_TIMEOUT); break; }
-            __nanosleep(256);
+            __nanosleep(128);
+            if (tid == 0) S.frontVal = ld_acquire(p.front);
+            __syncthreads();
+            f0 = min(max(f0, S.frontVal), (uint32_t)t);
+            __syncthreads();
         }
         __threadfence();
     }
@@ -681,6 +718,7 @@ __global__ void __launch_bounds__(NT, 3) scan_trace_kernel(const ScanParams p)
     if (tid == 0) {
         mbar_init(&S.mbar[0], 1);
         fence_mbar_init();
+        S.frontVal = 0;
     }
     uint32_t parity = 0;
     long long last = clock64();
