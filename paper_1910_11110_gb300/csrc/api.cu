@@ -122,12 +122,15 @@ int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
     L.workspace = workspace;
     L.profile = 3;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // candidates: stuck bitmap in shared memory (2^20 variables, one CTA per
-    // SM), read through L1 (more CTAs per SM), or none
-    static const int fb[3] = {1 << 20, -2, -1};
-    return autotune_run(shape_key("trace", n_ops, n_vars, 0), 3, 0, s, [&](int i) {
+    // candidates: stuck bitmap read through L1 (three CTAs per SM), in shared
+    // memory (2^20 variables, one CTA per SM) or none, each with groups of up
+    // to 16 tiles per claim where few ops are live; or L1 and single tiles
+    static const int fb[4] = {-2, 1 << 20, -1, -2};
+    static const int grp[4] = {16, 16, 16, 1};
+    return autotune_run(shape_key("trace", n_ops, n_vars, 0), 4, 0, s, [&](int i) {
         ScanLaunch C = L;
         C.fb_max_bits = fb[i];
+        C.group_max = grp[i];
         return launch_scan_trace(C, s);
     });
 }
@@ -170,9 +173,12 @@ int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_
     A.err = err;
     A.workspace = workspace;
     A.profile = 1;          // the profiled span covers both scans
-    static const int fb[3] = {1 << 20, -2, -1};
+    // the choice tuned for plain traces of this shape, if any
+    static const int fb[4] = {-2, 1 << 20, -1, -2};
+    static const int grp[4] = {16, 16, 16, 1};
     const int pick = autotune_lookup(shape_key("trace", n_ops, n_vars, 0));
-    A.fb_max_bits = fb[pick >= 0 && pick < 3 ? pick : 0];
+    A.fb_max_bits = fb[pick >= 0 && pick < 4 ? pick : 0];
+    A.group_max = grp[pick >= 0 && pick < 4 ? pick : 0];
     rc = launch_scan_trace(A, s);
     if (rc) return rc;
     // pass 2: GT resolved from the pre-status of the EN that follows it

@@ -27,6 +27,14 @@
 //     look-back restricted to the tiles that touch the variable;
 //  6. outputs are written in original order (coalesced 16-byte stores), first
 //     faults by atomicMin.
+// Where few ops are live (the stuck bitmap filters nearly all of them) a CTA
+// takes up to 16 tiles per claim instead ("group path"): it streams them from
+// global memory, writes the stuck ops' outputs at once, and runs steps 3-6 once
+// for the live ops of the whole group, with runs split per tile so that nodes
+// and registration stay per tile.  The claim size follows the live ops per
+// tile the CTA saw lately; a group with more live ops than one tile's buffers
+// hold is processed tile by tile.  A look-back walk stops early once the
+// aggregates it has passed send every status to F.
 // The only waits are on the registration frontier and on the mbarrier, both
 // bounded; an expired wait raises AMC_E_TIMEOUT and the kernel carries on.
 #include <cstdlib>
@@ -49,6 +57,8 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 constexpr int DEFAULT_FB_BITS = 1 << 20;      // shared stuck bitmap: 128 KB
 constexpr int N_PHASES = 12;
 constexpr int RANK_SORT_MAX = 128;             // live ops below which a rank sort replaces the radix passes
+constexpr int GROUP_MAX = 16;                  // tiles per claim in the group path (positions fit 16 bits)
+constexpr int GROUP_LIVE_TARGET = 2048;        // expected live ops per group when choosing its size
 
 }  // namespace
 
@@ -64,9 +74,14 @@ struct __align__(16) ScanSmem {
     KeyT vbuf[1][T + T / 32];        // bulk target of the var ids (first 4T bytes); after the
                                      // decode it holds the live ops' packed keys
     KeyT keyA[T + T / 32];
-    uint8_t kind[1][T];              // op bytes
-    uint8_t mel[T];                  // element ids of live ops
-    uint8_t out[T];
+    union {
+        struct {
+            uint8_t kind[1][T];      // op bytes (tile path)
+            uint8_t out[T];          // output tile (tile path)
+        };
+        uint16_t livePos[T];         // group path: tile in group << 12 | position, per live op
+    };
+    uint8_t mel[T];                  // element ids of live ops (by position; by live index in groups)
     uint8_t runEntry[T];
     uint8_t runAgg[T];
     union {                          // the radix histogram is free once the keys are sorted
@@ -76,6 +91,7 @@ struct __align__(16) ScanSmem {
     uint8_t comp[MAX_ELEMS * MAX_ELEMS];
     uint8_t app[MAX_ELEMS * 8];
     uint8_t elem_of[256];
+    uint32_t constF;                 // bit e: element e sends every status to F
     int scanTmp[NT / 32 + 2];
     uint8_t segF[NT / 32];
     uint8_t segV[NT / 32];
@@ -86,6 +102,7 @@ struct __align__(16) ScanSmem {
     int nPend;
     int nLive;
     uint32_t frontVal;
+    int grp[1];                      // tiles in the current claim
     // followed (dynamic shared memory) by the stuck bitmap: fbw 32-bit words
 };
 static_assert(sizeof(uint16_t) * ((THREADS / 32) << MAX_DIGIT_BITS) >= sizeof(uint32_t) * TILE,
@@ -637,6 +654,12 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                     active &= ~(1u << u);
                 } else {
                     a[u] = comp_of(S.comp, sv[u] & 31u, a[u]);     // earlier tile first
+                    // F is absorbing: once the tiles passed so far send every
+                    // status to F, the entry is F whatever came before them
+                    if ((S.constF >> a[u]) & 1u) {
+                        st[u] = 0;
+                        active &= ~(1u << u);
+                    }
                 }
             }
 #pragma unroll
@@ -690,6 +713,606 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
 #undef PHASE
 }
 
+// Group path: G consecutive tiles taken in one claim and read straight from
+// global memory.  Ops on variables known to be stuck get F at once (written
+// with the rest of their output word); the live ops of all G tiles -- at most T
+// of them -- are sorted, scanned, inserted, registered and looked back
+// together.  Runs are (variable, tile) pairs, so list nodes and registration
+// bits stay per tile and other CTAs see exactly the tile path's protocol.
+// Returns false, having registered nothing, when the group holds more than T
+// live ops; the caller then runs its tiles through the tile path.
+template <typename KeyT, int T, int NT>
+__device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint32_t* fsm, const int t0, const int G,
+                              const uint32_t refresh, long long& last)
+{
+#define PHASE(k)                                                                                 \
+    if (p.phase_on && threadIdx.x == 0) {                                                        \
+        const long long now = clock64();                                                         \
+        atomicAdd(&g_scan_phase_cycles[k], (unsigned long long)(now - last));                     \
+        last = now;                                                                              \
+    }
+    constexpr int E = T / NT;
+    constexpr int NW = NT / 32;
+    constexpr int G4 = 4;
+    constexpr int STEPS = E / G4;
+    constexpr int C = STEPS * NW;            // (step, warp) counts per tile
+    static_assert(2 * C <= (T / NT) * (NT / 32), "two count rows");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t ID = 0;
+    const uint32_t lt = lanemask_lt();
+    const int64_t gbase = (int64_t)t0 * T;
+    const int nTiles = (int)min((int64_t)G, (int64_t)p.n_tiles - t0);
+
+    const uint32_t* fbl1 = p.fbits + ((refresh >> 6) & 1u) * (uint32_t)p.fbits_words;
+    if (p.fbw) {
+        const uint32_t nq = (uint32_t)p.fbw / 4;
+        for (uint32_t r = 0; r < 2u * (uint32_t)nTiles; ++r) {
+            const uint32_t q = ((2 * refresh + r) * NT + tid) % nq;
+            reinterpret_cast<uint4*>(fsm)[q] = __ldcg(reinterpret_cast<const uint4*>(p.fbits) + q);
+        }
+    }
+
+    // ---- 1-2. stream and decode the tiles; compact the live ops ------------
+    KeyT* const keyIn = S.keyA;
+    int total = 0;                           // live ops so far (the same in every thread)
+    for (int g = 0; g < nTiles; ++g) {
+        const int64_t base = gbase + (int64_t)g * T;
+        const int n = (int)min((int64_t)T, p.n_ops - base);
+        const bool vec = n == T && p.bulk_ok;
+        uint32_t kwa[STEPS];
+        int4 vva[STEPS];
+        uint32_t fwa[STEPS][G4];
+#pragma unroll
+        for (int k = 0; k < STEPS; ++k) {
+            const int i0 = (k * NT + tid) * G4;
+            kwa[k] = 0;
+            vva[k] = make_int4(0, 0, 0, 0);
+            if (vec) {
+                kwa[k] = __ldcs(reinterpret_cast<const unsigned int*>(p.kind_side + base + i0));
+                vva[k] = __ldcs(reinterpret_cast<const int4*>(p.var + base + i0));
+            } else if (i0 < n) {
+                int32_t va[G4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int u = 0; u < G4; ++u)
+                    if (i0 + u < n) {
+                        kwa[k] |= (uint32_t)p.kind_side[base + i0 + u] << (8 * u);
+                        va[u] = p.var[base + i0 + u];
+                    }
+                vva[k] = make_int4(va[0], va[1], va[2], va[3]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < STEPS; ++k) {
+            const int32_t va[G4] = {vva[k].x, vva[k].y, vva[k].z, vva[k].w};
+#pragma unroll
+            for (int u = 0; u < G4; ++u) {
+                const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
+                fwa[k][u] = p.fb_mode == 2 ? __ldg(fbl1 + (uv >> 5))
+                                           : (uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : 0u);
+            }
+        }
+        uint32_t liveBits = 0, melw[STEPS];
+        int excl[STEPS];
+        uint16_t* const cnt = S.cnt + (g & 1) * C;
+#pragma unroll
+        for (int k = 0; k < STEPS; ++k) {
+            const int i0 = (k * NT + tid) * G4;
+            uint32_t c = 0;
+            melw[k] = 0;
+            if (i0 < n) {
+                const uint32_t kw = kwa[k];
+                const int32_t va[G4] = {vva[k].x, vva[k].y, vva[k].z, vva[k].w};
+                uint32_t outw = 0;
+#pragma unroll
+                for (int u = 0; u < G4; ++u) {
+                    const int i = i0 + u;
+                    const uint32_t ks = (kw >> (8 * u)) & 0xFFu;
+                    uint32_t o = ST_F;
+                    if (i < n) {
+                        if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
+                        uint32_t uv = (uint32_t)va[u];
+                        if (va[u] < 0 || va[u] >= p.n_vars) {
+                            raise_error(p.err, AMC_E_RANGE);
+                            uv = 0;
+                        }
+                        bool gt_ok = true;
+                        if ((ks & 15u) == AMC_K_GT) {
+                            // GT must be followed by EN of the same side on another variable
+                            const int64_t gi = base + i;
+                            uint32_t nks = 0xFF;
+                            int32_t nv = (int32_t)uv;
+                            if (gi + 1 < p.n_ops) {
+                                nks = p.kind_side[gi + 1];
+                                nv = p.var[gi + 1];
+                            }
+                            gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
+                            if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
+                        }
+                        const bool stuck = ((fwa[k][u] >> (uv & 31)) & 1u) != 0;
+                        if (!stuck) {
+                            uint32_t m = S.elem_of[ks];
+                            if (m == ELEM_GT) {
+                                if (!gt_ok || p.pre_mode) {
+                                    m = ID;
+                                } else if (!p.guard) {
+                                    raise_error(p.err, AMC_E_INVALID);
+                                    m = ID;
+                                } else {
+                                    const uint32_t gs = p.guard[base + i + 1];
+                                    const int side = ks >> 4;
+                                    const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
+                                    m = valid ? ID : p.tab.pull_of_side[side];
+                                }
+                            } else if (m == ELEM_BAD) {
+                                m = ID;
+                            }
+                            melw[k] |= m << (8 * u);
+                            liveBits |= 1u << (k * G4 + u);
+                            ++c;
+                            o = 0;                   // written once the run's entry is known
+                        }
+                    }
+                    outw |= o << (8 * u);
+                }
+                if (vec) {
+                    __stcs(reinterpret_cast<unsigned int*>(p.step + base + i0), outw);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < G4; ++u)
+                        if (i0 + u < n) p.step[base + i0 + u] = (uint8_t)(outw >> (8 * u));
+                }
+            }
+            const int incl = warp_incl_sum((int)c);
+            excl[k] = incl - (int)c;
+            if (lane == 31) cnt[k * NW + warp] = (uint16_t)incl;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            constexpr int PER = (C + 31) / 32;
+            int v[PER];
+            int sum = 0;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int idx = lane * PER + u;
+                v[u] = idx < C ? cnt[idx] : 0;
+                sum += v[u];
+            }
+            const int incl = warp_incl_sum(sum);
+            int run = total + incl - sum;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int idx = lane * PER + u;
+                if (idx < C) cnt[idx] = (uint16_t)min(run, 0xFFFF);
+                run += v[u];
+            }
+            if (lane == 31) S.nLive = total + incl;
+            if (lane == 0) S.nPend = 0;
+        }
+        __syncthreads();
+        const int newTotal = S.nLive;
+        if (newTotal > T) return false;          // too many live ops for one group
+#pragma unroll
+        for (int k = 0; k < STEPS; ++k) {
+            if (!((liveBits >> (k * G4)) & 0xFu)) continue;
+            const int i0 = (k * NT + tid) * G4;
+            const int32_t va[G4] = {vva[k].x, vva[k].y, vva[k].z, vva[k].w};
+            int c = cnt[k * NW + warp] + excl[k];
+#pragma unroll
+            for (int u = 0; u < G4; ++u) {
+                if (liveBits & (1u << (k * G4 + u))) {
+                    const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
+                    keyIn[pad(c)] = ((KeyT)uv << POS_BITS) | (KeyT)c;
+                    S.livePos[c] = (uint16_t)((g << POS_BITS) | (i0 + u));
+                    S.mel[c] = (uint8_t)((melw[k] >> (8 * u)) & 0xFFu);
+                    ++c;
+                }
+            }
+        }
+        total = newTotal;
+    }
+    const int nl = total;
+    if (p.phase_on && tid == 0) {
+        atomicAdd(&g_scan_phase_cycles[8], (unsigned long long)nTiles);
+        if (nl) atomicAdd(&g_scan_phase_cycles[9], 1ull);
+        atomicAdd(&g_scan_phase_cycles[10], (unsigned long long)nl);
+    }
+    auto register_tiles = [&]() {
+        if (tid == 0) {
+            __threadfence();
+            uint32_t w = (uint32_t)t0 >> 5, m = 0;
+            for (int u = 0; u < nTiles; ++u) {
+                const uint32_t tt = (uint32_t)(t0 + u);
+                if ((tt >> 5) != w) {
+                    atomicOr(p.regbits + w, m);
+                    w = tt >> 5;
+                    m = 0;
+                }
+                m |= 1u << (tt & 31);
+            }
+            atomicOr(p.regbits + w, m);
+        }
+    };
+    if (nl == 0 && !p.guard) {
+        // every op's variable was already stuck: all outputs are written
+        register_tiles();
+        return true;
+    }
+    const int D0 = 1 << p.digit_bits;
+    for (int i = lane; i < D0; i += 32) S.hist[warp * D0 + i] = 0;
+    __syncthreads();
+    PHASE(1)
+
+    // ---- 3. stable LSD radix sort of the live keys (by variable) -----------
+    KeyT* kin = keyIn;
+    KeyT* kout = S.vbuf[0];
+    const bool rank_sort = nl <= RANK_SORT_MAX;
+    if (nl > 0 && rank_sort) {
+        if (tid < nl) {
+            const KeyT kj = kin[pad(tid)];
+            int r = 0;
+            for (int i = 0; i < nl; ++i) r += kin[pad(i)] < kj;
+            kout[pad(r)] = kj;
+        }
+        __syncthreads();
+        KeyT* tk = kin;
+        kin = kout;
+        kout = tk;
+    }
+    for (int pass = 0; pass < (nl && !rank_sort ? p.passes : 0); ++pass) {
+        const int D = 1 << p.digit_bits;
+        const int shift = POS_BITS + pass * p.digit_bits;
+        uint16_t* hrow = S.hist + warp * D;
+        if (pass > 0) {
+            for (int i = lane; i < D; i += 32) hrow[i] = 0;
+            __syncwarp();
+        }
+        KeyT kk[E];
+        uint16_t lr[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int pos = warp * 32 * E + e * 32 + lane;
+            const bool ok = pos < nl;
+            const KeyT key = ok ? kin[pad(pos)] : (KeyT)0;
+            kk[e] = key;
+            const uint32_t dig = ok ? (uint32_t)((key >> shift) & (KeyT)(D - 1)) : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            const uint32_t rank = __popc(peers & lt);
+            uint16_t c = 0;
+            if (ok) c = hrow[dig];
+            lr[e] = (uint16_t)(c + rank);
+            __syncwarp();
+            if (ok && rank == 0) hrow[dig] = (uint16_t)(c + __popc(peers));
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int per = (D + NT - 1) / NT;
+            const int d0 = tid * per;
+            int sum = 0;
+            for (int d = d0; d < d0 + per && d < D; ++d)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) sum += S.hist[w * D + d];
+            int run = block_excl_sum<NT>(sum, S.scanTmp, nullptr);
+            for (int d = d0; d < d0 + per && d < D; ++d)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const int c = S.hist[w * D + d];
+                    S.hist[w * D + d] = (uint16_t)run;
+                    run += c;
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int pos = warp * 32 * E + e * 32 + lane;
+            if (pos < nl) {
+                const uint32_t dig = (uint32_t)((kk[e] >> shift) & (KeyT)(D - 1));
+                kout[pad(hrow[dig] + lr[e])] = kk[e];
+            }
+        }
+        __syncthreads();
+        KeyT* tk = kin;
+        kin = kout;
+        kout = tk;
+    }
+    PHASE(2)
+    const KeyT* K = kin;                       // sorted keys: (variable, position in group)
+    uint32_t* pend = reinterpret_cast<uint32_t*>(kout);   // the free buffer
+    auto kvar = [&](int j) -> uint32_t { return (uint32_t)(K[pad(j)] >> POS_BITS); };
+    auto kidx = [&](int j) -> int { return (int)(K[pad(j)] & (KeyT)(T - 1)); };
+    // run key: variable and tile in group (runs never cross a tile)
+    auto rkey = [&](int j) -> uint64_t {
+        return ((uint64_t)kvar(j) << 8) | (uint64_t)(S.livePos[kidx(j)] >> POS_BITS);
+    };
+
+    // ---- 4a. run boundaries; stuck-shortcut and list-head loads ------------
+    const int j0 = tid * E;
+    uint32_t headMask = 0, lastMask = 0;
+    uint32_t ffv[E], hdv[E];
+    {
+        uint64_t prev = (j0 > 0 && j0 - 1 < nl) ? rkey(j0 - 1) : ~0ull;
+        uint64_t cur = (j0 < nl) ? rkey(j0) : ~1ull;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int j = j0 + k;
+            const uint64_t nxt = (j + 1 < nl) ? rkey(j + 1) : ~2ull;
+            ffv[k] = 0xFFFFFFFFu;
+            hdv[k] = NIL;
+            if (j < nl) {
+                if (cur != prev) headMask |= 1u << k;
+                if (nxt != cur) {
+                    lastMask |= 1u << k;
+                    const uint32_t v = (uint32_t)(cur >> 8);
+                    ffv[k] = __ldcg(reinterpret_cast<const unsigned int*>(p.vff) + v);
+                    hdv[k] = __ldcg(p.head + v);
+                }
+            }
+            prev = cur;
+            cur = nxt;
+        }
+    }
+
+    // ---- 4b. segmented scan over runs (as in the tile path) ----------------
+#define getb(w, k) (((w)[(k) >> 2] >> (8 * ((k) & 3))) & 0xFFu)
+#define setb(w, k, v) ((w)[(k) >> 2] = ((w)[(k) >> 2] & ~(0xFFu << (8 * ((k) & 3)))) | ((uint32_t)(v) << (8 * ((k) & 3))))
+    uint32_t pmw[E / 4], xmw[E / 4];
+#pragma unroll
+    for (int i = 0; i < E / 4; ++i) pmw[i] = xmw[i] = 0;
+    const int nHeads = __popc(headMask);
+    uint32_t acc = ID;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int j = j0 + k;
+        if (j < nl) {
+            const uint32_t m = S.mel[kidx(j)];
+            if (headMask & (1u << k)) {
+                acc = m;
+            } else {
+                setb(xmw, k, acc);
+                acc = comp_of(S.comp, acc, m);
+            }
+            setb(pmw, k, acc);
+        }
+    }
+    uint32_t carry;
+    {
+        uint32_t f = headMask != 0, v = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t fu = __shfl_up_sync(0xffffffffu, f, o);
+            const uint32_t vu = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) {
+                if (!f) v = comp_of(S.comp, vu, v);
+                f |= fu;
+            }
+        }
+        uint32_t fe = __shfl_up_sync(0xffffffffu, f, 1);
+        uint32_t ve = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) { fe = 0; ve = ID; }
+        if (lane == 31) { S.segF[warp] = (uint8_t)f; S.segV[warp] = (uint8_t)v; }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t wf = lane < NW ? S.segF[lane] : 0, wv = lane < NW ? S.segV[lane] : ID;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t fu = __shfl_up_sync(0xffffffffu, wf, o);
+                const uint32_t vu = __shfl_up_sync(0xffffffffu, wv, o);
+                if (lane >= o) {
+                    if (!wf) wv = comp_of(S.comp, vu, wv);
+                    wf |= fu;
+                }
+            }
+            uint32_t xf = __shfl_up_sync(0xffffffffu, wf, 1);
+            uint32_t xv = __shfl_up_sync(0xffffffffu, wv, 1);
+            if (lane == 0) { xf = 0; xv = ID; }
+            if (lane < NW) { S.segF[lane] = (uint8_t)xf; S.segV[lane] = (uint8_t)xv; }
+        }
+        __syncthreads();
+        carry = fe ? ve : comp_of(S.comp, S.segV[warp], ve);
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        if ((headMask & ((2u << k) - 1)) == 0) {
+            setb(pmw, k, comp_of(S.comp, carry, getb(pmw, k)));
+            setb(xmw, k, comp_of(S.comp, carry, getb(xmw, k)));
+        }
+    }
+    const int runBase = block_excl_sum<NT>(nHeads, S.scanTmp, nullptr);
+    auto run_id = [&](int k) { return runBase - 1 + __popc(headMask & ((2u << k) - 1)); };
+    PHASE(3)
+
+    // ---- 5a. run entry: stuck shortcut, or a node in the variable's list ----
+    // node of run r in group tile g: (t0 + g) * T + r  (r < T: one per live op at most)
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        if (lastMask & (1u << k)) {
+            const int r = run_id(k);
+            const int g = S.livePos[kidx(j0 + k)] >> POS_BITS;
+            const int64_t rbase = gbase + (int64_t)g * T;
+            if ((int64_t)ffv[k] < rbase && ffv[k] != 0xFFFFFFFFu) {
+                S.runEntry[r] = ST_F;
+                const uint32_t v = kvar(j0 + k);
+                if (v < (uint32_t)p.fbw * 32u) atomicOr(fsm + (v >> 5), 1u << (v & 31));
+            } else {
+                const uint32_t agg = getb(pmw, k);
+                S.runEntry[r] = RUN_PENDING;
+                S.runAgg[r] = (uint8_t)agg;
+                S.runHead[r] = hdv[k];
+                pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
+                p.node_status[(uint32_t)(t0 + g) * (uint32_t)T + (uint32_t)r] = (uint8_t)(NODE_AGG | agg);
+            }
+        }
+    }
+    __syncthreads();
+    const int nPend = S.nPend;
+    if (p.phase_on && tid == 0 && nPend) atomicAdd(&g_scan_phase_cycles[11], 1ull);
+    constexpr int PW = 4;
+    for (int lo = 0; lo < nPend; lo += NT * PW) {
+        uint32_t c[PW], old[PW], node[PW], var[PW], ntile[PW];
+        uint32_t mine = 0, simple = 0;
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            const int i = lo + u * NT + tid;
+            c[u] = NIL;
+            node[u] = var[u] = ntile[u] = 0;
+            if (i < nPend) {
+                const uint32_t e = pend[i];
+                const int j = (int)(e >> 16);
+                mine |= 1u << u;
+                ntile[u] = (uint32_t)t0 + (uint32_t)(S.livePos[kidx(j)] >> POS_BITS);
+                node[u] = ntile[u] * (uint32_t)T + (e & 0xFFFFu);
+                var[u] = kvar(j);
+                c[u] = S.runHead[e & 0xFFFFu];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PW; ++u)
+            if ((mine & (1u << u)) && (c[u] == NIL || c[u] / T < ntile[u])) {
+                p.node_next[node[u]] = c[u];
+                simple |= 1u << u;
+            }
+        __threadfence();
+#pragma unroll
+        for (int u = 0; u < PW; ++u) old[u] = (simple & (1u << u)) ? atomicCAS(p.head + var[u], c[u], node[u]) : c[u];
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            if (!(mine & (1u << u)) || ((simple & (1u << u)) && old[u] == c[u])) continue;
+            uint32_t* link = p.head + var[u];
+            for (uint32_t it = 0;; ++it) {
+                const uint32_t cc = ld_acquire(link);
+                if (cc == NIL || cc / T < ntile[u]) {
+                    p.node_next[node[u]] = cc;
+                    __threadfence();
+                    if (atomicCAS(link, cc, node[u]) == cc) break;
+                } else {
+                    link = p.node_next + cc;
+                }
+                if (it > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
+            }
+        }
+    }
+    __syncthreads();
+    PHASE(4)
+
+    // ---- 5b. registration of the group's tiles; frontier --------------------
+    register_tiles();
+    if (nPend > 0 || p.guard) {
+        uint32_t f0 = min(S.frontVal, (uint32_t)t0);
+        for (uint32_t it = 0;; ++it) {
+            bool all = true;
+            for (uint32_t w = (f0 >> 5) + tid; f0 < (uint32_t)t0 && w <= ((uint32_t)t0 - 1) >> 5; w += NT) {
+                const uint32_t lo = max(f0, w << 5), hi = min((uint32_t)t0, (w << 5) + 32);
+                const uint32_t need = (hi - lo == 32) ? 0xFFFFFFFFu : (((1u << (hi - lo)) - 1u) << (lo & 31));
+                all &= (__ldcg(p.regbits + w) & need) == need;
+            }
+            if (__syncthreads_and(all)) {
+                if (tid == 0) {
+                    __threadfence();
+                    // the group's own tiles registered above
+                    atomicMax(p.front, (uint32_t)(t0 + nTiles));
+                    S.frontVal = (uint32_t)(t0 + nTiles);
+                }
+                break;
+            }
+            if (it > SPIN_LIMIT) { if (tid == 0) raise_error(p.err, AMC_E_TIMEOUT); break; }
+            __nanosleep(128);
+            if (tid == 0) S.frontVal = ld_acquire(p.front);
+            __syncthreads();
+            f0 = min(max(f0, S.frontVal), (uint32_t)t0);
+            __syncthreads();
+        }
+        __threadfence();
+    }
+    PHASE(5)
+
+    // ---- 5c. look-back along the lists -------------------------------------
+    for (int lo = 0; lo < nPend; lo += NT * PW) {
+        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW];
+        uint32_t active = 0;
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            const int i = lo + u * NT + tid;
+            a[u] = ID;
+            st[u] = 0;
+            q[u] = NIL;
+            node[u] = var[u] = rr[u] = 0;
+            if (i < nPend) {
+                const uint32_t e = pend[i];
+                const int j = (int)(e >> 16);
+                active |= 1u << u;
+                rr[u] = e & 0xFFFFu;
+                node[u] = ((uint32_t)t0 + (uint32_t)(S.livePos[kidx(j)] >> POS_BITS)) * (uint32_t)T + rr[u];
+                var[u] = kvar(j);
+                q[u] = ld_acquire(p.node_next + node[u]);
+            }
+        }
+        const uint32_t mine = active;
+        for (uint32_t hop = 0; active; ++hop) {
+            uint32_t sv[PW];
+#pragma unroll
+            for (int u = 0; u < PW; ++u)
+                sv[u] = ((active & (1u << u)) && q[u] != NIL) ? ld_acquire_u8(p.node_status + q[u]) : 0u;
+#pragma unroll
+            for (int u = 0; u < PW; ++u) {
+                if (!(active & (1u << u))) continue;
+                if (q[u] == NIL) {
+                    st[u] = p.init ? p.init[var[u]] : (uint32_t)AMC_ST_VI;
+                    active &= ~(1u << u);
+                } else if (sv[u] & NODE_INCL) {
+                    st[u] = sv[u] & 7u;
+                    active &= ~(1u << u);
+                } else {
+                    a[u] = comp_of(S.comp, sv[u] & 31u, a[u]);     // earlier tile first
+                    if ((S.constF >> a[u]) & 1u) {                  // entry F (absorbing)
+                        st[u] = 0;
+                        active &= ~(1u << u);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PW; ++u)
+                if (active & (1u << u)) q[u] = ld_acquire(p.node_next + q[u]);
+            if (hop > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
+        }
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            if (!(mine & (1u << u))) continue;
+            const uint32_t entry = S.app[a[u] * 8 + st[u]];
+            S.runEntry[rr[u]] = (uint8_t)entry;
+            st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
+        }
+    }
+    __syncthreads();
+    PHASE(6)
+
+    // ---- 6. outputs of the live ops (byte stores); first faults -------------
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int j = j0 + k;
+        if (j < nl) {
+            const uint32_t e = S.runEntry[run_id(k)];
+            const uint32_t pre = S.app[getb(xmw, k) * 8 + e];
+            const uint32_t post = S.app[getb(pmw, k) * 8 + e];
+            const int64_t gpos = gbase + (int64_t)S.livePos[kidx(j)];
+            p.step[gpos] = (uint8_t)(p.pre_mode ? pre : post);
+            if (post == ST_F && pre != ST_F) {
+                const uint32_t gi = (uint32_t)gpos;
+                const uint32_t v = kvar(j);
+                atomicMin(reinterpret_cast<uint32_t*>(p.vff) + v, gi);
+                atomicOr(p.fbits + (v >> 5), 1u << (v & 31));
+                atomicOr(p.fbits + p.fbits_words + (v >> 5), 1u << (v & 31));
+                if (v < (uint32_t)p.fbw * 32u) atomicOr(fsm + (v >> 5), 1u << (v & 31));
+                atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
+            }
+        }
+    }
+#undef getb
+#undef setb
+    PHASE(7)
+#undef PHASE
+    return true;
+}
+
 template <typename KeyT, int T, int NT>
 __device__ __forceinline__ void issue_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, int b, int t)
 {
@@ -714,6 +1337,15 @@ __global__ void __launch_bounds__(NT, 3) scan_trace_kernel(const ScanParams p)
     for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += NT) S.comp[i] = p.tab.comp[i];
     for (int i = tid; i < MAX_ELEMS * 8; i += NT) S.app[i] = p.tab.app[i];
     for (int i = tid; i < 256; i += NT) S.elem_of[i] = p.tab.elem_of[i];
+    if (tid < 32) {
+        // element e is the constant F function when it sends all four
+        // non-stuck statuses to F (F itself is absorbing)
+        const uint32_t e = (uint32_t)tid;
+        bool cf = e < (uint32_t)p.tab.n_elems;
+        for (int st = 0; st < 4; ++st) cf = cf && p.tab.app[e * 8 + st] == ST_F;
+        const uint32_t m = __ballot_sync(0xffffffffu, cf);
+        if (tid == 0) S.constF = m;
+    }
     for (int i = tid; i < p.fbw; i += NT) fsm[i] = __ldcg(p.fbits + i);
     if (tid == 0) {
         mbar_init(&S.mbar[0], 1);
@@ -722,19 +1354,60 @@ __global__ void __launch_bounds__(NT, 3) scan_trace_kernel(const ScanParams p)
     }
     uint32_t parity = 0;
     long long last = clock64();
-    // A CTA takes the next tile id only when it starts that tile: every tile
-    // below an id being processed has then started too, so it reaches its
+    uint32_t done = 0;               // tiles this CTA has processed (bitmap refresh clock)
+    uint32_t est = T;                // live ops per tile lately (thread 0's estimate)
+    bool failed = false;
+    // A CTA takes the next tile ids only when it starts them: every tile below
+    // an id being processed has then started too, so it reaches its
     // registration within one pre-registration phase (no queued tiles, no
-    // convoys of waits through other CTAs' queues).
-    for (uint32_t iter = 0;; ++iter) {
+    // convoys of waits through other CTAs' queues).  Where few ops are live
+    // the CTA takes a group of tiles at once (group path), sized so that the
+    // expected live ops fill about half of the shared buffers.
+    while (!failed) {
         if (tid == 0) {
-            const int t = (int)atomicAdd(p.tile_counter, 1u);
+            int G = 1;
+            if (p.group_max > 1) {
+                G = p.group_max;
+                while (!p.group_force && G > 1 && (uint32_t)G * est > (uint32_t)GROUP_LIVE_TARGET) G >>= 1;
+            }
+            const int t = (int)atomicAdd(p.tile_counter, (uint32_t)G);
             S.tile[0] = t;
-            issue_tile<KeyT, T, NT>(p, S, 0, t);
+            S.grp[0] = G;
+            if (G == 1) issue_tile<KeyT, T, NT>(p, S, 0, t);
         }
         __syncthreads();
         const int t = S.tile[0];
+        const int G = S.grp[0];
         if (t >= p.n_tiles) break;
+        if (G > 1) {
+            if (process_group<KeyT, T, NT>(p, S, fsm, t, G, done, last)) {
+                const int nt = min(G, p.n_tiles - t);
+                if (tid == 0) est = (est + (uint32_t)S.nLive / (uint32_t)nt + 1) / 2;
+                done += (uint32_t)nt;
+                __syncthreads();
+                continue;
+            }
+            // more live ops than one group holds: its tiles one by one
+            if (tid == 0) est = T;
+            for (int u = 0; u < G && t + u < p.n_tiles && !failed; ++u) {
+                __syncthreads();
+                if (tid == 0) issue_tile<KeyT, T, NT>(p, S, 0, t + u);
+                __syncthreads();
+                bool ok = true;
+                if (S.viaBulk[0]) {
+                    ok = mbar_wait_bounded(&S.mbar[0], parity, p.err);
+                    parity ^= 1;
+                }
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) mbar_wait_bounded(&S.mbar[0], parity ^ 1, p.err);   // drain, bounded
+                    failed = true;
+                    break;
+                }
+                process_tile<KeyT, T, NT>(p, S, fsm, t + u, 0, done++, last);
+                __syncthreads();
+            }
+            continue;
+        }
         bool ok = true;
         if (S.viaBulk[0]) {
             ok = mbar_wait_bounded(&S.mbar[0], parity, p.err);
@@ -749,7 +1422,8 @@ __global__ void __launch_bounds__(NT, 3) scan_trace_kernel(const ScanParams p)
             atomicAdd(&g_scan_phase_cycles[0], (unsigned long long)(now - last));
             last = now;
         }
-        process_tile<KeyT, T, NT>(p, S, fsm, t, 0, iter, last);
+        process_tile<KeyT, T, NT>(p, S, fsm, t, 0, done++, last);
+        if (tid == 0) est = (est + (uint32_t)S.nLive + 1) / 2;
         __syncthreads();
     }
 }
@@ -881,6 +1555,20 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     int kb = 1;
     while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
     p.passes = (kb + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
+    p.group_max = L.group_max > 0 ? min(L.group_max, GROUP_MAX) : GROUP_MAX;
+    if (const char* e = getenv("AMC_SCAN_GROUP")) {
+        // tuning and test override: N = at most N tiles per claim, -N = always N
+        const int g = atoi(e);
+        p.group_max = max(1, min(g < 0 ? -g : g, GROUP_MAX));
+        p.group_force = g < 0;
+    }
+    // the guard-resolving pass reads its guards from the buffer it writes; the
+    // tile path stores a tile only after its frontier wait, which orders those
+    // reads before the overwrite, while the group path writes during its decode
+    if (L.guard) {
+        p.group_max = 1;
+        p.group_force = 0;
+    }
     p.digit_bits = (kb + p.passes - 1) / p.passes;
     p.bulk_ok = ((uintptr_t)L.kind_side % 16 == 0) && ((uintptr_t)L.var % 16 == 0) &&
                 ((uintptr_t)L.step % 16 == 0);

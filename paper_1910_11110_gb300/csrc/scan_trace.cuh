@@ -32,6 +32,8 @@ struct ScanParams {
     int digit_bits;
     int bulk_ok;
     int phase_on;               // accumulate per-phase cycle counters
+    int group_max;              // most tiles per claim (1: tile path only)
+    int group_force;            // 1: every claim takes group_max tiles
     Tables tab;
 };
 
@@ -53,6 +55,7 @@ struct ScanLaunch {
     int profile = 0;                    // bit 0: record the start event, bit 1: the stop event
     int fb_max_bits = 0;                // shared stuck bitmap size in variables (0 = default,
                                         // -1 = no bitmap, -2 = bitmap read through L1)
+    int group_max = 0;                  // most tiles per claim (0 = default, 1 = tile path only)
 };
 
 int scan_tile_size();
