@@ -51,6 +51,7 @@ constexpr int THREADS = 256;
 constexpr int POS_BITS = 12;                // log2(TILE)
 constexpr int MAX_DIGIT_BITS = 10;
 constexpr uint8_t RUN_PENDING = 0xFF;
+constexpr uint32_t NO_NODE = 0x80000000u;      // pending-run flag: constant-F run, no list node
 constexpr uint32_t NODE_AGG = 0x40;
 constexpr uint32_t NODE_INCL = 0x80;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
@@ -521,9 +522,18 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 const uint32_t agg = getb(pmw, k);
                 S.runEntry[r] = RUN_PENDING;
                 S.runAgg[r] = (uint8_t)agg;
-                S.runHead[r] = hdv[k];
-                pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
-                p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | agg);
+                if ((S.constF >> agg) & 1u) {
+                    // stuck by the end of this tile whatever its entry: publish
+                    // that bound as the first fault (the exact one, recorded
+                    // below or earlier, is never larger) instead of a node;
+                    // later tiles take the stuck shortcut
+                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(base + T - 1));
+                    pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16) | NO_NODE;
+                } else {
+                    S.runHead[r] = hdv[k];
+                    pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
+                    p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | agg);
+                }
             }
         }
     }
@@ -541,7 +551,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             const int i = lo + u * NT + tid;
             c[u] = NIL;
             node[u] = var[u] = 0;
-            if (i < nPend) {
+            if (i < nPend && !(pend[i] & NO_NODE)) {
                 const uint32_t e = pend[i];
                 mine |= 1u << u;
                 node[u] = nodeBase + (e & 0xFFFFu);
@@ -619,8 +629,8 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     PHASE(5)
     // ---- 5c. look-back along the lists, PW runs per thread in step -----------
     for (int lo = 0; lo < nPend; lo += NT * PW) {
-        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW];
-        uint32_t active = 0;
+        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW], ffw[PW];
+        uint32_t active = 0, nonode = 0;
 #pragma unroll
         for (int u = 0; u < PW; ++u) {
             const int i = lo + u * NT + tid;
@@ -628,16 +638,29 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             st[u] = 0;
             q[u] = NIL;
             node[u] = var[u] = rr[u] = 0;
+            ffw[u] = 0xFFFFFFFFu;
             if (i < nPend) {
                 const uint32_t e = pend[i];
                 active |= 1u << u;
                 rr[u] = e & 0xFFFFu;
-                node[u] = nodeBase + rr[u];
-                var[u] = kvar((int)(e >> 16));
-                q[u] = ld_acquire(p.node_next + node[u]);
+                var[u] = kvar((int)((e >> 16) & 0x7FFFu));
+                if (e & NO_NODE) {
+                    nonode |= 1u << u;
+                    q[u] = ld_acquire(p.head + var[u]);         // from the newest node
+                } else {
+                    node[u] = nodeBase + rr[u];
+                    q[u] = ld_acquire(p.node_next + node[u]);
+                }
+                ffw[u] = ld_acquire(reinterpret_cast<const uint32_t*>(p.vff) + var[u]);
             }
         }
         const uint32_t mine = active;
+#pragma unroll
+        for (int u = 0; u < PW; ++u)
+            if ((active & (1u << u)) && ffw[u] < (uint32_t)base) {
+                st[u] = ST_F;                  // stuck before this tile (bound published since)
+                active &= ~(1u << u);
+            }
         for (uint32_t hop = 0; active; ++hop) {
             uint32_t sv[PW];
 #pragma unroll
@@ -649,6 +672,8 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 if (q[u] == NIL) {
                     st[u] = p.init ? p.init[var[u]] : (uint32_t)AMC_ST_VI;
                     active &= ~(1u << u);
+                } else if (q[u] / T >= (uint32_t)t) {
+                    // a node of this or a later tile (walks that start at the head)
                 } else if (sv[u] & NODE_INCL) {
                     st[u] = sv[u] & 7u;
                     active &= ~(1u << u);
@@ -672,7 +697,8 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             if (!(mine & (1u << u))) continue;
             const uint32_t entry = S.app[a[u] * 8 + st[u]];
             S.runEntry[rr[u]] = (uint8_t)entry;
-            st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
+            if (!(nonode & (1u << u)))
+                st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
         }
     }
     __syncthreads();
@@ -1137,9 +1163,15 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 const uint32_t agg = getb(pmw, k);
                 S.runEntry[r] = RUN_PENDING;
                 S.runAgg[r] = (uint8_t)agg;
-                S.runHead[r] = hdv[k];
-                pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
-                p.node_status[(uint32_t)(t0 + g) * (uint32_t)T + (uint32_t)r] = (uint8_t)(NODE_AGG | agg);
+                if ((S.constF >> agg) & 1u) {
+                    // stuck by the end of its tile: bound as first fault, no node
+                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(rbase + T - 1));
+                    pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16) | NO_NODE;
+                } else {
+                    S.runHead[r] = hdv[k];
+                    pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
+                    p.node_status[(uint32_t)(t0 + g) * (uint32_t)T + (uint32_t)r] = (uint8_t)(NODE_AGG | agg);
+                }
             }
         }
     }
@@ -1155,7 +1187,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             const int i = lo + u * NT + tid;
             c[u] = NIL;
             node[u] = var[u] = ntile[u] = 0;
-            if (i < nPend) {
+            if (i < nPend && !(pend[i] & NO_NODE)) {
                 const uint32_t e = pend[i];
                 const int j = (int)(e >> 16);
                 mine |= 1u << u;
@@ -1227,26 +1259,40 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
 
     // ---- 5c. look-back along the lists -------------------------------------
     for (int lo = 0; lo < nPend; lo += NT * PW) {
-        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW];
-        uint32_t active = 0;
+        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW], ffw[PW], rt[PW];
+        uint32_t active = 0, nonode = 0;
 #pragma unroll
         for (int u = 0; u < PW; ++u) {
             const int i = lo + u * NT + tid;
             a[u] = ID;
             st[u] = 0;
             q[u] = NIL;
-            node[u] = var[u] = rr[u] = 0;
+            node[u] = var[u] = rr[u] = rt[u] = 0;
+            ffw[u] = 0xFFFFFFFFu;
             if (i < nPend) {
                 const uint32_t e = pend[i];
-                const int j = (int)(e >> 16);
+                const int j = (int)((e >> 16) & 0x7FFFu);
                 active |= 1u << u;
                 rr[u] = e & 0xFFFFu;
-                node[u] = ((uint32_t)t0 + (uint32_t)(S.livePos[kidx(j)] >> POS_BITS)) * (uint32_t)T + rr[u];
+                rt[u] = (uint32_t)t0 + (uint32_t)(S.livePos[kidx(j)] >> POS_BITS);     // the run's tile
                 var[u] = kvar(j);
-                q[u] = ld_acquire(p.node_next + node[u]);
+                if (e & NO_NODE) {
+                    nonode |= 1u << u;
+                    q[u] = ld_acquire(p.head + var[u]);         // from the newest node
+                } else {
+                    node[u] = rt[u] * (uint32_t)T + rr[u];
+                    q[u] = ld_acquire(p.node_next + node[u]);
+                }
+                ffw[u] = ld_acquire(reinterpret_cast<const uint32_t*>(p.vff) + var[u]);
             }
         }
         const uint32_t mine = active;
+#pragma unroll
+        for (int u = 0; u < PW; ++u)
+            if ((active & (1u << u)) && ffw[u] < rt[u] * (uint32_t)T) {
+                st[u] = ST_F;                  // stuck before the run's tile (bound published since)
+                active &= ~(1u << u);
+            }
         for (uint32_t hop = 0; active; ++hop) {
             uint32_t sv[PW];
 #pragma unroll
@@ -1258,6 +1304,8 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 if (q[u] == NIL) {
                     st[u] = p.init ? p.init[var[u]] : (uint32_t)AMC_ST_VI;
                     active &= ~(1u << u);
+                } else if (q[u] / T >= rt[u]) {
+                    // a node of the run's tile or a later one (walks that start at the head)
                 } else if (sv[u] & NODE_INCL) {
                     st[u] = sv[u] & 7u;
                     active &= ~(1u << u);
@@ -1279,7 +1327,8 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             if (!(mine & (1u << u))) continue;
             const uint32_t entry = S.app[a[u] * 8 + st[u]];
             S.runEntry[rr[u]] = (uint8_t)entry;
-            st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
+            if (!(nonode & (1u << u)))
+                st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
         }
     }
     __syncthreads();
@@ -1444,6 +1493,21 @@ __global__ void finalize_trace_kernel(const int32_t* __restrict__ vff, const uin
     final_status[v] = f;
 }
 
+// Variables whose initial status is F are stuck before the first op: their
+// bits go into both copies of the stuck bitmap before the scan starts.
+__global__ void seed_stuck_kernel(const uint8_t* __restrict__ init, int32_t n_vars, uint32_t* __restrict__ fbits,
+                                  int fbits_words)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool f = v < n_vars && init[v] == ST_F;
+    const uint32_t m = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && m) {
+        const int64_t w = v >> 5;
+        fbits[w] = m;
+        fbits[w + fbits_words] = m;
+    }
+}
+
 template <typename KeyT>
 int launch_kernel(ScanParams p, const ScanLaunch& L, cudaStream_t s)
 {
@@ -1579,6 +1643,10 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     if (L.n_ops > 0) {
         if (cudaMemsetAsync(p.regbits, 0, regbytes, s) != cudaSuccess) return AMC_E_CUDA;
         if (fbytes && cudaMemsetAsync(p.fbits, 0, fbytes, s) != cudaSuccess) return AMC_E_CUDA;
+        if (L.init && L.n_vars > 0) {
+            seed_stuck_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(L.init, L.n_vars, p.fbits, p.fbits_words);
+            if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        }
         if (cudaMemsetAsync(p.tile_counter, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
         // keys pack (var << 12 | position): 32-bit while var ids fit 20 bits
         const int rc = kb + POS_BITS <= 32 ? launch_kernel<uint32_t>(p, L, s) : launch_kernel<uint64_t>(p, L, s);
