@@ -759,10 +759,6 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
     }
     constexpr int E = T / NT;
     constexpr int NW = NT / 32;
-    constexpr int G4 = 4;
-    constexpr int STEPS = E / G4;
-    constexpr int C = STEPS * NW;            // (step, warp) counts per tile
-    static_assert(2 * C <= (T / NT) * (NT / 32), "two count rows");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t ID = 0;
     const uint32_t lt = lanemask_lt();
@@ -779,163 +775,157 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
     }
 
     // ---- 1-2. stream and decode the tiles; compact the live ops ------------
+    // Thread tid takes ops [16 tid, 16 tid + 16) of each tile (one 16-byte load
+    // of op bytes, four of ids, one 16-byte store of outputs), so live ops in
+    // (warp, lane) order are in position order.  Nearly every op is on a
+    // stuck variable: a warp computes its live-op prefix (five ballots) only
+    // when it has a live op, and one barrier per tile tells whether the block
+    // has any.
+    constexpr int PER = T / NT;
+    static_assert(PER == 16, "16 ops per thread and tile");
     KeyT* const keyIn = S.keyA;
     int total = 0;                           // live ops so far (the same in every thread)
     for (int g = 0; g < nTiles; ++g) {
         const int64_t base = gbase + (int64_t)g * T;
         const int n = (int)min((int64_t)T, p.n_ops - base);
         const bool vec = n == T && p.bulk_ok;
-        uint32_t kwa[STEPS];
-        int4 vva[STEPS];
-        uint32_t fwa[STEPS][G4];
+        const int i0 = tid * PER;
+        uint32_t kw[PER / 4];
+        int32_t va[PER];
+        if (vec) {
+            const uint4 kk = __ldcs(reinterpret_cast<const uint4*>(p.kind_side + base + i0));
+            kw[0] = kk.x;
+            kw[1] = kk.y;
+            kw[2] = kk.z;
+            kw[3] = kk.w;
 #pragma unroll
-        for (int k = 0; k < STEPS; ++k) {
-            const int i0 = (k * NT + tid) * G4;
-            kwa[k] = 0;
-            vva[k] = make_int4(0, 0, 0, 0);
-            if (vec) {
-                kwa[k] = __ldcs(reinterpret_cast<const unsigned int*>(p.kind_side + base + i0));
-                vva[k] = __ldcs(reinterpret_cast<const int4*>(p.var + base + i0));
-            } else if (i0 < n) {
-                int32_t va[G4] = {0, 0, 0, 0};
-#pragma unroll
-                for (int u = 0; u < G4; ++u)
-                    if (i0 + u < n) {
-                        kwa[k] |= (uint32_t)p.kind_side[base + i0 + u] << (8 * u);
-                        va[u] = p.var[base + i0 + u];
-                    }
-                vva[k] = make_int4(va[0], va[1], va[2], va[3]);
+            for (int q = 0; q < PER / 4; ++q) {
+                const int4 v4 = __ldcs(reinterpret_cast<const int4*>(p.var + base + i0) + q);
+                va[4 * q] = v4.x;
+                va[4 * q + 1] = v4.y;
+                va[4 * q + 2] = v4.z;
+                va[4 * q + 3] = v4.w;
             }
-        }
+        } else {
 #pragma unroll
-        for (int k = 0; k < STEPS; ++k) {
-            const int32_t va[G4] = {vva[k].x, vva[k].y, vva[k].z, vva[k].w};
-#pragma unroll
-            for (int u = 0; u < G4; ++u) {
-                const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
-                fwa[k][u] = p.fb_mode == 2 ? __ldg(fbl1 + (uv >> 5))
-                                           : (uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : 0u);
-            }
-        }
-        uint32_t liveBits = 0, melw[STEPS];
-        int excl[STEPS];
-        uint16_t* const cnt = S.cnt + (g & 1) * C;
-#pragma unroll
-        for (int k = 0; k < STEPS; ++k) {
-            const int i0 = (k * NT + tid) * G4;
-            uint32_t c = 0;
-            melw[k] = 0;
-            if (i0 < n) {
-                const uint32_t kw = kwa[k];
-                const int32_t va[G4] = {vva[k].x, vva[k].y, vva[k].z, vva[k].w};
-                uint32_t outw = 0;
-#pragma unroll
-                for (int u = 0; u < G4; ++u) {
-                    const int i = i0 + u;
-                    const uint32_t ks = (kw >> (8 * u)) & 0xFFu;
-                    uint32_t o = ST_F;
-                    if (i < n) {
-                        if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
-                        uint32_t uv = (uint32_t)va[u];
-                        if (va[u] < 0 || va[u] >= p.n_vars) {
-                            raise_error(p.err, AMC_E_RANGE);
-                            uv = 0;
-                        }
-                        bool gt_ok = true;
-                        if ((ks & 15u) == AMC_K_GT) {
-                            // GT must be followed by EN of the same side on another variable
-                            const int64_t gi = base + i;
-                            uint32_t nks = 0xFF;
-                            int32_t nv = (int32_t)uv;
-                            if (gi + 1 < p.n_ops) {
-                                nks = p.kind_side[gi + 1];
-                                nv = p.var[gi + 1];
-                            }
-                            gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
-                            if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
-                        }
-                        const bool stuck = ((fwa[k][u] >> (uv & 31)) & 1u) != 0;
-                        if (!stuck) {
-                            uint32_t m = S.elem_of[ks];
-                            if (m == ELEM_GT) {
-                                if (!gt_ok || p.pre_mode) {
-                                    m = ID;
-                                } else if (!p.guard) {
-                                    raise_error(p.err, AMC_E_INVALID);
-                                    m = ID;
-                                } else {
-                                    const uint32_t gs = p.guard[base + i + 1];
-                                    const int side = ks >> 4;
-                                    const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
-                                    m = valid ? ID : p.tab.pull_of_side[side];
-                                }
-                            } else if (m == ELEM_BAD) {
-                                m = ID;
-                            }
-                            melw[k] |= m << (8 * u);
-                            liveBits |= 1u << (k * G4 + u);
-                            ++c;
-                            o = 0;                   // written once the run's entry is known
-                        }
-                    }
-                    outw |= o << (8 * u);
-                }
-                if (vec) {
-                    __stcs(reinterpret_cast<unsigned int*>(p.step + base + i0), outw);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < G4; ++u)
-                        if (i0 + u < n) p.step[base + i0 + u] = (uint8_t)(outw >> (8 * u));
-                }
-            }
-            const int incl = warp_incl_sum((int)c);
-            excl[k] = incl - (int)c;
-            if (lane == 31) cnt[k * NW + warp] = (uint16_t)incl;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            constexpr int PER = (C + 31) / 32;
-            int v[PER];
-            int sum = 0;
+            for (int q = 0; q < PER / 4; ++q) kw[q] = 0;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
-                const int idx = lane * PER + u;
-                v[u] = idx < C ? cnt[idx] : 0;
-                sum += v[u];
+                va[u] = 0;
+                if (i0 + u < n) {
+                    kw[u >> 2] |= (uint32_t)p.kind_side[base + i0 + u] << (8 * (u & 3));
+                    va[u] = p.var[base + i0 + u];
+                }
             }
-            const int incl = warp_incl_sum(sum);
-            int run = total + incl - sum;
+        }
+        uint32_t fw[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
+            fw[u] = p.fb_mode == 2 ? __ldg(fbl1 + (uv >> 5)) : (uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : 0u);
+        }
+        uint32_t outw[PER / 4], melw[PER / 4];
+        uint32_t liveMask = 0;
+#pragma unroll
+        for (int q = 0; q < PER / 4; ++q) outw[q] = melw[q] = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = i0 + u;
+            const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
+            uint32_t o = ST_F;
+            if (i < n) {
+                if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
+                uint32_t uv = (uint32_t)va[u];
+                if (va[u] < 0 || va[u] >= p.n_vars) {
+                    raise_error(p.err, AMC_E_RANGE);
+                    uv = 0;
+                }
+                bool gt_ok = true;
+                if ((ks & 15u) == AMC_K_GT) {
+                    // GT must be followed by EN of the same side on another variable
+                    const int64_t gi = base + i;
+                    uint32_t nks = 0xFF;
+                    int32_t nv = (int32_t)uv;
+                    if (gi + 1 < p.n_ops) {
+                        nks = p.kind_side[gi + 1];
+                        nv = p.var[gi + 1];
+                    }
+                    gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
+                    if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
+                }
+                if (!((fw[u] >> (uv & 31)) & 1u)) {
+                    uint32_t m = S.elem_of[ks];
+                    if (m == ELEM_GT) {
+                        if (!gt_ok || p.pre_mode) {
+                            m = ID;
+                        } else if (!p.guard) {
+                            raise_error(p.err, AMC_E_INVALID);
+                            m = ID;
+                        } else {
+                            const uint32_t gs = p.guard[base + i + 1];
+                            const int side = ks >> 4;
+                            const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
+                            m = valid ? ID : p.tab.pull_of_side[side];
+                        }
+                    } else if (m == ELEM_BAD) {
+                        m = ID;
+                    }
+                    melw[u >> 2] |= m << (8 * (u & 3));
+                    liveMask |= 1u << u;
+                    o = 0;                       // written once the run's entry is known
+                }
+            }
+            outw[u >> 2] |= o << (8 * (u & 3));
+        }
+        if (vec) {
+            __stcs(reinterpret_cast<uint4*>(p.step + base + i0), make_uint4(outw[0], outw[1], outw[2], outw[3]));
+        } else {
+#pragma unroll
+            for (int u = 0; u < PER; ++u)
+                if (i0 + u < n) p.step[base + i0 + u] = (uint8_t)(outw[u >> 2] >> (8 * (u & 3)));
+        }
+        // live-op prefix within the warp (counts are 0..16: five bits)
+        const int c = __popc(liveMask);
+        int pre = 0, wtot = 0;
+        if (__any_sync(0xffffffffu, c != 0)) {
+#pragma unroll
+            for (int bit = 0; bit < 5; ++bit) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, (c >> bit) & 1);
+                pre += __popc(bal & lt) << bit;
+                wtot += __popc(bal) << bit;
+            }
+        }
+        uint16_t* const cnt = S.cnt + (g & 1) * NW;
+        if (lane == 0) cnt[warp] = (uint16_t)wtot;
+        if (!__syncthreads_or(c != 0)) continue;     // no live op in the tile
+        int off = total, tileTot = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int cw = cnt[w];
+            if (w < warp) off += cw;
+            tileTot += cw;
+        }
+        if (total + tileTot > T) return false;   // too many live ops for one group
+        if (liveMask) {
+            int idx = off + pre;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
-                const int idx = lane * PER + u;
-                if (idx < C) cnt[idx] = (uint16_t)min(run, 0xFFFF);
-                run += v[u];
-            }
-            if (lane == 31) S.nLive = total + incl;
-            if (lane == 0) S.nPend = 0;
-        }
-        __syncthreads();
-        const int newTotal = S.nLive;
-        if (newTotal > T) return false;          // too many live ops for one group
-#pragma unroll
-        for (int k = 0; k < STEPS; ++k) {
-            if (!((liveBits >> (k * G4)) & 0xFu)) continue;
-            const int i0 = (k * NT + tid) * G4;
-            const int32_t va[G4] = {vva[k].x, vva[k].y, vva[k].z, vva[k].w};
-            int c = cnt[k * NW + warp] + excl[k];
-#pragma unroll
-            for (int u = 0; u < G4; ++u) {
-                if (liveBits & (1u << (k * G4 + u))) {
+                if (liveMask & (1u << u)) {
                     const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
-                    keyIn[pad(c)] = ((KeyT)uv << POS_BITS) | (KeyT)c;
-                    S.livePos[c] = (uint16_t)((g << POS_BITS) | (i0 + u));
-                    S.mel[c] = (uint8_t)((melw[k] >> (8 * u)) & 0xFFu);
-                    ++c;
+                    keyIn[pad(idx)] = ((KeyT)uv << POS_BITS) | (KeyT)idx;
+                    S.livePos[idx] = (uint16_t)((g << POS_BITS) | (i0 + u));
+                    S.mel[idx] = (uint8_t)((melw[u >> 2] >> (8 * (u & 3))) & 0xFFu);
+                    ++idx;
                 }
             }
         }
-        total = newTotal;
+        total += tileTot;
     }
+    if (tid == 0) {
+        S.nLive = total;
+        S.nPend = 0;
+    }
+    __syncthreads();
     const int nl = total;
     if (p.phase_on && tid == 0) {
         atomicAdd(&g_scan_phase_cycles[8], (unsigned long long)nTiles);
@@ -1529,6 +1519,8 @@ int launch_kernel(ScanParams p, const ScanLaunch& L, cudaStream_t s)
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_trace_kernel<KeyT, TILE, THREADS>, THREADS, smem);
     if (per_sm < 1) per_sm = 1;
+    if (L.ctas_per_sm > 0 && L.ctas_per_sm < per_sm) per_sm = L.ctas_per_sm;
+    if (const char* e = getenv("AMC_SCAN_CTAS_PER_SM")) per_sm = max(1, min(atoi(e), per_sm));   // tuning override
     int grid = n_sm * per_sm;
     if (grid > p.n_tiles) grid = p.n_tiles;
     if (L.max_ctas > 0 && grid > L.max_ctas) grid = L.max_ctas;

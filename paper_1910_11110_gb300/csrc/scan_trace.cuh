@@ -56,6 +56,7 @@ struct ScanLaunch {
     int fb_max_bits = 0;                // shared stuck bitmap size in variables (0 = default,
                                         // -1 = no bitmap, -2 = bitmap read through L1)
     int group_max = 0;                  // most tiles per claim (0 = default, 1 = tile path only)
+    int ctas_per_sm = 0;                // resident CTAs per SM (0 = as many as fit)
 };
 
 int scan_tile_size();
