@@ -268,13 +268,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     alg_bytes = 6 * n_ops + 5 * n_vars
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "scan_trace_zipf_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            traffic = json.load(open(tr_path)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = scan_traffic(n_ops, n_vars)
 
     # end-to-end through the public API: pinned host inputs, H2D, check, D2H
     e2e = None
@@ -548,6 +542,23 @@ def run_serve(args):
                       "slots": 32, "budget_gb": 32, "seed": 4},
                      serve=results)
     print(json.dumps(line), flush=True)
+
+
+def scan_traffic(n_ops, n_vars):
+    """DRAM bytes (read + write) of one scan launch from the recorded ncu
+    capture, or None when the capture was of another workload or the kernel
+    source has changed since (the record keeps its SHA-256)."""
+    import hashlib
+    tr_path = os.path.join(ROOT, "profiles", "scan_trace_zipf_traffic.json")
+    src = os.path.join(ROOT, "paper_1910_11110_gb300", "csrc", "scan_trace.cu")
+    try:
+        rec = json.load(open(tr_path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    if rec.get("source_sha256") != sha or rec.get("n_ops") != n_ops or rec.get("n_vars") != n_vars:
+        return None
+    return rec.get("bytes_per_launch")
 
 
 def main():
