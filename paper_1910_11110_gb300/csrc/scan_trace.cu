@@ -49,7 +49,7 @@ namespace {
 constexpr int TILE = 4096;
 constexpr int THREADS = 256;
 constexpr int POS_BITS = 12;                // log2(TILE)
-constexpr int MAX_DIGIT_BITS = 10;
+constexpr int MAX_DIGIT_BITS = 7;                // radix digit: 2 KB of histogram rows
 constexpr uint8_t RUN_PENDING = 0xFF;
 constexpr uint32_t NO_NODE = 0x80000000u;      // pending-run flag: constant-F run, no list node
 constexpr uint32_t NODE_AGG = 0x40;
@@ -59,6 +59,7 @@ constexpr int DEFAULT_FB_BITS = 1 << 20;      // shared stuck bitmap: 128 KB
 constexpr int N_PHASES = 12;
 constexpr int RANK_SORT_MAX = 128;             // live ops below which a rank sort replaces the radix passes
 constexpr int GROUP_MAX = 16;                  // tiles per claim in the group path (positions fit 16 bits)
+constexpr int MAX_CTAS_PER_SM = 3;             // resident CTAs per SM the launch bounds and carve-out assume
 constexpr int GROUP_LIVE_TARGET = 2048;        // expected live ops per group when choosing its size
 
 }  // namespace
@@ -84,11 +85,7 @@ struct __align__(16) ScanSmem {
     };
     uint8_t mel[T];                  // element ids of live ops (by position; by live index in groups)
     uint8_t runEntry[T];
-    uint8_t runAgg[T];
-    union {                          // the radix histogram is free once the keys are sorted
-        uint16_t hist[(NT / 32) << MAX_DIGIT_BITS];
-        uint32_t runHead[T];         // list head of each run's variable, loaded with the scan
-    };
+    uint16_t hist[(NT / 32) << MAX_DIGIT_BITS];   // per-warp rows of the radix histogram
     uint8_t comp[MAX_ELEMS * MAX_ELEMS];
     uint8_t app[MAX_ELEMS * 8];
     uint8_t elem_of[256];
@@ -106,10 +103,10 @@ struct __align__(16) ScanSmem {
     int grp[1];                      // tiles in the current claim
     // followed (dynamic shared memory) by the stuck bitmap: fbw 32-bit words
 };
-static_assert(sizeof(uint16_t) * ((THREADS / 32) << MAX_DIGIT_BITS) >= sizeof(uint32_t) * TILE,
-              "run heads must fit in the histogram's space");
-// three CTAs per SM with 32-bit keys (228 KB of shared memory per SM, 1 KB reserved per CTA)
-static_assert(3 * (sizeof(ScanSmem<uint32_t, TILE, THREADS>) + 1024) <= 228 * 1024, "shared memory per CTA");
+// three CTAs per SM with 32-bit keys within a 164 KB shared-memory carve-out (1 KB reserved
+// per CTA), which leaves 92 KB of L1 for the stuck bitmap read through it
+static_assert(MAX_CTAS_PER_SM * (sizeof(ScanSmem<uint32_t, TILE, THREADS>) + 1024) <= 164 * 1024,
+              "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t comp_of(const uint8_t* comp, uint32_t a, uint32_t b)
 {
@@ -413,7 +410,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     // that the segmented scan below hides their latency --------------------
     const int j0 = tid * E;
     uint32_t headMask = 0, lastMask = 0;
-    uint32_t ffv[E], hdv[E];
+    uint32_t ffv[E];
     {
         uint32_t prev = (j0 > 0 && j0 - 1 < nl) ? kvar(j0 - 1) : 0xFFFFFFFFu;
         uint32_t cur = (j0 < nl) ? kvar(j0) : 0xFFFFFFFEu;
@@ -422,13 +419,11 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             const int j = j0 + k;
             const uint32_t nxt = (j + 1 < nl) ? kvar(j + 1) : 0xFFFFFFFDu;
             ffv[k] = 0xFFFFFFFFu;
-            hdv[k] = NIL;
             if (j < nl) {
                 if (cur != prev) headMask |= 1u << k;
                 if (nxt != cur) {
                     lastMask |= 1u << k;
                     ffv[k] = __ldcg(reinterpret_cast<const unsigned int*>(p.vff) + cur);
-                    hdv[k] = __ldcg(p.head + cur);       // the list head, for the insertion
                 }
             }
             prev = cur;
@@ -521,7 +516,6 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             } else {
                 const uint32_t agg = getb(pmw, k);
                 S.runEntry[r] = RUN_PENDING;
-                S.runAgg[r] = (uint8_t)agg;
                 if ((S.constF >> agg) & 1u) {
                     // stuck by the end of this tile whatever its entry: publish
                     // that bound as the first fault (the exact one, recorded
@@ -530,7 +524,6 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                     atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(base + T - 1));
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16) | NO_NODE;
                 } else {
-                    S.runHead[r] = hdv[k];
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
                     p.node_status[nodeBase + r] = (uint8_t)(NODE_AGG | agg);
                 }
@@ -556,7 +549,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 mine |= 1u << u;
                 node[u] = nodeBase + (e & 0xFFFFu);
                 var[u] = kvar((int)(e >> 16));
-                c[u] = S.runHead[e & 0xFFFFu];           // prefetched; a stale value fails the CAS
+                c[u] = __ldcg(p.head + var[u]);
             }
         }
 #pragma unroll
@@ -629,7 +622,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     PHASE(5)
     // ---- 5c. look-back along the lists, PW runs per thread in step -----------
     for (int lo = 0; lo < nPend; lo += NT * PW) {
-        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW], ffw[PW];
+        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW], ffw[PW], ag[PW];
         uint32_t active = 0, nonode = 0;
 #pragma unroll
         for (int u = 0; u < PW; ++u) {
@@ -637,7 +630,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             a[u] = ID;
             st[u] = 0;
             q[u] = NIL;
-            node[u] = var[u] = rr[u] = 0;
+            node[u] = var[u] = rr[u] = ag[u] = 0;
             ffw[u] = 0xFFFFFFFFu;
             if (i < nPend) {
                 const uint32_t e = pend[i];
@@ -650,6 +643,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 } else {
                     node[u] = nodeBase + rr[u];
                     q[u] = ld_acquire(p.node_next + node[u]);
+                    ag[u] = __ldcg(p.node_status + node[u]) & 31u;   // the run's aggregate (AGG status)
                 }
                 ffw[u] = ld_acquire(reinterpret_cast<const uint32_t*>(p.vff) + var[u]);
             }
@@ -698,7 +692,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             const uint32_t entry = S.app[a[u] * 8 + st[u]];
             S.runEntry[rr[u]] = (uint8_t)entry;
             if (!(nonode & (1u << u)))
-                st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
+                st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[ag[u] * 8 + entry]);
         }
     }
     __syncthreads();
@@ -1041,10 +1035,10 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
         return ((uint64_t)kvar(j) << 8) | (uint64_t)(S.livePos[kidx(j)] >> POS_BITS);
     };
 
-    // ---- 4a. run boundaries; stuck-shortcut and list-head loads ------------
+    // ---- 4a. run boundaries; stuck-shortcut loads ---------------------------
     const int j0 = tid * E;
     uint32_t headMask = 0, lastMask = 0;
-    uint32_t ffv[E], hdv[E];
+    uint32_t ffv[E];
     {
         uint64_t prev = (j0 > 0 && j0 - 1 < nl) ? rkey(j0 - 1) : ~0ull;
         uint64_t cur = (j0 < nl) ? rkey(j0) : ~1ull;
@@ -1053,14 +1047,12 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             const int j = j0 + k;
             const uint64_t nxt = (j + 1 < nl) ? rkey(j + 1) : ~2ull;
             ffv[k] = 0xFFFFFFFFu;
-            hdv[k] = NIL;
             if (j < nl) {
                 if (cur != prev) headMask |= 1u << k;
                 if (nxt != cur) {
                     lastMask |= 1u << k;
                     const uint32_t v = (uint32_t)(cur >> 8);
                     ffv[k] = __ldcg(reinterpret_cast<const unsigned int*>(p.vff) + v);
-                    hdv[k] = __ldcg(p.head + v);
                 }
             }
             prev = cur;
@@ -1152,13 +1144,11 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             } else {
                 const uint32_t agg = getb(pmw, k);
                 S.runEntry[r] = RUN_PENDING;
-                S.runAgg[r] = (uint8_t)agg;
                 if ((S.constF >> agg) & 1u) {
                     // stuck by the end of its tile: bound as first fault, no node
                     atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(rbase + T - 1));
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16) | NO_NODE;
                 } else {
-                    S.runHead[r] = hdv[k];
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
                     p.node_status[(uint32_t)(t0 + g) * (uint32_t)T + (uint32_t)r] = (uint8_t)(NODE_AGG | agg);
                 }
@@ -1184,7 +1174,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 ntile[u] = (uint32_t)t0 + (uint32_t)(S.livePos[kidx(j)] >> POS_BITS);
                 node[u] = ntile[u] * (uint32_t)T + (e & 0xFFFFu);
                 var[u] = kvar(j);
-                c[u] = S.runHead[e & 0xFFFFu];
+                c[u] = __ldcg(p.head + var[u]);
             }
         }
 #pragma unroll
@@ -1249,7 +1239,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
 
     // ---- 5c. look-back along the lists -------------------------------------
     for (int lo = 0; lo < nPend; lo += NT * PW) {
-        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW], ffw[PW], rt[PW];
+        uint32_t q[PW], a[PW], st[PW], node[PW], var[PW], rr[PW], ffw[PW], rt[PW], ag[PW];
         uint32_t active = 0, nonode = 0;
 #pragma unroll
         for (int u = 0; u < PW; ++u) {
@@ -1257,7 +1247,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             a[u] = ID;
             st[u] = 0;
             q[u] = NIL;
-            node[u] = var[u] = rr[u] = rt[u] = 0;
+            node[u] = var[u] = rr[u] = rt[u] = ag[u] = 0;
             ffw[u] = 0xFFFFFFFFu;
             if (i < nPend) {
                 const uint32_t e = pend[i];
@@ -1272,6 +1262,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 } else {
                     node[u] = rt[u] * (uint32_t)T + rr[u];
                     q[u] = ld_acquire(p.node_next + node[u]);
+                    ag[u] = __ldcg(p.node_status + node[u]) & 31u;   // the run's aggregate (AGG status)
                 }
                 ffw[u] = ld_acquire(reinterpret_cast<const uint32_t*>(p.vff) + var[u]);
             }
@@ -1318,7 +1309,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             const uint32_t entry = S.app[a[u] * 8 + st[u]];
             S.runEntry[rr[u]] = (uint8_t)entry;
             if (!(nonode & (1u << u)))
-                st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[S.runAgg[rr[u]] * 8 + entry]);
+                st_relaxed_u8(p.node_status + node[u], NODE_INCL | S.app[ag[u] * 8 + entry]);
         }
     }
     __syncthreads();
@@ -1367,7 +1358,7 @@ __device__ __forceinline__ void issue_tile(const ScanParams& p, ScanSmem<KeyT, T
 }
 
 template <typename KeyT, int T, int NT>
-__global__ void __launch_bounds__(NT, 3) scan_trace_kernel(const ScanParams p)
+__global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const ScanParams p)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     ScanSmem<KeyT, T, NT>& S = *reinterpret_cast<ScanSmem<KeyT, T, NT>*>(smem_raw);
@@ -1509,10 +1500,21 @@ int launch_kernel(ScanParams p, const ScanLaunch& L, cudaStream_t s)
     if (p.fbw > room) p.fbw = room > 0 ? (int)room : 0;          // shared bitmap words (multiple of 4)
     const size_t smem = sizeof(ScanSmem<KeyT, TILE, THREADS>) + 4 * (size_t)p.fbw;
     static size_t attr_set[64] = {};
-    if (dev >= 64 || attr_set[dev] < smem) {
+    if (dev >= 64 || attr_set[dev] != smem) {
         if (cudaFuncSetAttribute(scan_trace_kernel<KeyT, TILE, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return AMC_E_CUDA;
+        // ask for the smallest shared-memory carve-out that still holds the
+        // resident CTAs, so that the rest of the SM's memory serves as L1 for
+        // the stuck bitmap
+        int per_sm_smem = 0;
+        cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (per_sm_smem > 0) {
+            const size_t need = (size_t)MAX_CTAS_PER_SM * (smem + 1024);
+            const int pct = (int)min((size_t)100, (need * 100 + (size_t)per_sm_smem - 1) / (size_t)per_sm_smem);
+            cudaFuncSetAttribute(scan_trace_kernel<KeyT, TILE, THREADS>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        }
         if (dev < 64) attr_set[dev] = smem;
     }
     int n_sm = 0, per_sm = 0;
