@@ -656,10 +656,20 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 active &= ~(1u << u);
             }
         for (uint32_t hop = 0; active; ++hop) {
-            uint32_t sv[PW];
+            // a node's status and its next pointer are read together: below
+            // the walking tile the list no longer changes (every earlier tile
+            // has inserted before the frontier passed), and either status of
+            // a node (aggregate or inclusive) is a valid answer
+            uint32_t sv[PW], nx[PW];
 #pragma unroll
-            for (int u = 0; u < PW; ++u)
-                sv[u] = ((active & (1u << u)) && q[u] != NIL) ? ld_acquire_u8(p.node_status + q[u]) : 0u;
+            for (int u = 0; u < PW; ++u) {
+                sv[u] = 0;
+                nx[u] = NIL;
+                if ((active & (1u << u)) && q[u] != NIL) {
+                    sv[u] = ld_relaxed_u8(p.node_status + q[u]);
+                    nx[u] = ld_relaxed(p.node_next + q[u]);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < PW; ++u) {
                 if (!(active & (1u << u))) continue;
@@ -683,7 +693,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
             }
 #pragma unroll
             for (int u = 0; u < PW; ++u)
-                if (active & (1u << u)) q[u] = ld_acquire(p.node_next + q[u]);
+                if (active & (1u << u)) q[u] = nx[u];
             if (hop > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
         }
 #pragma unroll
@@ -1275,10 +1285,20 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 active &= ~(1u << u);
             }
         for (uint32_t hop = 0; active; ++hop) {
-            uint32_t sv[PW];
+            // a node's status and its next pointer are read together: below
+            // the walking tile the list no longer changes (every earlier tile
+            // has inserted before the frontier passed), and either status of
+            // a node (aggregate or inclusive) is a valid answer
+            uint32_t sv[PW], nx[PW];
 #pragma unroll
-            for (int u = 0; u < PW; ++u)
-                sv[u] = ((active & (1u << u)) && q[u] != NIL) ? ld_acquire_u8(p.node_status + q[u]) : 0u;
+            for (int u = 0; u < PW; ++u) {
+                sv[u] = 0;
+                nx[u] = NIL;
+                if ((active & (1u << u)) && q[u] != NIL) {
+                    sv[u] = ld_relaxed_u8(p.node_status + q[u]);
+                    nx[u] = ld_relaxed(p.node_next + q[u]);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < PW; ++u) {
                 if (!(active & (1u << u))) continue;
@@ -1300,7 +1320,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             }
 #pragma unroll
             for (int u = 0; u < PW; ++u)
-                if (active & (1u << u)) q[u] = ld_acquire(p.node_next + q[u]);
+                if (active & (1u << u)) q[u] = nx[u];
             if (hop > SPIN_LIMIT) { raise_error(p.err, AMC_E_TIMEOUT); break; }
         }
 #pragma unroll
