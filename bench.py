@@ -428,6 +428,17 @@ def run_programs(args):
     print(json.dumps(line), flush=True)
 
 
+def vectorpu_launches(n_statements, n_vars):
+    """Kernels of one translation + guarded check: 11 for the translation
+    (two overlap passes, count, emit, total, two 3-kernel scans), then per
+    check pass 3 on the reduce / carry / apply path (traces over at most
+    16,384 variables from 2^20 ops on), else the scan kernel plus, in the
+    second pass, the final-status kernel."""
+    if n_vars <= 16384 and n_statements >= (1 << 20) and os.environ.get("AMC_SCAN_DENSE", "") != "0":
+        return 11 + 2 * 3
+    return 11 + 1 + 2
+
+
 def run_vectorpu(args):
     """Translation + guarded check of the 2^24-call VectorPU workload."""
     import numpy as np
@@ -460,7 +471,7 @@ def run_vectorpu(args):
     n_calls = d["call_side"].numel()
     line = base_line(args, n / (ms * 1e-3), ms,
                      {"workload": "vectorpu_calls", "n_arrays": A, "n_calls": n_calls, "statements": n, "seed": 2},
-                     calls_per_s=n_calls / (ms * 1e-3), gpu_launches=args.steps * 12)
+                     calls_per_s=n_calls / (ms * 1e-3), gpu_launches=args.steps * vectorpu_launches(n, 2 * A))
     print(json.dumps(line), flush=True)
 
 

@@ -17,9 +17,12 @@ namespace {
 
 inline bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
 
-size_t guarded_extra_bytes(int32_t n_vars)
+// the guard pass's first faults (discarded), then its pre-statuses: the guards
+// of the second pass, in a buffer of their own so that no pass reads what it
+// writes
+size_t guarded_extra_bytes(int64_t n_ops, int32_t n_vars)
 {
-    return align_up(4 * (size_t)n_vars, 256) + 256;
+    return align_up(4 * (size_t)n_vars, 256) + 256 + align_up((size_t)n_ops, 256);
 }
 
 int check_trace_args(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
@@ -138,7 +141,7 @@ int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
 size_t amc_check_guarded_trace_workspace(int64_t n_ops, int32_t n_vars)
 {
     if (n_ops < 0 || n_vars < 0) return 0;
-    return scan_workspace_bytes(n_ops, n_vars) + guarded_extra_bytes(n_vars);
+    return scan_workspace_bytes(n_ops, n_vars) + guarded_extra_bytes(n_ops, n_vars);
 }
 
 int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
@@ -158,6 +161,7 @@ int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_
     uint8_t* extra = w + scan_workspace_bytes(n_ops, n_vars);
     int32_t* vff_scratch = reinterpret_cast<int32_t*>(extra);
     int64_t* ff_scratch = reinterpret_cast<int64_t*>(extra + align_up(4 * (size_t)n_vars, 256));
+    uint8_t* guard = extra + align_up(4 * (size_t)n_vars, 256) + 256;
     // pass 1: pre-statuses of every op with GT as Noop (guards read abstract
     // variables, which GT never touches)
     ScanLaunch A;
@@ -166,7 +170,7 @@ int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_
     A.n_ops = n_ops;
     A.n_vars = n_vars;
     A.init = init_status;
-    A.step = step_status;
+    A.step = guard;
     A.vff = vff_scratch;
     A.first_fault = ff_scratch;
     A.pre_mode = 1;
@@ -187,7 +191,7 @@ int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_
     B.final_status = final_status;
     B.vff = var_first_fault;
     B.first_fault = first_fault;
-    B.guard = step_status;
+    B.guard = guard;
     B.pre_mode = 0;
     B.profile = 2;
     return launch_scan_trace(B, s);

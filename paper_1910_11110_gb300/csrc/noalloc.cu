@@ -45,7 +45,8 @@ extern "C" int amc_check_trace_noalloc(const uint8_t* kind_side, const int32_t* 
 {
     if (n_ops < 0 || n_vars < 0) return AMC_E_INVALID;
     if (n_ops > AMC_NOALLOC_MAX_OPS || n_vars > AMC_NOALLOC_MAX_VARS) return AMC_E_RANGE;
-    if (amc::scan_workspace_bytes(n_ops, n_vars) > (size_t)AMC_NOALLOC_SCRATCH_BYTES) return AMC_E_RANGE;
+    // the single-pass path only: its scratch fits the array at the maximum sizes
+    if (amc::scan_workspace_bytes(n_ops, n_vars, false) > (size_t)AMC_NOALLOC_SCRATCH_BYTES) return AMC_E_RANGE;
     if (n_ops > 0 && (n_vars < 1 || !kind_side || !var || !step_status)) return AMC_E_INVALID;
     if (n_vars > 0 && (!final_status || !var_first_fault)) return AMC_E_INVALID;
     if (!first_fault) return AMC_E_INVALID;
@@ -64,5 +65,6 @@ extern "C" int amc_check_trace_noalloc(const uint8_t* kind_side, const int32_t* 
     L.first_fault = first_fault;
     L.err = err;
     L.workspace = scratch;
+    L.dense = 0;
     return amc::launch_scan_trace(L, static_cast<cudaStream_t>(stream));
 }

@@ -1,0 +1,447 @@
+// scan_dense.cu -- the trace check for traces over few variables (reduce,
+// carry, apply), where nearly every op stays live.
+//
+// What it computes is what scan_trace.cu computes: for every op the status of
+// its variable after (or, in the guard pass, before) the op, by applying the
+// transfer functions of Fig. Opsem in trace order; sequencing is associative
+// (Section 3.2), so the trace may be cut into chunks whose per-variable
+// compositions are combined afterwards.
+//
+// Over few variables the per-variable lists of the single-pass kernel become
+// long and every tile in flight contends for the same ones.  Here instead:
+//  1. reduce: CTA c takes chunk c (consecutive 4,096-op tiles) and, tile by
+//     tile, sorts the ops by variable, composes each variable's run and folds
+//     it into a dense per-variable element vector in shared memory; the vector
+//     is written out (one byte per variable and chunk);
+//  2. carry: one thread per variable walks the chunks in order, applying the
+//     chunk aggregates to the initial status: the status at every chunk entry
+//     and the final status;
+//  3. apply: CTA c runs its tiles again from the entry statuses, writes every
+//     op's status, the per-variable first faults (atomicMin) and the global one.
+// No CTA waits on another, so the grid may exceed what is resident.
+#include <cstdlib>
+
+#include "amc_internal.cuh"
+#include "scan_trace.cuh"
+
+namespace amc {
+
+namespace {
+
+constexpr int DT = 4096;                 // ops per tile
+constexpr int DNT = 256;                 // threads per CTA
+constexpr int DE = DT / DNT;             // sorted slots per thread
+constexpr int DNW = DNT / 32;
+constexpr int DPOS = 12;                 // log2(DT): position bits of a key
+constexpr int DDIG = 7;                  // radix digit bits
+constexpr int DENSE_MAX_VARS = 16384;    // the dense vector lives in shared memory
+constexpr int DENSE_MAX_CHUNKS = 2048;
+constexpr int64_t DENSE_MIN_OPS = 1 << 20;
+
+__device__ __forceinline__ int dpad(int i) { return i + (i >> 5); }
+
+struct DenseParams {
+    const uint8_t* kind_side;
+    const int32_t* var;
+    int64_t n_ops;
+    int32_t n_vars;
+    const uint8_t* init;
+    uint8_t* step;
+    int32_t* vff;
+    int64_t* first_fault;
+    uint8_t* final_status;
+    const uint8_t* guard;
+    int pre_mode;
+    int* err;
+    uint8_t* aggs;                       // [n_chunks][n_vars] chunk aggregates (elements)
+    uint8_t* entry;                      // [n_chunks][n_vars] statuses at chunk entry
+    int n_tiles;
+    int n_chunks;
+    int tiles_per_chunk;
+    int passes;
+    int digit_bits;
+    Tables tab;
+};
+
+struct __align__(16) DenseSmem {
+    uint32_t keyA[DT + DT / 32];
+    uint32_t keyB[DT + DT / 32];         // staged var ids, then a sort buffer
+    uint8_t kind[DT];
+    uint8_t mel[DT];                     // element of each op, by position
+    uint8_t out[DT];
+    uint16_t hist[DNW << DDIG];
+    uint8_t comp[MAX_ELEMS * MAX_ELEMS];
+    uint8_t app[MAX_ELEMS * 8];
+    uint8_t elem_of[256];
+    int scanTmp[DNW + 2];
+    uint8_t segF[DNW];
+    uint8_t segV[DNW];
+    // followed (dynamic shared memory) by the per-variable vector: n_vars bytes
+};
+
+// One tile: load, decode, sort by variable, segmented scan; then either fold
+// the runs into the aggregate vector (REDUCE) or emit the ops' statuses from
+// the status vector and advance it (APPLY).
+template <bool APPLY>
+__device__ void dense_tile(const DenseParams& p, DenseSmem& S, uint8_t* vec, const int t)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t ID = p.tab.identity;
+    const int64_t base = (int64_t)t * DT;
+    const int n = (int)min((int64_t)DT, p.n_ops - base);
+    int32_t* vraw = reinterpret_cast<int32_t*>(S.keyB);
+
+    // ---- load (coalesced 16-byte loads for a full, aligned tile) ------------
+    const bool vec16 = n == DT && ((uintptr_t)(p.kind_side + base) % 16 == 0) && ((uintptr_t)(p.var + base) % 16 == 0);
+    if (vec16) {
+        for (int i = tid; i < DT / 16; i += DNT)
+            reinterpret_cast<uint4*>(S.kind)[i] = __ldcs(reinterpret_cast<const uint4*>(p.kind_side + base) + i);
+        for (int i = tid; i < DT / 4; i += DNT)
+            reinterpret_cast<int4*>(vraw)[i] = __ldcs(reinterpret_cast<const int4*>(p.var + base) + i);
+    } else {
+        for (int i = tid; i < n; i += DNT) {
+            S.kind[i] = p.kind_side[base + i];
+            vraw[i] = p.var[base + i];
+        }
+    }
+    __syncthreads();
+
+    // ---- decode: element per op, validation, keys (var << 12 | position) ----
+    for (int i = tid; i < n; i += DNT) {
+        const uint32_t ks = S.kind[i];
+        if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
+        int32_t v = vraw[i];
+        if (v < 0 || v >= p.n_vars) {
+            raise_error(p.err, AMC_E_RANGE);
+            v = 0;
+        }
+        uint32_t m = S.elem_of[ks];
+        if (m == ELEM_GT) {
+            // GT must be followed by EN of the same side on another variable
+            const int64_t gi = base + i;
+            uint32_t nks = 0xFF;
+            int32_t nv = v;
+            if (gi + 1 < p.n_ops) {
+                nks = (i + 1 < n) ? S.kind[i + 1] : p.kind_side[gi + 1];
+                nv = (i + 1 < n) ? vraw[i + 1] : p.var[gi + 1];
+            }
+            const bool gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != v;
+            if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
+            if (!gt_ok || p.pre_mode) {
+                m = ID;                              // guard pass: GT does not touch guards
+            } else if (!p.guard) {
+                raise_error(p.err, AMC_E_INVALID);   // GT needs the guarded entry point
+                m = ID;
+            } else {
+                // guard = status of the EN's variable before the EN (guard pass)
+                const uint32_t gs = p.guard[gi + 1];
+                const int side = ks >> 4;
+                const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
+                m = valid ? ID : p.tab.pull_of_side[side];
+            }
+        } else if (m == ELEM_BAD) {
+            m = ID;
+        }
+        S.mel[i] = (uint8_t)m;
+        S.keyA[dpad(i)] = ((uint32_t)v << DPOS) | (uint32_t)i;
+    }
+    __syncthreads();
+
+    // ---- stable LSD radix sort by variable (warp ranking with match.any) ----
+    uint32_t* kin = S.keyA;
+    uint32_t* kout = S.keyB;
+    for (int pass = 0; pass < p.passes; ++pass) {
+        const int D = 1 << p.digit_bits;
+        const int shift = DPOS + pass * p.digit_bits;
+        uint16_t* hrow = S.hist + warp * D;
+        for (int i = lane; i < D; i += 32) hrow[i] = 0;
+        __syncwarp();
+        uint32_t kk[DE];
+        uint16_t lr[DE];
+#pragma unroll
+        for (int e = 0; e < DE; ++e) {
+            const int pos = warp * 32 * DE + e * 32 + lane;
+            const bool ok = pos < n;
+            const uint32_t key = ok ? kin[dpad(pos)] : 0u;
+            kk[e] = key;
+            const uint32_t dig = ok ? ((key >> shift) & (uint32_t)(D - 1)) : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+            const uint32_t rank = __popc(peers & lt);
+            uint16_t c = 0;
+            if (ok) c = hrow[dig];
+            lr[e] = (uint16_t)(c + rank);
+            __syncwarp();
+            if (ok && rank == 0) hrow[dig] = (uint16_t)(c + __popc(peers));
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            // exclusive scan of the counts in (digit, warp) order
+            const int per = (D + DNT - 1) / DNT;
+            const int d0 = tid * per;
+            int sum = 0;
+            for (int d = d0; d < d0 + per && d < D; ++d)
+#pragma unroll
+                for (int w = 0; w < DNW; ++w) sum += S.hist[w * D + d];
+            int run = block_excl_sum<DNT>(sum, S.scanTmp, nullptr);
+            for (int d = d0; d < d0 + per && d < D; ++d)
+#pragma unroll
+                for (int w = 0; w < DNW; ++w) {
+                    const int c = S.hist[w * D + d];
+                    S.hist[w * D + d] = (uint16_t)run;
+                    run += c;
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < DE; ++e) {
+            const int pos = warp * 32 * DE + e * 32 + lane;
+            if (pos < n) {
+                const uint32_t dig = (kk[e] >> shift) & (uint32_t)(D - 1);
+                kout[dpad(hrow[dig] + lr[e])] = kk[e];
+            }
+        }
+        __syncthreads();
+        uint32_t* tk = kin;
+        kin = kout;
+        kout = tk;
+    }
+    const uint32_t* K = kin;
+    auto kvar = [&](int j) -> uint32_t { return K[dpad(j)] >> DPOS; };
+    auto kpos = [&](int j) -> int { return (int)(K[dpad(j)] & (uint32_t)(DT - 1)); };
+
+    // ---- segmented scan over runs (blocked: thread owns DE sorted slots) -----
+    const int j0 = tid * DE;
+    uint32_t headMask = 0, lastMask = 0;
+    {
+        uint32_t prev = (j0 > 0 && j0 - 1 < n) ? kvar(j0 - 1) : 0xFFFFFFFFu;
+        uint32_t cur = (j0 < n) ? kvar(j0) : 0xFFFFFFFEu;
+#pragma unroll
+        for (int k = 0; k < DE; ++k) {
+            const int j = j0 + k;
+            const uint32_t nxt = (j + 1 < n) ? kvar(j + 1) : 0xFFFFFFFDu;
+            if (j < n) {
+                if (cur != prev) headMask |= 1u << k;
+                if (nxt != cur) lastMask |= 1u << k;
+            }
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    uint8_t pm[DE], xm[DE];
+    uint32_t acc = ID;
+#pragma unroll
+    for (int k = 0; k < DE; ++k) {
+        const int j = j0 + k;
+        pm[k] = xm[k] = (uint8_t)ID;
+        if (j < n) {
+            const uint32_t m = S.mel[kpos(j)];
+            if (headMask & (1u << k)) {
+                acc = m;
+            } else {
+                xm[k] = (uint8_t)acc;
+                acc = S.comp[acc * MAX_ELEMS + m];
+            }
+            pm[k] = (uint8_t)acc;
+        }
+    }
+    uint32_t carry;
+    {
+        uint32_t f = headMask != 0, v = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t fu = __shfl_up_sync(0xffffffffu, f, o);
+            const uint32_t vu = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) {
+                if (!f) v = S.comp[vu * MAX_ELEMS + v];
+                f |= fu;
+            }
+        }
+        uint32_t fe = __shfl_up_sync(0xffffffffu, f, 1);
+        uint32_t ve = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) { fe = 0; ve = ID; }
+        if (lane == 31) { S.segF[warp] = (uint8_t)f; S.segV[warp] = (uint8_t)v; }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t wf = lane < DNW ? S.segF[lane] : 0, wv = lane < DNW ? S.segV[lane] : ID;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t fu = __shfl_up_sync(0xffffffffu, wf, o);
+                const uint32_t vu = __shfl_up_sync(0xffffffffu, wv, o);
+                if (lane >= o) {
+                    if (!wf) wv = S.comp[vu * MAX_ELEMS + wv];
+                    wf |= fu;
+                }
+            }
+            uint32_t xf = __shfl_up_sync(0xffffffffu, wf, 1);
+            uint32_t xv = __shfl_up_sync(0xffffffffu, wv, 1);
+            if (lane == 0) { xf = 0; xv = ID; }
+            if (lane < DNW) { S.segF[lane] = (uint8_t)xf; S.segV[lane] = (uint8_t)xv; }
+        }
+        __syncthreads();
+        carry = fe ? ve : S.comp[S.segV[warp] * MAX_ELEMS + ve];
+    }
+    // slots before the thread's first head continue a run from earlier threads
+#pragma unroll
+    for (int k = 0; k < DE; ++k) {
+        if ((headMask & ((2u << k) - 1)) == 0) {
+            pm[k] = S.comp[carry * MAX_ELEMS + pm[k]];
+            xm[k] = S.comp[carry * MAX_ELEMS + xm[k]];
+        }
+    }
+
+    if constexpr (!APPLY) {
+        // fold each run (one per variable in the tile) into the chunk aggregate
+#pragma unroll
+        for (int k = 0; k < DE; ++k)
+            if (lastMask & (1u << k)) {
+                const uint32_t v = kvar(j0 + k);
+                vec[v] = S.comp[vec[v] * MAX_ELEMS + pm[k]];
+            }
+        __syncthreads();
+    } else {
+    // ---- apply: statuses from the variable's status at tile entry ------------
+    uint8_t post_last[DE];
+#pragma unroll
+    for (int k = 0; k < DE; ++k) {
+        const int j = j0 + k;
+        post_last[k] = 0;
+        if (j < n) {
+            const uint32_t v = kvar(j);
+            const uint32_t e = vec[v];
+            const uint32_t pre = S.app[xm[k] * 8 + e];
+            const uint32_t post = S.app[pm[k] * 8 + e];
+            const int pos = kpos(j);
+            S.out[pos] = (uint8_t)(p.pre_mode ? pre : post);
+            post_last[k] = (uint8_t)post;
+            if (post == ST_F && pre != ST_F) {
+                const uint32_t gi = (uint32_t)(base + pos);
+                atomicMin(reinterpret_cast<uint32_t*>(p.vff) + v, gi);
+                atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
+            }
+        }
+    }
+    __syncthreads();                         // every op has read its entry status
+#pragma unroll
+    for (int k = 0; k < DE; ++k)
+        if (lastMask & (1u << k)) vec[kvar(j0 + k)] = post_last[k];
+    if (vec16 && ((uintptr_t)(p.step + base) % 16 == 0)) {
+        for (int i = tid; i < DT / 16; i += DNT)
+            reinterpret_cast<uint4*>(p.step + base)[i] = reinterpret_cast<const uint4*>(S.out)[i];
+    } else {
+        for (int i = tid; i < n; i += DNT) p.step[base + i] = S.out[i];
+    }
+    __syncthreads();
+    }
+}
+
+template <bool APPLY>
+__global__ void __launch_bounds__(DNT) dense_chunk_kernel(const DenseParams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    DenseSmem& S = *reinterpret_cast<DenseSmem*>(smem);
+    uint8_t* vec = smem + sizeof(DenseSmem);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += DNT) S.comp[i] = p.tab.comp[i];
+    for (int i = tid; i < MAX_ELEMS * 8; i += DNT) S.app[i] = p.tab.app[i];
+    for (int i = tid; i < 256; i += DNT) S.elem_of[i] = p.tab.elem_of[i];
+    const int c = blockIdx.x;
+    for (int v = tid; v < p.n_vars; v += DNT)
+        vec[v] = APPLY ? p.entry[(size_t)c * p.n_vars + v] : p.tab.identity;
+    __syncthreads();
+    const int t0 = c * p.tiles_per_chunk;
+    const int t1 = min(t0 + p.tiles_per_chunk, p.n_tiles);
+    for (int t = t0; t < t1; ++t) dense_tile<APPLY>(p, S, vec, t);
+    if (!APPLY)
+        for (int v = tid; v < p.n_vars; v += DNT) p.aggs[(size_t)c * p.n_vars + v] = vec[v];
+}
+
+// Thread per variable: status at every chunk entry, then the final status.
+__global__ void dense_carry_kernel(const DenseParams p)
+{
+    __shared__ uint8_t app[MAX_ELEMS * 8];
+    for (int i = threadIdx.x; i < MAX_ELEMS * 8; i += blockDim.x) app[i] = p.tab.app[i];
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= p.n_vars) return;
+    uint32_t e = p.init ? p.init[v] : (uint32_t)AMC_ST_VI;
+    const size_t V = (size_t)p.n_vars;
+#pragma unroll 8
+    for (int c = 0; c < p.n_chunks; ++c) {
+        p.entry[(size_t)c * V + v] = (uint8_t)e;
+        e = app[p.aggs[(size_t)c * V + v] * 8 + e];
+    }
+    if (p.final_status) p.final_status[v] = (uint8_t)e;
+}
+
+void dense_shape(int64_t n_ops, int& n_tiles, int& n_chunks, int& tpc)
+{
+    n_tiles = (int)((n_ops + DT - 1) / DT);
+    const int want = n_tiles < DENSE_MAX_CHUNKS ? n_tiles : DENSE_MAX_CHUNKS;
+    tpc = want > 0 ? (n_tiles + want - 1) / want : 1;
+    n_chunks = tpc > 0 ? (n_tiles + tpc - 1) / tpc : 0;
+}
+
+}  // namespace
+
+bool scan_dense_eligible(int64_t n_ops, int32_t n_vars)
+{
+    if (n_vars < 1 || n_vars > DENSE_MAX_VARS || n_ops < 1) return false;
+    if (const char* e = getenv("AMC_SCAN_DENSE")) return e[0] == '1';   // tuning and test override
+    return n_ops >= DENSE_MIN_OPS;
+}
+
+size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)
+{
+    if (n_vars < 1 || n_vars > DENSE_MAX_VARS || n_ops < 1) return 0;
+    int n_tiles, n_chunks, tpc;
+    dense_shape(n_ops, n_tiles, n_chunks, tpc);
+    return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256);
+}
+
+int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
+{
+    DenseParams p{};
+    p.kind_side = L.kind_side;
+    p.var = L.var;
+    p.n_ops = L.n_ops;
+    p.n_vars = L.n_vars;
+    p.init = L.init;
+    p.step = L.step;
+    p.vff = L.vff;
+    p.first_fault = L.first_fault;
+    p.final_status = L.final_status;
+    p.guard = L.guard;
+    p.pre_mode = L.pre_mode;
+    p.err = L.err;
+    p.tab = host_tables();
+    dense_shape(L.n_ops, p.n_tiles, p.n_chunks, p.tiles_per_chunk);
+    const size_t vb = align_up((size_t)p.n_chunks * (size_t)L.n_vars, 256);
+    p.aggs = ws;
+    p.entry = ws + vb;
+    int kb = 1;
+    while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
+    p.passes = (kb + DDIG - 1) / DDIG;
+    p.digit_bits = (kb + p.passes - 1) / p.passes;
+
+    if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
+    const size_t smem = sizeof(DenseSmem) + (size_t)L.n_vars;
+    if (cudaFuncSetAttribute(dense_chunk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(dense_chunk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return AMC_E_CUDA;
+    if (L.profile & 1) profile_begin(s);
+    dense_chunk_kernel<false><<<p.n_chunks, DNT, smem, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    dense_carry_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    dense_chunk_kernel<true><<<p.n_chunks, DNT, smem, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    if (L.profile & 2) profile_end(s);
+    return AMC_OK;
+}
+
+}  // namespace amc

@@ -1574,7 +1574,7 @@ int scan_phase_profile(int enable, unsigned long long* host_out)
     return AMC_OK;
 }
 
-size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars)
+size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars, bool with_dense)
 {
     const int64_t n_tiles = (n_ops + TILE - 1) / TILE;
     size_t b = 0;
@@ -1584,6 +1584,7 @@ size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars)
     b += align_up(4 * (size_t)((n_tiles + 31) / 32), 256);  // registration bits
     b += 2 * align_up(16 * (size_t)((n_vars + 127) / 128), 256); // stuck bitmap, two copies
     b += 256;                                               // tile counter, frontier
+    if (with_dense) b += scan_dense_workspace_bytes(n_ops, n_vars);   // reduce / carry / apply path
     return b;
 }
 
@@ -1629,6 +1630,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     }
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
+    if (L.dense != 0 && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
     // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
     int kb = 1;
     while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
@@ -1639,13 +1641,6 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
         const int g = atoi(e);
         p.group_max = max(1, min(g < 0 ? -g : g, GROUP_MAX));
         p.group_force = g < 0;
-    }
-    // the guard-resolving pass reads its guards from the buffer it writes; the
-    // tile path stores a tile only after its frontier wait, which orders those
-    // reads before the overwrite, while the group path writes during its decode
-    if (L.guard) {
-        p.group_max = 1;
-        p.group_force = 0;
     }
     p.digit_bits = (kb + p.passes - 1) / p.passes;
     p.bulk_ok = ((uintptr_t)L.kind_side % 16 == 0) && ((uintptr_t)L.var % 16 == 0) &&

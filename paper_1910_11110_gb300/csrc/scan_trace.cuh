@@ -57,11 +57,18 @@ struct ScanLaunch {
                                         // -1 = no bitmap, -2 = bitmap read through L1)
     int group_max = 0;                  // most tiles per claim (0 = default, 1 = tile path only)
     int ctas_per_sm = 0;                // resident CTAs per SM (0 = as many as fit)
+    int dense = -1;                     // reduce / carry / apply path: -1 when eligible, 0 never
 };
 
 int scan_tile_size();
-size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars);
+size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars, bool with_dense = true);
 int launch_scan_trace(const ScanLaunch& L, cudaStream_t s);
+// Traces over at most 16,384 variables and of 2^20 ops or more (or whenever
+// AMC_SCAN_DENSE=1; never when it is 0) take the reduce / carry / apply path
+// of scan_dense.cu; its scratch follows the single-pass workspace.
+bool scan_dense_eligible(int64_t n_ops, int32_t n_vars);
+size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars);
+int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
 // enable >= 0: switch phase counting on/off and zero the counters; host_out
 // (nullable): copy the 8 counters (cycles summed over CTAs).
 int scan_phase_profile(int enable, unsigned long long* host_out);
