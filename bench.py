@@ -333,9 +333,9 @@ def run_ours(args):
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_kind": peak_kind,
                              "frac_of_8tbs": achieved / 8000.0, "traffic": traffic,
-                             "kernel": "scan_trace_kernel", "kernel_ms": k_ms,
+                             "kernel": trace_kernels(n_ops, n_vars)[0], "kernel_ms": k_ms,
                              "algorithmic_bytes": alg_bytes},
-                "gpu_launches": 2 * args.steps,
+                "gpu_launches": trace_kernels(n_ops, n_vars)[1] * args.steps,
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -553,6 +553,22 @@ def run_serve(args):
                       "slots": 32, "budget_gb": 32, "seed": 4},
                      serve=results)
     print(json.dumps(line), flush=True)
+
+
+def trace_kernels(n_ops, n_vars):
+    """(what the timed span covers, kernels launched per check) for
+    amc_check_trace without initial statuses: the reduce / carry / apply path
+    over at most 16,384 variables from 2^20 ops; over more (at most 2^20)
+    variables from 2^24 ops that path on the first 2^22 ops, then the stuck
+    bitmap seeded from its final statuses, the single-pass scan, the final
+    statuses and the first-fault merge; else the scan and the final statuses."""
+    if os.environ.get("AMC_SCAN_DENSE", "") == "0":
+        return "scan_trace_kernel", 2
+    if n_vars <= 16384 and n_ops >= (1 << 20):
+        return "dense reduce + carry + apply kernels", 3
+    if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
+        return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7
+    return "scan_trace_kernel", 2
 
 
 def scan_traffic(n_ops, n_vars):

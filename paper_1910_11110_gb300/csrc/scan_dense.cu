@@ -44,6 +44,7 @@ struct DenseParams {
     const uint8_t* kind_side;
     const int32_t* var;
     int64_t n_ops;
+    int64_t n_ops_follow;                // ops readable after position i (a GT's EN may lie beyond n_ops)
     int32_t n_vars;
     const uint8_t* init;
     uint8_t* step;
@@ -122,7 +123,7 @@ __device__ void dense_tile(const DenseParams& p, DenseSmem& S, uint8_t* vec, con
             const int64_t gi = base + i;
             uint32_t nks = 0xFF;
             int32_t nv = v;
-            if (gi + 1 < p.n_ops) {
+            if (gi + 1 < p.n_ops_follow) {
                 nks = (i + 1 < n) ? S.kind[i + 1] : p.kind_side[gi + 1];
                 nv = (i + 1 < n) ? vraw[i + 1] : p.var[gi + 1];
             }
@@ -336,25 +337,39 @@ __device__ void dense_tile(const DenseParams& p, DenseSmem& S, uint8_t* vec, con
     }
 }
 
-template <bool APPLY>
+// GV: the per-variable vector is the chunk's own row of aggs (reduce) or entry
+// (apply) in global memory, for variable counts beyond shared memory; the
+// CTA's tiles run in order and only this CTA touches the row.
+template <bool APPLY, bool GV>
 __global__ void __launch_bounds__(DNT) dense_chunk_kernel(const DenseParams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     DenseSmem& S = *reinterpret_cast<DenseSmem*>(smem);
-    uint8_t* vec = smem + sizeof(DenseSmem);
     const int tid = threadIdx.x;
     for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += DNT) S.comp[i] = p.tab.comp[i];
     for (int i = tid; i < MAX_ELEMS * 8; i += DNT) S.app[i] = p.tab.app[i];
     for (int i = tid; i < 256; i += DNT) S.elem_of[i] = p.tab.elem_of[i];
     const int c = blockIdx.x;
-    for (int v = tid; v < p.n_vars; v += DNT)
-        vec[v] = APPLY ? p.entry[(size_t)c * p.n_vars + v] : p.tab.identity;
+    const size_t V = (size_t)p.n_vars;
+    uint8_t* vec;
+    if (GV) {
+        vec = (APPLY ? p.entry : p.aggs) + (size_t)c * V;
+        if (!APPLY) {
+            const uint32_t id4 = p.tab.identity * 0x01010101u;
+            const size_t n16 = (V % 16 == 0) ? V / 16 : 0;
+            for (size_t i = tid; i < n16; i += DNT) reinterpret_cast<uint4*>(vec)[i] = make_uint4(id4, id4, id4, id4);
+            for (size_t v = n16 * 16 + tid; v < V; v += DNT) vec[v] = p.tab.identity;
+        }
+    } else {
+        vec = smem + sizeof(DenseSmem);
+        for (int v = tid; v < p.n_vars; v += DNT) vec[v] = APPLY ? p.entry[(size_t)c * V + v] : p.tab.identity;
+    }
     __syncthreads();
     const int t0 = c * p.tiles_per_chunk;
     const int t1 = min(t0 + p.tiles_per_chunk, p.n_tiles);
     for (int t = t0; t < t1; ++t) dense_tile<APPLY>(p, S, vec, t);
-    if (!APPLY)
-        for (int v = tid; v < p.n_vars; v += DNT) p.aggs[(size_t)c * p.n_vars + v] = vec[v];
+    if (!APPLY && !GV)
+        for (int v = tid; v < p.n_vars; v += DNT) p.aggs[(size_t)c * V + v] = vec[v];
 }
 
 // Thread per variable: status at every chunk entry, then the final status.
@@ -375,12 +390,92 @@ __global__ void dense_carry_kernel(const DenseParams p)
     if (p.final_status) p.final_status[v] = (uint8_t)e;
 }
 
-void dense_shape(int64_t n_ops, int& n_tiles, int& n_chunks, int& tpc)
+void dense_shape(int64_t n_ops, int max_chunks, int& n_tiles, int& n_chunks, int& tpc)
 {
     n_tiles = (int)((n_ops + DT - 1) / DT);
-    const int want = n_tiles < DENSE_MAX_CHUNKS ? n_tiles : DENSE_MAX_CHUNKS;
+    const int want = n_tiles < max_chunks ? n_tiles : max_chunks;
     tpc = want > 0 ? (n_tiles + want - 1) / want : 1;
     n_chunks = tpc > 0 ? (n_tiles + tpc - 1) / tpc : 0;
+}
+
+// Large traces over many variables (more than 16,384, at most 2^20): the first
+// PREFIX_OPS ops -- where nearly every op is live and the single-pass kernel's
+// lists are most contended -- take this path with global per-chunk rows; the
+// rest continues in the single-pass kernel from the prefix's final statuses.
+constexpr int PREFIX_LOG2 = 22;
+constexpr int PREFIX_CHUNKS = 256;
+constexpr int64_t PREFIX_MIN_OPS = (int64_t)1 << 24;
+
+int64_t prefix_ops(int64_t n_ops, int32_t n_vars)
+{
+    if (n_vars <= DENSE_MAX_VARS || n_vars > (1 << 20)) return 0;
+    int lg = PREFIX_LOG2;
+    int64_t min_ops = PREFIX_MIN_OPS;
+    if (const char* e = getenv("AMC_SCAN_DENSE"))
+        if (e[0] == '0') return 0;
+    if (const char* e = getenv("AMC_SCAN_PREFIX")) {   // test override: prefix of 2^k ops at any size
+        lg = atoi(e);
+        min_ops = 0;
+        if (lg < 12 || lg > 30) return 0;
+    }
+    const int64_t P = (int64_t)1 << lg;
+    return (n_ops >= min_ops && n_ops > P) ? P : 0;
+}
+
+int launch_dense_range(const ScanLaunch& L, int max_chunks, int64_t n_follow, uint8_t* ws, cudaStream_t s)
+{
+    DenseParams p{};
+    p.kind_side = L.kind_side;
+    p.var = L.var;
+    p.n_ops = L.n_ops;
+    p.n_ops_follow = n_follow;
+    p.n_vars = L.n_vars;
+    p.init = L.init;
+    p.step = L.step;
+    p.vff = L.vff;
+    p.first_fault = L.first_fault;
+    p.final_status = L.final_status;
+    p.guard = L.guard;
+    p.pre_mode = L.pre_mode;
+    p.err = L.err;
+    p.tab = host_tables();
+    dense_shape(L.n_ops, max_chunks, p.n_tiles, p.n_chunks, p.tiles_per_chunk);
+    const size_t vb = align_up((size_t)p.n_chunks * (size_t)L.n_vars, 256);
+    p.aggs = ws;
+    p.entry = ws + vb;
+    int kb = 1;
+    while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
+    p.passes = (kb + DDIG - 1) / DDIG;
+    p.digit_bits = (kb + p.passes - 1) / p.passes;
+    const bool gv = L.n_vars > DENSE_MAX_VARS;
+
+    if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
+    const size_t smem = sizeof(DenseSmem) + (gv ? 0 : (size_t)L.n_vars);
+    auto kr = gv ? dense_chunk_kernel<false, true> : dense_chunk_kernel<false, false>;
+    auto ka = gv ? dense_chunk_kernel<true, true> : dense_chunk_kernel<true, false>;
+    if (cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return AMC_E_CUDA;
+    if (L.profile & 1) profile_begin(s);
+    kr<<<p.n_chunks, DNT, smem, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    dense_carry_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    ka<<<p.n_chunks, DNT, smem, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    if (L.profile & 2) profile_end(s);
+    return AMC_OK;
+}
+
+// First faults of a prefix and the suffix after it: the prefix's where it has
+// one, else the suffix's moved by the prefix length.
+__global__ void merge_faults_kernel(int32_t* __restrict__ vff, const int32_t* __restrict__ vff_suffix, int32_t n_vars,
+                                    int64_t* __restrict__ ff, const int64_t* __restrict__ ff_suffix, int64_t P)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n_vars && vff[v] == -1 && vff_suffix[v] != -1) vff[v] = (int32_t)(vff_suffix[v] + P);
+    if (v == 0 && *ff == -1 && *ff_suffix != -1) *ff = *ff_suffix + P;
 }
 
 }  // namespace
@@ -394,54 +489,61 @@ bool scan_dense_eligible(int64_t n_ops, int32_t n_vars)
 
 size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)
 {
-    if (n_vars < 1 || n_vars > DENSE_MAX_VARS || n_ops < 1) return 0;
     int n_tiles, n_chunks, tpc;
-    dense_shape(n_ops, n_tiles, n_chunks, tpc);
+    if (const int64_t P = prefix_ops(n_ops, n_vars)) {
+        // prefix rows, then the suffix's first faults and the prefix's final statuses
+        dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
+        return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256) + align_up(4 * (size_t)n_vars, 256) + 256 +
+               align_up((size_t)n_vars, 256);
+    }
+    if (n_vars < 1 || n_vars > DENSE_MAX_VARS || n_ops < 1) return 0;
+    dense_shape(n_ops, DENSE_MAX_CHUNKS, n_tiles, n_chunks, tpc);
     return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256);
+}
+
+bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars) { return prefix_ops(n_ops, n_vars) > 0; }
+
+int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
+{
+    const int64_t P = prefix_ops(L.n_ops, L.n_vars);
+    int n_tiles, n_chunks, tpc;
+    dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
+    uint8_t* w = ws + 2 * align_up((size_t)n_chunks * (size_t)L.n_vars, 256);
+    int32_t* vff_suffix = reinterpret_cast<int32_t*>(w);
+    w += align_up(4 * (size_t)L.n_vars, 256);
+    int64_t* ff_suffix = reinterpret_cast<int64_t*>(w);
+    w += 256;
+    uint8_t* pfinal = w;
+
+    ScanLaunch A = L;                       // the prefix: faults straight into the outputs
+    A.n_ops = P;
+    A.final_status = pfinal;
+    A.profile = L.profile & 1;
+    int rc = launch_dense_range(A, PREFIX_CHUNKS, L.n_ops, ws, s);
+    if (rc) return rc;
+    ScanLaunch B = L;                       // the rest, from the prefix's final statuses
+    B.kind_side = L.kind_side + P;
+    B.var = L.var + P;
+    B.n_ops = L.n_ops - P;
+    B.step = L.step + P;
+    B.guard = L.guard ? L.guard + P : nullptr;
+    B.init = pfinal;
+    B.vff = vff_suffix;
+    B.first_fault = ff_suffix;
+    B.dense = 0;
+    B.profile = 0;
+    rc = launch_scan_trace(B, s);
+    if (rc) return rc;
+    merge_faults_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(L.vff, vff_suffix, L.n_vars,
+                                                                           L.first_fault, ff_suffix, P);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    if (L.profile & 2) profile_end(s);
+    return AMC_OK;
 }
 
 int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 {
-    DenseParams p{};
-    p.kind_side = L.kind_side;
-    p.var = L.var;
-    p.n_ops = L.n_ops;
-    p.n_vars = L.n_vars;
-    p.init = L.init;
-    p.step = L.step;
-    p.vff = L.vff;
-    p.first_fault = L.first_fault;
-    p.final_status = L.final_status;
-    p.guard = L.guard;
-    p.pre_mode = L.pre_mode;
-    p.err = L.err;
-    p.tab = host_tables();
-    dense_shape(L.n_ops, p.n_tiles, p.n_chunks, p.tiles_per_chunk);
-    const size_t vb = align_up((size_t)p.n_chunks * (size_t)L.n_vars, 256);
-    p.aggs = ws;
-    p.entry = ws + vb;
-    int kb = 1;
-    while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
-    p.passes = (kb + DDIG - 1) / DDIG;
-    p.digit_bits = (kb + p.passes - 1) / p.passes;
-
-    if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
-    if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
-    const size_t smem = sizeof(DenseSmem) + (size_t)L.n_vars;
-    if (cudaFuncSetAttribute(dense_chunk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(dense_chunk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return AMC_E_CUDA;
-    if (L.profile & 1) profile_begin(s);
-    dense_chunk_kernel<false><<<p.n_chunks, DNT, smem, s>>>(p);
-    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-    dense_carry_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(p);
-    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-    dense_chunk_kernel<true><<<p.n_chunks, DNT, smem, s>>>(p);
-    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-    if (L.profile & 2) profile_end(s);
-    return AMC_OK;
+    return launch_dense_range(L, DENSE_MAX_CHUNKS, L.n_ops, ws, s);
 }
 
 }  // namespace amc

@@ -52,6 +52,13 @@ constexpr int POS_BITS = 12;                // log2(TILE)
 constexpr int MAX_DIGIT_BITS = 7;                // radix digit: 2 KB of histogram rows
 constexpr uint8_t RUN_PENDING = 0xFF;
 constexpr uint32_t NO_NODE = 0x80000000u;      // pending-run flag: constant-F run, no list node
+// A first-fault entry with this bit set is a bound, not a position: the
+// variable is stuck by the end of the position in the low bits (a run of that
+// tile sends every status to F).  An exact fault is never larger than a bound
+// of its variable, so atomicMin keeps it once recorded; a bound that is still
+// there at the end belongs to a variable that was already F at the start
+// (no fault inside the trace) and is cleared by the final-status pass.
+constexpr uint32_t VFF_BOUND = 0x80000000u;
 constexpr uint32_t NODE_AGG = 0x40;
 constexpr uint32_t NODE_INCL = 0x80;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
@@ -508,7 +515,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     for (int k = 0; k < E; ++k) {
         if (lastMask & (1u << k)) {
             const int r = run_id(k);
-            if (ffv[k] < (uint32_t)base) {
+            if ((ffv[k] & ~VFF_BOUND) < (uint32_t)base) {
                 S.runEntry[r] = ST_F;
                 // stuck before this tile, hence before every later tile of this CTA
                 const uint32_t v = kvar(j0 + k);
@@ -521,7 +528,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                     // that bound as the first fault (the exact one, recorded
                     // below or earlier, is never larger) instead of a node;
                     // later tiles take the stuck shortcut
-                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(base + T - 1));
+                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(base + T - 1) | VFF_BOUND);
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16) | NO_NODE;
                 } else {
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
@@ -651,7 +658,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
         const uint32_t mine = active;
 #pragma unroll
         for (int u = 0; u < PW; ++u)
-            if ((active & (1u << u)) && ffw[u] < (uint32_t)base) {
+            if ((active & (1u << u)) && (ffw[u] & ~VFF_BOUND) < (uint32_t)base) {
                 st[u] = ST_F;                  // stuck before this tile (bound published since)
                 active &= ~(1u << u);
             }
@@ -1147,7 +1154,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             const int r = run_id(k);
             const int g = S.livePos[kidx(j0 + k)] >> POS_BITS;
             const int64_t rbase = gbase + (int64_t)g * T;
-            if ((int64_t)ffv[k] < rbase && ffv[k] != 0xFFFFFFFFu) {
+            if ((ffv[k] & ~VFF_BOUND) < (uint32_t)rbase) {
                 S.runEntry[r] = ST_F;
                 const uint32_t v = kvar(j0 + k);
                 if (v < (uint32_t)p.fbw * 32u) atomicOr(fsm + (v >> 5), 1u << (v & 31));
@@ -1156,7 +1163,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 S.runEntry[r] = RUN_PENDING;
                 if ((S.constF >> agg) & 1u) {
                     // stuck by the end of its tile: bound as first fault, no node
-                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(rbase + T - 1));
+                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + kvar(j0 + k), (uint32_t)(rbase + T - 1) | VFF_BOUND);
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16) | NO_NODE;
                 } else {
                     pend[atomicAdd(&S.nPend, 1)] = (uint32_t)r | ((uint32_t)(j0 + k) << 16);
@@ -1280,7 +1287,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
         const uint32_t mine = active;
 #pragma unroll
         for (int u = 0; u < PW; ++u)
-            if ((active & (1u << u)) && ffw[u] < rt[u] * (uint32_t)T) {
+            if ((active & (1u << u)) && (ffw[u] & ~VFF_BOUND) < rt[u] * (uint32_t)T) {
                 st[u] = ST_F;                  // stuck before the run's tile (bound published since)
                 active &= ~(1u << u);
             }
@@ -1478,20 +1485,22 @@ __global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const S
     }
 }
 
-__global__ void finalize_trace_kernel(const int32_t* __restrict__ vff, const uint32_t* __restrict__ head,
+__global__ void finalize_trace_kernel(int32_t* __restrict__ vff, const uint32_t* __restrict__ head,
                                       const uint8_t* __restrict__ node_status, const uint8_t* __restrict__ init,
                                       int32_t n_vars, uint8_t* __restrict__ final_status)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_vars) return;
+    const uint32_t ff = (uint32_t)vff[v];
     uint8_t f;
-    if (vff[v] != -1) {
+    if (ff != 0xFFFFFFFFu) {
         f = ST_F;
+        if (ff & VFF_BOUND) vff[v] = -1;       // stuck from the start: no fault inside the trace
     } else {
         const uint32_t h = head[v];
         f = (h == NIL) ? (init ? init[v] : (uint8_t)AMC_ST_VI) : (uint8_t)(node_status[h] & 7u);
     }
-    final_status[v] = f;
+    if (final_status) final_status[v] = f;
 }
 
 // Variables whose initial status is F are stuck before the first op: their
@@ -1631,6 +1640,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
     if (L.dense != 0 && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
+    if (L.dense != 0 && scan_prefix_eligible(L.n_ops, L.n_vars)) return launch_scan_prefix(L, w + 256, s);
     // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
     int kb = 1;
     while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;
@@ -1661,7 +1671,8 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
         const int rc = kb + POS_BITS <= 32 ? launch_kernel<uint32_t>(p, L, s) : launch_kernel<uint64_t>(p, L, s);
         if (rc) return rc;
     }
-    if (L.final_status) {
+    {
+        // final statuses (when asked for) and first-fault bounds cleared
         const int nb = (int)((L.n_vars + 255) / 256);
         if (nb > 0) {
             finalize_trace_kernel<<<nb, 256, 0, s>>>(L.vff, p.head, p.node_status, L.init, L.n_vars,

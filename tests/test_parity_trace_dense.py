@@ -99,3 +99,48 @@ def test_dense_path_reports_bad_input(amc, monkeypatch):
     amc.check_trace(ks, var, 4)
     assert amc.sync_status() == amc.E_INVALID
     assert amc.sync_status() == 0
+
+
+# ---- prefix split: traces over more than 16,384 variables ------------------
+# From 2^24 ops the first 2^22 ops take the reduce / carry / apply path with
+# per-chunk rows in global memory and the rest the single-pass kernel from the
+# prefix's final statuses; AMC_SCAN_PREFIX=k forces a 2^k-op prefix at any size.
+
+def test_prefix_split_zipf(amc, oracle_mod, monkeypatch):
+    monkeypatch.setenv("AMC_SCAN_PREFIX", "18")
+    ks, var = workloads.trace_zipf(3 * (1 << 20) + 5, 1 << 20, seed=52, device="cuda")
+    check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
+
+
+def test_prefix_split_ragged(amc, oracle_mod, monkeypatch):
+    monkeypatch.setenv("AMC_SCAN_PREFIX", "14")
+    rng = np.random.default_rng(53)
+    ks, var = workloads.trace_random(rng, 200_003, 70_000, zipf_s=1.05)
+    check(amc, oracle_mod, ks, var, 70_000)
+
+
+def test_prefix_split_initial_statuses(amc, oracle_mod, monkeypatch):
+    monkeypatch.setenv("AMC_SCAN_PREFIX", "15")
+    rng = np.random.default_rng(54)
+    ks, var = workloads.trace_random(rng, 150_000, 20_000)
+    init = rng.integers(0, 5, 20_000).astype(np.uint8)
+    check(amc, oracle_mod, ks, var, 20_000, init)
+
+
+def test_prefix_split_guarded_gt_at_boundary(amc, oracle_mod, monkeypatch):
+    # 9,000 arrays (18,000 variables); this seed's translated trace has a GT at
+    # position 2^15 - 1, so the GT / EN pair straddles a 2^15-op prefix
+    monkeypatch.setenv("AMC_SCAN_PREFIX", "15")
+    w = workloads.vectorpu_calls(seed=61, n_arrays=9000, space=1 << 16, n_calls=30_000,
+                                 len_log2=(4.0, 9.0), drop_p=0.01)
+    res = oracle_mod.vectorpu(**w)
+    assert (res["kind_side"][(1 << 15) - 1] & 15) == 6
+    A = len(w["arr_start"])
+    dev = torch.device("cuda")
+    out = amc.check_trace(torch.from_numpy(res["kind_side"]).to(dev), torch.from_numpy(res["var"]).to(dev),
+                          2 * A, guarded=True)
+    assert amc.sync_status() == 0
+    assert np.array_equal(out["step_status"].cpu().numpy(), res["step_status"])
+    assert np.array_equal(out["final_status"].cpu().numpy(), res["final_status"])
+    assert np.array_equal(out["var_first_fault"].cpu().numpy(), res["var_first_fault"])
+    assert int(out["first_fault"].cpu()[0]) == res["first_fault"]
