@@ -175,3 +175,17 @@ def test_autotune_cache_file(tmp_path):
     assert r.returncode == 0, r.stderr[-2000:]
     lines = cache.read_text().split()
     assert lines and lines[0].startswith("trace:")
+
+
+@pytest.mark.parametrize("fb", ["-1", "1048576", "-2"])
+@pytest.mark.parametrize("group", ["1", "-2"])
+def test_initial_statuses_every_bitmap_mode(amc, oracle_mod, monkeypatch, fb, group):
+    # variables that are F from the start fault nowhere inside the trace, whether
+    # or not the stuck bitmap (none / shared memory / through L1) filters them
+    monkeypatch.setenv("AMC_SCAN_FB_BITS", fb)
+    monkeypatch.setenv("AMC_SCAN_GROUP", group)
+    rng = np.random.default_rng(36)
+    ks, var = workloads.trace_random(rng, 90_000, 64)
+    init = rng.integers(0, 5, 64).astype(np.uint8)
+    assert (init == 4).any()
+    assert_same(*run_both(amc, oracle_mod, ks, var, 64, init))
