@@ -572,15 +572,18 @@ def trace_kernels(n_ops, n_vars):
 
 
 def scan_traffic(n_ops, n_vars):
-    """DRAM bytes (read + write) of one scan launch from the recorded ncu
-    capture, or None when the capture was of another workload or the kernel
-    source has changed since (the record keeps its SHA-256)."""
+    """DRAM bytes (read + write) of one check -- every kernel of the timed span
+    -- from the recorded ncu capture, or None when the capture was of another
+    workload or the kernel sources have changed since (the record keeps the
+    SHA-256 of scan_trace.cu and scan_dense.cu)."""
     import hashlib
     tr_path = os.path.join(ROOT, "profiles", "scan_trace_zipf_traffic.json")
-    src = os.path.join(ROOT, "paper_1910_11110_gb300", "csrc", "scan_trace.cu")
+    h = hashlib.sha256()
     try:
         rec = json.load(open(tr_path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        for f in ("scan_trace.cu", "scan_dense.cu"):
+            h.update(open(os.path.join(ROOT, "paper_1910_11110_gb300", "csrc", f), "rb").read())
+        sha = h.hexdigest()
     except Exception:
         return None
     if rec.get("source_sha256") != sha or rec.get("n_ops") != n_ops or rec.get("n_vars") != n_vars:
