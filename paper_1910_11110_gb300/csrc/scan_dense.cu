@@ -406,7 +406,10 @@ constexpr int PREFIX_LOG2 = 22;
 constexpr int PREFIX_CHUNKS = 256;
 constexpr int64_t PREFIX_MIN_OPS = (int64_t)1 << 24;
 
-int64_t prefix_ops(int64_t n_ops, int32_t n_vars)
+// has_init: a caller's initial statuses may already make most variables
+// stuck (a trace continued from an earlier one), so the start is not dense:
+// the prefix is then taken only when forced.
+int64_t prefix_ops(int64_t n_ops, int32_t n_vars, bool has_init)
 {
     if (n_vars <= DENSE_MAX_VARS || n_vars > (1 << 20)) return 0;
     int lg = PREFIX_LOG2;
@@ -418,6 +421,7 @@ int64_t prefix_ops(int64_t n_ops, int32_t n_vars)
         min_ops = 0;
         if (lg < 12 || lg > 30) return 0;
     }
+    if (has_init && min_ops > 0) return 0;
     const int64_t P = (int64_t)1 << lg;
     return (n_ops >= min_ops && n_ops > P) ? P : 0;
 }
@@ -490,7 +494,7 @@ bool scan_dense_eligible(int64_t n_ops, int32_t n_vars)
 size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)
 {
     int n_tiles, n_chunks, tpc;
-    if (const int64_t P = prefix_ops(n_ops, n_vars)) {
+    if (const int64_t P = prefix_ops(n_ops, n_vars, false)) {   // the larger workspace
         // prefix rows, then the suffix's first faults and the prefix's final statuses
         dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
         return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256) + align_up(4 * (size_t)n_vars, 256) + 256 +
@@ -501,11 +505,14 @@ size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)
     return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256);
 }
 
-bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars) { return prefix_ops(n_ops, n_vars) > 0; }
+bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars, bool has_init)
+{
+    return prefix_ops(n_ops, n_vars, has_init) > 0;
+}
 
 int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 {
-    const int64_t P = prefix_ops(L.n_ops, L.n_vars);
+    const int64_t P = prefix_ops(L.n_ops, L.n_vars, L.init != nullptr);
     int n_tiles, n_chunks, tpc;
     dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
     uint8_t* w = ws + 2 * align_up((size_t)n_chunks * (size_t)L.n_vars, 256);

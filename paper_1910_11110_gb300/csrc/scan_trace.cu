@@ -1640,7 +1640,8 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
     if (L.dense != 0 && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
-    if (L.dense != 0 && scan_prefix_eligible(L.n_ops, L.n_vars)) return launch_scan_prefix(L, w + 256, s);
+    if (L.dense != 0 && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr))
+        return launch_scan_prefix(L, w + 256, s);
     // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
     int kb = 1;
     while (kb < 31 && ((int64_t)1 << kb) < (int64_t)L.n_vars) ++kb;

@@ -70,9 +70,10 @@ bool scan_dense_eligible(int64_t n_ops, int32_t n_vars);
 size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars);
 int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
 // Traces over more than 16,384 (at most 2^20) variables and of 2^24 ops or
-// more: the first 2^22 ops take that path with per-chunk rows in global memory
-// and the rest the single-pass kernel, from the prefix's final statuses.
-bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars);
+// more, without initial statuses: the first 2^22 ops take that path with
+// per-chunk rows in global memory and the rest the single-pass kernel, from the
+// prefix's final statuses.
+bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars, bool has_init);
 int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
 // enable >= 0: switch phase counting on/off and zero the counters; host_out
 // (nullable): copy the 8 counters (cycles summed over CTAs).
