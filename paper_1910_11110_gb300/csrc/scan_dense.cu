@@ -372,7 +372,34 @@ __global__ void __launch_bounds__(DNT) dense_chunk_kernel(const DenseParams p)
         for (int v = tid; v < p.n_vars; v += DNT) p.aggs[(size_t)c * V + v] = vec[v];
 }
 
-// Thread per variable: status at every chunk entry, then the final status.
+// Thread per four variables (one 32-bit word of every chunk row; rows are
+// n_vars bytes long, a multiple of 4 here): status at every chunk entry, then
+// the final status.
+__global__ void dense_carry4_kernel(const DenseParams p)
+{
+    __shared__ uint8_t app[MAX_ELEMS * 8];
+    for (int i = threadIdx.x; i < MAX_ELEMS * 8; i += blockDim.x) app[i] = p.tab.app[i];
+    __syncthreads();
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;      // word: variables 4w .. 4w+3
+    const size_t V = (size_t)p.n_vars;
+    if (4 * w >= (int64_t)V) return;
+    uint32_t e[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) e[b] = p.init ? p.init[4 * w + b] : (uint32_t)AMC_ST_VI;
+    const size_t W = V / 4;
+#pragma unroll 4
+    for (int c = 0; c < p.n_chunks; ++c) {
+        const uint32_t a = reinterpret_cast<const uint32_t*>(p.aggs)[(size_t)c * W + w];
+        reinterpret_cast<uint32_t*>(p.entry)[(size_t)c * W + w] = e[0] | (e[1] << 8) | (e[2] << 16) | (e[3] << 24);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) e[b] = app[((a >> (8 * b)) & 0xFFu) * 8 + e[b]];
+    }
+    if (p.final_status)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) p.final_status[4 * w + b] = (uint8_t)e[b];
+}
+
+// Thread per variable (any row length).
 __global__ void dense_carry_kernel(const DenseParams p)
 {
     __shared__ uint8_t app[MAX_ELEMS * 8];
@@ -388,6 +415,250 @@ __global__ void dense_carry_kernel(const DenseParams p)
         e = app[p.aggs[(size_t)c * V + v] * 8 + e];
     }
     if (p.final_status) p.final_status[v] = (uint8_t)e;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-sequential variant for at most 8,192 variables: every warp owns a
+// contiguous sub-chunk (a multiple of 32 ops) and a dense per-variable vector
+// in shared memory, and walks its sub-chunk in batches of 32 consecutive ops.
+// The lanes of a batch that touch the same variable are grouped by match.any;
+// a group's ops are composed in lane (= trace) order from a per-warp staging
+// array, so no sort is needed.  The sub-chunks are the carry's chunks.
+constexpr int WARP_MAX_VARS = 8192;
+constexpr int WARP_CHUNKS_MAX = 8192;
+constexpr int SEG = 64;                 // chunks per carry segment
+
+template <bool APPLY>
+__global__ void __launch_bounds__(256) warp_chunk_kernel(const DenseParams p, const int64_t cs)
+{
+    extern __shared__ __align__(16) uint8_t wsm[];
+    uint8_t* comp = wsm;                                  // [32 * 32]
+    uint8_t* app = comp + MAX_ELEMS * MAX_ELEMS;          // [32 * 8]
+    uint8_t* elem_of = app + MAX_ELEMS * 8;               // [256]
+    uint8_t* mbuf = elem_of + 256;                        // [8 warps][32]
+    uint8_t* vecs = mbuf + 256;                           // [8 warps][n_vars]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += 256) comp[i] = p.tab.comp[i];
+    for (int i = tid; i < MAX_ELEMS * 8; i += 256) app[i] = p.tab.app[i];
+    for (int i = tid; i < 256; i += 256) elem_of[i] = p.tab.elem_of[i];
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * 8 + warp;
+    if (g >= p.n_chunks) return;                          // no block barrier below
+    const size_t V = (size_t)p.n_vars;
+    const uint32_t ID = p.tab.identity;
+    const uint32_t lt = lanemask_lt();
+    uint8_t* vec = vecs + (size_t)warp * V;
+    uint8_t* mb = mbuf + warp * 32;
+    for (size_t v = lane; v < V; v += 32) vec[v] = APPLY ? p.entry[(size_t)g * V + v] : (uint8_t)ID;
+    __syncwarp();
+    const int64_t lo = g * cs;
+    const int64_t hi = min(lo + cs, p.n_ops);
+    constexpr int UB = 8;                                 // batches whose loads are in flight together
+    for (int64_t b0 = lo; b0 < hi; b0 += 32 * UB) {
+    uint32_t ksb[UB];
+    int32_t vb[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        const int64_t i = b0 + 32 * u + lane;
+        ksb[u] = i < hi ? (uint32_t)__ldcs(p.kind_side + i) : 0u;
+        vb[u] = i < hi ? __ldcs(p.var + i) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        const int64_t b = b0 + 32 * u;
+        if (b >= hi) break;                               // warp-uniform
+        const int64_t i = b + lane;
+        const bool ok = i < hi;
+        uint32_t ks = ksb[u];
+        int32_t v = vb[u];
+        if (ok) {
+            if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
+            if (v < 0 || v >= p.n_vars) {
+                raise_error(p.err, AMC_E_RANGE);
+                v = 0;
+            }
+        }
+        const uint32_t nks_l = __shfl_down_sync(0xffffffffu, ks, 1);
+        const int32_t nv_l = __shfl_down_sync(0xffffffffu, v, 1);
+        uint32_t m = ok ? elem_of[ks] : ID;
+        if (ok && m == ELEM_GT) {
+            // GT must be followed by EN of the same side on another variable
+            uint32_t nks = 0xFF;
+            int32_t nv = v;
+            if (i + 1 < p.n_ops_follow) {
+                const bool in_batch = lane < 31 && i + 1 < hi;
+                nks = in_batch ? nks_l : p.kind_side[i + 1];
+                nv = in_batch ? nv_l : p.var[i + 1];
+            }
+            const bool gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != v;
+            if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
+            if (!gt_ok || p.pre_mode) {
+                m = ID;
+            } else if (!p.guard) {
+                raise_error(p.err, AMC_E_INVALID);
+                m = ID;
+            } else {
+                const uint32_t gs = p.guard[i + 1];
+                const int side = ks >> 4;
+                const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
+                m = valid ? ID : p.tab.pull_of_side[side];
+            }
+        } else if (m == ELEM_BAD) {
+            m = ID;
+        }
+        mb[lane] = (uint8_t)m;
+        const uint32_t peers = __match_any_sync(0xffffffffu, ok ? (uint32_t)v : 0xFFFFFFFFu);
+        __syncwarp();
+        if constexpr (!APPLY) {
+            if (ok && lane == __ffs(peers) - 1) {             // the group's first lane folds it in
+                uint32_t acc = vec[v];
+                for (uint32_t q = peers; q; q &= q - 1) acc = comp[acc * MAX_ELEMS + mb[__ffs(q) - 1]];
+                vec[v] = (uint8_t)acc;
+            }
+        } else {
+            const uint32_t e = ok ? vec[v] : 0u;                  // the variable's status before the batch
+            __syncwarp();
+            if (ok) {
+                uint32_t acc = ID;
+                for (uint32_t q = peers & lt; q; q &= q - 1) acc = comp[acc * MAX_ELEMS + mb[__ffs(q) - 1]];
+                const uint32_t pre = app[acc * 8 + e];
+                const uint32_t post = app[comp[acc * MAX_ELEMS + m] * 8 + e];
+                p.step[i] = (uint8_t)(p.pre_mode ? pre : post);
+                if (post == ST_F && pre != ST_F) {
+                    atomicMin(reinterpret_cast<uint32_t*>(p.vff) + v, (uint32_t)i);
+                    atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)i);
+                }
+                if (lane == 31 - __clz(peers)) vec[v] = (uint8_t)post;   // the group's last lane
+            }
+        }
+        __syncwarp();
+    }
+    }
+    if constexpr (!APPLY)
+        for (size_t v = lane; v < V; v += 32) p.aggs[(size_t)g * V + v] = vec[v];
+}
+
+// Segmented carry over many chunks: (1) compose each segment's chunk
+// aggregates, (2) carry the initial statuses over the segments, (3) expand
+// every chunk's entry statuses inside its segment.  Thread per (segment,
+// variable); composition is associative, so this equals the serial carry.
+__global__ void seg_reduce_kernel(const DenseParams p, uint8_t* __restrict__ seg_agg, int n_segs)
+{
+    __shared__ uint8_t comp[MAX_ELEMS * MAX_ELEMS];
+    for (int i = threadIdx.x; i < MAX_ELEMS * MAX_ELEMS; i += blockDim.x) comp[i] = p.tab.comp[i];
+    __syncthreads();
+    const size_t V = (size_t)p.n_vars;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_segs * (int64_t)V) return;
+    const int s = (int)(t / (int64_t)V);
+    const size_t v = (size_t)(t % (int64_t)V);
+    uint32_t acc = p.tab.identity;
+    const int c1 = min((s + 1) * SEG, p.n_chunks);
+    for (int c = s * SEG; c < c1; ++c) acc = comp[acc * MAX_ELEMS + p.aggs[(size_t)c * V + v]];
+    seg_agg[(size_t)s * V + v] = (uint8_t)acc;
+}
+
+__global__ void seg_carry_kernel(const DenseParams p, const uint8_t* __restrict__ seg_agg,
+                                 uint8_t* __restrict__ seg_entry, int n_segs)
+{
+    __shared__ uint8_t app[MAX_ELEMS * 8];
+    for (int i = threadIdx.x; i < MAX_ELEMS * 8; i += blockDim.x) app[i] = p.tab.app[i];
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= p.n_vars) return;
+    const size_t V = (size_t)p.n_vars;
+    uint32_t e = p.init ? p.init[v] : (uint32_t)AMC_ST_VI;
+    for (int s = 0; s < n_segs; ++s) {
+        seg_entry[(size_t)s * V + v] = (uint8_t)e;
+        e = app[seg_agg[(size_t)s * V + v] * 8 + e];
+    }
+    if (p.final_status) p.final_status[v] = (uint8_t)e;
+}
+
+__global__ void seg_expand_kernel(const DenseParams p, const uint8_t* __restrict__ seg_entry, int n_segs)
+{
+    __shared__ uint8_t app[MAX_ELEMS * 8];
+    for (int i = threadIdx.x; i < MAX_ELEMS * 8; i += blockDim.x) app[i] = p.tab.app[i];
+    __syncthreads();
+    const size_t V = (size_t)p.n_vars;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_segs * (int64_t)V) return;
+    const int s = (int)(t / (int64_t)V);
+    const size_t v = (size_t)(t % (int64_t)V);
+    uint32_t e = seg_entry[(size_t)s * V + v];
+    const int c1 = min((s + 1) * SEG, p.n_chunks);
+    for (int c = s * SEG; c < c1; ++c) {
+        p.entry[(size_t)c * V + v] = (uint8_t)e;
+        e = app[p.aggs[(size_t)c * V + v] * 8 + e];
+    }
+}
+
+// Warp sub-chunks of a trace: chunk length (a multiple of 32) and count.
+void warp_shape(int64_t n_ops, int64_t& cs, int& n_chunks)
+{
+    int64_t want = (n_ops + 4095) / 4096;                 // at least a tile's worth per warp
+    if (want > WARP_CHUNKS_MAX) want = WARP_CHUNKS_MAX;
+    if (want < 1) want = 1;
+    cs = ((n_ops + want - 1) / want + 31) / 32 * 32;
+    if (cs < 32) cs = 32;
+    n_chunks = (int)((n_ops + cs - 1) / cs);
+}
+
+size_t warp_workspace_bytes(int64_t n_ops, int32_t n_vars)
+{
+    int64_t cs;
+    int n_chunks;
+    warp_shape(n_ops, cs, n_chunks);
+    const int n_segs = (n_chunks + SEG - 1) / SEG;
+    return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256) + 2 * align_up((size_t)n_segs * (size_t)n_vars, 256);
+}
+
+int launch_warp_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
+{
+    DenseParams p{};
+    p.kind_side = L.kind_side;
+    p.var = L.var;
+    p.n_ops = L.n_ops;
+    p.n_ops_follow = L.n_ops;
+    p.n_vars = L.n_vars;
+    p.init = L.init;
+    p.step = L.step;
+    p.vff = L.vff;
+    p.first_fault = L.first_fault;
+    p.final_status = L.final_status;
+    p.guard = L.guard;
+    p.pre_mode = L.pre_mode;
+    p.err = L.err;
+    p.tab = host_tables();
+    int64_t cs;
+    warp_shape(L.n_ops, cs, p.n_chunks);
+    const int n_segs = (p.n_chunks + SEG - 1) / SEG;
+    const size_t V = (size_t)L.n_vars;
+    p.aggs = ws;
+    p.entry = ws + align_up((size_t)p.n_chunks * V, 256);
+    uint8_t* seg_agg = p.entry + align_up((size_t)p.n_chunks * V, 256);
+    uint8_t* seg_entry = seg_agg + align_up((size_t)n_segs * V, 256);
+    if (cudaMemsetAsync(L.vff, 0xFF, 4 * V, s) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
+    const size_t smem = MAX_ELEMS * MAX_ELEMS + MAX_ELEMS * 8 + 256 + 256 + 8 * V;
+    if (cudaFuncSetAttribute(warp_chunk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(warp_chunk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return AMC_E_CUDA;
+    const unsigned grid = (unsigned)((p.n_chunks + 7) / 8);
+    const unsigned segv = (unsigned)(((int64_t)n_segs * (int64_t)V + 255) / 256);
+    if (L.profile & 1) profile_begin(s);
+    warp_chunk_kernel<false><<<grid, 256, smem, s>>>(p, cs);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    seg_reduce_kernel<<<segv, 256, 0, s>>>(p, seg_agg, n_segs);
+    seg_carry_kernel<<<(unsigned)((V + 255) / 256), 256, 0, s>>>(p, seg_agg, seg_entry, n_segs);
+    seg_expand_kernel<<<segv, 256, 0, s>>>(p, seg_entry, n_segs);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    warp_chunk_kernel<true><<<grid, 256, smem, s>>>(p, cs);
+    if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    if (L.profile & 2) profile_end(s);
+    return AMC_OK;
 }
 
 void dense_shape(int64_t n_ops, int max_chunks, int& n_tiles, int& n_chunks, int& tpc)
@@ -464,7 +735,10 @@ int launch_dense_range(const ScanLaunch& L, int max_chunks, int64_t n_follow, ui
     if (L.profile & 1) profile_begin(s);
     kr<<<p.n_chunks, DNT, smem, s>>>(p);
     if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-    dense_carry_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(p);
+    if (L.n_vars % 4 == 0)       // rows start 256-byte aligned; 4-byte words when n_vars is a multiple of 4
+        dense_carry4_kernel<<<(unsigned)((L.n_vars / 4 + 255) / 256), 256, 0, s>>>(p);
+    else
+        dense_carry_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(p);
     if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
     ka<<<p.n_chunks, DNT, smem, s>>>(p);
     if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
@@ -502,7 +776,9 @@ size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)
     }
     if (n_vars < 1 || n_vars > DENSE_MAX_VARS || n_ops < 1) return 0;
     dense_shape(n_ops, DENSE_MAX_CHUNKS, n_tiles, n_chunks, tpc);
-    return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256);
+    const size_t sorted = 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256);
+    const size_t warped = n_vars <= WARP_MAX_VARS ? warp_workspace_bytes(n_ops, n_vars) : 0;
+    return sorted > warped ? sorted : warped;
 }
 
 bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars, bool has_init)
@@ -550,6 +826,9 @@ int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 
 int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 {
+    // up to 8,192 variables: warp-sequential batches; else tile sorts
+    const char* e = getenv("AMC_SCAN_DENSE_SORT");                // test override: the sorted variant
+    if (L.n_vars <= WARP_MAX_VARS && !(e && e[0] == '1')) return launch_warp_dense(L, ws, s);
     return launch_dense_range(L, DENSE_MAX_CHUNKS, L.n_ops, ws, s);
 }
 

@@ -83,8 +83,133 @@ __global__ void overlap_kernel(const TrParams p)
 
 // Statements of call c.  EMIT = false only counts; EMIT = true writes them at
 // out_base.  Returns the count, or -1 for a malformed call.
+// One call.  NMAX >= the call's operand count; every array below is indexed
+// only by unrolled loop counters (the operand that matches an array id is
+// found by comparing against all slots), so for small NMAX they stay in
+// registers.  The statements and their order are the same for every NMAX.
+template <bool EMIT, int NMAX>
+__device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_base, const int32_t k0, const int n,
+                                    const uint32_t side)
+{
+    const int32_t A = p.n_arrays;
+    int32_t arr[NMAX];
+    uint8_t mode[NMAX], eff[NMAX];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        arr[i] = -1;
+        mode[i] = eff[i] = 0;
+        if (i < n) {
+            arr[i] = p.opnd_array[k0 + i];
+            mode[i] = p.opnd_mode[k0 + i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        if (i >= n) break;
+        if ((mode[i] & 0x7C) || (mode[i] & 3) == 0) {
+            if (!EMIT) raise_error(p.err, AMC_E_INVALID);
+            return -1;
+        }
+        if (arr[i] < 0 || arr[i] >= A) {
+            if (!EMIT) raise_error(p.err, AMC_E_RANGE);
+            return -1;
+        }
+        bool dup = false;
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j) dup |= j < i && arr[j] == arr[i];
+        if (dup) {                          // one declaration per variable (Section 3.3)
+            if (!EMIT) raise_error(p.err, AMC_E_INVALID);
+            return -1;
+        }
+        eff[i] = (mode[i] & AMC_MODE_DROPPED) ? 0 : (mode[i] & 3);
+    }
+    auto is_arg = [&](int32_t y) {
+        bool f = false;
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j) f |= j < n && arr[j] == y;
+        return f;
+    };
+    if (p.infer) {
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) {
+            if (i >= n) break;
+            if ((mode[i] & AMC_MODE_DROPPED) || !(mode[i] & AMC_MODE_W)) continue;
+            const bool x_rw = (mode[i] & 3) == AMC_MODE_RW;
+            for (int64_t q = p.ov_off[arr[i]]; q < p.ov_off[arr[i] + 1]; ++q) {
+                const int32_t y = p.ov_idx[q];
+#pragma unroll
+                for (int j = 0; j < NMAX; ++j)
+                    if (j < n && arr[j] == y && !(mode[j] & AMC_MODE_DROPPED) && (x_rw || (mode[j] & 3) != AMC_MODE_W))
+                        eff[j] = AMC_MODE_RW;
+            }
+        }
+    }
+    int64_t o = out_base;
+    const uint8_t sb = (uint8_t)(side << 4);
+    auto put = [&](uint32_t kind, int32_t v) {
+        if (EMIT) {
+            p.out_ks[o] = (uint8_t)(kind | sb);
+            p.out_var[o] = v;
+        }
+        ++o;
+    };
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        if (i >= n) break;
+        const int32_t x = arr[i];
+        const int me = eff[i], mo = mode[i] & 3;
+        if (me == AMC_MODE_R || me == AMC_MODE_RW) {
+            put(AMC_K_GT, x);
+            put(AMC_K_EN, A + x);
+        }
+        if (me == AMC_MODE_W || me == AMC_MODE_RW) put(AMC_K_W, A + x);
+        if (mo == AMC_MODE_R || mo == AMC_MODE_RW) put(AMC_K_R, x);
+        if (mo == AMC_MODE_W || mo == AMC_MODE_RW) put(AMC_K_W, x);
+    }
+    if (p.infer) {
+        // shadows: union of the overlap lists of declared written operands,
+        // minus the call's arguments, ascending (merge of sorted lists)
+        int64_t cur[NMAX], end[NMAX];
+#pragma unroll
+        for (int l = 0; l < NMAX; ++l) {
+            cur[l] = end[l] = 0;
+            if (l < n && !(mode[l] & AMC_MODE_DROPPED) && (mode[l] & AMC_MODE_W)) {
+                cur[l] = p.ov_off[arr[l]];
+                end[l] = p.ov_off[arr[l] + 1];
+            }
+        }
+        for (;;) {
+            int32_t y = INT32_MAX;
+#pragma unroll
+            for (int l = 0; l < NMAX; ++l)
+                if (cur[l] < end[l]) y = min(y, p.ov_idx[cur[l]]);
+            if (y == INT32_MAX) break;
+#pragma unroll
+            for (int l = 0; l < NMAX; ++l)
+                if (cur[l] < end[l] && p.ov_idx[cur[l]] == y) ++cur[l];
+            if (is_arg(y)) continue;
+            put(AMC_K_GT, y);
+            put(AMC_K_EN, A + y);
+            put(AMC_K_W, A + y);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        if (i >= n) break;
+        if (!(mode[i] & AMC_MODE_W)) continue;           // the body writes x (declared or not)
+        const int32_t x = arr[i];
+        const int32_t sx = p.arr_start[x], lx = p.arr_len[x];
+        for (int64_t q = p.ov_off[x]; q < p.ov_off[x + 1]; ++q) {
+            const int32_t y = p.ov_idx[q];
+            put(iv_contains(sx, lx, p.arr_start[y], p.arr_len[y]) ? AMC_K_W : AMC_K_PW, y);
+        }
+    }
+    return o - out_base;
+}
+
+// Calls with more than 8 operands (rare): the same statements, arrays in local memory.
 template <bool EMIT>
-__device__ int64_t translate_call(const TrParams& p, int64_t c, int64_t out_base)
+__device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c, int64_t out_base)
 {
     const uint32_t side = p.call_side[c];
     const int32_t k0 = p.call_off[c], k1 = p.call_off[c + 1];
@@ -183,6 +308,21 @@ __device__ int64_t translate_call(const TrParams& p, int64_t c, int64_t out_base
         }
     }
     return o - out_base;
+}
+
+template <bool EMIT>
+__device__ int64_t translate_call(const TrParams& p, int64_t c, int64_t out_base)
+{
+    const uint32_t side = p.call_side[c];
+    const int32_t k0 = p.call_off[c], k1 = p.call_off[c + 1];
+    if (side > 1 || k0 < 0 || k1 < k0 || (int64_t)k1 > p.n_operands || k1 - k0 > MAX_OPND) {
+        if (!EMIT) raise_error(p.err, AMC_E_INVALID);
+        return -1;
+    }
+    const int n = k1 - k0;
+    if (n <= 4) return translate_call_n<EMIT, 4>(p, c, out_base, k0, n, side);
+    if (n <= 8) return translate_call_n<EMIT, 8>(p, c, out_base, k0, n, side);
+    return translate_call_dyn<EMIT>(p, c, out_base);
 }
 
 __global__ void count_kernel(const TrParams p)

@@ -1,9 +1,11 @@
 """GPU parity of the reduce / carry / apply path of the trace check.
 
-Traces over at most 16,384 variables take that path from 2^20 ops on;
-AMC_SCAN_DENSE=1 forces it at any size so that ragged tails, single tiles,
-chunks of several tiles (more than 2,048 tiles), one variable, the largest
-variable count, initial statuses and the guard pass all run through it.
+Traces over at most 16,384 variables take that path from 2^20 ops on (up to
+8,192 variables as warp-sequential batches, above that with tile sorts);
+AMC_SCAN_DENSE=1 forces it at any size and AMC_SCAN_DENSE_SORT=1 the sorted
+variant, so that ragged tails, single tiles, chunks of several tiles (more
+than 2,048 tiles), one variable, the largest variable count, initial
+statuses and the guard pass all run through both.
 Bit-exact against the oracle on every output."""
 import numpy as np
 import pytest
@@ -46,9 +48,12 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("variant", ["warp", "sort"])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_dense_path(amc, oracle_mod, monkeypatch, case):
+def test_dense_path(amc, oracle_mod, monkeypatch, case, variant):
+    # up to 8,192 variables warp-sequential batches by default; "sort" forces the tile sorts
     monkeypatch.setenv("AMC_SCAN_DENSE", "1")
+    monkeypatch.setenv("AMC_SCAN_DENSE_SORT", "1" if variant == "sort" else "0")
     rng = np.random.default_rng(41 + sorted(CASES).index(case))
     (ks, var), n_vars, init = CASES[case](rng)
     check(amc, oracle_mod, ks, var, n_vars, init)
@@ -71,8 +76,10 @@ def test_dense_and_list_paths_agree_at_default_threshold(amc, oracle_mod, monkey
     check(amc, oracle_mod, ks, var, 2000)
 
 
-def test_dense_path_guarded(amc, oracle_mod, monkeypatch):
+@pytest.mark.parametrize("variant", ["warp", "sort"])
+def test_dense_path_guarded(amc, oracle_mod, monkeypatch, variant):
     monkeypatch.setenv("AMC_SCAN_DENSE", "1")
+    monkeypatch.setenv("AMC_SCAN_DENSE_SORT", "1" if variant == "sort" else "0")
     w = workloads.vectorpu_calls(seed=51, n_arrays=64, space=1 << 14, n_calls=20_000,
                                  len_log2=(4.0, 10.0), drop_p=0.01)
     res = oracle_mod.vectorpu(**w)
