@@ -431,11 +431,12 @@ def run_programs(args):
 def vectorpu_launches(n_statements, n_vars):
     """Kernels of one translation + guarded check: 11 for the translation
     (two overlap passes, count, emit, total, two 3-kernel scans), then per
-    check pass 3 on the reduce / carry / apply path (traces over at most
-    16,384 variables from 2^20 ops on), else the scan kernel plus, in the
+    check pass the reduce / carry / apply path (traces over at most 16,384
+    variables from 2^20 ops on: 5 kernels up to 8,192 variables -- warp
+    batches and a two-level carry -- else 3), or the scan kernel plus, in the
     second pass, the final-status kernel."""
     if n_vars <= 16384 and n_statements >= (1 << 20) and os.environ.get("AMC_SCAN_DENSE", "") != "0":
-        return 11 + 2 * 3
+        return 11 + 2 * (5 if n_vars <= 8192 else 3)
     return 11 + 1 + 2
 
 
@@ -564,6 +565,8 @@ def trace_kernels(n_ops, n_vars):
     statuses and the first-fault merge; else the scan and the final statuses."""
     if os.environ.get("AMC_SCAN_DENSE", "") == "0":
         return "scan_trace_kernel", 2
+    if n_vars <= 8192 and n_ops >= (1 << 20):
+        return "warp reduce + carry + apply kernels", 5
     if n_vars <= 16384 and n_ops >= (1 << 20):
         return "dense reduce + carry + apply kernels", 3
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
