@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default="trace", choices=["trace", "programs", "vectorpu", "serve"])
     ap.add_argument("--rates", default="1000,10000,100000")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--n-progs", type=int, default=100_000, help="programs workload: number of programs")
+    ap.add_argument("--no-plain", action="store_true", help="programs workload: skip the one-launch-per-program run")
     return ap.parse_args()
 
 
@@ -378,7 +380,7 @@ def run_programs(args):
     import workloads
     torch.cuda.set_device(0)
     amc.build()
-    b = workloads.programs()
+    b = workloads.programs(n_progs=args.n_progs)
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     tok, pay, off, nv = t(b["tok"]), t(b["payload"]), t(b["prog_tok_off"]), t(b["prog_nvars"])
@@ -415,16 +417,18 @@ def run_programs(args):
                                   P_(out["step_mask"].data_ptr()), P_(out["final_mask"].data_ptr()),
                                   P_(out["prog_first_fault"].data_ptr() + 8 * i), 0, P_(ws.data_ptr()), ws.numel(),
                                   sp)
-        plain()
-        assert amc.sync_status(stream) == 0
-        ms_p = timed(plain, 1, stream)
+        ms_p = None
+        if not args.no_plain:
+            plain()
+            assert amc.sync_status(stream) == 0
+            ms_p = timed(plain, 1, stream)
     leaf = int(b["n_leaf"].sum())
     line = base_line(args, n_tok / (ms_b * 1e-3), ms_b,
                      {"workload": "programs", "n_progs": P, "tokens": n_tok, "leaf_ops": leaf, "seed": 3,
                       "mode": "batched persistent launch, CUDA graph replay, longest-first queue"},
-                     plain={"value": n_tok / (ms_p * 1e-3), "ms_per_step": ms_p,
-                            "mode": "one launch per program, same kernel"},
-                     batched_over_plain=ms_p / ms_b, gpu_launches=args.steps * 4)
+                     plain=None if ms_p is None else {"value": n_tok / (ms_p * 1e-3), "ms_per_step": ms_p,
+                                                      "mode": "one launch per program, same kernel"},
+                     batched_over_plain=None if ms_p is None else ms_p / ms_b, gpu_launches=args.steps * 4)
     print(json.dumps(line), flush=True)
 
 
