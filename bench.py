@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--n-vars", type=int, default=1 << 20)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunk", type=int, default=0, help="ops per chunk of the host-buffer check (0: 2^25)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="trace", choices=["trace", "programs", "vectorpu", "serve"])
@@ -279,21 +280,18 @@ def run_ours(args):
         var_h = torch.empty(n_ops, dtype=torch.int32, pin_memory=True)
         ks_h.copy_(ks)
         var_h.copy_(var)
-        step_h = torch.empty(n_ops, dtype=torch.uint8, pin_memory=True)
-        fin_h = torch.empty(n_vars, dtype=torch.uint8, pin_memory=True)
-        vff_h = torch.empty(n_vars, dtype=torch.int32, pin_memory=True)
-        ff_h = torch.empty(1, dtype=torch.int64, pin_memory=True)
-        ks_d = torch.empty_like(ks)
-        var_d = torch.empty_like(var)
+        hout = dict(step_status=torch.empty(n_ops, dtype=torch.uint8, pin_memory=True),
+                    final_status=torch.empty(n_vars, dtype=torch.uint8, pin_memory=True),
+                    var_first_fault=torch.empty(n_vars, dtype=torch.int32, pin_memory=True),
+                    first_fault=torch.empty(1, dtype=torch.int64, pin_memory=True))
+        hws = torch.empty(amc.trace_host_workspace_bytes(n_ops, n_vars, args.e2e_chunk) + 256, dtype=torch.uint8,
+                          device=dev)
+        hws = hws[(-hws.data_ptr()) % 256:]
 
         def e2e_step():
-            ks_d.copy_(ks_h, non_blocking=True)
-            var_d.copy_(var_h, non_blocking=True)
-            amc.check_trace(ks_d, var_d, n_vars, out=out, workspace=ws, stream=stream)
-            step_h.copy_(out["step_status"], non_blocking=True)
-            fin_h.copy_(out["final_status"], non_blocking=True)
-            vff_h.copy_(out["var_first_fault"], non_blocking=True)
-            ff_h.copy_(out["first_fault"], non_blocking=True)
+            # one call: chunked H2D of the pinned inputs, checks, D2H of every output
+            amc.check_trace_host(ks_h, var_h, n_vars, chunk_ops=args.e2e_chunk, out=hout, workspace=hws,
+                                 stream=stream)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -310,9 +308,17 @@ def run_ours(args):
         e_ms = max_over_ranks(a.elapsed_time(b) / n_e2e, world)
         e2e = {"value": n_ops * world / (e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": 5 * n_ops, "d2h_bytes_per_step": n_ops + 5 * n_vars + 8,
-               "ms_per_step": e_ms}
+               "ms_per_step": e_ms, "api": "amc_check_trace_host",
+               "chunk_ops": args.e2e_chunk or (1 << 25),
+               "mode": "pinned host buffers; copies in, checks and copies out of chunks overlapped"}
         if amc.sync_status() != 0:
             raise RuntimeError("device error during e2e steps")
+        # the host-buffer check must agree with the device-buffer one
+        if not (torch.equal(hout["final_status"], out["final_status"].cpu()) and
+                torch.equal(hout["var_first_fault"], out["var_first_fault"].cpu()) and
+                torch.equal(hout["first_fault"], out["first_fault"].cpu()) and
+                torch.equal(hout["step_status"][::997], out["step_status"][::997].cpu())):
+            raise RuntimeError("host-buffer check differs from the device-buffer check")
         host_copy = (ks_h.numpy(), var_h.numpy())
     else:
         host_copy = None

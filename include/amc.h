@@ -173,6 +173,37 @@ AMC_API int amc_check_trace_noalloc(const uint8_t* kind_side, const int32_t* var
                                     const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
                                     int32_t* var_first_fault, int64_t* first_fault, void* stream);
 
+/* amc_check_trace over HOST buffers: Section 3.2's check of one straight-line
+ * trace (same op kinds, statuses and first-fault rules), with the inputs read
+ * from and the outputs written to host memory.  The trace is cut into chunks
+ * of chunk_ops ops (<= 0: 2^25; rounded up to a multiple of 4,096).  Chunk c
+ * is checked from the final statuses of chunk c - 1 (Section 3.2: a trace's
+ * statuses depend only on the statuses before it), and its first faults are
+ * offset and folded into those of the earlier chunks.  Three chunks are in
+ * flight: while chunk c is checked on `stream`, chunk c + 1 is copied in and
+ * the step statuses of chunk c - 1 are copied out on two copy streams of this
+ * library.
+ *   kind_side, var [n_ops]        host inputs, as for amc_check_trace
+ *   init_status [n_vars]          host, or NULL for all (V,I)
+ *   step_status [n_ops], final_status, var_first_fault [n_vars],
+ *   first_fault [1]               host outputs, as for amc_check_trace
+ *   workspace, ws_bytes           DEVICE workspace, 256-byte aligned, at
+ *                                 least amc_check_trace_host_workspace(...)
+ *   stream                        the check's stream; the call waits for the
+ *                                 work already on it and returns at once.
+ * The outputs are complete once `stream` has synchronised (amc_sync_status).
+ * Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister): the
+ * copies then overlap the checks; pageable buffers give the same results with
+ * the copies serialised.  The caller keeps every buffer alive and untouched
+ * until the stream has synchronised.  Concurrent calls from several host
+ * threads are serialised while they enqueue.
+ * Errors: as amc_check_trace; AMC_E_NOMEM when ws_bytes is too small. */
+AMC_API size_t amc_check_trace_host_workspace(int64_t n_ops, int32_t n_vars, int64_t chunk_ops);
+AMC_API int amc_check_trace_host(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
+                                 const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                                 int32_t* var_first_fault, int64_t* first_fault, int64_t chunk_ops,
+                                 void* workspace, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* (2) VectorPU calls -> core trace -- Fig. sem-AM (translation of access    */
 /*     modes), Section 3.5 (one abstract status per array), Table            */

@@ -50,6 +50,9 @@ def lib():
         L.amc_check_guarded_trace_workspace.restype = sz
         L.amc_check_guarded_trace_workspace.argtypes = [i64, i32]
         L.amc_check_guarded_trace.argtypes = [P, P, i64, i32, P, P, P, P, P, P, sz, P]
+        L.amc_check_trace_host_workspace.restype = sz
+        L.amc_check_trace_host_workspace.argtypes = [i64, i32, i64]
+        L.amc_check_trace_host.argtypes = [P, P, i64, i32, P, P, P, P, P, i64, P, sz, P]
         if hasattr(L, "amc_translate_vectorpu"):
             L.amc_translate_vectorpu_workspace.restype = sz
             L.amc_translate_vectorpu_workspace.argtypes = [i32, i64, i64]
@@ -156,6 +159,58 @@ def check_trace(kind_side, var, n_vars, init_status=None, *, guarded=False, out=
             _p(ws), ws.numel(), _stream_ptr(stream))
     _check(rc, "amc_check_trace")
     return out
+
+
+def _host(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise TypeError(f"{name} must be a CPU tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def check_trace_host(kind_side, var, n_vars, init_status=None, *, chunk_ops=0, out=None, workspace=None,
+                     stream=None, device=None):
+    """Check one trace held in host memory (amc_check_trace_host): the library
+    copies it in chunk by chunk, checks each chunk on the GPU and copies the
+    step statuses back while the next chunk is on its way.
+
+    kind_side: uint8 CPU tensor [n_ops]; var: int32 CPU tensor [n_ops];
+    init_status: uint8 CPU tensor [n_vars] or None.  Pinned tensors
+    (``pin_memory=True``) let the copies overlap the checks.  Returns
+    dict(step_status, final_status, var_first_fault, first_fault) of CPU
+    tensors (pinned when allocated here), complete once ``stream`` (default:
+    the current stream) has synchronised, e.g. through ``sync_status``.
+    """
+    _host(kind_side, torch.uint8, "kind_side")
+    _host(var, torch.int32, "var")
+    n = kind_side.numel()
+    if var.numel() != n:
+        raise ValueError("kind_side and var differ in length")
+    if init_status is not None:
+        _host(init_status, torch.uint8, "init_status")
+        if init_status.numel() != n_vars:
+            raise ValueError("init_status must hold n_vars statuses")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if out is None:
+        out = dict(step_status=torch.empty(n, dtype=torch.uint8, pin_memory=True),
+                   final_status=torch.empty(max(n_vars, 0), dtype=torch.uint8, pin_memory=True),
+                   var_first_fault=torch.empty(max(n_vars, 0), dtype=torch.int32, pin_memory=True),
+                   first_fault=torch.empty(1, dtype=torch.int64, pin_memory=True))
+    L = lib()
+    nbytes = int(L.amc_check_trace_host_workspace(n, n_vars, int(chunk_ops)))
+    ws = workspace if workspace is not None else _ws.get(nbytes, dev)
+    rc = L.amc_check_trace_host(_p(kind_side), _p(var), n, n_vars, _p(init_status), _p(out["step_status"]),
+                                _p(out["final_status"]), _p(out["var_first_fault"]), _p(out["first_fault"]),
+                                int(chunk_ops), _p(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_check_trace_host")
+    return out
+
+
+def trace_host_workspace_bytes(n_ops: int, n_vars: int, chunk_ops: int = 0) -> int:
+    return int(lib().amc_check_trace_host_workspace(n_ops, n_vars, chunk_ops))
 
 
 def translate_vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd_mode, *,

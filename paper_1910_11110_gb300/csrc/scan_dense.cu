@@ -832,4 +832,12 @@ int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
     return launch_dense_range(L, DENSE_MAX_CHUNKS, L.n_ops, ws, s);
 }
 
+int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, int64_t* ff,
+                        const int64_t* ff_part, int64_t offset, cudaStream_t s)
+{
+    merge_faults_kernel<<<(unsigned)((n_vars + 255) / 256 > 0 ? (n_vars + 255) / 256 : 1), 256, 0, s>>>(
+        vff, vff_part, n_vars, ff, ff_part, offset);
+    return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
+}
+
 }  // namespace amc

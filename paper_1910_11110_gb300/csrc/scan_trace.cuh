@@ -75,6 +75,11 @@ int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
 // prefix's final statuses.
 bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars, bool has_init);
 int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
+// First faults of a check of ops [offset, ...) folded into those of the ops
+// before it: vff[v] = vff_part[v] + offset where vff[v] is -1 and vff_part[v]
+// is not; the same for *ff.
+int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, int64_t* ff,
+                        const int64_t* ff_part, int64_t offset, cudaStream_t s);
 // enable >= 0: switch phase counting on/off and zero the counters; host_out
 // (nullable): copy the 8 counters (cycles summed over CTAs).
 int scan_phase_profile(int enable, unsigned long long* host_out);
