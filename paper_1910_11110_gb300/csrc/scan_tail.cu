@@ -1,0 +1,462 @@
+// scan_tail.cu -- the tail of a long trace checked in epochs: stream filter,
+// compacted candidates, scatter.
+//
+// Section 3.2: F is absorbing, so once a variable's status is F every later
+// op on it yields F (Property Progress: a stuck variable stays stuck).  On a
+// long trace nearly every op after the first few per variable is such an op.
+// The first part of the trace, [0, S), is checked as usual (scan_trace.cu,
+// scan_dense.cu); the rest is cut into epochs of E ops, and for each epoch
+//   1. the statuses at its start are exact (the previous part's final
+//      statuses); variables with status F form a bitmap;
+//   2. a streaming kernel writes F for every op on a variable of the bitmap
+//      and collects the other ops ("candidates"), in position order;
+//   3. the candidates, a trace of their own over the same variables (an op's
+//      status depends only on the earlier ops on its variable), are checked
+//      by the single-pass scan from the epoch's start statuses, with the op
+//      count read from device memory;
+//   4. their statuses are scattered back to the epoch's positions and their
+//      first faults mapped to trace positions and folded into the earlier
+//      ones; the final statuses start the next epoch.
+// Outputs are identical to one scan over the whole trace.
+#include <cstdio>
+#include <cstdlib>
+
+#include "amc_internal.cuh"
+#include "scan_trace.cuh"
+
+namespace amc {
+
+namespace {
+
+constexpr int TF_THREADS = 1024;          // filter CTA: one per SM (the bitmap fills shared memory)
+constexpr int TF_CHUNK = 4096;            // ops per warp chunk (candidate slots per chunk)
+constexpr int TF_PER = 16;                // ops per lane and step
+constexpr int TAIL_MIN_VARS = 16385;      // fewer variables take the reduce / carry / apply path
+constexpr int TAIL_MAX_VARS = 1 << 20;    // bitmap of 128 KB in shared memory
+constexpr int DEFAULT_SPLIT_SHIFT = 4;    // S = n_ops / 16
+constexpr int DEFAULT_EPOCH_SHIFT = 2;    // E = n_ops / 4 (scratch about 17 B per epoch op)
+constexpr int64_t DEFAULT_MIN_OPS = (int64_t)1 << 29;
+
+struct TailShape {
+    int64_t S = 0;        // ops of the first part
+    int64_t E = 0;        // ops per epoch
+};
+
+// AMC_SCAN_TAIL="s,e": first part 2^s ops, epochs of 2^e ops, for every
+// trace longer than 2^s ops (test and tuning override); "0" disables.
+bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh)
+{
+    if (guarded || n_vars < TAIL_MIN_VARS || n_vars > TAIL_MAX_VARS) return false;
+    if (const char* e = getenv("AMC_SCAN_TAIL")) {
+        if (e[0] == '0' && e[1] == 0) return false;
+        int a = 0, b = 0;
+        if (sscanf(e, "%d,%d", &a, &b) == 2 && a >= 12 && a < 31 && b >= 12 && b < 31) {
+            sh.S = (int64_t)1 << a;
+            sh.E = (int64_t)1 << b;
+            return n_ops > sh.S;
+        }
+    }
+    if (n_ops < DEFAULT_MIN_OPS) return false;
+    sh.S = (n_ops >> DEFAULT_SPLIT_SHIFT) / TF_CHUNK * TF_CHUNK;
+    sh.E = (n_ops >> DEFAULT_EPOCH_SHIFT) / TF_CHUNK * TF_CHUNK;
+    return true;
+}
+
+struct TailLayout {
+    size_t part1 = 0;     // workspace of the first part
+    size_t st0, st1, bm, cnt, off, ncand, sks, svar, spos, cks, cvar, cpos, cstep, cvff, cff, cws, total;
+};
+
+TailLayout tail_layout(const TailShape& sh, int32_t n_vars)
+{
+    TailLayout t;
+    const size_t E = (size_t)sh.E;
+    const size_t n_chunks = (E + TF_CHUNK - 1) / TF_CHUNK;
+    size_t o = scan_workspace_bytes(sh.S, n_vars);
+    t.part1 = o;
+    auto take = [&](size_t b) { const size_t at = o; o += align_up(b, 256); return at; };
+    t.st0 = take((size_t)n_vars);
+    t.st1 = take((size_t)n_vars);
+    t.bm = take(4 * (size_t)((n_vars + 31) / 32));
+    t.cnt = take(4 * n_chunks);
+    t.off = take(4 * n_chunks);
+    t.ncand = take(8);
+    t.cks = take(E);
+    t.cvar = take(4 * E);
+    t.cpos = take(4 * E);
+    t.cstep = take(E);
+    t.cvff = take(4 * (size_t)n_vars);
+    t.cff = take(8);
+    // one region, used in turn by the filter's chunk slots (until the gather)
+    // and by the candidates' scan
+    t.cws = o;
+    t.sks = o;
+    t.svar = t.sks + align_up(E, 256);
+    t.spos = t.svar + align_up(4 * E, 256);
+    const size_t slots = align_up(E, 256) + align_up(4 * E, 256) + align_up(2 * E, 256);
+    const size_t scan = scan_workspace_bytes(sh.E, n_vars, false);
+    o += slots > scan ? slots : scan;
+    t.total = o;
+    return t;
+}
+
+// bit v: status of v is F
+__global__ void tail_bitmap_kernel(const uint8_t* __restrict__ st, int32_t n_vars, uint32_t* __restrict__ bm)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool f = v < n_vars && st[v] == ST_F;
+    const uint32_t m = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && v < n_vars) bm[v >> 5] = m;
+}
+
+struct FilterParams {
+    const uint8_t* kind_side;   // the epoch's first op
+    const int32_t* var;
+    int64_t n;                  // ops in the epoch
+    int64_t n_after;            // ops of the trace from the epoch's first op on (GT pairing)
+    int32_t n_vars;
+    const uint32_t* bm;         // stuck bitmap at the epoch's start
+    int bm_words;
+    uint8_t* step;              // the epoch's outputs
+    uint8_t* sks;               // candidate slots: TF_CHUNK per chunk
+    int32_t* svar;
+    uint16_t* spos;             // position within the chunk
+    uint32_t* cnt;              // candidates per chunk
+    int* err;
+    int bulk_ok;
+};
+
+// Each warp takes chunks of TF_CHUNK ops in steps of 32 x 16 (lane L: ops
+// [16 L, 16 L + 16) of a step: one 16-byte load of op bytes and four of ids);
+// ops on stuck variables get F, the others are staged in the chunk's slots in
+// position order.  Op bytes and ids are checked as in the
+// scan (malformed bytes, ids out of range, GT not followed by its EN).
+__global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const FilterParams q)
+{
+    extern __shared__ __align__(16) uint32_t sbm[];
+    for (int i = threadIdx.x; i < q.bm_words; i += TF_THREADS) sbm[i] = q.bm[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t n_chunks = (q.n + TF_CHUNK - 1) / TF_CHUNK;
+    for (int64_t c = (int64_t)blockIdx.x * (TF_THREADS / 32) + warp; c < n_chunks;
+         c += (int64_t)gridDim.x * (TF_THREADS / 32)) {
+        const int64_t c0 = c * TF_CHUNK;
+        const int cn = (int)min((int64_t)TF_CHUNK, q.n - c0);
+        int wcount = 0;
+        for (int s0 = 0; s0 < cn; s0 += 32 * TF_PER) {
+            const int off = s0 + lane * TF_PER;              // offset in the chunk
+            const int64_t i0 = c0 + off;                     // offset in the epoch
+            const int nl = (int)min((int64_t)TF_PER, q.n - i0);
+            const bool vec = nl == TF_PER && q.bulk_ok;
+            uint32_t kw[TF_PER / 4];
+            int32_t va[TF_PER];
+            uint32_t outw[TF_PER / 4];
+            uint32_t liveMask = 0;
+            if (vec) {
+                // full step: four op bytes per 32-bit word are checked at once
+                const uint4 kk = __ldcs(reinterpret_cast<const uint4*>(q.kind_side + i0));
+                kw[0] = kk.x;
+                kw[1] = kk.y;
+                kw[2] = kk.z;
+                kw[3] = kk.w;
+#pragma unroll
+                for (int h = 0; h < TF_PER / 4; ++h) {
+                    const int4 v4 = __ldcs(reinterpret_cast<const int4*>(q.var + i0) + h);
+                    va[4 * h] = v4.x;
+                    va[4 * h + 1] = v4.y;
+                    va[4 * h + 2] = v4.z;
+                    va[4 * h + 3] = v4.w;
+                }
+                uint32_t badk = 0, gt = 0, badv = 0;
+#pragma unroll
+                for (int h = 0; h < TF_PER / 4; ++h) {
+                    // a valid byte has bits 3 and 5-7 clear (kinds 0..7, side bit 4)
+                    badk |= kw[h] & 0xE8E8E8E8u;
+                    // bytes whose kind is GT (6): zero bytes of (kind ^ 6)
+                    const uint32_t x = (kw[h] & 0x0F0F0F0Fu) ^ 0x06060606u;
+                    gt |= (x - 0x01010101u) & ~x & 0x80808080u;
+                    outw[h] = 0;
+                }
+#pragma unroll
+                for (int u = 0; u < TF_PER; ++u) {
+                    const uint32_t v = (uint32_t)va[u];
+                    const bool ok = v < (uint32_t)q.n_vars;
+                    badv |= !ok;
+                    const uint32_t uv = ok ? v : 0u;
+                    const uint32_t stuck = (sbm[uv >> 5] >> (uv & 31)) & 1u;
+                    liveMask |= (stuck ^ 1u) << u;
+                    outw[u >> 2] |= stuck << (8 * (u & 3) + 2);       // F = 4 where stuck, else 0
+                }
+                if (badk) raise_error(q.err, AMC_E_INVALID);
+                if (badv) raise_error(q.err, AMC_E_RANGE);
+                if (gt) {
+                    // GT must be followed by EN of the same side on another variable
+#pragma unroll
+                    for (int u = 0; u < TF_PER; ++u) {
+                        const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
+                        if ((ks & 15u) != AMC_K_GT) continue;
+                        const uint32_t uv = (uint32_t)va[u] < (uint32_t)q.n_vars ? (uint32_t)va[u] : 0u;
+                        uint32_t nks = 0xFF;
+                        int32_t nv = (int32_t)uv;
+                        if (i0 + u + 1 < q.n_after) {
+                            nks = q.kind_side[i0 + u + 1];
+                            nv = q.var[i0 + u + 1];
+                        }
+                        if (!((nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv))
+                            raise_error(q.err, AMC_E_INVALID);
+                    }
+                }
+                __stcs(reinterpret_cast<uint4*>(q.step + i0), make_uint4(outw[0], outw[1], outw[2], outw[3]));
+            } else {
+#pragma unroll
+                for (int h = 0; h < TF_PER / 4; ++h) kw[h] = outw[h] = 0;
+#pragma unroll
+                for (int u = 0; u < TF_PER; ++u) {
+                    va[u] = 0;
+                    if (u < nl) {
+                        kw[u >> 2] |= (uint32_t)q.kind_side[i0 + u] << (8 * (u & 3));
+                        va[u] = q.var[i0 + u];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < TF_PER; ++u) {
+                    const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
+                    uint32_t o = ST_F;
+                    if (u < nl) {
+                        if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(q.err, AMC_E_INVALID);
+                        uint32_t uv = (uint32_t)va[u];
+                        if (va[u] < 0 || va[u] >= q.n_vars) {
+                            raise_error(q.err, AMC_E_RANGE);
+                            uv = 0;
+                        }
+                        if ((ks & 15u) == AMC_K_GT) {
+                            uint32_t nks = 0xFF;
+                            int32_t nv = (int32_t)uv;
+                            if (i0 + u + 1 < q.n_after) {
+                                nks = q.kind_side[i0 + u + 1];
+                                nv = q.var[i0 + u + 1];
+                            }
+                            if (!((nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv))
+                                raise_error(q.err, AMC_E_INVALID);
+                        }
+                        if (!((sbm[uv >> 5] >> (uv & 31)) & 1u)) {
+                            liveMask |= 1u << u;
+                            o = 0;                            // scattered after the candidates' check
+                        }
+                        q.step[i0 + u] = (uint8_t)o;
+                    }
+                }
+            }
+            const int cl = __popc(liveMask);
+            if (!__any_sync(0xffffffffu, cl != 0)) continue;
+            int pre = 0, wtot = 0;
+#pragma unroll
+            for (int bit = 0; bit < 6; ++bit) {                 // counts 0..32
+                const uint32_t bal = __ballot_sync(0xffffffffu, (cl >> bit) & 1);
+                pre += __popc(bal & lt) << bit;
+                wtot += __popc(bal) << bit;
+            }
+            int idx = (int)(c0 + wcount + pre);      // < c0 + cn: at most every op of the chunk
+#pragma unroll
+            for (int u = 0; u < TF_PER; ++u) {
+                if (liveMask & (1u << u)) {
+                    q.sks[idx] = (uint8_t)((kw[u >> 2] >> (8 * (u & 3))) & 0xFFu);
+                    q.svar[idx] = va[u];
+                    q.spos[idx] = (uint16_t)(off + u);
+                    ++idx;
+                }
+            }
+            wcount += wtot;
+        }
+        if (lane == 0) q.cnt[c] = (uint32_t)wcount;
+    }
+}
+
+// Exclusive offsets of the chunks' candidate counts and their total (one CTA).
+__global__ void __launch_bounds__(1024) tail_offsets_kernel(const uint32_t* __restrict__ cnt, int n_chunks,
+                                                            uint32_t* __restrict__ off, int64_t* __restrict__ n_cand)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < n_chunks; b += 1024) {
+        const int i = b + tid;
+        const uint32_t x = i < n_chunks ? cnt[i] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            wsum[lane] = w;                  // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t base = carry + (warp > 0 ? wsum[warp - 1] : 0u);
+        if (i < n_chunks) off[i] = base + incl - x;
+        __syncthreads();
+        if (tid == 0) carry += wsum[31];
+        __syncthreads();
+    }
+    if (tid == 0) *n_cand = (int64_t)carry;
+}
+
+// Chunk slots -> dense candidate trace (one CTA of 128 threads per chunk).
+__global__ void tail_gather_kernel(const uint8_t* __restrict__ sks, const int32_t* __restrict__ svar,
+                                   const uint16_t* __restrict__ spos, const uint32_t* __restrict__ cnt,
+                                   const uint32_t* __restrict__ off, uint8_t* __restrict__ cks,
+                                   int32_t* __restrict__ cvar, uint32_t* __restrict__ cpos)
+{
+    const int64_t c = blockIdx.x;
+    const uint32_t n = cnt[c], o = off[c];
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t src = c * TF_CHUNK + j;
+        cks[o + j] = sks[src];
+        cvar[o + j] = svar[src];
+        cpos[o + j] = (uint32_t)(c * TF_CHUNK) + spos[src];
+    }
+}
+
+// Candidates' statuses to their positions; their first faults (indices into
+// the candidate trace) to trace positions, kept only where the earlier ops had
+// none.
+__global__ void tail_scatter_kernel(const uint8_t* __restrict__ cstep, const uint32_t* __restrict__ cpos,
+                                    const int64_t* __restrict__ n_cand, uint8_t* __restrict__ step,
+                                    const int32_t* __restrict__ cvff, int32_t n_vars, int32_t* __restrict__ vff,
+                                    const int64_t* __restrict__ cff, int64_t* __restrict__ ff, int64_t epoch0)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nc = *n_cand;
+    for (int64_t j = g; j < nc; j += stride) step[cpos[j]] = cstep[j];
+    for (int64_t v = g; v < n_vars; v += stride) {
+        const int32_t c = cvff[v];
+        if (c >= 0 && vff[v] < 0) vff[v] = (int32_t)(epoch0 + cpos[c]);
+    }
+    if (g == 0 && *cff >= 0 && *ff < 0) *ff = epoch0 + cpos[*cff];
+}
+
+}  // namespace
+
+bool scan_tail_eligible(const ScanLaunch& L)
+{
+    TailShape sh;
+    return L.dense != 0 && !L.n_dev && !L.guard && !L.pre_mode &&
+           tail_shape(L.n_ops, L.n_vars, false, sh);
+}
+
+size_t scan_tail_workspace_bytes(int64_t n_ops, int32_t n_vars)
+{
+    TailShape sh;
+    if (!tail_shape(n_ops, n_vars, false, sh)) return 0;
+    return tail_layout(sh, n_vars).total;
+}
+
+int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
+{
+    TailShape sh;
+    if (!tail_shape(L.n_ops, L.n_vars, false, sh)) return AMC_E_INVALID;
+    const TailLayout lay = tail_layout(sh, L.n_vars);
+    uint8_t* w = static_cast<uint8_t*>(L.workspace);
+    uint8_t* st[2] = {w + lay.st0, w + lay.st1};
+    uint32_t* bm = reinterpret_cast<uint32_t*>(w + lay.bm);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(w + lay.cnt);
+    uint32_t* off = reinterpret_cast<uint32_t*>(w + lay.off);
+    int64_t* ncand = reinterpret_cast<int64_t*>(w + lay.ncand);
+    uint8_t* sks = w + lay.sks;
+    int32_t* svar = reinterpret_cast<int32_t*>(w + lay.svar);
+    uint16_t* spos = reinterpret_cast<uint16_t*>(w + lay.spos);
+    uint8_t* cks = w + lay.cks;
+    int32_t* cvar = reinterpret_cast<int32_t*>(w + lay.cvar);
+    uint32_t* cpos = reinterpret_cast<uint32_t*>(w + lay.cpos);
+    uint8_t* cstep = w + lay.cstep;
+    int32_t* cvff = reinterpret_cast<int32_t*>(w + lay.cvff);
+    int64_t* cff = reinterpret_cast<int64_t*>(w + lay.cff);
+
+    int dev = 0, n_sm = 0, max_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int bm_words = (L.n_vars + 31) / 32;
+    const size_t fsmem = 4 * (size_t)bm_words;
+    if ((int)fsmem > max_optin) return AMC_E_INVALID;
+    static size_t attr_set[64] = {};
+    if (dev >= 64 || attr_set[dev] < fsmem) {
+        if (cudaFuncSetAttribute(tail_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem) !=
+            cudaSuccess)
+            return AMC_E_CUDA;
+        if (dev < 64) attr_set[dev] = fsmem;
+    }
+
+    // first part: the usual scan of ops [0, S), final statuses to st[0]
+    ScanLaunch A = L;
+    A.n_ops = sh.S;
+    A.final_status = st[0];
+    A.profile = L.profile & 1;
+    int rc = launch_scan_trace(A, s);
+    if (rc) return rc;
+
+    int cur = 0;
+    for (int64_t e0 = sh.S; e0 < L.n_ops; e0 += sh.E) {
+        const int64_t n = L.n_ops - e0 < sh.E ? L.n_ops - e0 : sh.E;
+        const bool last = e0 + n >= L.n_ops;
+        tail_bitmap_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(st[cur], L.n_vars, bm);
+        FilterParams q;
+        q.kind_side = L.kind_side + e0;
+        q.var = L.var + e0;
+        q.n = n;
+        q.n_after = L.n_ops - e0;
+        q.n_vars = L.n_vars;
+        q.bm = bm;
+        q.bm_words = bm_words;
+        q.step = L.step + e0;
+        q.sks = sks;
+        q.svar = svar;
+        q.spos = spos;
+        q.cnt = cnt;
+        q.err = L.err;
+        q.bulk_ok = ((uintptr_t)q.kind_side % 16 == 0) && ((uintptr_t)q.var % 16 == 0) &&
+                    ((uintptr_t)q.step % 16 == 0);
+        const int n_chunks = (int)((n + TF_CHUNK - 1) / TF_CHUNK);
+        const int fgrid = (int)min((int64_t)n_sm, ((int64_t)n_chunks + TF_THREADS / 32 - 1) / (TF_THREADS / 32));
+        tail_filter_kernel<<<fgrid, TF_THREADS, fsmem, s>>>(q);
+        tail_offsets_kernel<<<1, 1024, 0, s>>>(cnt, n_chunks, off, ncand);
+        tail_gather_kernel<<<n_chunks, 128, 0, s>>>(sks, svar, spos, cnt, off, cks, cvar, cpos);
+        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        // the candidates: a trace of at most n ops (count on the device)
+        ScanLaunch C = L;
+        C.kind_side = cks;
+        C.var = cvar;
+        C.n_ops = n;
+        C.n_dev = ncand;
+        C.init = st[cur];
+        C.step = cstep;
+        C.final_status = (last && L.final_status) ? L.final_status : st[cur ^ 1];
+        C.vff = cvff;
+        C.first_fault = cff;
+        C.workspace = w + lay.cws;
+        C.dense = 0;
+        C.profile = 0;
+        rc = launch_scan_trace(C, s);
+        if (rc) return rc;
+        tail_scatter_kernel<<<n_sm * 4, 256, 0, s>>>(cstep, cpos, ncand, L.step + e0, cvff, L.n_vars, L.vff, cff,
+                                                    L.first_fault, e0);
+        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        cur ^= 1;
+    }
+    if (L.profile & 2) profile_end(s);
+    return AMC_OK;
+}
+
+}  // namespace amc

@@ -108,6 +108,8 @@ struct __align__(16) ScanSmem {
     int nLive;
     uint32_t frontVal;
     int grp[1];                      // tiles in the current claim
+    int64_t nOps;                    // ops of the trace (the host count, or the device one)
+    int nTiles;
     // followed (dynamic shared memory) by the stuck bitmap: fbw 32-bit words
 };
 // three CTAs per SM with 32-bit keys within a 164 KB shared-memory carve-out (1 KB reserved
@@ -134,7 +136,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)t * T;
-    const int n = (int)min((int64_t)T, p.n_ops - base);
+    const int n = (int)min((int64_t)T, S.nOps - base);
     uint8_t* kb = S.kind[b];
     int32_t* vraw = reinterpret_cast<int32_t*>(S.vbuf[b]);
     const uint32_t ID = 0;
@@ -190,8 +192,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
 #pragma unroll
         for (int u = 0; u < G; ++u) {
             const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
-            fwa[k][u] = p.fb_mode == 2 ? __ldg(fbl1 + (uv >> 5))
-                                       : (uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : 0u);
+            fwa[k][u] = uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : (p.fb_mode >= 2 ? __ldg(fbl1 + (uv >> 5)) : 0u);
         }
     }
 #pragma unroll
@@ -222,7 +223,7 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                         const int64_t gi = base + i;
                         uint32_t nks = 0xFF;
                         int32_t nv = (int32_t)uv;
-                        if (gi + 1 < p.n_ops) {
+                        if (gi + 1 < S.nOps) {
                             nks = (i + 1 < n) ? kb[i + 1] : p.kind_side[gi + 1];
                             nv = (i + 1 < n) ? vraw[i + 1] : p.var[gi + 1];
                         }
@@ -732,7 +733,9 @@ __device__ void process_tile(const ScanParams& p, ScanSmem<KeyT, T, NT>& S, uint
                 atomicOr(p.fbits + (v >> 5), 1u << (v & 31));
                 atomicOr(p.fbits + p.fbits_words + (v >> 5), 1u << (v & 31));
                 if (v < (uint32_t)p.fbw * 32u) atomicOr(fsm + (v >> 5), 1u << (v & 31));
-                atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
+                // the global minimum only falls: skip the atomic once it is below gi
+                if ((unsigned long long)gi < *reinterpret_cast<volatile unsigned long long*>(p.first_fault))
+                    atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
             }
         }
     }
@@ -774,44 +777,52 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
     const uint32_t ID = 0;
     const uint32_t lt = lanemask_lt();
     const int64_t gbase = (int64_t)t0 * T;
-    const int nTiles = (int)min((int64_t)G, (int64_t)p.n_tiles - t0);
+    const int nTiles = (int)min((int64_t)G, (int64_t)S.nTiles - t0);
 
     const uint32_t* fbl1 = p.fbits + ((refresh >> 6) & 1u) * (uint32_t)p.fbits_words;
     if (p.fbw) {
         const uint32_t nq = (uint32_t)p.fbw / 4;
-        for (uint32_t r = 0; r < 2u * (uint32_t)nTiles; ++r) {
+        const uint32_t reps = min(2u * (uint32_t)nTiles, (nq + NT - 1) / NT);   // at most one full pass
+        for (uint32_t r = 0; r < reps; ++r) {
             const uint32_t q = ((2 * refresh + r) * NT + tid) % nq;
             reinterpret_cast<uint4*>(fsm)[q] = __ldcg(reinterpret_cast<const uint4*>(p.fbits) + q);
         }
     }
 
     // ---- 1-2. stream and decode the tiles; compact the live ops ------------
-    // Thread tid takes ops [16 tid, 16 tid + 16) of each tile (one 16-byte load
-    // of op bytes, four of ids, one 16-byte store of outputs), so live ops in
-    // (warp, lane) order are in position order.  Nearly every op is on a
-    // stuck variable: a warp computes its live-op prefix (five ballots) only
-    // when it has a live op, and one barrier per tile tells whether the block
-    // has any.
+    // Warp w takes the contiguous ops [w R, (w + 1) R) of the group (R =
+    // nTiles * T / NW) in steps of 32 * 16 ops; lane L takes ops [16 L, 16 L +
+    // 16) of a step (one 16-byte load of op bytes, four of ids, one 16-byte
+    // store of outputs).  No block barrier inside the loop: each warp stages
+    // its live ops, in position order, in a slice of its own (T / NW entries;
+    // a fuller slice sends the group to the tile path), and one barrier at
+    // the end concatenates the slices.
     constexpr int PER = T / NT;
-    static_assert(PER == 16, "16 ops per thread and tile");
+    static_assert(PER == 16, "16 ops per thread and step");
+    constexpr int CAP = T / NW;                                  // staged live ops per warp
     KeyT* const keyIn = S.keyA;
-    int total = 0;                           // live ops so far (the same in every thread)
-    for (int g = 0; g < nTiles; ++g) {
-        const int64_t base = gbase + (int64_t)g * T;
-        const int n = (int)min((int64_t)T, p.n_ops - base);
-        const bool vec = n == T && p.bulk_ok;
-        const int i0 = tid * PER;
+    uint32_t* const stVar = reinterpret_cast<uint32_t*>(S.vbuf[0]);   // staged var ids
+    uint32_t* const stPos = reinterpret_cast<uint32_t*>(S.keyA);      // staged offset | element << 16
+    const int gops = (int)min((int64_t)nTiles * T, S.nOps - gbase);  // ops in the group (<= 2^16)
+    const int R = nTiles * (T / NW);
+    int wcount = 0;                          // live ops staged by this warp (warp-uniform)
+    bool over = false;
+    for (int s0 = warp * R; s0 < (warp + 1) * R && s0 < gops; s0 += 32 * PER) {
+        const int i0 = s0 + lane * PER;                          // group offset of the lane's first op
+        const int n = min(PER, gops - i0);                       // its ops in the trace (may be <= 0)
+        const int64_t base = gbase + i0;
+        const bool vec = n == PER && p.bulk_ok;
         uint32_t kw[PER / 4];
         int32_t va[PER];
         if (vec) {
-            const uint4 kk = __ldcs(reinterpret_cast<const uint4*>(p.kind_side + base + i0));
+            const uint4 kk = __ldcs(reinterpret_cast<const uint4*>(p.kind_side + base));
             kw[0] = kk.x;
             kw[1] = kk.y;
             kw[2] = kk.z;
             kw[3] = kk.w;
 #pragma unroll
             for (int q = 0; q < PER / 4; ++q) {
-                const int4 v4 = __ldcs(reinterpret_cast<const int4*>(p.var + base + i0) + q);
+                const int4 v4 = __ldcs(reinterpret_cast<const int4*>(p.var + base) + q);
                 va[4 * q] = v4.x;
                 va[4 * q + 1] = v4.y;
                 va[4 * q + 2] = v4.z;
@@ -823,9 +834,9 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 va[u] = 0;
-                if (i0 + u < n) {
-                    kw[u >> 2] |= (uint32_t)p.kind_side[base + i0 + u] << (8 * (u & 3));
-                    va[u] = p.var[base + i0 + u];
+                if (u < n) {
+                    kw[u >> 2] |= (uint32_t)p.kind_side[base + u] << (8 * (u & 3));
+                    va[u] = p.var[base + u];
                 }
             }
         }
@@ -833,7 +844,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
-            fw[u] = p.fb_mode == 2 ? __ldg(fbl1 + (uv >> 5)) : (uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : 0u);
+            fw[u] = uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : (p.fb_mode >= 2 ? __ldg(fbl1 + (uv >> 5)) : 0u);
         }
         uint32_t outw[PER / 4], melw[PER / 4];
         uint32_t liveMask = 0;
@@ -841,10 +852,9 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
         for (int q = 0; q < PER / 4; ++q) outw[q] = melw[q] = 0;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
-            const int i = i0 + u;
             const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
             uint32_t o = ST_F;
-            if (i < n) {
+            if (u < n) {
                 if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
                 uint32_t uv = (uint32_t)va[u];
                 if (va[u] < 0 || va[u] >= p.n_vars) {
@@ -854,10 +864,10 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 bool gt_ok = true;
                 if ((ks & 15u) == AMC_K_GT) {
                     // GT must be followed by EN of the same side on another variable
-                    const int64_t gi = base + i;
+                    const int64_t gi = base + u;
                     uint32_t nks = 0xFF;
                     int32_t nv = (int32_t)uv;
-                    if (gi + 1 < p.n_ops) {
+                    if (gi + 1 < S.nOps) {
                         nks = p.kind_side[gi + 1];
                         nv = p.var[gi + 1];
                     }
@@ -873,7 +883,7 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                             raise_error(p.err, AMC_E_INVALID);
                             m = ID;
                         } else {
-                            const uint32_t gs = p.guard[base + i + 1];
+                            const uint32_t gs = p.guard[base + u + 1];
                             const int side = ks >> 4;
                             const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
                             m = valid ? ID : p.tab.pull_of_side[side];
@@ -889,48 +899,78 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
             outw[u >> 2] |= o << (8 * (u & 3));
         }
         if (vec) {
-            __stcs(reinterpret_cast<uint4*>(p.step + base + i0), make_uint4(outw[0], outw[1], outw[2], outw[3]));
+            __stcs(reinterpret_cast<uint4*>(p.step + base), make_uint4(outw[0], outw[1], outw[2], outw[3]));
         } else {
 #pragma unroll
             for (int u = 0; u < PER; ++u)
-                if (i0 + u < n) p.step[base + i0 + u] = (uint8_t)(outw[u >> 2] >> (8 * (u & 3)));
+                if (u < n) p.step[base + u] = (uint8_t)(outw[u >> 2] >> (8 * (u & 3)));
         }
         // live-op prefix within the warp (counts are 0..16: five bits)
         const int c = __popc(liveMask);
+        if (!__any_sync(0xffffffffu, c != 0)) continue;
         int pre = 0, wtot = 0;
-        if (__any_sync(0xffffffffu, c != 0)) {
 #pragma unroll
-            for (int bit = 0; bit < 5; ++bit) {
-                const uint32_t bal = __ballot_sync(0xffffffffu, (c >> bit) & 1);
-                pre += __popc(bal & lt) << bit;
-                wtot += __popc(bal) << bit;
-            }
+        for (int bit = 0; bit < 5; ++bit) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (c >> bit) & 1);
+            pre += __popc(bal & lt) << bit;
+            wtot += __popc(bal) << bit;
         }
-        uint16_t* const cnt = S.cnt + (g & 1) * NW;
-        if (lane == 0) cnt[warp] = (uint16_t)wtot;
-        if (!__syncthreads_or(c != 0)) continue;     // no live op in the tile
-        int off = total, tileTot = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int cw = cnt[w];
-            if (w < warp) off += cw;
-            tileTot += cw;
+        if (wcount + wtot > CAP) {               // too many live ops for the warp's slice
+            over = true;
+            break;
         }
-        if (total + tileTot > T) return false;   // too many live ops for one group
         if (liveMask) {
-            int idx = off + pre;
+            int idx = warp * CAP + wcount + pre;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 if (liveMask & (1u << u)) {
-                    const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
-                    keyIn[pad(idx)] = ((KeyT)uv << POS_BITS) | (KeyT)idx;
-                    S.livePos[idx] = (uint16_t)((g << POS_BITS) | (i0 + u));
-                    S.mel[idx] = (uint8_t)((melw[u >> 2] >> (8 * (u & 3))) & 0xFFu);
+                    stVar[idx] = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
+                    stPos[idx] = (uint32_t)(i0 + u) | (((melw[u >> 2] >> (8 * (u & 3))) & 0xFFu) << 16);
                     ++idx;
                 }
             }
         }
-        total += tileTot;
+        wcount += wtot;
+    }
+    if (lane == 0) S.cnt[warp] = over ? 0xFFFFu : (uint16_t)wcount;
+    __syncthreads();
+    int total = 0, woff[NW];
+    bool anyOver = false;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int cw = S.cnt[w];
+        anyOver |= cw == 0xFFFF;
+        woff[w] = total;
+        total += cw == 0xFFFF ? 0 : cw;
+    }
+    if (anyOver) return false;               // the tile path takes the group (every thread agrees)
+    if (total > 0) {
+        // slices -> position-ordered live indices (keys, offsets, elements)
+        uint32_t sv[PER], sp[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = k * NT + tid;
+            sv[k] = sp[k] = 0;
+            if (i < total) {
+                int w = 0;
+#pragma unroll
+                for (int x = 1; x < NW; ++x)
+                    if (i >= woff[x]) w = x;
+                const int src = w * CAP + (i - woff[w]);
+                sv[k] = stVar[src];
+                sp[k] = stPos[src];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = k * NT + tid;
+            if (i < total) {
+                keyIn[pad(i)] = ((KeyT)sv[k] << POS_BITS) | (KeyT)i;
+                S.livePos[i] = (uint16_t)(sp[k] & 0xFFFFu);
+                S.mel[i] = (uint8_t)(sp[k] >> 16);
+            }
+        }
     }
     if (tid == 0) {
         S.nLive = total;
@@ -1359,7 +1399,9 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 atomicOr(p.fbits + (v >> 5), 1u << (v & 31));
                 atomicOr(p.fbits + p.fbits_words + (v >> 5), 1u << (v & 31));
                 if (v < (uint32_t)p.fbw * 32u) atomicOr(fsm + (v >> 5), 1u << (v & 31));
-                atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
+                // the global minimum only falls: skip the atomic once it is below gi
+                if ((unsigned long long)gi < *reinterpret_cast<volatile unsigned long long*>(p.first_fault))
+                    atomicMin(reinterpret_cast<unsigned long long*>(p.first_fault), (unsigned long long)gi);
             }
         }
     }
@@ -1375,7 +1417,7 @@ __device__ __forceinline__ void issue_tile(const ScanParams& p, ScanSmem<KeyT, T
 {
     const int64_t base = (int64_t)t * T;
     S.viaBulk[b] = 0;
-    if (t < p.n_tiles && base + T <= p.n_ops && p.bulk_ok) {
+    if (t < S.nTiles && base + T <= S.nOps && p.bulk_ok) {
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&S.mbar[b], (uint32_t)(T + 4 * T));
         bulk_g2s(S.kind[b], p.kind_side + base, T, &S.mbar[b]);
@@ -1408,6 +1450,13 @@ __global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const S
         mbar_init(&S.mbar[0], 1);
         fence_mbar_init();
         S.frontVal = 0;
+        int64_t n = p.n_ops;
+        if (p.n_dev) {
+            const int64_t d = *p.n_dev;
+            n = d < 0 ? 0 : (d < n ? d : n);
+        }
+        S.nOps = n;
+        S.nTiles = (int)((n + T - 1) / T);
     }
     uint32_t parity = 0;
     long long last = clock64();
@@ -1435,10 +1484,10 @@ __global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const S
         __syncthreads();
         const int t = S.tile[0];
         const int G = S.grp[0];
-        if (t >= p.n_tiles) break;
+        if (t >= S.nTiles) break;
         if (G > 1) {
             if (process_group<KeyT, T, NT>(p, S, fsm, t, G, done, last)) {
-                const int nt = min(G, p.n_tiles - t);
+                const int nt = min(G, S.nTiles - t);
                 if (tid == 0) est = (est + (uint32_t)S.nLive / (uint32_t)nt + 1) / 2;
                 done += (uint32_t)nt;
                 __syncthreads();
@@ -1446,7 +1495,7 @@ __global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const S
             }
             // more live ops than one group holds: its tiles one by one
             if (tid == 0) est = T;
-            for (int u = 0; u < G && t + u < p.n_tiles && !failed; ++u) {
+            for (int u = 0; u < G && t + u < S.nTiles && !failed; ++u) {
                 __syncthreads();
                 if (tid == 0) issue_tile<KeyT, T, NT>(p, S, 0, t + u);
                 __syncthreads();
@@ -1593,16 +1642,22 @@ size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars, bool with_dense)
     b += align_up(4 * (size_t)((n_tiles + 31) / 32), 256);  // registration bits
     b += 2 * align_up(16 * (size_t)((n_vars + 127) / 128), 256); // stuck bitmap, two copies
     b += 256;                                               // tile counter, frontier
-    if (with_dense) b += scan_dense_workspace_bytes(n_ops, n_vars);   // reduce / carry / apply path
+    if (with_dense) {
+        b += scan_dense_workspace_bytes(n_ops, n_vars);    // reduce / carry / apply path
+        const size_t t = scan_tail_workspace_bytes(n_ops, n_vars);   // epochs of a long trace
+        if (t > b) b = t;
+    }
     return b;
 }
 
 int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
 {
+    if (scan_tail_eligible(L)) return launch_scan_tail(L, s);
     ScanParams p{};
     p.kind_side = L.kind_side;
     p.var = L.var;
     p.n_ops = L.n_ops;
+    p.n_dev = L.n_dev;
     p.n_vars = L.n_vars;
     p.init = L.init;
     p.step = L.step;
@@ -1633,14 +1688,17 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
         const int64_t words = (int64_t)(fbytes / 4);
         int64_t bits = L.fb_max_bits ? L.fb_max_bits : DEFAULT_FB_BITS;
         if (const char* e = getenv("AMC_SCAN_FB_BITS")) bits = atoll(e);       // tuning override
-        p.fb_mode = bits > 0 ? 1 : (bits == -2 ? 2 : 0);    // -2: L1-cached global copies
-        const int64_t cap = bits > 0 ? bits / 32 : 0;
+        // > 0: shared copy of the first `bits` variables, the rest live;
+        // -2: L1-cached global copies; < -2: shared copy of the first -bits
+        // variables (the most frequent ids of a Zipf trace), the rest L1
+        p.fb_mode = bits > 0 ? 1 : (bits == -2 ? 2 : (bits < -2 ? 3 : 0));
+        const int64_t cap = (bits > 0 ? bits / 32 : (bits < -2 ? -bits / 32 : 0)) & ~(int64_t)3;
         p.fbw = (int)(words < cap ? words : cap);
     }
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
-    if (L.dense != 0 && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
-    if (L.dense != 0 && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr))
+    if (L.dense != 0 && !L.n_dev && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
+    if (L.dense != 0 && !L.n_dev && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr))
         return launch_scan_prefix(L, w + 256, s);
     // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
     int kb = 1;

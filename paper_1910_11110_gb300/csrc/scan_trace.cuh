@@ -8,7 +8,8 @@ namespace amc {
 struct ScanParams {
     const uint8_t* kind_side;
     const int32_t* var;
-    int64_t n_ops;
+    int64_t n_ops;              // ops (with n_dev: the capacity of the arrays)
+    const int64_t* n_dev;       // nullable: device word with the op count (clamped to n_ops)
     int32_t n_vars;
     const uint8_t* init;        // nullable: all (V,I)
     uint8_t* step;              // [n_ops] post-statuses (pre-statuses in pre_mode)
@@ -24,7 +25,7 @@ struct ScanParams {
     uint32_t* fbits;            // bit v set: variable v is known to be stuck
     int fbw;                    // words of fbits copied to shared memory (multiple of 4)
     int fbits_words;            // words per copy of fbits (two copies)
-    int fb_mode;                // 0 none, 1 shared copy, 2 L1-cached global copies
+    int fb_mode;                // 0 none, 1 shared copy, 2 L1-cached global copies, 3 both
     uint32_t* tile_counter;
     uint32_t* front;            // every tile < *front has registered
     int n_tiles;
@@ -58,6 +59,8 @@ struct ScanLaunch {
     int group_max = 0;                  // most tiles per claim (0 = default, 1 = tile path only)
     int ctas_per_sm = 0;                // resident CTAs per SM (0 = as many as fit)
     int dense = -1;                     // reduce / carry / apply path: -1 when eligible, 0 never
+    const int64_t* n_dev = nullptr;     // device op count, read by the kernel (n_ops = capacity);
+                                        // single-pass kernel only, not with a guard
 };
 
 int scan_tile_size();
@@ -80,6 +83,14 @@ int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
 // is not; the same for *ff.
 int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, int64_t* ff,
                         const int64_t* ff_part, int64_t offset, cudaStream_t s);
+// Traces over 16,385 to 2^20 variables and of 2^29 ops or more, without a
+// guard: the first n_ops / 16 ops as usual, the rest in epochs of n_ops / 4
+// (stream filter on the stuck bitmap, compacted candidates checked from the
+// epoch's start statuses, scatter); its scratch replaces the single-pass
+// workspace (scan_workspace_bytes covers both).
+bool scan_tail_eligible(const ScanLaunch& L);
+size_t scan_tail_workspace_bytes(int64_t n_ops, int32_t n_vars);
+int launch_scan_tail(const ScanLaunch& L, cudaStream_t s);
 // enable >= 0: switch phase counting on/off and zero the counters; host_out
 // (nullable): copy the 8 counters (cycles summed over CTAs).
 int scan_phase_profile(int enable, unsigned long long* host_out);

@@ -189,3 +189,16 @@ def test_initial_statuses_every_bitmap_mode(amc, oracle_mod, monkeypatch, fb, gr
     init = rng.integers(0, 5, 64).astype(np.uint8)
     assert (init == 4).any()
     assert_same(*run_both(amc, oracle_mod, ks, var, 64, init))
+
+
+@pytest.mark.parametrize("group", ["1", "-2", "16"])
+def test_shared_window_with_l1_bitmap(amc, oracle_mod, monkeypatch, group):
+    # stuck bits of the first 4,096 variables in shared memory, the others
+    # read through L1: both lookups in one warp, stale copies only conservative
+    monkeypatch.setenv("AMC_SCAN_FB_BITS", "-4096")
+    monkeypatch.setenv("AMC_SCAN_GROUP", group)
+    rng = np.random.default_rng(37)
+    ks, var = workloads.trace_random(rng, 700_001, 1 << 16, zipf_s=1.05)
+    assert_same(*run_both(amc, oracle_mod, ks, var, 1 << 16))
+    init = rng.integers(0, 5, 1 << 16).astype(np.uint8)
+    assert_same(*run_both(amc, oracle_mod, ks, var, 1 << 16, init))

@@ -1,0 +1,93 @@
+"""GPU parity of the epoch path for the tail of long traces (the first part
+checked as usual, then per epoch: stream filter on the stuck bitmap, the
+compacted candidates checked from the epoch's start statuses, scatter).
+
+Traces over 16,385 to 2^20 variables take it from 2^29 ops on (first part
+n / 16 ops, epochs of n / 4);
+AMC_SCAN_TAIL="s,e" forces a first part of 2^s ops and epochs of 2^e ops at
+any length, so that many epochs, ragged last epochs, epochs with almost every
+op a candidate, initial statuses and bad input all run.  Bit-exact against the
+oracle on every output."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amc():
+    import paper_1910_11110_gb300 as m
+    m.build()
+    return m
+
+
+def check(amc, oracle_mod, ks, var, n_vars, init=None):
+    exp = oracle_mod.check_trace(ks, var, n_vars, init)
+    dev = torch.device("cuda")
+    out = amc.check_trace(torch.from_numpy(ks).to(dev), torch.from_numpy(var).to(dev), n_vars,
+                          None if init is None else torch.from_numpy(init).to(dev))
+    assert amc.sync_status() == 0
+    got = (out["step_status"].cpu().numpy(), out["final_status"].cpu().numpy(),
+           out["var_first_fault"].cpu().numpy(), int(out["first_fault"].cpu()[0]))
+    for name, e, g in zip(("step_status", "final_status", "var_first_fault"), exp[:3], got[:3]):
+        assert np.array_equal(e, g), (name, np.nonzero(e != g)[0][:10])
+    assert exp[3] == got[3]
+
+
+@pytest.mark.parametrize("shape", ["18,18", "16,20", "20,16"])
+def test_zipf_epochs(amc, oracle_mod, monkeypatch, shape):
+    monkeypatch.setenv("AMC_SCAN_TAIL", shape)
+    ks, var = workloads.trace_zipf(3 * (1 << 20) + 5, 1 << 20, seed=90, device="cuda")
+    check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
+
+
+def test_initial_statuses(amc, oracle_mod, monkeypatch):
+    monkeypatch.setenv("AMC_SCAN_TAIL", "14,14")
+    rng = np.random.default_rng(91)
+    ks, var = workloads.trace_random(rng, 300_007, 40_000, zipf_s=1.05)
+    init = rng.integers(0, 5, 40_000).astype(np.uint8)
+    check(amc, oracle_mod, ks, var, 40_000, init)
+
+
+def test_every_op_a_candidate(amc, oracle_mod, monkeypatch):
+    # writes and Noops only: nothing faults, every op of every epoch is checked
+    monkeypatch.setenv("AMC_SCAN_TAIL", "15,15")
+    rng = np.random.default_rng(92)
+    ks, var = workloads.trace_random(rng, 200_003, 20_000, p=[0.0, 0.7, 0.0, 0.0, 0.3])
+    check(amc, oracle_mod, ks, var, 20_000)
+
+
+def test_faults_late_and_uniform_ids(amc, oracle_mod, monkeypatch):
+    monkeypatch.setenv("AMC_SCAN_TAIL", "13,14")
+    rng = np.random.default_rng(93)
+    ks, var = workloads.trace_random(rng, 150_001, 17_000, p=[0.01, 0.6, 0.04, 0.04, 0.31])
+    check(amc, oracle_mod, ks, var, 17_000)
+
+
+def test_bad_input_in_the_tail(amc, monkeypatch):
+    monkeypatch.setenv("AMC_SCAN_TAIL", "13,13")
+    dev = torch.device("cuda")
+    n, nv = 50_000, 20_000
+    ks = torch.zeros(n, dtype=torch.uint8, device=dev)
+    var = torch.arange(n, dtype=torch.int32, device=dev) % nv
+    var[40_000] = nv + 3                           # id out of range, in an epoch
+    amc.check_trace(ks, var, nv)
+    assert amc.sync_status() == amc.E_RANGE
+    var[40_000] = 5
+    ks[30_001] = 0x21                              # malformed byte
+    amc.check_trace(ks, var, nv)
+    assert amc.sync_status() == amc.E_INVALID
+    ks[30_001] = 6                                 # GT in a plain check
+    amc.check_trace(ks, var, nv)
+    assert amc.sync_status() == amc.E_INVALID
+    assert amc.sync_status() == 0
+
+
+def test_default_split_at_2p29(amc, oracle_mod):
+    # 2^29 ops over 2^20 variables: the default first part (2^25 ops) and
+    # epochs of 2^27 ops, against the oracle on every output
+    ks, var = workloads.trace_zipf(1 << 29, 1 << 20, seed=94, device="cuda")
+    check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
