@@ -29,12 +29,13 @@ namespace amc {
 namespace {
 
 constexpr int TF_THREADS = 1024;          // filter CTA: one per SM (the bitmap fills shared memory)
-constexpr int TF_CHUNK = 4096;            // ops per warp chunk (candidate slots per chunk)
+constexpr int TF_CHUNK = 4096;            // ops per warp chunk
+constexpr int TF_SLOTS = 512;             // candidate slots per chunk (more: the epoch falls back)
+constexpr int CAND_DIV = 8;               // candidate capacity: epoch ops / 8 (more: falls back)
 constexpr int TF_PER = 16;                // ops per lane and step
 constexpr int TAIL_MIN_VARS = 16385;      // fewer variables take the reduce / carry / apply path
 constexpr int TAIL_MAX_VARS = 1 << 20;    // bitmap of 128 KB in shared memory
-constexpr int DEFAULT_SPLIT_SHIFT = 4;    // S = n_ops / 16
-constexpr int DEFAULT_EPOCH_SHIFT = 2;    // E = n_ops / 4 (scratch about 17 B per epoch op)
+constexpr int DEFAULT_SPLIT_SHIFT = 4;    // S = n_ops / 16, then one epoch
 constexpr int64_t DEFAULT_MIN_OPS = (int64_t)1 << 29;
 
 struct TailShape {
@@ -53,27 +54,39 @@ bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh)
         if (sscanf(e, "%d,%d", &a, &b) == 2 && a >= 12 && a < 31 && b >= 12 && b < 31) {
             sh.S = (int64_t)1 << a;
             sh.E = (int64_t)1 << b;
-            return n_ops > sh.S;
+            if (n_ops <= sh.S) return false;
+            if (sh.E > n_ops - sh.S) sh.E = n_ops - sh.S;
+            return true;
         }
     }
     if (n_ops < DEFAULT_MIN_OPS) return false;
     sh.S = (n_ops >> DEFAULT_SPLIT_SHIFT) / TF_CHUNK * TF_CHUNK;
-    sh.E = (n_ops >> DEFAULT_EPOCH_SHIFT) / TF_CHUNK * TF_CHUNK;
+    sh.E = n_ops - sh.S;
     return true;
 }
 
 struct TailLayout {
-    size_t part1 = 0;     // workspace of the first part
-    size_t st0, st1, bm, cnt, off, ncand, sks, svar, spos, cks, cvar, cpos, cstep, cvff, cff, cws, total;
+    int64_t C = 0;        // candidate capacity per epoch
+    size_t st0, st1, bm, cnt, off, ncand, ovf, cvff, cff, fvff, fff;
+    size_t region;        // shared region: first part, then candidates, then the fallback scan
+    size_t cks, cvar, cpos, cstep, sks, svar, spos, cws;     // offsets inside the region
+    size_t total;
 };
 
+// Scratch: a few per-variable arrays, then one region used in turn by the
+// first part's scan, by an epoch's candidates (chunk slots, the compacted
+// trace, its scan), and by the epoch's fallback scan over all its ops (taken
+// when the candidates overflow their slots).  The region is as large as the
+// largest of the three, about 5 bytes per op of the longer of S and E.
 TailLayout tail_layout(const TailShape& sh, int32_t n_vars)
 {
     TailLayout t;
     const size_t E = (size_t)sh.E;
     const size_t n_chunks = (E + TF_CHUNK - 1) / TF_CHUNK;
-    size_t o = scan_workspace_bytes(sh.S, n_vars);
-    t.part1 = o;
+    size_t C = (E + CAND_DIV - 1) / CAND_DIV;
+    C = (C + TF_CHUNK - 1) / TF_CHUNK * TF_CHUNK;
+    t.C = (int64_t)C;
+    size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o += align_up(b, 256); return at; };
     t.st0 = take((size_t)n_vars);
     t.st1 = take((size_t)n_vars);
@@ -81,22 +94,34 @@ TailLayout tail_layout(const TailShape& sh, int32_t n_vars)
     t.cnt = take(4 * n_chunks);
     t.off = take(4 * n_chunks);
     t.ncand = take(8);
-    t.cks = take(E);
-    t.cvar = take(4 * E);
-    t.cpos = take(4 * E);
-    t.cstep = take(E);
+    t.ovf = take(4);
     t.cvff = take(4 * (size_t)n_vars);
     t.cff = take(8);
-    // one region, used in turn by the filter's chunk slots (until the gather)
-    // and by the candidates' scan
-    t.cws = o;
-    t.sks = o;
-    t.svar = t.sks + align_up(E, 256);
-    t.spos = t.svar + align_up(4 * E, 256);
-    const size_t slots = align_up(E, 256) + align_up(4 * E, 256) + align_up(2 * E, 256);
-    const size_t scan = scan_workspace_bytes(sh.E, n_vars, false);
-    o += slots > scan ? slots : scan;
-    t.total = o;
+    t.fvff = take(4 * (size_t)n_vars);
+    t.fff = take(8);
+    t.region = o;
+    // candidates: compacted trace and statuses, then the slots (until the
+    // gather) sharing their space with the candidates' scan
+    size_t r = 0;
+    auto rtake = [&](size_t b) { const size_t at = r; r += align_up(b, 256); return at; };
+    t.cks = rtake(C);
+    t.cvar = rtake(4 * C);
+    t.cpos = rtake(4 * C);
+    t.cstep = rtake(C);
+    t.cws = r;
+    t.sks = r;
+    t.svar = t.sks + align_up(n_chunks * TF_SLOTS, 256);
+    t.spos = t.svar + align_up(4 * n_chunks * TF_SLOTS, 256);
+    const size_t slots = align_up(n_chunks * TF_SLOTS, 256) + align_up(4 * n_chunks * TF_SLOTS, 256) +
+                         align_up(2 * n_chunks * TF_SLOTS, 256);
+    const size_t cscan = scan_workspace_bytes((int64_t)C, n_vars, false);
+    r += slots > cscan ? slots : cscan;
+    size_t reg = r;
+    const size_t part1 = scan_workspace_bytes(sh.S, n_vars);
+    const size_t fallback = scan_workspace_bytes(sh.E, n_vars, false);
+    if (part1 > reg) reg = part1;
+    if (fallback > reg) reg = fallback;
+    t.total = o + reg;
     return t;
 }
 
@@ -118,10 +143,11 @@ struct FilterParams {
     const uint32_t* bm;         // stuck bitmap at the epoch's start
     int bm_words;
     uint8_t* step;              // the epoch's outputs
-    uint8_t* sks;               // candidate slots: TF_CHUNK per chunk
+    uint8_t* sks;               // candidate slots: TF_SLOTS per chunk
     int32_t* svar;
     uint16_t* spos;             // position within the chunk
     uint32_t* cnt;              // candidates per chunk
+    int* ovf;                   // set when a chunk has more candidates than slots
     int* err;
     int bulk_ok;
 };
@@ -144,6 +170,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
         const int64_t c0 = c * TF_CHUNK;
         const int cn = (int)min((int64_t)TF_CHUNK, q.n - c0);
         int wcount = 0;
+        bool full = false;                                   // slots exhausted (warp-uniform)
         for (int s0 = 0; s0 < cn; s0 += 32 * TF_PER) {
             const int off = s0 + lane * TF_PER;              // offset in the chunk
             const int64_t i0 = c0 + off;                     // offset in the epoch
@@ -249,7 +276,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
                 }
             }
             const int cl = __popc(liveMask);
-            if (!__any_sync(0xffffffffu, cl != 0)) continue;
+            if (full || !__any_sync(0xffffffffu, cl != 0)) continue;
             int pre = 0, wtot = 0;
 #pragma unroll
             for (int bit = 0; bit < 6; ++bit) {                 // counts 0..32
@@ -257,7 +284,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
                 pre += __popc(bal & lt) << bit;
                 wtot += __popc(bal) << bit;
             }
-            int idx = (int)(c0 + wcount + pre);      // < c0 + cn: at most every op of the chunk
+            if (wcount + wtot > TF_SLOTS) {
+                // more candidates than slots: the epoch is rechecked whole
+                if (lane == 0) atomicExch(q.ovf, 1);
+                full = true;
+                continue;
+            }
+            int64_t idx = c * TF_SLOTS + wcount + pre;
 #pragma unroll
             for (int u = 0; u < TF_PER; ++u) {
                 if (liveMask & (1u << u)) {
@@ -275,7 +308,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
 
 // Exclusive offsets of the chunks' candidate counts and their total (one CTA).
 __global__ void __launch_bounds__(1024) tail_offsets_kernel(const uint32_t* __restrict__ cnt, int n_chunks,
-                                                            uint32_t* __restrict__ off, int64_t* __restrict__ n_cand)
+                                                            uint32_t* __restrict__ off, int64_t* __restrict__ n_cand,
+                                                            int64_t cap, int* ovf)
 {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
@@ -309,19 +343,24 @@ __global__ void __launch_bounds__(1024) tail_offsets_kernel(const uint32_t* __re
         if (tid == 0) carry += wsum[31];
         __syncthreads();
     }
-    if (tid == 0) *n_cand = (int64_t)carry;
+    if (tid == 0) {
+        // more candidates than the compacted trace holds: the epoch is rechecked whole
+        if ((int64_t)carry > cap) *ovf = 1;
+        *n_cand = *ovf ? 0 : (int64_t)carry;
+    }
 }
 
 // Chunk slots -> dense candidate trace (one CTA of 128 threads per chunk).
 __global__ void tail_gather_kernel(const uint8_t* __restrict__ sks, const int32_t* __restrict__ svar,
                                    const uint16_t* __restrict__ spos, const uint32_t* __restrict__ cnt,
                                    const uint32_t* __restrict__ off, uint8_t* __restrict__ cks,
-                                   int32_t* __restrict__ cvar, uint32_t* __restrict__ cpos)
+                                   int32_t* __restrict__ cvar, uint32_t* __restrict__ cpos, const int* ovf)
 {
+    if (*ovf) return;
     const int64_t c = blockIdx.x;
     const uint32_t n = cnt[c], o = off[c];
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const int64_t src = c * TF_CHUNK + j;
+        const int64_t src = c * TF_SLOTS + j;
         cks[o + j] = sks[src];
         cvar[o + j] = svar[src];
         cpos[o + j] = (uint32_t)(c * TF_CHUNK) + spos[src];
@@ -334,8 +373,10 @@ __global__ void tail_gather_kernel(const uint8_t* __restrict__ sks, const int32_
 __global__ void tail_scatter_kernel(const uint8_t* __restrict__ cstep, const uint32_t* __restrict__ cpos,
                                     const int64_t* __restrict__ n_cand, uint8_t* __restrict__ step,
                                     const int32_t* __restrict__ cvff, int32_t n_vars, int32_t* __restrict__ vff,
-                                    const int64_t* __restrict__ cff, int64_t* __restrict__ ff, int64_t epoch0)
+                                    const int64_t* __restrict__ cff, int64_t* __restrict__ ff, int64_t epoch0,
+                                    const int* ovf)
 {
+    if (*ovf) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nc = *n_cand;
@@ -352,7 +393,7 @@ __global__ void tail_scatter_kernel(const uint8_t* __restrict__ cstep, const uin
 bool scan_tail_eligible(const ScanLaunch& L)
 {
     TailShape sh;
-    return L.dense != 0 && !L.n_dev && !L.guard && !L.pre_mode &&
+    return L.dense != 0 && !L.n_dev && !L.gate && !L.guard && !L.pre_mode &&
            tail_shape(L.n_ops, L.n_vars, false, sh);
 }
 
@@ -374,15 +415,19 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     uint32_t* cnt = reinterpret_cast<uint32_t*>(w + lay.cnt);
     uint32_t* off = reinterpret_cast<uint32_t*>(w + lay.off);
     int64_t* ncand = reinterpret_cast<int64_t*>(w + lay.ncand);
-    uint8_t* sks = w + lay.sks;
-    int32_t* svar = reinterpret_cast<int32_t*>(w + lay.svar);
-    uint16_t* spos = reinterpret_cast<uint16_t*>(w + lay.spos);
-    uint8_t* cks = w + lay.cks;
-    int32_t* cvar = reinterpret_cast<int32_t*>(w + lay.cvar);
-    uint32_t* cpos = reinterpret_cast<uint32_t*>(w + lay.cpos);
-    uint8_t* cstep = w + lay.cstep;
+    int* ovf = reinterpret_cast<int*>(w + lay.ovf);
     int32_t* cvff = reinterpret_cast<int32_t*>(w + lay.cvff);
     int64_t* cff = reinterpret_cast<int64_t*>(w + lay.cff);
+    int32_t* fvff = reinterpret_cast<int32_t*>(w + lay.fvff);
+    int64_t* fff = reinterpret_cast<int64_t*>(w + lay.fff);
+    uint8_t* reg = w + lay.region;
+    uint8_t* sks = reg + lay.sks;
+    int32_t* svar = reinterpret_cast<int32_t*>(reg + lay.svar);
+    uint16_t* spos = reinterpret_cast<uint16_t*>(reg + lay.spos);
+    uint8_t* cks = reg + lay.cks;
+    int32_t* cvar = reinterpret_cast<int32_t*>(reg + lay.cvar);
+    uint32_t* cpos = reinterpret_cast<uint32_t*>(reg + lay.cpos);
+    uint8_t* cstep = reg + lay.cstep;
 
     int dev = 0, n_sm = 0, max_optin = 0;
     cudaGetDevice(&dev);
@@ -403,6 +448,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     ScanLaunch A = L;
     A.n_ops = sh.S;
     A.final_status = st[0];
+    A.workspace = reg;
     A.profile = L.profile & 1;
     int rc = launch_scan_trace(A, s);
     if (rc) return rc;
@@ -411,6 +457,8 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     for (int64_t e0 = sh.S; e0 < L.n_ops; e0 += sh.E) {
         const int64_t n = L.n_ops - e0 < sh.E ? L.n_ops - e0 : sh.E;
         const bool last = e0 + n >= L.n_ops;
+        uint8_t* fin = (last && L.final_status) ? L.final_status : st[cur ^ 1];
+        if (cudaMemsetAsync(ovf, 0, sizeof(int), s) != cudaSuccess) return AMC_E_CUDA;
         tail_bitmap_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(st[cur], L.n_vars, bm);
         FilterParams q;
         q.kind_side = L.kind_side + e0;
@@ -425,34 +473,58 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         q.svar = svar;
         q.spos = spos;
         q.cnt = cnt;
+        q.ovf = ovf;
         q.err = L.err;
         q.bulk_ok = ((uintptr_t)q.kind_side % 16 == 0) && ((uintptr_t)q.var % 16 == 0) &&
                     ((uintptr_t)q.step % 16 == 0);
         const int n_chunks = (int)((n + TF_CHUNK - 1) / TF_CHUNK);
         const int fgrid = (int)min((int64_t)n_sm, ((int64_t)n_chunks + TF_THREADS / 32 - 1) / (TF_THREADS / 32));
         tail_filter_kernel<<<fgrid, TF_THREADS, fsmem, s>>>(q);
-        tail_offsets_kernel<<<1, 1024, 0, s>>>(cnt, n_chunks, off, ncand);
-        tail_gather_kernel<<<n_chunks, 128, 0, s>>>(sks, svar, spos, cnt, off, cks, cvar, cpos);
+        tail_offsets_kernel<<<1, 1024, 0, s>>>(cnt, n_chunks, off, ncand, lay.C, ovf);
+        tail_gather_kernel<<<n_chunks, 128, 0, s>>>(sks, svar, spos, cnt, off, cks, cvar, cpos, ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-        // the candidates: a trace of at most n ops (count on the device)
+        // the candidates: a trace of at most C ops (count on the device); gated
+        // off when they overflowed
         ScanLaunch C = L;
         C.kind_side = cks;
         C.var = cvar;
-        C.n_ops = n;
+        C.n_ops = lay.C;
         C.n_dev = ncand;
+        C.gate = ovf;
+        C.gate_on = 0;
         C.init = st[cur];
         C.step = cstep;
-        C.final_status = (last && L.final_status) ? L.final_status : st[cur ^ 1];
+        C.final_status = fin;
         C.vff = cvff;
         C.first_fault = cff;
-        C.workspace = w + lay.cws;
+        C.workspace = reg + lay.cws;
         C.dense = 0;
         C.profile = 0;
         rc = launch_scan_trace(C, s);
         if (rc) return rc;
         tail_scatter_kernel<<<n_sm * 4, 256, 0, s>>>(cstep, cpos, ncand, L.step + e0, cvff, L.n_vars, L.vff, cff,
-                                                    L.first_fault, e0);
+                                                    L.first_fault, e0, ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        // fallback, gated on by an overflow: the single-pass scan over all the
+        // epoch's ops from its start statuses
+        ScanLaunch F = L;
+        F.kind_side = L.kind_side + e0;
+        F.var = L.var + e0;
+        F.n_ops = n;
+        F.gate = ovf;
+        F.gate_on = 1;
+        F.init = st[cur];
+        F.step = L.step + e0;
+        F.final_status = fin;
+        F.vff = fvff;
+        F.first_fault = fff;
+        F.workspace = reg;
+        F.dense = 0;
+        F.profile = 0;
+        rc = launch_scan_trace(F, s);
+        if (rc) return rc;
+        rc = launch_merge_faults(L.vff, fvff, L.n_vars, L.first_fault, fff, e0, s);
+        if (rc) return rc;
         cur ^= 1;
     }
     if (L.profile & 2) profile_end(s);

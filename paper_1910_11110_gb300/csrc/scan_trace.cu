@@ -814,7 +814,38 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
         const bool vec = n == PER && p.bulk_ok;
         uint32_t kw[PER / 4];
         int32_t va[PER];
+        uint32_t outw[PER / 4], melw[PER / 4];
+        uint32_t liveMask = 0;
+        // element of a live op (GT resolved from its guard, malformed bytes as identity)
+        auto live_elem = [&](const uint32_t ks, const uint32_t uv, const int u) -> uint32_t {
+            uint32_t m = S.elem_of[ks];
+            if (m == ELEM_GT) {
+                const int64_t gi = base + u;
+                uint32_t nks = 0xFF;
+                int32_t nv = (int32_t)uv;
+                if (gi + 1 < S.nOps) {
+                    nks = p.kind_side[gi + 1];
+                    nv = p.var[gi + 1];
+                }
+                const bool gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
+                if (!gt_ok || p.pre_mode) {
+                    m = ID;
+                } else if (!p.guard) {
+                    raise_error(p.err, AMC_E_INVALID);
+                    m = ID;
+                } else {
+                    const uint32_t gs = p.guard[gi + 1];
+                    const int side = ks >> 4;
+                    const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
+                    m = valid ? ID : p.tab.pull_of_side[side];
+                }
+            } else if (m == ELEM_BAD) {
+                m = ID;
+            }
+            return m;
+        };
         if (vec) {
+            // full step: four op bytes per 32-bit word are checked at once
             const uint4 kk = __ldcs(reinterpret_cast<const uint4*>(p.kind_side + base));
             kw[0] = kk.x;
             kw[1] = kk.y;
@@ -828,9 +859,65 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                 va[4 * q + 2] = v4.z;
                 va[4 * q + 3] = v4.w;
             }
+            uint32_t badk = 0, gtw = 0, badv = 0;
+#pragma unroll
+            for (int q = 0; q < PER / 4; ++q) {
+                // a valid byte has bits 3 and 5-7 clear (kinds 0..7, side bit 4)
+                badk |= kw[q] & 0xE8E8E8E8u;
+                // bytes whose kind is GT (6): zero bytes of (kind ^ 6)
+                const uint32_t x = (kw[q] & 0x0F0F0F0Fu) ^ 0x06060606u;
+                gtw |= (x - 0x01010101u) & ~x & 0x80808080u;
+                outw[q] = melw[q] = 0;
+            }
+            uint32_t fw[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const uint32_t v = (uint32_t)va[u];
+                const uint32_t uv = v < (uint32_t)p.n_vars ? v : 0u;
+                badv |= v >= (uint32_t)p.n_vars;
+                fw[u] = uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : (p.fb_mode >= 2 ? __ldg(fbl1 + (uv >> 5)) : 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const uint32_t v = (uint32_t)va[u];
+                const uint32_t uv = v < (uint32_t)p.n_vars ? v : 0u;
+                const uint32_t stuck = (fw[u] >> (uv & 31)) & 1u;
+                liveMask |= (stuck ^ 1u) << u;
+                outw[u >> 2] |= stuck << (8 * (u & 3) + 2);      // F = 4 where stuck; live: set later
+            }
+            if (badk) raise_error(p.err, AMC_E_INVALID);
+            if (badv) raise_error(p.err, AMC_E_RANGE);
+            if (gtw) {
+                // GT must be followed by EN of the same side on another variable
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
+                    if ((ks & 15u) != AMC_K_GT) continue;
+                    const uint32_t uv = (uint32_t)va[u] < (uint32_t)p.n_vars ? (uint32_t)va[u] : 0u;
+                    const int64_t gi = base + u;
+                    uint32_t nks = 0xFF;
+                    int32_t nv = (int32_t)uv;
+                    if (gi + 1 < S.nOps) {
+                        nks = p.kind_side[gi + 1];
+                        nv = p.var[gi + 1];
+                    }
+                    if (!((nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv))
+                        raise_error(p.err, AMC_E_INVALID);
+                }
+            }
+            if (liveMask) {
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    if (!(liveMask & (1u << u))) continue;
+                    const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
+                    const uint32_t uv = (uint32_t)va[u] < (uint32_t)p.n_vars ? (uint32_t)va[u] : 0u;
+                    melw[u >> 2] |= live_elem(ks, uv, u) << (8 * (u & 3));
+                }
+            }
+            __stcs(reinterpret_cast<uint4*>(p.step + base), make_uint4(outw[0], outw[1], outw[2], outw[3]));
         } else {
 #pragma unroll
-            for (int q = 0; q < PER / 4; ++q) kw[q] = 0;
+            for (int q = 0; q < PER / 4; ++q) kw[q] = outw[q] = melw[q] = 0;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 va[u] = 0;
@@ -839,31 +926,17 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                     va[u] = p.var[base + u];
                 }
             }
-        }
-        uint32_t fw[PER];
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const uint32_t uv = (va[u] < 0 || va[u] >= p.n_vars) ? 0u : (uint32_t)va[u];
-            fw[u] = uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : (p.fb_mode >= 2 ? __ldg(fbl1 + (uv >> 5)) : 0u);
-        }
-        uint32_t outw[PER / 4], melw[PER / 4];
-        uint32_t liveMask = 0;
-#pragma unroll
-        for (int q = 0; q < PER / 4; ++q) outw[q] = melw[q] = 0;
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
-            uint32_t o = ST_F;
-            if (u < n) {
+            for (int u = 0; u < PER; ++u) {
+                if (u >= n) continue;
+                const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
                 if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(p.err, AMC_E_INVALID);
                 uint32_t uv = (uint32_t)va[u];
                 if (va[u] < 0 || va[u] >= p.n_vars) {
                     raise_error(p.err, AMC_E_RANGE);
                     uv = 0;
                 }
-                bool gt_ok = true;
                 if ((ks & 15u) == AMC_K_GT) {
-                    // GT must be followed by EN of the same side on another variable
                     const int64_t gi = base + u;
                     uint32_t nks = 0xFF;
                     int32_t nv = (int32_t)uv;
@@ -871,39 +944,19 @@ __device__ __noinline__ bool process_group(const ScanParams& p, ScanSmem<KeyT, T
                         nks = p.kind_side[gi + 1];
                         nv = p.var[gi + 1];
                     }
-                    gt_ok = (nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv;
-                    if (!gt_ok) raise_error(p.err, AMC_E_INVALID);
+                    if (!((nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv))
+                        raise_error(p.err, AMC_E_INVALID);
                 }
-                if (!((fw[u] >> (uv & 31)) & 1u)) {
-                    uint32_t m = S.elem_of[ks];
-                    if (m == ELEM_GT) {
-                        if (!gt_ok || p.pre_mode) {
-                            m = ID;
-                        } else if (!p.guard) {
-                            raise_error(p.err, AMC_E_INVALID);
-                            m = ID;
-                        } else {
-                            const uint32_t gs = p.guard[base + u + 1];
-                            const int side = ks >> 4;
-                            const bool valid = gs != ST_F && (gs & (side == 0 ? 1u : 2u));
-                            m = valid ? ID : p.tab.pull_of_side[side];
-                        }
-                    } else if (m == ELEM_BAD) {
-                        m = ID;
-                    }
-                    melw[u >> 2] |= m << (8 * (u & 3));
+                const uint32_t fwu =
+                    uv < (uint32_t)p.fbw * 32u ? fsm[uv >> 5] : (p.fb_mode >= 2 ? __ldg(fbl1 + (uv >> 5)) : 0u);
+                uint32_t o = ST_F;
+                if (!((fwu >> (uv & 31)) & 1u)) {
+                    melw[u >> 2] |= live_elem(ks, uv, u) << (8 * (u & 3));
                     liveMask |= 1u << u;
                     o = 0;                       // written once the run's entry is known
                 }
+                p.step[base + u] = (uint8_t)o;
             }
-            outw[u >> 2] |= o << (8 * (u & 3));
-        }
-        if (vec) {
-            __stcs(reinterpret_cast<uint4*>(p.step + base), make_uint4(outw[0], outw[1], outw[2], outw[3]));
-        } else {
-#pragma unroll
-            for (int u = 0; u < PER; ++u)
-                if (u < n) p.step[base + u] = (uint8_t)(outw[u >> 2] >> (8 * (u & 3)));
         }
         // live-op prefix within the warp (counts are 0..16: five bits)
         const int c = __popc(liveMask);
@@ -1455,6 +1508,7 @@ __global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const S
             const int64_t d = *p.n_dev;
             n = d < 0 ? 0 : (d < n ? d : n);
         }
+        if (p.gate && ((*p.gate != 0) != (p.gate_on != 0))) n = 0;    // gated off: no work
         S.nOps = n;
         S.nTiles = (int)((n + T - 1) / T);
     }
@@ -1536,10 +1590,12 @@ __global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const S
 
 __global__ void finalize_trace_kernel(int32_t* __restrict__ vff, const uint32_t* __restrict__ head,
                                       const uint8_t* __restrict__ node_status, const uint8_t* __restrict__ init,
-                                      int32_t n_vars, uint8_t* __restrict__ final_status)
+                                      int32_t n_vars, uint8_t* __restrict__ final_status, const int* gate,
+                                      int gate_on)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_vars) return;
+    if (gate && ((*gate != 0) != (gate_on != 0))) return;     // gated off: the other launch writes
     const uint32_t ff = (uint32_t)vff[v];
     uint8_t f;
     if (ff != 0xFFFFFFFFu) {
@@ -1658,6 +1714,8 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.var = L.var;
     p.n_ops = L.n_ops;
     p.n_dev = L.n_dev;
+    p.gate = L.gate;
+    p.gate_on = L.gate_on;
     p.n_vars = L.n_vars;
     p.init = L.init;
     p.step = L.step;
@@ -1697,8 +1755,9 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     }
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
-    if (L.dense != 0 && !L.n_dev && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
-    if (L.dense != 0 && !L.n_dev && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr))
+    const bool plain = !L.n_dev && !L.gate;
+    if (L.dense != 0 && plain && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
+    if (L.dense != 0 && plain && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr))
         return launch_scan_prefix(L, w + 256, s);
     // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
     int kb = 1;
@@ -1735,7 +1794,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
         const int nb = (int)((L.n_vars + 255) / 256);
         if (nb > 0) {
             finalize_trace_kernel<<<nb, 256, 0, s>>>(L.vff, p.head, p.node_status, L.init, L.n_vars,
-                                                     L.final_status);
+                                                     L.final_status, L.gate, L.gate_on);
             if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         }
     }

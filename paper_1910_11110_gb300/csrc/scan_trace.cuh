@@ -10,6 +10,8 @@ struct ScanParams {
     const int32_t* var;
     int64_t n_ops;              // ops (with n_dev: the capacity of the arrays)
     const int64_t* n_dev;       // nullable: device word with the op count (clamped to n_ops)
+    const int* gate;            // nullable: the launch works only while (*gate != 0) == gate_on
+    int gate_on;
     int32_t n_vars;
     const uint8_t* init;        // nullable: all (V,I)
     uint8_t* step;              // [n_ops] post-statuses (pre-statuses in pre_mode)
@@ -61,6 +63,8 @@ struct ScanLaunch {
     int dense = -1;                     // reduce / carry / apply path: -1 when eligible, 0 never
     const int64_t* n_dev = nullptr;     // device op count, read by the kernel (n_ops = capacity);
                                         // single-pass kernel only, not with a guard
+    const int* gate = nullptr;          // device flag: the scan and its final-status pass do
+    int gate_on = 0;                    // nothing unless (*gate != 0) == gate_on (single-pass only)
 };
 
 int scan_tile_size();

@@ -91,3 +91,18 @@ def test_default_split_at_2p29(amc, oracle_mod):
     # epochs of 2^27 ops, against the oracle on every output
     ks, var = workloads.trace_zipf(1 << 29, 1 << 20, seed=94, device="cuda")
     check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
+
+
+def test_overflow_falls_back_in_one_epoch(amc, oracle_mod, monkeypatch):
+    # epochs of 2^16 ops after a 2^15-op first part; the third epoch holds a
+    # burst of writes on variables never touched before (none faults there),
+    # more candidates than its chunks' slots: that epoch is rechecked whole,
+    # the others take the compacted candidates
+    monkeypatch.setenv("AMC_SCAN_TAIL", "15,16")
+    rng = np.random.default_rng(95)
+    nv = 30_000
+    ks, var = workloads.trace_random(rng, 300_000, 20_000, zipf_s=1.05)
+    lo = (1 << 15) + 2 * (1 << 16) + 1000
+    ks[lo:lo + 9000] = 0x01                          # CPU writes
+    var[lo:lo + 9000] = 20_000 + (np.arange(9000) % 10_000)
+    check(amc, oracle_mod, ks, var, nv)
