@@ -572,13 +572,20 @@ def trace_kernels(n_ops, n_vars):
     over at most 16,384 variables from 2^20 ops; over more (at most 2^20)
     variables from 2^24 ops that path on the first 2^22 ops, then the stuck
     bitmap seeded from its final statuses, the single-pass scan, the final
-    statuses and the first-fault merge; else the scan and the final statuses."""
+    statuses and the first-fault merge (7 kernels); from 2^29 ops that on the
+    first n/16 ops, then one epoch: stuck bitmap, stream filter, offsets,
+    gather, the candidates' scan (seed, scan, final statuses), scatter, the
+    gated fallback scan (seed, scan, final statuses) and the first-fault merge
+    (12 kernels); else the scan and the final statuses."""
     if os.environ.get("AMC_SCAN_DENSE", "") == "0":
         return "scan_trace_kernel", 2
     if n_vars <= 8192 and n_ops >= (1 << 20):
         return "warp reduce + carry + apply kernels", 5
     if n_vars <= 16384 and n_ops >= (1 << 20):
         return "dense reduce + carry + apply kernels", 3
+    if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 29) and os.environ.get("AMC_SCAN_TAIL", "") != "0":
+        return ("first n/16 ops: prefix (dense reduce + carry + apply) + scan_trace_kernel; rest: "
+                "tail_filter_kernel + compacted candidates' scan_trace_kernel + scatter"), 19
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
         return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7
     return "scan_trace_kernel", 2
@@ -588,13 +595,13 @@ def scan_traffic(n_ops, n_vars):
     """DRAM bytes (read + write) of one check -- every kernel of the timed span
     -- from the recorded ncu capture, or None when the capture was of another
     workload or the kernel sources have changed since (the record keeps the
-    SHA-256 of scan_trace.cu and scan_dense.cu)."""
+    SHA-256 of scan_trace.cu, scan_dense.cu and scan_tail.cu)."""
     import hashlib
     tr_path = os.path.join(ROOT, "profiles", "scan_trace_zipf_traffic.json")
     h = hashlib.sha256()
     try:
         rec = json.load(open(tr_path))
-        for f in ("scan_trace.cu", "scan_dense.cu"):
+        for f in ("scan_trace.cu", "scan_dense.cu", "scan_tail.cu"):
             h.update(open(os.path.join(ROOT, "paper_1910_11110_gb300", "csrc", f), "rb").read())
         sha = h.hexdigest()
     except Exception:

@@ -306,64 +306,109 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
     }
 }
 
-// Exclusive offsets of the chunks' candidate counts and their total (one CTA).
-__global__ void __launch_bounds__(1024) tail_offsets_kernel(const uint32_t* __restrict__ cnt, int n_chunks,
-                                                            uint32_t* __restrict__ off, int64_t* __restrict__ n_cand,
-                                                            int64_t cap, int* ovf)
+// Candidates per block of 1024 chunks.
+__global__ void __launch_bounds__(1024) tail_blocksum_kernel(const uint32_t* __restrict__ cnt, int n_chunks,
+                                                             uint32_t* __restrict__ bsum)
 {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0;
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    uint32_t x = i < n_chunks ? cnt[i] : 0u;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    if (lane == 0) ws[warp] = x;
     __syncthreads();
-    for (int b = 0; b < n_chunks; b += 1024) {
-        const int i = b + tid;
-        const uint32_t x = i < n_chunks ? cnt[i] : 0u;
-        uint32_t incl = x;
+    if (warp == 0) {
+        uint32_t y = ws[lane];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t w = wsum[lane];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
-                if (lane >= d) w += y;
-            }
-            wsum[lane] = w;                  // inclusive over warps
-        }
-        __syncthreads();
-        const uint32_t base = carry + (warp > 0 ? wsum[warp - 1] : 0u);
-        if (i < n_chunks) off[i] = base + incl - x;
-        __syncthreads();
-        if (tid == 0) carry += wsum[31];
-        __syncthreads();
-    }
-    if (tid == 0) {
-        // more candidates than the compacted trace holds: the epoch is rechecked whole
-        if ((int64_t)carry > cap) *ovf = 1;
-        *n_cand = *ovf ? 0 : (int64_t)carry;
+        for (int d = 16; d; d >>= 1) y += __shfl_xor_sync(0xffffffffu, y, d);
+        if (lane == 0) bsum[blockIdx.x] = y;
     }
 }
 
-// Chunk slots -> dense candidate trace (one CTA of 128 threads per chunk).
-__global__ void tail_gather_kernel(const uint8_t* __restrict__ sks, const int32_t* __restrict__ svar,
-                                   const uint16_t* __restrict__ spos, const uint32_t* __restrict__ cnt,
-                                   const uint32_t* __restrict__ off, uint8_t* __restrict__ cks,
-                                   int32_t* __restrict__ cvar, uint32_t* __restrict__ cpos, const int* ovf)
+// Chunk slots -> dense candidate trace, in position order.  Block b takes
+// chunks [1024 b, 1024 b + 1024): its base is the sum of the earlier blocks'
+// counts, its chunks' offsets a block scan; each warp copies 32 chunks.  Every
+// block also forms the grand total, so all agree on an overflow (more
+// candidates than the compacted trace holds, or a chunk with more than its
+// slots): then nothing is copied and the epoch's fallback scan runs instead.
+__global__ void __launch_bounds__(1024) tail_gather_kernel(const uint8_t* __restrict__ sks,
+                                                           const int32_t* __restrict__ svar,
+                                                           const uint16_t* __restrict__ spos,
+                                                           const uint32_t* __restrict__ cnt, int n_chunks,
+                                                           const uint32_t* __restrict__ bsum, int n_blocks,
+                                                           int64_t cap, uint8_t* __restrict__ cks,
+                                                           int32_t* __restrict__ cvar, uint32_t* __restrict__ cpos,
+                                                           int64_t* __restrict__ n_cand, int* ovf)
 {
-    if (*ovf) return;
-    const int64_t c = blockIdx.x;
-    const uint32_t n = cnt[c], o = off[c];
-    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const int64_t src = c * TF_SLOTS + j;
-        cks[o + j] = sks[src];
-        cvar[o + j] = svar[src];
-        cpos[o + j] = (uint32_t)(c * TF_CHUNK) + spos[src];
+    __shared__ unsigned long long rb[32], rt[32];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t offs[1024];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b = blockIdx.x;
+    unsigned long long before = 0, total = 0;
+    for (int j = tid; j < n_blocks; j += 1024) {
+        const unsigned long long v = bsum[j];
+        total += v;
+        if (j < b) before += v;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, d);
+        total += __shfl_xor_sync(0xffffffffu, total, d);
+    }
+    if (lane == 0) {
+        rb[warp] = before;
+        rt[warp] = total;
+    }
+    const int filter_ovf = *ovf;              // read before any block can write it
+    __syncthreads();
+    before = total = 0;
+#pragma unroll 4
+    for (int w = 0; w < 32; ++w) {
+        before += rb[w];
+        total += rt[w];
+    }
+    if (filter_ovf || total > (unsigned long long)cap) {
+        if (b == 0 && tid == 0) {
+            *ovf = 1;
+            *n_cand = 0;
+        }
+        return;
+    }
+    if (b == 0 && tid == 0) *n_cand = (int64_t)total;
+    const int i = b * 1024 + tid;
+    const uint32_t x = i < n_chunks ? cnt[i] : 0u;
+    uint32_t incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += y;
+        }
+        wsum[lane] = v;                      // inclusive over warps
+    }
+    __syncthreads();
+    offs[tid] = (uint32_t)before + (warp > 0 ? wsum[warp - 1] : 0u) + incl - x;
+    __syncthreads();
+    for (int k = warp * 32; k < warp * 32 + 32; ++k) {
+        const int c = b * 1024 + k;
+        if (c >= n_chunks) break;
+        const uint32_t nk = cnt[c], o = offs[k];
+        for (uint32_t j = lane; j < nk; j += 32) {
+            const int64_t src = (int64_t)c * TF_SLOTS + j;
+            cks[o + j] = sks[src];
+            cvar[o + j] = svar[src];
+            cpos[o + j] = (uint32_t)c * (uint32_t)TF_CHUNK + spos[src];
+        }
     }
 }
 
@@ -413,7 +458,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     uint8_t* st[2] = {w + lay.st0, w + lay.st1};
     uint32_t* bm = reinterpret_cast<uint32_t*>(w + lay.bm);
     uint32_t* cnt = reinterpret_cast<uint32_t*>(w + lay.cnt);
-    uint32_t* off = reinterpret_cast<uint32_t*>(w + lay.off);
+    uint32_t* bsum = reinterpret_cast<uint32_t*>(w + lay.off);    // candidates per 1024 chunks
     int64_t* ncand = reinterpret_cast<int64_t*>(w + lay.ncand);
     int* ovf = reinterpret_cast<int*>(w + lay.ovf);
     int32_t* cvff = reinterpret_cast<int32_t*>(w + lay.cvff);
@@ -480,8 +525,10 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         const int n_chunks = (int)((n + TF_CHUNK - 1) / TF_CHUNK);
         const int fgrid = (int)min((int64_t)n_sm, ((int64_t)n_chunks + TF_THREADS / 32 - 1) / (TF_THREADS / 32));
         tail_filter_kernel<<<fgrid, TF_THREADS, fsmem, s>>>(q);
-        tail_offsets_kernel<<<1, 1024, 0, s>>>(cnt, n_chunks, off, ncand, lay.C, ovf);
-        tail_gather_kernel<<<n_chunks, 128, 0, s>>>(sks, svar, spos, cnt, off, cks, cvar, cpos, ovf);
+        const int n_blocks = (n_chunks + 1023) / 1024;
+        tail_blocksum_kernel<<<n_blocks, 1024, 0, s>>>(cnt, n_chunks, bsum);
+        tail_gather_kernel<<<n_blocks, 1024, 0, s>>>(sks, svar, spos, cnt, n_chunks, bsum, n_blocks, lay.C, cks,
+                                                     cvar, cpos, ncand, ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // the candidates: a trace of at most C ops (count on the device); gated
         // off when they overflowed
