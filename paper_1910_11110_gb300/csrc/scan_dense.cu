@@ -772,7 +772,7 @@ size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)
         // prefix rows, then the suffix's first faults and the prefix's final statuses
         dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
         return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256) + align_up(4 * (size_t)n_vars, 256) + 256 +
-               align_up((size_t)n_vars, 256);
+               align_up((size_t)n_vars, 256) + 256;
     }
     if (n_vars < 1 || n_vars > DENSE_MAX_VARS || n_ops < 1) return 0;
     dense_shape(n_ops, DENSE_MAX_CHUNKS, n_tiles, n_chunks, tpc);
@@ -786,9 +786,41 @@ bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars, bool has_init)
     return prefix_ops(n_ops, n_vars, has_init) > 0;
 }
 
+namespace {
+
+// the prefix a launch takes: forced (prefix_log2) or by size
+int64_t launch_prefix_ops(const ScanLaunch& L)
+{
+    if (L.prefix_log2 > 0) {
+        if (L.n_vars <= DENSE_MAX_VARS || L.n_vars > (1 << 20) || L.prefix_log2 < 12 || L.prefix_log2 > 30) return 0;
+        const int64_t P = (int64_t)1 << L.prefix_log2;
+        return L.n_ops > P ? P : 0;
+    }
+    return prefix_ops(L.n_ops, L.n_vars, L.init != nullptr);
+}
+
+// *out = max(0, *n - P): the suffix's op count when the trace's count is on the device
+__global__ void suffix_count_kernel(const int64_t* n, int64_t P, int64_t* out)
+{
+    const int64_t r = *n - P;
+    *out = r > 0 ? r : 0;
+}
+
+}  // namespace
+
+size_t scan_prefix_workspace_bytes(int64_t P, int32_t n_vars)
+{
+    int n_tiles, n_chunks, tpc;
+    dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
+    return 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256) + align_up(4 * (size_t)n_vars, 256) + 256 +
+           align_up((size_t)n_vars, 256) + 256;
+}
+
+bool scan_forced_prefix(const ScanLaunch& L) { return launch_prefix_ops(L) > 0 && L.prefix_log2 > 0; }
+
 int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 {
-    const int64_t P = prefix_ops(L.n_ops, L.n_vars, L.init != nullptr);
+    const int64_t P = launch_prefix_ops(L);
     int n_tiles, n_chunks, tpc;
     dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
     uint8_t* w = ws + 2 * align_up((size_t)n_chunks * (size_t)L.n_vars, 256);
@@ -797,9 +829,13 @@ int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
     int64_t* ff_suffix = reinterpret_cast<int64_t*>(w);
     w += 256;
     uint8_t* pfinal = w;
+    w += align_up((size_t)L.n_vars, 256);
+    int64_t* n_suffix = reinterpret_cast<int64_t*>(w);      // with a device count: the suffix's
 
     ScanLaunch A = L;                       // the prefix: faults straight into the outputs
     A.n_ops = P;
+    A.n_dev = nullptr;                      // the first P ops are always there (padded by the caller)
+    A.gate = nullptr;
     A.final_status = pfinal;
     A.profile = L.profile & 1;
     int rc = launch_dense_range(A, PREFIX_CHUNKS, L.n_ops, ws, s);
@@ -814,7 +850,13 @@ int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
     B.vff = vff_suffix;
     B.first_fault = ff_suffix;
     B.dense = 0;
+    B.prefix_log2 = 0;
     B.profile = 0;
+    if (L.n_dev) {
+        suffix_count_kernel<<<1, 1, 0, s>>>(L.n_dev, P, n_suffix);
+        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        B.n_dev = n_suffix;
+    }
     rc = launch_scan_trace(B, s);
     if (rc) return rc;
     merge_faults_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(L.vff, vff_suffix, L.n_vars,

@@ -32,6 +32,7 @@ constexpr int TF_THREADS = 1024;          // filter CTA: one per SM (the bitmap 
 constexpr int TF_CHUNK = 4096;            // ops per warp chunk
 constexpr int TF_SLOTS = 512;             // candidate slots per chunk (more: the epoch falls back)
 constexpr int CAND_DIV = 8;               // candidate capacity: epoch ops / 8 (more: falls back)
+constexpr int CAND_PREFIX_LOG2 = 21;      // the candidates' first 2^21 ops take the reduce / carry / apply path
 constexpr int TF_PER = 16;                // ops per lane and step
 constexpr int TAIL_MIN_VARS = 16385;      // fewer variables take the reduce / carry / apply path
 constexpr int TAIL_MAX_VARS = 1 << 20;    // bitmap of 128 KB in shared memory
@@ -63,6 +64,18 @@ bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh)
     sh.S = (n_ops >> DEFAULT_SPLIT_SHIFT) / TF_CHUNK * TF_CHUNK;
     sh.E = n_ops - sh.S;
     return true;
+}
+
+// The candidates' trace starts dense in live ops (each candidate variable's
+// first ops in the epoch), like a trace's start: its first 2^k candidates take
+// the reduce / carry / apply prefix (padded with Noops when there are fewer).
+// AMC_SCAN_TAIL_PREFIX=k overrides k (0: none).  0 when C is not larger.
+int cand_prefix_log2(int64_t C)
+{
+    int k = CAND_PREFIX_LOG2;
+    if (const char* e = getenv("AMC_SCAN_TAIL_PREFIX")) k = atoi(e);
+    if (k < 12 || k > 30 || ((int64_t)1 << k) >= C) return 0;
+    return k;
 }
 
 struct TailLayout {
@@ -114,7 +127,8 @@ TailLayout tail_layout(const TailShape& sh, int32_t n_vars)
     t.spos = t.svar + align_up(4 * n_chunks * TF_SLOTS, 256);
     const size_t slots = align_up(n_chunks * TF_SLOTS, 256) + align_up(4 * n_chunks * TF_SLOTS, 256) +
                          align_up(2 * n_chunks * TF_SLOTS, 256);
-    const size_t cscan = scan_workspace_bytes((int64_t)C, n_vars, false);
+    size_t cscan = scan_workspace_bytes((int64_t)C, n_vars, false);
+    if (const int k = cand_prefix_log2((int64_t)C)) cscan += scan_prefix_workspace_bytes((int64_t)1 << k, n_vars);
     r += slots > cscan ? slots : cscan;
     size_t reg = r;
     const size_t part1 = scan_workspace_bytes(sh.S, n_vars);
@@ -433,6 +447,18 @@ __global__ void tail_scatter_kernel(const uint8_t* __restrict__ cstep, const uin
     if (g == 0 && *cff >= 0 && *ff < 0) *ff = epoch0 + cpos[*cff];
 }
 
+// Noops on variable 0 after the candidates, up to the prefix length: they
+// change no status and fault nowhere.
+__global__ void tail_pad_kernel(uint8_t* __restrict__ cks, int32_t* __restrict__ cvar,
+                                const int64_t* __restrict__ n_cand, int64_t P)
+{
+    for (int64_t j = *n_cand + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        cks[j] = (uint8_t)AMC_K_NOOP;
+        cvar[j] = 0;
+    }
+}
+
 }  // namespace
 
 bool scan_tail_eligible(const ScanLaunch& L)
@@ -532,6 +558,11 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // the candidates: a trace of at most C ops (count on the device); gated
         // off when they overflowed
+        const int cpl = cand_prefix_log2(lay.C);
+        if (cpl) {
+            tail_pad_kernel<<<n_sm * 4, 256, 0, s>>>(cks, cvar, ncand, (int64_t)1 << cpl);
+            if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+        }
         ScanLaunch C = L;
         C.kind_side = cks;
         C.var = cvar;
@@ -545,7 +576,8 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         C.vff = cvff;
         C.first_fault = cff;
         C.workspace = reg + lay.cws;
-        C.dense = 0;
+        C.dense = cpl ? -1 : 0;
+        C.prefix_log2 = cpl;
         C.profile = 0;
         rc = launch_scan_trace(C, s);
         if (rc) return rc;

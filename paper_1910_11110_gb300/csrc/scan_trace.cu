@@ -1757,7 +1757,8 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.front = p.tile_counter + 1;
     const bool plain = !L.n_dev && !L.gate;
     if (L.dense != 0 && plain && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
-    if (L.dense != 0 && plain && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr))
+    if (L.dense != 0 && (L.prefix_log2 > 0 ? scan_forced_prefix(L)
+                                           : plain && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr)))
         return launch_scan_prefix(L, w + 256, s);
     // key bits: var ids are < n_vars; at most MAX_DIGIT_BITS per pass
     int kb = 1;

@@ -63,6 +63,8 @@ struct ScanLaunch {
     int dense = -1;                     // reduce / carry / apply path: -1 when eligible, 0 never
     const int64_t* n_dev = nullptr;     // device op count, read by the kernel (n_ops = capacity);
                                         // single-pass kernel only, not with a guard
+    int prefix_log2 = 0;                // > 0: a 2^k-op reduce / carry / apply prefix whatever the
+                                        // size, initial statuses or device count (many variables)
     const int* gate = nullptr;          // device flag: the scan and its final-status pass do
     int gate_on = 0;                    // nothing unless (*gate != 0) == gate_on (single-pass only)
 };
@@ -82,6 +84,10 @@ int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
 // prefix's final statuses.
 bool scan_prefix_eligible(int64_t n_ops, int32_t n_vars, bool has_init);
 int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
+// Scratch of a P-op prefix (after the single-pass workspace); and whether L
+// asks for a forced prefix that applies.
+size_t scan_prefix_workspace_bytes(int64_t P, int32_t n_vars);
+bool scan_forced_prefix(const ScanLaunch& L);
 // First faults of a check of ops [offset, ...) folded into those of the ops
 // before it: vff[v] = vff_part[v] + offset where vff[v] is -1 and vff_part[v]
 // is not; the same for *ff.

@@ -106,3 +106,28 @@ def test_overflow_falls_back_in_one_epoch(amc, oracle_mod, monkeypatch):
     ks[lo:lo + 9000] = 0x01                          # CPU writes
     var[lo:lo + 9000] = 20_000 + (np.arange(9000) % 10_000)
     check(amc, oracle_mod, ks, var, nv)
+
+
+@pytest.mark.parametrize("k", ["12", "14"])
+def test_candidates_prefix(amc, oracle_mod, monkeypatch, k):
+    # the candidates' first 2^k ops through the reduce / carry / apply prefix
+    monkeypatch.setenv("AMC_SCAN_TAIL", "16,20")
+    monkeypatch.setenv("AMC_SCAN_TAIL_PREFIX", k)
+    ks, var = workloads.trace_zipf(3 * (1 << 20) + 5, 1 << 20, seed=97, device="cuda")
+    check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
+
+
+def test_candidates_prefix_padded(amc, oracle_mod, monkeypatch):
+    # fewer candidates (937, all on one variable) than the 2^16-op prefix:
+    # the rest of the prefix is Noops on variable 0
+    monkeypatch.setenv("AMC_SCAN_TAIL", "15,20")
+    monkeypatch.setenv("AMC_SCAN_TAIL_PREFIX", "16")
+    nv = 20_000
+    n_ops = (1 << 15) + 600_000
+    i = np.arange(n_ops)
+    ks = np.full(n_ops, 0x10, np.uint8)
+    var = (i % (nv - 1)).astype(np.int32)
+    tail = (i >= (1 << 15)) & (i % 640 == 0)
+    ks[tail] = np.where(i[tail] % 3 == 0, 0x00, 0x01)
+    var[tail] = nv - 1
+    check(amc, oracle_mod, ks, var, nv)
