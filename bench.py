@@ -577,10 +577,11 @@ def trace_kernels(n_ops, n_vars):
     variables from 2^24 ops that path on the first 2^22 ops, then the stuck
     bitmap seeded from its final statuses, the single-pass scan, the final
     statuses and the first-fault merge (7 kernels); from 2^29 ops that on the
-    first n/16 ops, then one epoch: stuck bitmap, stream filter, offsets,
-    gather, the candidates' scan (seed, scan, final statuses), scatter, the
-    gated fallback scan (seed, scan, final statuses) and the first-fault merge
-    (12 kernels); else the scan and the final statuses."""
+    first n/16 ops, then one epoch: stuck bitmap, stream filter, block sums,
+    gather, Noop padding, the candidates' check (reduce / carry / apply on
+    their first 2^21 ops, suffix count, seed, scan, final statuses, merge),
+    scatter, the gated fallback scan (seed, scan, final statuses) and the
+    first-fault merge (18 kernels); else the scan and the final statuses."""
     if os.environ.get("AMC_SCAN_DENSE", "") == "0":
         return "scan_trace_kernel", 2
     if n_vars <= 8192 and n_ops >= (1 << 20):
@@ -589,7 +590,7 @@ def trace_kernels(n_ops, n_vars):
         return "dense reduce + carry + apply kernels", 3
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 29) and os.environ.get("AMC_SCAN_TAIL", "") != "0":
         return ("first n/16 ops: prefix (dense reduce + carry + apply) + scan_trace_kernel; rest: "
-                "tail_filter_kernel + compacted candidates' scan_trace_kernel + scatter"), 19
+                "tail_filter_kernel + compacted candidates' prefix + scan_trace_kernel + scatter"), 25
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
         return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7
     return "scan_trace_kernel", 2
