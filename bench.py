@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -71,7 +72,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: AMC_CLOCKS_DIR if set, else the temporary directory
+        out_dir = os.environ.get("AMC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"amc_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
