@@ -61,3 +61,23 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(amc, "_lib", None)
     with pytest.raises(RuntimeError):
         amc.lib()
+
+
+def test_workspace_sizes_at_the_bench_size(libamc):
+    # the trace check's scratch stays about 5.5 B per op at 2^30 ops over 2^20
+    # variables (the epoch path shares one region with its fallback); the
+    # host-buffer check's device scratch is three chunk slots (6 B per op) plus
+    # one chunk's scan (with the dense prefix's rows), whatever the trace length
+    libamc.amc_check_trace_workspace.restype = ctypes.c_size_t
+    libamc.amc_check_trace_workspace.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    libamc.amc_check_trace_host_workspace.restype = ctypes.c_size_t
+    libamc.amc_check_trace_host_workspace.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64]
+    n, v = 1 << 30, 1 << 20
+    ws = libamc.amc_check_trace_workspace(n, v)
+    assert 5 * n < ws < 6 * n
+    h = libamc.amc_check_trace_host_workspace(n, v, 0)
+    h2 = libamc.amc_check_trace_host_workspace(n // 4, v, 0)
+    assert h == h2                      # independent of the trace length
+    assert 18 * (1 << 25) < h < 48 * (1 << 25)
+    assert libamc.amc_check_trace_host_workspace(n, v, 1 << 20) < h
+    assert libamc.amc_check_trace_host_workspace(-1, v, 0) == 0
