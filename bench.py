@@ -573,18 +573,28 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def tail_epochs(n_ops):
+    """Epochs of the long-trace path at its default shape (first part 2^20
+    ops, each epoch ending at four times its start)."""
+    e0, k = 1 << 20, 0
+    while e0 < n_ops:
+        e0, k = min(e0 << 2, n_ops), k + 1
+    return k
+
+
 def trace_kernels(n_ops, n_vars):
     """(what the timed span covers, kernels launched per check) for
     amc_check_trace without initial statuses: the reduce / carry / apply path
     over at most 16,384 variables from 2^20 ops; over more (at most 2^20)
     variables from 2^24 ops that path on the first 2^22 ops, then the stuck
     bitmap seeded from its final statuses, the single-pass scan, the final
-    statuses and the first-fault merge (7 kernels); from 2^29 ops that on the
-    first n/16 ops, then one epoch: stuck bitmap, stream filter, block sums,
-    gather, Noop padding, the candidates' check (reduce / carry / apply on
-    their first 2^21 ops, suffix count, seed, scan, final statuses, merge),
-    scatter, the gated fallback scan (seed, scan, final statuses) and the
-    first-fault merge (18 kernels); else the scan and the final statuses."""
+    statuses and the first-fault merge (7 kernels); from 2^29 ops the first
+    2^20 ops as pairs sorted by variable (pairs, 3 radix passes of histogram,
+    scan and scatter, then the segmented scan's reduce, carry and apply: 13
+    kernels), then per epoch the stuck bitmap, stream filter, block sums,
+    gather, the candidates' sorted check (12), the gated fallback scan (seed,
+    scan, final statuses) and the first-fault merge (20 kernels); else the scan
+    and the final statuses."""
     if os.environ.get("AMC_SCAN_DENSE", "") == "0":
         return "scan_trace_kernel", 2
     if n_vars <= 8192 and n_ops >= (1 << 20):
@@ -592,8 +602,8 @@ def trace_kernels(n_ops, n_vars):
     if n_vars <= 16384 and n_ops >= (1 << 20):
         return "dense reduce + carry + apply kernels", 3
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 29) and os.environ.get("AMC_SCAN_TAIL", "") != "0":
-        return ("first n/16 ops: prefix (dense reduce + carry + apply) + scan_trace_kernel; rest: "
-                "tail_filter_kernel + compacted candidates' prefix + scan_trace_kernel + scatter"), 25
+        return ("first 2^20 ops: sorted check (radix sort by variable + segmented scan); epochs to 4x their "
+                "start: tail_filter_kernel + gather + sorted check of the candidates"), 13 + 20 * tail_epochs(n_ops)
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
         return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7
     return "scan_trace_kernel", 2
@@ -603,13 +613,13 @@ def scan_traffic(n_ops, n_vars):
     """DRAM bytes (read + write) of one check -- every kernel of the timed span
     -- from the recorded ncu capture, or None when the capture was of another
     workload or the kernel sources have changed since (the record keeps the
-    SHA-256 of scan_trace.cu, scan_dense.cu and scan_tail.cu)."""
+    SHA-256 of scan_trace.cu, scan_dense.cu, scan_tail.cu and scan_sorted.cu)."""
     import hashlib
     tr_path = os.path.join(ROOT, "profiles", "scan_trace_zipf_traffic.json")
     h = hashlib.sha256()
     try:
         rec = json.load(open(tr_path))
-        for f in ("scan_trace.cu", "scan_dense.cu", "scan_tail.cu"):
+        for f in ("scan_trace.cu", "scan_dense.cu", "scan_tail.cu", "scan_sorted.cu"):
             h.update(open(os.path.join(ROOT, "paper_1910_11110_gb300", "csrc", f), "rb").read())
         sha = h.hexdigest()
     except Exception:

@@ -1,23 +1,24 @@
-// scan_tail.cu -- the tail of a long trace checked in epochs: stream filter,
-// compacted candidates, scatter.
+// scan_tail.cu -- long traces checked in epochs: stream filter, compacted
+// candidates, each set checked by sorting it by variable.
 //
 // Section 3.2: F is absorbing, so once a variable's status is F every later
 // op on it yields F (Property Progress: a stuck variable stays stuck).  On a
 // long trace nearly every op after the first few per variable is such an op.
-// The first part of the trace, [0, S), is checked as usual (scan_trace.cu,
-// scan_dense.cu); the rest is cut into epochs of E ops, and for each epoch
+// The first part of the trace, [0, S), is checked by sorting its ops by
+// variable (scan_sorted.cu); the rest is cut into epochs (by default each
+// ends at four times its start), and for each epoch
 //   1. the statuses at its start are exact (the previous part's final
 //      statuses); variables with status F form a bitmap;
-//   2. a streaming kernel writes F for every op on a variable of the bitmap
-//      and collects the other ops ("candidates"), in position order;
-//   3. the candidates, a trace of their own over the same variables (an op's
-//      status depends only on the earlier ops on its variable), are checked
-//      by the single-pass scan from the epoch's start statuses, with the op
-//      count read from device memory;
-//   4. their statuses are scattered back to the epoch's positions and their
-//      first faults mapped to trace positions and folded into the earlier
-//      ones; the final statuses start the next epoch.
-// Outputs are identical to one scan over the whole trace.
+//   2. a streaming kernel writes F at every position and collects the ops on
+//      variables outside the bitmap ("candidates"), in position order;
+//   3. the candidates, a set of ops over the same variables (an op's status
+//      depends only on the earlier ops on its variable), are checked by
+//      sorting them by variable, from the epoch's start statuses, with their
+//      count read from device memory: the statuses that are not F go to their
+//      positions, first faults to trace positions, final statuses start the
+//      next epoch.
+// Outputs are identical to one scan over the whole trace.  An epoch whose
+// candidates overflow their slots is rechecked whole by the single-pass scan.
 #include <cstdio>
 #include <cstdlib>
 
@@ -30,75 +31,94 @@ namespace {
 
 constexpr int TF_THREADS = 1024;          // filter CTA: one per SM (the bitmap fills shared memory)
 constexpr int TF_CHUNK = 4096;            // ops per warp chunk
-constexpr int TF_SLOTS = 512;             // candidate slots per chunk (more: the epoch falls back)
-constexpr int CAND_DIV = 8;               // candidate capacity: epoch ops / 8 (more: falls back)
-constexpr int CAND_PREFIX_LOG2 = 21;      // the candidates' first 2^21 ops take the reduce / carry / apply path
+constexpr int TF_SLOTS = 1024;            // candidate slots per chunk (more: the epoch falls back)
+constexpr int CAND_DIV = 4;               // candidate capacity: epoch ops / 4 (more: falls back)
+constexpr int64_t CAND_MAX = (int64_t)1 << 27;   // and at most 2^27 (set index << 4 fits 32 bits)
 constexpr int TF_PER = 16;                // ops per lane and step
 constexpr int TAIL_MIN_VARS = 16385;      // fewer variables take the reduce / carry / apply path
 constexpr int TAIL_MAX_VARS = 1 << 20;    // bitmap of 128 KB in shared memory
-constexpr int DEFAULT_SPLIT_SHIFT = 4;    // S = n_ops / 16, then one epoch
+constexpr int DEFAULT_FIRST_LOG2 = 20;    // first part 2^20 ops,
+constexpr int DEFAULT_GROW = 2;           // then epochs ending at 4 times their start
 constexpr int64_t DEFAULT_MIN_OPS = (int64_t)1 << 29;
 
 struct TailShape {
     int64_t S = 0;        // ops of the first part
-    int64_t E = 0;        // ops per epoch
+    int64_t E = 0;        // ops per epoch (grow == 0)
+    int grow = 0;         // > 0: each epoch ends at 2^grow times its start
 };
 
-// AMC_SCAN_TAIL="s,e": first part 2^s ops, epochs of 2^e ops, for every
-// trace longer than 2^s ops (test and tuning override); "0" disables.
+// AMC_SCAN_TAIL="s,e": first part 2^s ops, epochs of 2^e ops; "s,-g": first
+// part 2^s ops, each epoch ending at 2^g times its start; for every trace
+// longer than 2^s ops (test and tuning override); "0" disables.
 bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh)
 {
     if (guarded || n_vars < TAIL_MIN_VARS || n_vars > TAIL_MAX_VARS) return false;
     if (const char* e = getenv("AMC_SCAN_TAIL")) {
         if (e[0] == '0' && e[1] == 0) return false;
         int a = 0, b = 0;
-        if (sscanf(e, "%d,%d", &a, &b) == 2 && a >= 12 && a < 31 && b >= 12 && b < 31) {
+        if (sscanf(e, "%d,%d", &a, &b) == 2 && a >= 12 && a <= 27 && ((b >= 12 && b < 31) || (b >= -4 && b <= -1))) {
             sh.S = (int64_t)1 << a;
-            sh.E = (int64_t)1 << b;
             if (n_ops <= sh.S) return false;
-            if (sh.E > n_ops - sh.S) sh.E = n_ops - sh.S;
+            if (b > 0) {
+                sh.E = (int64_t)1 << b;
+                if (sh.E > n_ops - sh.S) sh.E = n_ops - sh.S;
+            } else {
+                sh.grow = -b;
+            }
             return true;
         }
     }
     if (n_ops < DEFAULT_MIN_OPS) return false;
-    sh.S = (n_ops >> DEFAULT_SPLIT_SHIFT) / TF_CHUNK * TF_CHUNK;
-    sh.E = n_ops - sh.S;
+    sh.S = (int64_t)1 << DEFAULT_FIRST_LOG2;
+    sh.grow = DEFAULT_GROW;
     return true;
 }
 
-// The candidates' trace starts dense in live ops (each candidate variable's
-// first ops in the epoch), like a trace's start: its first 2^k candidates take
-// the reduce / carry / apply prefix (padded with Noops when there are fewer).
-// AMC_SCAN_TAIL_PREFIX=k overrides k (0: none).  0 when C is not larger.
-int cand_prefix_log2(int64_t C)
+int64_t epoch_end(const TailShape& sh, int64_t e0, int64_t n_ops)
 {
-    int k = CAND_PREFIX_LOG2;
-    if (const char* e = getenv("AMC_SCAN_TAIL_PREFIX")) k = atoi(e);
-    if (k < 12 || k > 30 || ((int64_t)1 << k) >= C) return 0;
-    return k;
+    const int64_t e1 = sh.grow ? (e0 << sh.grow) : e0 + sh.E;
+    return e1 < n_ops ? e1 : n_ops;
+}
+
+int64_t longest_epoch(const TailShape& sh, int64_t n_ops)
+{
+    int64_t m = 0;
+    for (int64_t e0 = sh.S; e0 < n_ops; e0 = epoch_end(sh, e0, n_ops)) {
+        const int64_t len = epoch_end(sh, e0, n_ops) - e0;
+        if (len > m) m = len;
+    }
+    return m;
+}
+
+// candidate capacity of an epoch of E ops
+int64_t cand_cap(int64_t E)
+{
+    int64_t C = (E + CAND_DIV - 1) / CAND_DIV;
+    C = (C + TF_CHUNK - 1) / TF_CHUNK * TF_CHUNK;
+    return C < CAND_MAX ? C : CAND_MAX;
 }
 
 struct TailLayout {
-    int64_t C = 0;        // candidate capacity per epoch
-    size_t st0, st1, bm, cnt, off, ncand, ovf, cvff, cff, fvff, fff;
-    size_t region;        // shared region: first part, then candidates, then the fallback scan
-    size_t cks, cvar, cpos, cstep, sks, svar, spos, cws;     // offsets inside the region
+    int64_t K = 0;        // pairs the sort buffers hold: the first part or an epoch's candidates
+    size_t st0, st1, bm, cnt, off, ncand, ovf, fvff, fff;
+    size_t region;        // shared region: pairs and slots, or the fallback scan
+    size_t key0, val0, pos, key1, val1, sks, svar, spos, scratch;   // offsets inside the region
     size_t total;
 };
 
 // Scratch: a few per-variable arrays, then one region used in turn by the
-// first part's scan, by an epoch's candidates (chunk slots, the compacted
-// trace, its scan), and by the epoch's fallback scan over all its ops (taken
-// when the candidates overflow their slots).  The region is as large as the
-// largest of the three, about 5 bytes per op of the longer of S and E.
-TailLayout tail_layout(const TailShape& sh, int32_t n_vars)
+// first part's pairs, by an epoch's candidates (chunk slots, sharing their
+// space with the sort's second buffers, the pairs, their positions, the sort's
+// scratch), and by the epoch's fallback scan over all its ops (taken when the
+// candidates overflow their slots).
+TailLayout tail_layout(const TailShape& sh, int32_t n_vars, int64_t n_ops)
 {
     TailLayout t;
-    const size_t E = (size_t)sh.E;
-    const size_t n_chunks = (E + TF_CHUNK - 1) / TF_CHUNK;
-    size_t C = (E + CAND_DIV - 1) / CAND_DIV;
-    C = (C + TF_CHUNK - 1) / TF_CHUNK * TF_CHUNK;
-    t.C = (int64_t)C;
+    const int64_t Emax = longest_epoch(sh, n_ops);
+    const size_t n_chunks = (size_t)((Emax + TF_CHUNK - 1) / TF_CHUNK);
+    const int64_t C = cand_cap(Emax);
+    t.K = C > sh.S ? C : sh.S;
+    const size_t K = (size_t)t.K;
     size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o += align_up(b, 256); return at; };
     t.st0 = take((size_t)n_vars);
@@ -108,32 +128,28 @@ TailLayout tail_layout(const TailShape& sh, int32_t n_vars)
     t.off = take(4 * n_chunks);
     t.ncand = take(8);
     t.ovf = take(4);
-    t.cvff = take(4 * (size_t)n_vars);
-    t.cff = take(8);
     t.fvff = take(4 * (size_t)n_vars);
     t.fff = take(8);
     t.region = o;
-    // candidates: compacted trace and statuses, then the slots (until the
-    // gather) sharing their space with the candidates' scan
     size_t r = 0;
     auto rtake = [&](size_t b) { const size_t at = r; r += align_up(b, 256); return at; };
-    t.cks = rtake(C);
-    t.cvar = rtake(4 * C);
-    t.cpos = rtake(4 * C);
-    t.cstep = rtake(C);
-    t.cws = r;
-    t.sks = r;
+    t.key0 = rtake(4 * K);
+    t.val0 = rtake(4 * K);
+    t.pos = rtake(4 * K);
+    t.scratch = rtake(sorted_check_scratch_bytes(t.K));
+    // the slots live until the gather; the sort's second buffers after it
+    const size_t shared_at = r;
+    t.key1 = shared_at;
+    t.val1 = shared_at + align_up(4 * K, 256);
+    const size_t second = 2 * align_up(4 * K, 256);
+    t.sks = shared_at;
     t.svar = t.sks + align_up(n_chunks * TF_SLOTS, 256);
     t.spos = t.svar + align_up(4 * n_chunks * TF_SLOTS, 256);
     const size_t slots = align_up(n_chunks * TF_SLOTS, 256) + align_up(4 * n_chunks * TF_SLOTS, 256) +
                          align_up(2 * n_chunks * TF_SLOTS, 256);
-    size_t cscan = scan_workspace_bytes((int64_t)C, n_vars, false);
-    if (const int k = cand_prefix_log2((int64_t)C)) cscan += scan_prefix_workspace_bytes((int64_t)1 << k, n_vars);
-    r += slots > cscan ? slots : cscan;
+    r += second > slots ? second : slots;
     size_t reg = r;
-    const size_t part1 = scan_workspace_bytes(sh.S, n_vars);
-    const size_t fallback = scan_workspace_bytes(sh.E, n_vars, false);
-    if (part1 > reg) reg = part1;
+    const size_t fallback = scan_workspace_bytes(Emax, n_vars, false);
     if (fallback > reg) reg = fallback;
     t.total = o + reg;
     return t;
@@ -168,9 +184,11 @@ struct FilterParams {
 
 // Each warp takes chunks of TF_CHUNK ops in steps of 32 x 16 (lane L: ops
 // [16 L, 16 L + 16) of a step: one 16-byte load of op bytes and four of ids);
-// ops on stuck variables get F, the others are staged in the chunk's slots in
-// position order.  Op bytes and ids are checked as in the
-// scan (malformed bytes, ids out of range, GT not followed by its EN).
+// every position gets F (the candidates' statuses that are not F are written
+// after their check), the ops on variables outside the bitmap are staged in
+// the chunk's slots in position order.  Op bytes and ids are checked as in the
+// scan (malformed bytes, ids out of range, GT not followed by its EN); an id
+// out of range is staged as 0.
 __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const FilterParams q)
 {
     extern __shared__ __align__(16) uint32_t sbm[];
@@ -192,7 +210,6 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
             const bool vec = nl == TF_PER && q.bulk_ok;
             uint32_t kw[TF_PER / 4];
             int32_t va[TF_PER];
-            uint32_t outw[TF_PER / 4];
             uint32_t liveMask = 0;
             if (vec) {
                 // full step: four op bytes per 32-bit word are checked at once
@@ -217,7 +234,6 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
                     // bytes whose kind is GT (6): zero bytes of (kind ^ 6)
                     const uint32_t x = (kw[h] & 0x0F0F0F0Fu) ^ 0x06060606u;
                     gt |= (x - 0x01010101u) & ~x & 0x80808080u;
-                    outw[h] = 0;
                 }
 #pragma unroll
                 for (int u = 0; u < TF_PER; ++u) {
@@ -225,9 +241,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
                     const bool ok = v < (uint32_t)q.n_vars;
                     badv |= !ok;
                     const uint32_t uv = ok ? v : 0u;
+                    va[u] = (int32_t)uv;
                     const uint32_t stuck = (sbm[uv >> 5] >> (uv & 31)) & 1u;
                     liveMask |= (stuck ^ 1u) << u;
-                    outw[u >> 2] |= stuck << (8 * (u & 3) + 2);       // F = 4 where stuck, else 0
                 }
                 if (badk) raise_error(q.err, AMC_E_INVALID);
                 if (badv) raise_error(q.err, AMC_E_RANGE);
@@ -248,10 +264,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
                             raise_error(q.err, AMC_E_INVALID);
                     }
                 }
-                __stcs(reinterpret_cast<uint4*>(q.step + i0), make_uint4(outw[0], outw[1], outw[2], outw[3]));
+                constexpr uint32_t F4 = 0x01010101u * ST_F;
+                __stcs(reinterpret_cast<uint4*>(q.step + i0), make_uint4(F4, F4, F4, F4));
             } else {
 #pragma unroll
-                for (int h = 0; h < TF_PER / 4; ++h) kw[h] = outw[h] = 0;
+                for (int h = 0; h < TF_PER / 4; ++h) kw[h] = 0;
 #pragma unroll
                 for (int u = 0; u < TF_PER; ++u) {
                     va[u] = 0;
@@ -263,7 +280,6 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
 #pragma unroll
                 for (int u = 0; u < TF_PER; ++u) {
                     const uint32_t ks = (kw[u >> 2] >> (8 * (u & 3))) & 0xFFu;
-                    uint32_t o = ST_F;
                     if (u < nl) {
                         if ((ks & 0xE0u) || (ks & 15u) > AMC_K_EN) raise_error(q.err, AMC_E_INVALID);
                         uint32_t uv = (uint32_t)va[u];
@@ -281,11 +297,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
                             if (!((nks & 15) == AMC_K_EN && (nks >> 4) == (ks >> 4) && nv != (int32_t)uv))
                                 raise_error(q.err, AMC_E_INVALID);
                         }
-                        if (!((sbm[uv >> 5] >> (uv & 31)) & 1u)) {
-                            liveMask |= 1u << u;
-                            o = 0;                            // scattered after the candidates' check
-                        }
-                        q.step[i0 + u] = (uint8_t)o;
+                        va[u] = (int32_t)uv;
+                        if (!((sbm[uv >> 5] >> (uv & 31)) & 1u)) liveMask |= 1u << u;
+                        q.step[i0 + u] = (uint8_t)ST_F;
                     }
                 }
             }
@@ -340,7 +354,9 @@ __global__ void __launch_bounds__(1024) tail_blocksum_kernel(const uint32_t* __r
     }
 }
 
-// Chunk slots -> dense candidate trace, in position order.  Block b takes
+// Chunk slots -> the candidates as pairs for the sorted check (variable,
+// candidate index << 4 | code) and their positions in the epoch, in position
+// order.  Block b takes
 // chunks [1024 b, 1024 b + 1024): its base is the sum of the earlier blocks'
 // counts, its chunks' offsets a block scan; each warp copies 32 chunks.  Every
 // block also forms the grand total, so all agree on an overflow (more
@@ -351,8 +367,8 @@ __global__ void __launch_bounds__(1024) tail_gather_kernel(const uint8_t* __rest
                                                            const uint16_t* __restrict__ spos,
                                                            const uint32_t* __restrict__ cnt, int n_chunks,
                                                            const uint32_t* __restrict__ bsum, int n_blocks,
-                                                           int64_t cap, uint8_t* __restrict__ cks,
-                                                           int32_t* __restrict__ cvar, uint32_t* __restrict__ cpos,
+                                                           int64_t cap, uint32_t* __restrict__ ckey,
+                                                           uint32_t* __restrict__ cval, uint32_t* __restrict__ cpos,
                                                            int64_t* __restrict__ n_cand, int* ovf)
 {
     __shared__ unsigned long long rb[32], rt[32];
@@ -419,43 +435,10 @@ __global__ void __launch_bounds__(1024) tail_gather_kernel(const uint8_t* __rest
         const uint32_t nk = cnt[c], o = offs[k];
         for (uint32_t j = lane; j < nk; j += 32) {
             const int64_t src = (int64_t)c * TF_SLOTS + j;
-            cks[o + j] = sks[src];
-            cvar[o + j] = svar[src];
+            ckey[o + j] = (uint32_t)svar[src];
+            cval[o + j] = (o + j) << 4 | sorted_code_of(sks[src]);
             cpos[o + j] = (uint32_t)c * (uint32_t)TF_CHUNK + spos[src];
         }
-    }
-}
-
-// Candidates' statuses to their positions; their first faults (indices into
-// the candidate trace) to trace positions, kept only where the earlier ops had
-// none.
-__global__ void tail_scatter_kernel(const uint8_t* __restrict__ cstep, const uint32_t* __restrict__ cpos,
-                                    const int64_t* __restrict__ n_cand, uint8_t* __restrict__ step,
-                                    const int32_t* __restrict__ cvff, int32_t n_vars, int32_t* __restrict__ vff,
-                                    const int64_t* __restrict__ cff, int64_t* __restrict__ ff, int64_t epoch0,
-                                    const int* ovf)
-{
-    if (*ovf) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nc = *n_cand;
-    for (int64_t j = g; j < nc; j += stride) step[cpos[j]] = cstep[j];
-    for (int64_t v = g; v < n_vars; v += stride) {
-        const int32_t c = cvff[v];
-        if (c >= 0 && vff[v] < 0) vff[v] = (int32_t)(epoch0 + cpos[c]);
-    }
-    if (g == 0 && *cff >= 0 && *ff < 0) *ff = epoch0 + cpos[*cff];
-}
-
-// Noops on variable 0 after the candidates, up to the prefix length: they
-// change no status and fault nowhere.
-__global__ void tail_pad_kernel(uint8_t* __restrict__ cks, int32_t* __restrict__ cvar,
-                                const int64_t* __restrict__ n_cand, int64_t P)
-{
-    for (int64_t j = *n_cand + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        cks[j] = (uint8_t)AMC_K_NOOP;
-        cvar[j] = 0;
     }
 }
 
@@ -472,14 +455,14 @@ size_t scan_tail_workspace_bytes(int64_t n_ops, int32_t n_vars)
 {
     TailShape sh;
     if (!tail_shape(n_ops, n_vars, false, sh)) return 0;
-    return tail_layout(sh, n_vars).total;
+    return tail_layout(sh, n_vars, n_ops).total;
 }
 
 int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
 {
     TailShape sh;
     if (!tail_shape(L.n_ops, L.n_vars, false, sh)) return AMC_E_INVALID;
-    const TailLayout lay = tail_layout(sh, L.n_vars);
+    const TailLayout lay = tail_layout(sh, L.n_vars, L.n_ops);
     uint8_t* w = static_cast<uint8_t*>(L.workspace);
     uint8_t* st[2] = {w + lay.st0, w + lay.st1};
     uint32_t* bm = reinterpret_cast<uint32_t*>(w + lay.bm);
@@ -487,18 +470,18 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     uint32_t* bsum = reinterpret_cast<uint32_t*>(w + lay.off);    // candidates per 1024 chunks
     int64_t* ncand = reinterpret_cast<int64_t*>(w + lay.ncand);
     int* ovf = reinterpret_cast<int*>(w + lay.ovf);
-    int32_t* cvff = reinterpret_cast<int32_t*>(w + lay.cvff);
-    int64_t* cff = reinterpret_cast<int64_t*>(w + lay.cff);
     int32_t* fvff = reinterpret_cast<int32_t*>(w + lay.fvff);
     int64_t* fff = reinterpret_cast<int64_t*>(w + lay.fff);
     uint8_t* reg = w + lay.region;
     uint8_t* sks = reg + lay.sks;
     int32_t* svar = reinterpret_cast<int32_t*>(reg + lay.svar);
     uint16_t* spos = reinterpret_cast<uint16_t*>(reg + lay.spos);
-    uint8_t* cks = reg + lay.cks;
-    int32_t* cvar = reinterpret_cast<int32_t*>(reg + lay.cvar);
-    uint32_t* cpos = reinterpret_cast<uint32_t*>(reg + lay.cpos);
-    uint8_t* cstep = reg + lay.cstep;
+    uint32_t* key0 = reinterpret_cast<uint32_t*>(reg + lay.key0);
+    uint32_t* val0 = reinterpret_cast<uint32_t*>(reg + lay.val0);
+    uint32_t* key1 = reinterpret_cast<uint32_t*>(reg + lay.key1);
+    uint32_t* val1 = reinterpret_cast<uint32_t*>(reg + lay.val1);
+    uint32_t* cpos = reinterpret_cast<uint32_t*>(reg + lay.pos);
+    void* scratch = reg + lay.scratch;
 
     int dev = 0, n_sm = 0, max_optin = 0;
     cudaGetDevice(&dev);
@@ -514,20 +497,41 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
             return AMC_E_CUDA;
         if (dev < 64) attr_set[dev] = fsmem;
     }
+    if (L.profile & 1) profile_begin(s);
 
-    // first part: the usual scan of ops [0, S), final statuses to st[0]
-    ScanLaunch A = L;
-    A.n_ops = sh.S;
-    A.final_status = st[0];
-    A.workspace = reg;
-    A.profile = L.profile & 1;
-    int rc = launch_scan_trace(A, s);
+    // first part: ops [0, S) checked by sorting them by variable, from the
+    // initial statuses; final statuses to st[0]
+    if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
+    if (L.init) {
+        if (cudaMemcpyAsync(st[0], L.init, (size_t)L.n_vars, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return AMC_E_CUDA;
+    } else if (cudaMemsetAsync(st[0], AMC_ST_VI, (size_t)L.n_vars, s) != cudaSuccess) {
+        return AMC_E_CUDA;
+    }
+    int rc = launch_ss_keys(L.kind_side, L.var, sh.S, L.n_ops, L.n_vars, key0, val0, L.step, L.err, s);
+    if (rc) return rc;
+    SortedCheck A;
+    A.key[0] = key0;
+    A.key[1] = key1;
+    A.val[0] = val0;
+    A.val[1] = val1;
+    A.cap = sh.S;
+    A.n_vars = L.n_vars;
+    A.init = L.init;
+    A.step = L.step;
+    A.fin = st[0];
+    A.vff = L.vff;
+    A.ff = L.first_fault;
+    A.scratch = scratch;
+    rc = launch_sorted_check(A, s);
     if (rc) return rc;
 
     int cur = 0;
-    for (int64_t e0 = sh.S; e0 < L.n_ops; e0 += sh.E) {
-        const int64_t n = L.n_ops - e0 < sh.E ? L.n_ops - e0 : sh.E;
-        const bool last = e0 + n >= L.n_ops;
+    for (int64_t e0 = sh.S; e0 < L.n_ops;) {
+        const int64_t e1 = epoch_end(sh, e0, L.n_ops);
+        const int64_t n = e1 - e0;
+        const bool last = e1 >= L.n_ops;
         uint8_t* fin = (last && L.final_status) ? L.final_status : st[cur ^ 1];
         if (cudaMemsetAsync(ovf, 0, sizeof(int), s) != cudaSuccess) return AMC_E_CUDA;
         tail_bitmap_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(st[cur], L.n_vars, bm);
@@ -552,38 +556,34 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         const int fgrid = (int)min((int64_t)n_sm, ((int64_t)n_chunks + TF_THREADS / 32 - 1) / (TF_THREADS / 32));
         tail_filter_kernel<<<fgrid, TF_THREADS, fsmem, s>>>(q);
         const int n_blocks = (n_chunks + 1023) / 1024;
+        const int64_t C = cand_cap(n);
         tail_blocksum_kernel<<<n_blocks, 1024, 0, s>>>(cnt, n_chunks, bsum);
-        tail_gather_kernel<<<n_blocks, 1024, 0, s>>>(sks, svar, spos, cnt, n_chunks, bsum, n_blocks, lay.C, cks,
-                                                     cvar, cpos, ncand, ovf);
+        tail_gather_kernel<<<n_blocks, 1024, 0, s>>>(sks, svar, spos, cnt, n_chunks, bsum, n_blocks, C, key0, val0,
+                                                     cpos, ncand, ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-        // the candidates: a trace of at most C ops (count on the device); gated
-        // off when they overflowed
-        const int cpl = cand_prefix_log2(lay.C);
-        if (cpl) {
-            tail_pad_kernel<<<n_sm * 4, 256, 0, s>>>(cks, cvar, ncand, (int64_t)1 << cpl);
-            if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-        }
-        ScanLaunch C = L;
-        C.kind_side = cks;
-        C.var = cvar;
-        C.n_ops = lay.C;
-        C.n_dev = ncand;
-        C.gate = ovf;
-        C.gate_on = 0;
-        C.init = st[cur];
-        C.step = cstep;
-        C.final_status = fin;
-        C.vff = cvff;
-        C.first_fault = cff;
-        C.workspace = reg + lay.cws;
-        C.dense = cpl ? -1 : 0;
-        C.prefix_log2 = cpl;
-        C.profile = 0;
-        rc = launch_scan_trace(C, s);
+        // the candidates, at most C (count on the device), from the epoch's
+        // start statuses; gated off when they overflowed
+        if (cudaMemcpyAsync(fin, st[cur], (size_t)L.n_vars, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return AMC_E_CUDA;
+        SortedCheck K;
+        K.key[0] = key0;
+        K.key[1] = key1;
+        K.val[0] = val0;
+        K.val[1] = val1;
+        K.pos = cpos;
+        K.n_dev = ncand;
+        K.cap = C;
+        K.gate = ovf;
+        K.n_vars = L.n_vars;
+        K.init = st[cur];
+        K.step = L.step + e0;
+        K.fin = fin;
+        K.vff = L.vff;
+        K.ff = L.first_fault;
+        K.offset = e0;
+        K.scratch = scratch;
+        rc = launch_sorted_check(K, s);
         if (rc) return rc;
-        tail_scatter_kernel<<<n_sm * 4, 256, 0, s>>>(cstep, cpos, ncand, L.step + e0, cvff, L.n_vars, L.vff, cff,
-                                                    L.first_fault, e0, ovf);
-        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // fallback, gated on by an overflow: the single-pass scan over all the
         // epoch's ops from its start statuses
         ScanLaunch F = L;
@@ -605,6 +605,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         rc = launch_merge_faults(L.vff, fvff, L.n_vars, L.first_fault, fff, e0, s);
         if (rc) return rc;
         cur ^= 1;
+        e0 = e1;
     }
     if (L.profile & 2) profile_end(s);
     return AMC_OK;

@@ -94,13 +94,46 @@ bool scan_forced_prefix(const ScanLaunch& L);
 int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, int64_t* ff,
                         const int64_t* ff_part, int64_t offset, cudaStream_t s);
 // Traces over 16,385 to 2^20 variables and of 2^29 ops or more, without a
-// guard: the first n_ops / 16 ops as usual, the rest in epochs of n_ops / 4
-// (stream filter on the stuck bitmap, compacted candidates checked from the
-// epoch's start statuses, scatter); its scratch replaces the single-pass
-// workspace (scan_workspace_bytes covers both).
+// guard: the first 2^20 ops checked by sorting them by variable, the rest in
+// epochs that each end at four times their start (stream filter on the stuck
+// bitmap, the compacted candidates checked by sorting them by variable from
+// the epoch's start statuses); its scratch replaces the single-pass workspace
+// (scan_workspace_bytes covers both).
 bool scan_tail_eligible(const ScanLaunch& L);
 size_t scan_tail_workspace_bytes(int64_t n_ops, int32_t n_vars);
 int launch_scan_tail(const ScanLaunch& L, cudaStream_t s);
+// A set of ops checked by sorting it by variable (scan_sorted.cu): the pairs
+// (variable id, set index << 4 | 4-bit code of the op byte) sit in key[0] /
+// val[0]; key[1] / val[1] are the sort's second buffers.  Writes the status of
+// every op whose status is not F to step[pos] (the caller wrote F at every
+// position), the first fault of each variable that faults in the set
+// (vff[v] = offset + pos, only ever written for variables not F at entry),
+// folds them into *ff, and writes final statuses to fin (the caller copies the
+// entry statuses there first).  Nothing runs while *gate != 0.
+struct SortedCheck {
+    uint32_t* key[2] = {nullptr, nullptr};
+    uint32_t* val[2] = {nullptr, nullptr};
+    const uint32_t* pos = nullptr;      // nullable: set index j is at position j
+    const int64_t* n_dev = nullptr;     // nullable: the set's size on the device (clamped to cap)
+    int64_t cap = 0;                    // the set's size, or its capacity with n_dev
+    const int* gate = nullptr;
+    int32_t n_vars = 0;
+    const uint8_t* init = nullptr;      // entry statuses; nullable: all (V,I)
+    uint8_t* step = nullptr;
+    uint8_t* fin = nullptr;
+    int32_t* vff = nullptr;
+    int64_t* ff = nullptr;
+    int64_t offset = 0;
+    void* scratch = nullptr;            // sorted_check_scratch_bytes(cap)
+};
+// 4-bit code of an op byte in a pair: kind (bits 0-2) and side (bit 3)
+__host__ __device__ __forceinline__ uint32_t sorted_code_of(uint32_t ks) { return (ks & 7u) | ((ks >> 1) & 8u); }
+size_t sorted_check_scratch_bytes(int64_t cap);
+int launch_sorted_check(const SortedCheck& C, cudaStream_t s);
+// Ops [0, n) of a trace as pairs for launch_sorted_check, checked for bad
+// bytes, ids out of range and GT without its EN; F written to step[0, n).
+int launch_ss_keys(const uint8_t* kind_side, const int32_t* var, int64_t n, int64_t n_after, int32_t n_vars,
+                   uint32_t* key, uint32_t* val, uint8_t* step, int* err, cudaStream_t s);
 // enable >= 0: switch phase counting on/off and zero the counters; host_out
 // (nullable): copy the 8 counters (cycles summed over CTAs).
 int scan_phase_profile(int enable, unsigned long long* host_out);

@@ -1,13 +1,15 @@
-"""GPU parity of the epoch path for the tail of long traces (the first part
-checked as usual, then per epoch: stream filter on the stuck bitmap, the
-compacted candidates checked from the epoch's start statuses, scatter).
+"""GPU parity of the epoch path for long traces (the first part checked by
+sorting its ops by variable, then per epoch: stream filter on the stuck bitmap,
+the compacted candidates checked by sorting them by variable from the epoch's
+start statuses).
 
-Traces over 16,385 to 2^20 variables take it from 2^29 ops on (first part
-n / 16 ops, epochs of n / 4);
-AMC_SCAN_TAIL="s,e" forces a first part of 2^s ops and epochs of 2^e ops at
-any length, so that many epochs, ragged last epochs, epochs with almost every
-op a candidate, initial statuses and bad input all run.  Bit-exact against the
-oracle on every output."""
+Traces over 16,385 to 2^20 variables take it from 2^29 ops on (first part 2^20
+ops, each epoch ending at four times its start); AMC_SCAN_TAIL="s,e" forces a
+first part of 2^s ops and epochs of 2^e ops, "s,-g" epochs ending at 2^g times
+their start, at any length, so that many epochs, ragged last epochs, epochs
+with almost every op a candidate, runs of one variable across many sort tiles,
+initial statuses and bad input all run.  Bit-exact against the oracle on every
+output."""
 import numpy as np
 import pytest
 import torch
@@ -87,8 +89,9 @@ def test_bad_input_in_the_tail(amc, monkeypatch):
 
 
 def test_default_split_at_2p29(amc, oracle_mod):
-    # 2^29 ops over 2^20 variables: the default first part (2^25 ops) and
-    # epochs of 2^27 ops, against the oracle on every output
+    # 2^29 ops over 2^20 variables: the default first part (2^20 ops) and
+    # epochs ending at 2^22, 2^24, 2^26, 2^28 and 2^29 ops, against the oracle
+    # on every output
     ks, var = workloads.trace_zipf(1 << 29, 1 << 20, seed=94, device="cuda")
     check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
 
@@ -108,26 +111,56 @@ def test_overflow_falls_back_in_one_epoch(amc, oracle_mod, monkeypatch):
     check(amc, oracle_mod, ks, var, nv)
 
 
-@pytest.mark.parametrize("k", ["12", "14"])
-def test_candidates_prefix(amc, oracle_mod, monkeypatch, k):
-    # the candidates' first 2^k ops through the reduce / carry / apply prefix
-    monkeypatch.setenv("AMC_SCAN_TAIL", "16,20")
-    monkeypatch.setenv("AMC_SCAN_TAIL_PREFIX", k)
-    ks, var = workloads.trace_zipf(3 * (1 << 20) + 5, 1 << 20, seed=97, device="cuda")
-    check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
+@pytest.mark.parametrize("shape", ["14,-2", "13,-1", "16,-3"])
+def test_zipf_growing_epochs(amc, oracle_mod, monkeypatch, shape):
+    # 20,000 variables: the first epoch's candidates overflow their slots under
+    # 14,-2 and 13,-1 (fallback scan), the later ones take the sorted check
+    monkeypatch.setenv("AMC_SCAN_TAIL", shape)
+    ks, var = workloads.trace_zipf(3 * (1 << 20) + 5, 20_000, seed=97, device="cuda")
+    check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 20_000)
 
 
-def test_candidates_prefix_padded(amc, oracle_mod, monkeypatch):
-    # fewer candidates (937, all on one variable) than the 2^16-op prefix:
-    # the rest of the prefix is Noops on variable 0
-    monkeypatch.setenv("AMC_SCAN_TAIL", "15,20")
-    monkeypatch.setenv("AMC_SCAN_TAIL_PREFIX", "16")
-    nv = 20_000
-    n_ops = (1 << 15) + 600_000
-    i = np.arange(n_ops)
-    ks = np.full(n_ops, 0x10, np.uint8)
-    var = (i % (nv - 1)).astype(np.int32)
-    tail = (i >= (1 << 15)) & (i % 640 == 0)
-    ks[tail] = np.where(i[tail] % 3 == 0, 0x00, 0x01)
-    var[tail] = nv - 1
+def test_long_run_across_sort_tiles(amc, oracle_mod, monkeypatch):
+    # a tenth of the ops are CPU reads and writes of variable 7 (and no other
+    # op is), so it never faults: in the last epoch its ~97,000 candidates span
+    # many 4,096-pair tiles of the sorted check (the carry between tiles),
+    # beside a Zipf background; the earlier epochs overflow into the fallback
+    monkeypatch.setenv("AMC_SCAN_TAIL", "15,-2")
+    rng = np.random.default_rng(98)
+    nv = 40_000
+    ks, var = workloads.trace_random(rng, 1_500_001, nv, zipf_s=1.05)
+    var[var == 7] = 8
+    hot = rng.random(ks.size) < 0.1
+    ks[hot] = rng.integers(0, 2, int(hot.sum())).astype(np.uint8)     # CPU r / w
+    var[hot] = 7
     check(amc, oracle_mod, ks, var, nv)
+
+
+def test_first_part_with_faults_and_initial_statuses(amc, oracle_mod, monkeypatch):
+    # first part 2^16 ops over 20,000 variables with every initial status,
+    # uniform ids (about three ops per variable there), epochs of 2^16 ops
+    monkeypatch.setenv("AMC_SCAN_TAIL", "16,16")
+    rng = np.random.default_rng(99)
+    nv = 20_000
+    ks, var = workloads.trace_random(rng, 400_000, nv)
+    init = rng.integers(0, 5, nv).astype(np.uint8)
+    check(amc, oracle_mod, ks, var, nv, init)
+
+
+def test_bad_input_in_the_first_part(amc, monkeypatch):
+    monkeypatch.setenv("AMC_SCAN_TAIL", "14,14")
+    dev = torch.device("cuda")
+    n, nv = 50_000, 20_000
+    ks = torch.zeros(n, dtype=torch.uint8, device=dev)
+    var = torch.arange(n, dtype=torch.int32, device=dev) % nv
+    var[100] = -3                                  # id out of range, in the first part
+    amc.check_trace(ks, var, nv)
+    assert amc.sync_status() == amc.E_RANGE
+    var[100] = 5
+    ks[2_000] = 0x68                               # malformed byte
+    amc.check_trace(ks, var, nv)
+    assert amc.sync_status() == amc.E_INVALID
+    ks[2_000] = 0x16                               # GT (GPU side) in a plain check, not before its EN
+    amc.check_trace(ks, var, nv)
+    assert amc.sync_status() == amc.E_INVALID
+    assert amc.sync_status() == 0
