@@ -749,8 +749,10 @@ int launch_dense_range(const ScanLaunch& L, int max_chunks, int64_t n_follow, ui
 // First faults of a prefix and the suffix after it: the prefix's where it has
 // one, else the suffix's moved by the prefix length.
 __global__ void merge_faults_kernel(int32_t* __restrict__ vff, const int32_t* __restrict__ vff_suffix, int32_t n_vars,
-                                    int64_t* __restrict__ ff, const int64_t* __restrict__ ff_suffix, int64_t P)
+                                    int64_t* __restrict__ ff, const int64_t* __restrict__ ff_suffix, int64_t P,
+                                    const int* only_if)
 {
+    if (only_if && *only_if == 0) return;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v < n_vars && vff[v] == -1 && vff_suffix[v] != -1) vff[v] = (int32_t)(vff_suffix[v] + P);
     if (v == 0 && *ff == -1 && *ff_suffix != -1) *ff = *ff_suffix + P;
@@ -860,7 +862,7 @@ int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
     rc = launch_scan_trace(B, s);
     if (rc) return rc;
     merge_faults_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(L.vff, vff_suffix, L.n_vars,
-                                                                           L.first_fault, ff_suffix, P);
+                                                                           L.first_fault, ff_suffix, P, nullptr);
     if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
     if (L.profile & 2) profile_end(s);
     return AMC_OK;
@@ -875,10 +877,10 @@ int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 }
 
 int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, int64_t* ff,
-                        const int64_t* ff_part, int64_t offset, cudaStream_t s)
+                        const int64_t* ff_part, int64_t offset, cudaStream_t s, const int* only_if)
 {
     merge_faults_kernel<<<(unsigned)((n_vars + 255) / 256 > 0 ? (n_vars + 255) / 256 : 1), 256, 0, s>>>(
-        vff, vff_part, n_vars, ff, ff_part, offset);
+        vff, vff_part, n_vars, ff, ff_part, offset, only_if);
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 

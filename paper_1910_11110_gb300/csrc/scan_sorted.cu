@@ -12,7 +12,9 @@
 //   1. pairs: key = variable id, value = index of the op in the set << 4 | its
 //      kind and side (4 bits);
 //   2. LSD radix sort by key, 7-bit digits; per pass a histogram per tile of
-//      4,096 pairs, one exclusive scan over (digit, tile), and a stable scatter
+//      4,096 pairs, an exclusive scan of each digit's row over the tiles (one
+//      CTA per digit; the digits' totals are scanned by every scatter CTA),
+//      and a stable scatter
 //      (each pair's rank from per-thread digit counters in shared memory over a
 //      blocked arrangement, the tile staged in shared memory in digit order);
 //   3. segmented scan over the sorted pairs: every tile's aggregate of its
@@ -110,48 +112,28 @@ __global__ void __launch_bounds__(SNT) ss_hist_kernel(const uint32_t* __restrict
     }
 }
 
-// (2) exclusive scan of hist[0 .. SRAD * n_tiles) in place, one CTA: warp w
-// owns a contiguous stretch and walks it 32 entries at a time.
-__global__ void __launch_bounds__(1024) ss_hscan_kernel(uint32_t* __restrict__ hist, const int64_t* n_dev,
-                                                        int64_t cap, const int* gate)
+// (2) CTA d: exclusive scan of digit d's row hist[d * n_tiles, + n_tiles) in
+// place; the row's total to dtot[d]
+__global__ void __launch_bounds__(1024) ss_hscan_kernel(uint32_t* __restrict__ hist, uint32_t* __restrict__ dtot,
+                                                        const int64_t* n_dev, int64_t cap, const int* gate)
 {
-    __shared__ uint32_t wbase[32];
+    __shared__ int tmp[1024 / 32 + 1];
     if (gated(gate)) return;
     const int64_t n = set_count(n_dev, cap);
-    const int64_t tot = (n + ST - 1) / ST * SRAD;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t per = (tot + 31) / 32;
-    const int64_t lo = warp * per, hi = lo + per < tot ? lo + per : tot;
+    const int64_t nt = (n + ST - 1) / ST;
+    uint32_t* row = hist + (int64_t)blockIdx.x * nt;
+    const int64_t per = (nt + 1023) / 1024;
+    const int64_t lo = threadIdx.x * per, hi = lo + per < nt ? lo + per : nt;
     uint32_t s = 0;
-    for (int64_t i = lo + lane; i < hi; i += 32) s += hist[i];
-#pragma unroll
-    for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-    if (lane == 0) wbase[warp] = s;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = wbase[lane];
-        uint32_t incl = w;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        wbase[lane] = incl - w;
+    for (int64_t i = lo; i < hi; ++i) s += row[i];
+    int total = 0;
+    uint32_t run = (uint32_t)block_excl_sum<1024>((int)s, tmp, &total);
+    for (int64_t i = lo; i < hi; ++i) {
+        const uint32_t x = row[i];
+        row[i] = run;
+        run += x;
     }
-    __syncthreads();
-    uint32_t run = wbase[warp];
-    for (int64_t i0 = lo; i0 < hi; i0 += 32) {
-        const int64_t i = i0 + lane;
-        const uint32_t x = i < hi ? hist[i] : 0u;
-        uint32_t incl = x;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        if (i < hi) hist[i] = run + incl - x;
-        run += __shfl_sync(0xffffffffu, incl, 31);
-    }
+    if (threadIdx.x == 0) dtot[blockIdx.x] = (uint32_t)total;
 }
 
 // (3) stable scatter of one pass.  Counters: thread t's count of digit d sits
@@ -162,15 +144,22 @@ __global__ void __launch_bounds__(SNT, 3) ss_scatter_kernel(const uint32_t* __re
                                                          const uint32_t* __restrict__ vin,
                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          const int64_t* n_dev, int64_t cap, int shift,
-                                                         const uint32_t* __restrict__ hist, const int* gate)
+                                                         const uint32_t* __restrict__ hist,
+                                                         const uint32_t* __restrict__ dtot, const int* gate)
 {
     extern __shared__ __align__(16) uint32_t sm[];          // CPHYS counter words, then the staged tile
     __shared__ uint32_t gbase[SRAD];
+    __shared__ uint32_t dpre[SRAD];                         // pairs of all tiles with a smaller digit
     __shared__ int tmp[SNT / 32 + 1];
     if (gated(gate)) return;
     const int64_t n = set_count(n_dev, cap);
     const int64_t nt = (n + ST - 1) / ST;
     const int t = threadIdx.x;
+    {
+        const int x = t < SRAD ? (int)dtot[t] : 0;
+        const int e = block_excl_sum<SNT>(x, tmp, nullptr);
+        if (t < SRAD) dpre[t] = (uint32_t)e;
+    }
     for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         const int64_t b = tile * ST;
         const int m = (int)(n - b < ST ? n - b : ST);
@@ -216,7 +205,7 @@ __global__ void __launch_bounds__(SNT, 3) ss_scatter_kernel(const uint32_t* __re
             const int p = cphys((int)(d & (CROWS - 1)) * SNT);
             const uint32_t sh = (d >> 6) * 16;
             const uint32_t dstart = ((sm[p] >> sh) & 0xFFFFu) + (sh ? low_total : 0u);
-            gbase[t] = hist[(int64_t)t * nt + tile] - dstart;
+            gbase[t] = dpre[t] + hist[(int64_t)t * nt + tile] - dstart;
         }
         __syncthreads();
         uint32_t* sk = sm;
@@ -494,7 +483,7 @@ int key_bits_of(int32_t n_vars)
 size_t sorted_check_scratch_bytes(int64_t cap)
 {
     const size_t nt = (size_t)((cap + ST - 1) / ST);
-    return align_up(4 * SRAD * nt, 256) + 2 * align_up(nt, 256);
+    return align_up(4 * SRAD * nt, 256) + align_up(4 * SRAD, 256) + 2 * align_up(nt, 256);
 }
 
 int launch_ss_keys(const uint8_t* kind_side, const int32_t* var, int64_t n, int64_t n_after, int32_t n_vars,
@@ -528,6 +517,8 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     uint8_t* w = static_cast<uint8_t*>(C.scratch);
     uint32_t* hist = reinterpret_cast<uint32_t*>(w);
     w += align_up(4 * SRAD * (size_t)tiles, 256);
+    uint32_t* dtot = reinterpret_cast<uint32_t*>(w);
+    w += align_up(4 * SRAD, 256);
     uint8_t* tagg = w;
     w += align_up((size_t)tiles, 256);
     uint8_t* carry = w;
@@ -538,9 +529,9 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
         const int src = ps & 1;
         const int shift = ps * SDIG;
         ss_hist_kernel<<<grid(8), SNT, 0, s>>>(C.key[src], C.n_dev, C.cap, shift, hist, C.gate);
-        ss_hscan_kernel<<<1, 1024, 0, s>>>(hist, C.n_dev, C.cap, C.gate);
+        ss_hscan_kernel<<<SRAD, 1024, 0, s>>>(hist, dtot, C.n_dev, C.cap, C.gate);
         ss_scatter_kernel<<<grid(3), SNT, smem, s>>>(C.key[src], C.val[src], C.key[src ^ 1], C.val[src ^ 1],
-                                                     C.n_dev, C.cap, shift, hist, C.gate);
+                                                     C.n_dev, C.cap, shift, hist, dtot, C.gate);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
     }
     SegParams p;

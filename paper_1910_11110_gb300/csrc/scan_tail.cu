@@ -100,7 +100,7 @@ int64_t cand_cap(int64_t E)
 
 struct TailLayout {
     int64_t K = 0;        // pairs the sort buffers hold: the first part or an epoch's candidates
-    size_t st0, st1, bm, cnt, off, ncand, ovf, fvff, fff;
+    size_t st0, st1, bm, cnt, off, coff, ncand, ovf, fvff, fff;
     size_t region;        // shared region: pairs and slots, or the fallback scan
     size_t key0, val0, pos, key1, val1, sks, svar, spos, scratch;   // offsets inside the region
     size_t total;
@@ -126,6 +126,7 @@ TailLayout tail_layout(const TailShape& sh, int32_t n_vars, int64_t n_ops)
     t.bm = take(4 * (size_t)((n_vars + 31) / 32));
     t.cnt = take(4 * n_chunks);
     t.off = take(4 * n_chunks);
+    t.coff = take(4 * n_chunks);
     t.ncand = take(8);
     t.ovf = take(4);
     t.fvff = take(4 * (size_t)n_vars);
@@ -354,26 +355,19 @@ __global__ void __launch_bounds__(1024) tail_blocksum_kernel(const uint32_t* __r
     }
 }
 
-// Chunk slots -> the candidates as pairs for the sorted check (variable,
-// candidate index << 4 | code) and their positions in the epoch, in position
-// order.  Block b takes
+// Offsets of the chunks' candidates in the compacted set, in position order.  Block b takes
 // chunks [1024 b, 1024 b + 1024): its base is the sum of the earlier blocks'
 // counts, its chunks' offsets a block scan; each warp copies 32 chunks.  Every
 // block also forms the grand total, so all agree on an overflow (more
 // candidates than the compacted trace holds, or a chunk with more than its
 // slots): then nothing is copied and the epoch's fallback scan runs instead.
-__global__ void __launch_bounds__(1024) tail_gather_kernel(const uint8_t* __restrict__ sks,
-                                                           const int32_t* __restrict__ svar,
-                                                           const uint16_t* __restrict__ spos,
-                                                           const uint32_t* __restrict__ cnt, int n_chunks,
-                                                           const uint32_t* __restrict__ bsum, int n_blocks,
-                                                           int64_t cap, uint32_t* __restrict__ ckey,
-                                                           uint32_t* __restrict__ cval, uint32_t* __restrict__ cpos,
-                                                           int64_t* __restrict__ n_cand, int* ovf)
+__global__ void __launch_bounds__(1024) tail_offsets_kernel(const uint32_t* __restrict__ cnt, int n_chunks,
+                                                            const uint32_t* __restrict__ bsum, int n_blocks,
+                                                            int64_t cap, uint32_t* __restrict__ coff,
+                                                            int64_t* __restrict__ n_cand, int* ovf)
 {
     __shared__ unsigned long long rb[32], rt[32];
     __shared__ uint32_t wsum[32];
-    __shared__ uint32_t offs[1024];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = blockIdx.x;
     unsigned long long before = 0, total = 0;
@@ -427,14 +421,26 @@ __global__ void __launch_bounds__(1024) tail_gather_kernel(const uint8_t* __rest
         wsum[lane] = v;                      // inclusive over warps
     }
     __syncthreads();
-    offs[tid] = (uint32_t)before + (warp > 0 ? wsum[warp - 1] : 0u) + incl - x;
-    __syncthreads();
-    for (int k = warp * 32; k < warp * 32 + 32; ++k) {
-        const int c = b * 1024 + k;
-        if (c >= n_chunks) break;
-        const uint32_t nk = cnt[c], o = offs[k];
+    if (i < n_chunks) coff[i] = (uint32_t)before + (warp > 0 ? wsum[warp - 1] : 0u) + incl - x;
+}
+
+// Warp per chunk: its slots to [coff[c], coff[c] + cnt[c]) of the pairs.
+__global__ void __launch_bounds__(256) tail_gather_kernel(const uint8_t* __restrict__ sks,
+                                                          const int32_t* __restrict__ svar,
+                                                          const uint16_t* __restrict__ spos,
+                                                          const uint32_t* __restrict__ cnt,
+                                                          const uint32_t* __restrict__ coff, int n_chunks,
+                                                          uint32_t* __restrict__ ckey, uint32_t* __restrict__ cval,
+                                                          uint32_t* __restrict__ cpos, const int* ovf)
+{
+    if (*ovf) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = w0; c < n_chunks; c += nw) {
+        const uint32_t nk = cnt[c], o = coff[c];
         for (uint32_t j = lane; j < nk; j += 32) {
-            const int64_t src = (int64_t)c * TF_SLOTS + j;
+            const int64_t src = c * TF_SLOTS + j;
             ckey[o + j] = (uint32_t)svar[src];
             cval[o + j] = (o + j) << 4 | sorted_code_of(sks[src]);
             cpos[o + j] = (uint32_t)c * (uint32_t)TF_CHUNK + spos[src];
@@ -468,6 +474,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     uint32_t* bm = reinterpret_cast<uint32_t*>(w + lay.bm);
     uint32_t* cnt = reinterpret_cast<uint32_t*>(w + lay.cnt);
     uint32_t* bsum = reinterpret_cast<uint32_t*>(w + lay.off);    // candidates per 1024 chunks
+    uint32_t* coff = reinterpret_cast<uint32_t*>(w + lay.coff);   // first candidate of each chunk
     int64_t* ncand = reinterpret_cast<int64_t*>(w + lay.ncand);
     int* ovf = reinterpret_cast<int*>(w + lay.ovf);
     int32_t* fvff = reinterpret_cast<int32_t*>(w + lay.fvff);
@@ -558,8 +565,9 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         const int n_blocks = (n_chunks + 1023) / 1024;
         const int64_t C = cand_cap(n);
         tail_blocksum_kernel<<<n_blocks, 1024, 0, s>>>(cnt, n_chunks, bsum);
-        tail_gather_kernel<<<n_blocks, 1024, 0, s>>>(sks, svar, spos, cnt, n_chunks, bsum, n_blocks, C, key0, val0,
-                                                     cpos, ncand, ovf);
+        tail_offsets_kernel<<<n_blocks, 1024, 0, s>>>(cnt, n_chunks, bsum, n_blocks, C, coff, ncand, ovf);
+        const int ggrid = (int)min((int64_t)n_sm * 8, ((int64_t)n_chunks + 7) / 8);
+        tail_gather_kernel<<<ggrid, 256, 0, s>>>(sks, svar, spos, cnt, coff, n_chunks, key0, val0, cpos, ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // the candidates, at most C (count on the device), from the epoch's
         // start statuses; gated off when they overflowed
@@ -602,7 +610,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         F.profile = 0;
         rc = launch_scan_trace(F, s);
         if (rc) return rc;
-        rc = launch_merge_faults(L.vff, fvff, L.n_vars, L.first_fault, fff, e0, s);
+        rc = launch_merge_faults(L.vff, fvff, L.n_vars, L.first_fault, fff, e0, s, ovf);
         if (rc) return rc;
         cur ^= 1;
         e0 = e1;

@@ -1483,6 +1483,9 @@ template <typename KeyT, int T, int NT>
 __global__ void __launch_bounds__(NT, MAX_CTAS_PER_SM) scan_trace_kernel(const ScanParams p)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
+    // gated off: return before touching the tile counter or any other state
+    // (a gated launch's set-up is gated the same way, so that state is stale)
+    if (p.gate && ((*p.gate != 0) != (p.gate_on != 0))) return;
     ScanSmem<KeyT, T, NT>& S = *reinterpret_cast<ScanSmem<KeyT, T, NT>*>(smem_raw);
     uint32_t* fsm = reinterpret_cast<uint32_t*>(smem_raw + sizeof(ScanSmem<KeyT, T, NT>));
     const int tid = threadIdx.x;
@@ -1611,8 +1614,9 @@ __global__ void finalize_trace_kernel(int32_t* __restrict__ vff, const uint32_t*
 // Variables whose initial status is F are stuck before the first op: their
 // bits go into both copies of the stuck bitmap before the scan starts.
 __global__ void seed_stuck_kernel(const uint8_t* __restrict__ init, int32_t n_vars, uint32_t* __restrict__ fbits,
-                                  int fbits_words)
+                                  int fbits_words, const int* gate, int gate_on)
 {
+    if (gate && ((*gate != 0) != (gate_on != 0))) return;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool f = v < n_vars && init[v] == ST_F;
     const uint32_t m = __ballot_sync(0xffffffffu, f);
@@ -1620,6 +1624,41 @@ __global__ void seed_stuck_kernel(const uint8_t* __restrict__ init, int32_t n_va
         const int64_t w = v >> 5;
         fbits[w] = m;
         fbits[w + fbits_words] = m;
+    }
+}
+
+// The set-up of a gated launch, done on the device so that a launch gated off
+// costs no memsets: list heads, first faults and the global first fault to -1,
+// registration bits and the tile counter / frontier to 0, both copies of the
+// stuck bitmap from the initial statuses (F: stuck before the first op).
+__global__ void gated_init_kernel(const int* gate, int gate_on, uint32_t* __restrict__ head,
+                                  int32_t* __restrict__ vff, int32_t n_vars, int64_t* __restrict__ ff,
+                                  uint32_t* __restrict__ regbits, int64_t reg_words, uint32_t* __restrict__ fbits,
+                                  int64_t f_words, const uint8_t* __restrict__ init,
+                                  uint32_t* __restrict__ tile_counter)
+{
+    if ((*gate != 0) != (gate_on != 0)) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t v = g; v < n_vars; v += stride) {
+        head[v] = NIL;
+        vff[v] = -1;
+    }
+    for (int64_t w = g; w < reg_words; w += stride) regbits[w] = 0;
+    for (int64_t w = g; w < f_words; w += stride) {            // f_words per copy
+        uint32_t m = 0;
+        if (init)
+            for (int j = 0; j < 32; ++j) {
+                const int64_t v = 32 * w + j;
+                if (v < n_vars && init[v] == ST_F) m |= 1u << j;
+            }
+        fbits[w] = m;
+        fbits[w + f_words] = m;
+    }
+    if (g == 0) {
+        *ff = -1;
+        tile_counter[0] = 0;
+        tile_counter[1] = 0;
     }
 }
 
@@ -1775,17 +1814,31 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.bulk_ok = ((uintptr_t)L.kind_side % 16 == 0) && ((uintptr_t)L.var % 16 == 0) &&
                 ((uintptr_t)L.step % 16 == 0);
 
-    if (cudaMemsetAsync(p.head, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
-    if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
-    if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
+    if (L.gate) {
+        // a gated launch (the epoch path's fallback) sets itself up on the device
+        const int64_t nw = L.n_vars > (int64_t)(fbytes / 4) ? L.n_vars : (int64_t)(fbytes / 4);
+        const int nb = (int)((nw + 255) / 256 < 4096 ? (nw + 255) / 256 : 4096);
+        gated_init_kernel<<<nb > 0 ? nb : 1, 256, 0, s>>>(L.gate, L.gate_on, p.head, L.vff, L.n_vars,
+                                                          L.first_fault, p.regbits, L.n_ops > 0 ? regbytes / 4 : 0,
+                                                          p.fbits, L.n_ops > 0 ? p.fbits_words : 0, L.init,
+                                                          p.tile_counter);
+        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    } else {
+        if (cudaMemsetAsync(p.head, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaMemsetAsync(L.vff, 0xFF, 4 * (size_t)L.n_vars, s) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaMemsetAsync(L.first_fault, 0xFF, 8, s) != cudaSuccess) return AMC_E_CUDA;
+    }
     if (L.n_ops > 0) {
-        if (cudaMemsetAsync(p.regbits, 0, regbytes, s) != cudaSuccess) return AMC_E_CUDA;
-        if (fbytes && cudaMemsetAsync(p.fbits, 0, fbytes, s) != cudaSuccess) return AMC_E_CUDA;
-        if (L.init && L.n_vars > 0) {
-            seed_stuck_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(L.init, L.n_vars, p.fbits, p.fbits_words);
+        if (!L.gate) {
+            if (cudaMemsetAsync(p.regbits, 0, regbytes, s) != cudaSuccess) return AMC_E_CUDA;
+            if (fbytes && cudaMemsetAsync(p.fbits, 0, fbytes, s) != cudaSuccess) return AMC_E_CUDA;
+        }
+        if (L.init && L.n_vars > 0 && !L.gate) {
+            seed_stuck_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(L.init, L.n_vars, p.fbits,
+                                                                                p.fbits_words, L.gate, L.gate_on);
             if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         }
-        if (cudaMemsetAsync(p.tile_counter, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
+        if (!L.gate && cudaMemsetAsync(p.tile_counter, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
         // keys pack (var << 12 | position): 32-bit while var ids fit 20 bits
         const int rc = kb + POS_BITS <= 32 ? launch_kernel<uint32_t>(p, L, s) : launch_kernel<uint64_t>(p, L, s);
         if (rc) return rc;

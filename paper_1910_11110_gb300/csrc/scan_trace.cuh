@@ -90,9 +90,9 @@ size_t scan_prefix_workspace_bytes(int64_t P, int32_t n_vars);
 bool scan_forced_prefix(const ScanLaunch& L);
 // First faults of a check of ops [offset, ...) folded into those of the ops
 // before it: vff[v] = vff_part[v] + offset where vff[v] is -1 and vff_part[v]
-// is not; the same for *ff.
+// is not; the same for *ff.  With only_if, nothing happens while *only_if == 0.
 int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, int64_t* ff,
-                        const int64_t* ff_part, int64_t offset, cudaStream_t s);
+                        const int64_t* ff_part, int64_t offset, cudaStream_t s, const int* only_if = nullptr);
 // Traces over 16,385 to 2^20 variables and of 2^29 ops or more, without a
 // guard: the first 2^20 ops checked by sorting them by variable, the rest in
 // epochs that each end at four times their start (stream filter on the stuck
