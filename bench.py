@@ -574,9 +574,9 @@ def run_serve(args):
 
 
 def tail_epochs(n_ops):
-    """Epochs of the long-trace path at its default shape (first part 2^20
+    """Epochs of the long-trace path at its default shape (first part 2^22
     ops, each epoch ending at four times its start)."""
-    e0, k = 1 << 20, 0
+    e0, k = 1 << 22, 0
     while e0 < n_ops:
         e0, k = min(e0 << 2, n_ops), k + 1
     return k
@@ -589,7 +589,7 @@ def trace_kernels(n_ops, n_vars):
     variables from 2^24 ops that path on the first 2^22 ops, then the stuck
     bitmap seeded from its final statuses, the single-pass scan, the final
     statuses and the first-fault merge (7 kernels); from 2^29 ops the first
-    2^20 ops as pairs sorted by variable (pairs, 3 radix passes of histogram,
+    2^22 ops as pairs sorted by variable (pairs, 3 radix passes of histogram,
     scan and scatter, then the segmented scan's reduce, carry and apply: 13
     kernels), then per epoch the stuck bitmap, stream filter, block sums,
     chunk offsets, gather, the candidates' sorted check (12), the gated
@@ -602,7 +602,7 @@ def trace_kernels(n_ops, n_vars):
     if n_vars <= 16384 and n_ops >= (1 << 20):
         return "dense reduce + carry + apply kernels", 3
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 29) and os.environ.get("AMC_SCAN_TAIL", "") != "0":
-        return ("first 2^20 ops: sorted check (radix sort by variable + segmented scan); epochs to 4x their "
+        return ("first 2^22 ops: sorted check (radix sort by variable + segmented scan); epochs to 4x their "
                 "start: tail_filter_kernel + gather + sorted check of the candidates"), 13 + 21 * tail_epochs(n_ops)
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
         return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7

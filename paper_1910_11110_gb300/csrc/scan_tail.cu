@@ -37,7 +37,7 @@ constexpr int64_t CAND_MAX = (int64_t)1 << 27;   // and at most 2^27 (set index 
 constexpr int TF_PER = 16;                // ops per lane and step
 constexpr int TAIL_MIN_VARS = 16385;      // fewer variables take the reduce / carry / apply path
 constexpr int TAIL_MAX_VARS = 1 << 20;    // bitmap of 128 KB in shared memory
-constexpr int DEFAULT_FIRST_LOG2 = 20;    // first part 2^20 ops,
+constexpr int DEFAULT_FIRST_LOG2 = 22;    // first part 2^22 ops,
 constexpr int DEFAULT_GROW = 2;           // then epochs ending at 4 times their start
 constexpr int64_t DEFAULT_MIN_OPS = (int64_t)1 << 29;
 
@@ -424,26 +424,51 @@ __global__ void __launch_bounds__(1024) tail_offsets_kernel(const uint32_t* __re
     if (i < n_chunks) coff[i] = (uint32_t)before + (warp > 0 ? wsum[warp - 1] : 0u) + incl - x;
 }
 
-// Warp per chunk: its slots to [coff[c], coff[c] + cnt[c]) of the pairs.
+// Warp per G consecutive chunks (G a power of two up to 32, larger where the
+// epoch has many chunks and few candidates each), whose candidates are
+// contiguous in the compacted set: lane L copies entries L, L + 32, ... of
+// that stretch (the stores coalesce), finding each entry's chunk by a binary
+// search over the G chunks' prefix counts, which lanes 0..G-1 hold.
 __global__ void __launch_bounds__(256) tail_gather_kernel(const uint8_t* __restrict__ sks,
                                                           const int32_t* __restrict__ svar,
                                                           const uint16_t* __restrict__ spos,
                                                           const uint32_t* __restrict__ cnt,
                                                           const uint32_t* __restrict__ coff, int n_chunks,
                                                           uint32_t* __restrict__ ckey, uint32_t* __restrict__ cval,
-                                                          uint32_t* __restrict__ cpos, const int* ovf)
+                                                          uint32_t* __restrict__ cpos, int G, const int* ovf)
 {
     if (*ovf) return;
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = w0; c < n_chunks; c += nw) {
-        const uint32_t nk = cnt[c], o = coff[c];
-        for (uint32_t j = lane; j < nk; j += 32) {
-            const int64_t src = c * TF_SLOTS + j;
-            ckey[o + j] = (uint32_t)svar[src];
-            cval[o + j] = (o + j) << 4 | sorted_code_of(sks[src]);
-            cpos[o + j] = (uint32_t)c * (uint32_t)TF_CHUNK + spos[src];
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * G < n_chunks; g += nw) {
+        const int64_t c = g * G + lane;
+        const bool mine = lane < G && c < n_chunks;
+        const uint32_t nk = mine ? cnt[c] : 0u;
+        const uint32_t base = __shfl_sync(0xffffffffu, mine ? coff[c] : 0u, 0);
+        uint32_t incl = nk;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - nk;
+        for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+            const uint32_t idx = i0 + lane;
+            int k = 0;                                      // largest k < G with excl_k <= idx
+            for (int step = G >> 1; step; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, excl, k + step);
+                if (e <= idx) k += step;
+            }
+            const uint32_t first = __shfl_sync(0xffffffffu, excl, k);
+            if (idx < total) {
+                const int64_t ch = g * G + k;
+                const int64_t src = ch * TF_SLOTS + (idx - first);
+                const uint32_t o = base + idx;
+                ckey[o] = (uint32_t)svar[src];
+                cval[o] = o << 4 | sorted_code_of(sks[src]);
+                cpos[o] = (uint32_t)ch * (uint32_t)TF_CHUNK + spos[src];
+            }
         }
     }
 }
@@ -566,8 +591,11 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         const int64_t C = cand_cap(n);
         tail_blocksum_kernel<<<n_blocks, 1024, 0, s>>>(cnt, n_chunks, bsum);
         tail_offsets_kernel<<<n_blocks, 1024, 0, s>>>(cnt, n_chunks, bsum, n_blocks, C, coff, ncand, ovf);
-        const int ggrid = (int)min((int64_t)n_sm * 8, ((int64_t)n_chunks + 7) / 8);
-        tail_gather_kernel<<<ggrid, 256, 0, s>>>(sks, svar, spos, cnt, coff, n_chunks, key0, val0, cpos, ovf);
+        int G = 1;                                   // chunks per gather warp: about 8,192 warps
+        while (G < 32 && n_chunks / (2 * G) >= 8192) G *= 2;
+        const int64_t groups = ((int64_t)n_chunks + G - 1) / G;
+        const int ggrid = (int)min((int64_t)n_sm * 8, (groups + 7) / 8);
+        tail_gather_kernel<<<ggrid, 256, 0, s>>>(sks, svar, spos, cnt, coff, n_chunks, key0, val0, cpos, G, ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // the candidates, at most C (count on the device), from the epoch's
         // start statuses; gated off when they overflowed

@@ -94,7 +94,7 @@ bool scan_forced_prefix(const ScanLaunch& L);
 int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, int64_t* ff,
                         const int64_t* ff_part, int64_t offset, cudaStream_t s, const int* only_if = nullptr);
 // Traces over 16,385 to 2^20 variables and of 2^29 ops or more, without a
-// guard: the first 2^20 ops checked by sorting them by variable, the rest in
+// guard: the first 2^22 ops checked by sorting them by variable, the rest in
 // epochs that each end at four times their start (stream filter on the stuck
 // bitmap, the compacted candidates checked by sorting them by variable from
 // the epoch's start statuses); its scratch replaces the single-pass workspace
