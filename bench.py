@@ -590,11 +590,11 @@ def trace_kernels(n_ops, n_vars):
     bitmap seeded from its final statuses, the single-pass scan, the final
     statuses and the first-fault merge (7 kernels); from 2^29 ops the first
     2^22 ops as pairs sorted by variable (pairs, 3 radix passes of histogram,
-    scan and scatter, then the segmented scan's reduce, carry and apply: 13
-    kernels), then per epoch the stuck bitmap, stream filter, block sums,
-    chunk offsets, gather, the candidates' sorted check (12), the gated
-    fallback scan (set-up, scan, final statuses) and the gated first-fault
-    merge (21 kernels); else the scan and the final statuses."""
+    scan and scatter, then the single-pass segmented scan: 11 kernels), then
+    per epoch the stuck bitmap, stream filter, block sums, chunk offsets,
+    gather, the candidates' sorted check (10), the gated fallback scan
+    (set-up, scan, final statuses) and the gated first-fault merge (19
+    kernels); else the scan and the final statuses."""
     if os.environ.get("AMC_SCAN_DENSE", "") == "0":
         return "scan_trace_kernel", 2
     if n_vars <= 8192 and n_ops >= (1 << 20):
@@ -603,7 +603,7 @@ def trace_kernels(n_ops, n_vars):
         return "dense reduce + carry + apply kernels", 3
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 29) and os.environ.get("AMC_SCAN_TAIL", "") != "0":
         return ("first 2^22 ops: sorted check (radix sort by variable + segmented scan); epochs to 4x their "
-                "start: tail_filter_kernel + gather + sorted check of the candidates"), 13 + 21 * tail_epochs(n_ops)
+                "start: tail_filter_kernel + gather + sorted check of the candidates"), 11 + 19 * tail_epochs(n_ops)
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
         return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7
     return "scan_trace_kernel", 2

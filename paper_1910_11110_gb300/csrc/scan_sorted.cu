@@ -17,9 +17,9 @@
 //      and a stable scatter
 //      (each pair's rank from per-thread digit counters in shared memory over a
 //      blocked arrangement, the tile staged in shared memory in digit order);
-//   3. segmented scan over the sorted pairs: every tile's aggregate of its
-//      trailing run, one CTA scans the tile aggregates (the carry into each
-//      tile's leading run), then every op's prefix is formed and applied.
+//   3. segmented scan over the sorted pairs in one pass (decoupled look-back
+//      over the tiles' published values gives the carry into each tile's
+//      leading run), every op's prefix applied to its variable's entry status.
 // Outputs: the status of every op whose status is not F (the caller has
 // written F at every position of the set), the first fault of each variable
 // that faults in the set, the global first fault, and the final statuses.
@@ -286,8 +286,9 @@ struct SegParams {
     int32_t* vff;
     int64_t* ff;
     int64_t offset;
-    uint8_t* tagg;              // [n_tiles] trailing-run aggregate of each tile
-    uint8_t* carry;             // [n_tiles] element carried into each tile's leading run
+    uint32_t* tstat;            // [n_tiles] published scan value of each tile (zeroed before)
+    uint32_t* tile_counter;     // tiles claimed so far (zeroed before)
+    int* err;
     Tables tab;
 };
 
@@ -322,83 +323,65 @@ __device__ __forceinline__ void thread_run(const SegParams& p, const SegTables& 
     R.agg = a;
 }
 
-// (4) trailing-run aggregate of every tile
-__global__ void __launch_bounds__(SNT) ss_seg_reduce_kernel(const SegParams p)
+// (4) every pair's prefix, applied to its variable's entry status, in one
+// pass: CTAs claim tiles in order; a tile publishes its aggregate (the fold of
+// its trailing run, and whether a run starts inside), then looks back over the
+// earlier tiles' published values until one that covers everything before it
+// (an inclusive value, or an aggregate in which a run starts), publishes its
+// inclusive value and carries the exclusive one into its leading run.  A
+// claimed tile belongs to a running CTA that publishes its aggregate before it
+// waits on anything, so every look-back ends; the wait is bounded all the same
+// (AMC_E_TIMEOUT).
+constexpr uint32_t TS_AGG = 1u << 30, TS_INCL = 2u << 30, TS_FLAGS = 3u << 30, TS_VAL = 0x1FFu;
+
+__global__ void __launch_bounds__(SNT) ss_seg_kernel(const SegParams p)
 {
     __shared__ SegTables S;
     __shared__ uint32_t wtot[SNT / 32];
+    __shared__ uint32_t s_tile, s_carry;
     if (gated(p.gate)) return;
     load_seg_tables(S, p.tab);
     __syncthreads();
     const int64_t n = set_count(p.n_dev, p.cap);
     const int64_t nt = (n + ST - 1) / ST;
-    for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(p.tile_counter, 1u);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= nt) break;
         const int64_t b = tile * ST;
         const int m = (int)(n - b < ST ? n - b : ST);
         ThreadRun R;
         thread_run(p, S, n, b, m, R);
         uint32_t all;
-        seg_block_excl(R.agg, S.id, S.comp, wtot, &all);
-        if (threadIdx.x == 0) p.tagg[tile] = (uint8_t)((all & 31u) | ((all >> 1) & 0x80u));
-    }
-}
-
-// (5) one CTA: exclusive segmented scan of the tile aggregates; the carry into
-// tile t is the scan's element when t's first pair continues the run of the
-// pair before it, else the identity.
-__global__ void __launch_bounds__(1024) ss_seg_carry_kernel(const SegParams p)
-{
-    __shared__ uint8_t comp[MAX_ELEMS * MAX_ELEMS];
-    __shared__ uint32_t wtot[32];
-    if (gated(p.gate)) return;
-    for (int i = threadIdx.x; i < MAX_ELEMS * MAX_ELEMS; i += blockDim.x) comp[i] = p.tab.comp[i];
-    __syncthreads();
-    const uint32_t ID = p.tab.identity;
-    const int64_t n = set_count(p.n_dev, p.cap);
-    const int64_t nt = (n + ST - 1) / ST;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t per = (nt + 1023) / 1024;
-    const int64_t lo = threadIdx.x * per, hi = lo + per < nt ? lo + per : nt;
-    auto unpack = [](uint8_t a) { return (uint32_t)(a & 31u) | ((uint32_t)(a & 0x80u) << 1); };
-    uint32_t s = ID;
-    for (int64_t t = lo; t < hi; ++t) s = seg_combine(s, unpack(p.tagg[t]), comp);
-    uint32_t incl = s;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl = seg_combine(y, incl, comp);
-    }
-    uint32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
-    if (lane == 0) ex = ID;
-    if (lane == 31) wtot[warp] = incl;
-    __syncthreads();
-    uint32_t pre = ID;
-    for (int w = 0; w < warp; ++w) pre = seg_combine(pre, wtot[w], comp);
-    uint32_t run = seg_combine(pre, ex, comp);
-    for (int64_t t = lo; t < hi; ++t) {
-        const bool cont = t > 0 && p.key[t * ST - 1] == p.key[t * ST];
-        p.carry[t] = (uint8_t)(cont ? (run & 31u) : ID);
-        run = seg_combine(run, unpack(p.tagg[t]), comp);
-    }
-}
-
-// (6) every pair's prefix, applied to its variable's entry status
-__global__ void __launch_bounds__(SNT) ss_seg_apply_kernel(const SegParams p)
-{
-    __shared__ SegTables S;
-    __shared__ uint32_t wtot[SNT / 32];
-    if (gated(p.gate)) return;
-    load_seg_tables(S, p.tab);
-    __syncthreads();
-    const int64_t n = set_count(p.n_dev, p.cap);
-    const int64_t nt = (n + ST - 1) / ST;
-    for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-        const int64_t b = tile * ST;
-        const int m = (int)(n - b < ST ? n - b : ST);
-        ThreadRun R;
-        thread_run(p, S, n, b, m, R);
-        const uint32_t ex = seg_block_excl(R.agg, S.id, S.comp, wtot, nullptr);
-        const uint32_t c = p.carry[tile];
+        const uint32_t ex = seg_block_excl(R.agg, S.id, S.comp, wtot, &all);
+        if (threadIdx.x == 0) {
+            uint32_t carry = S.id;
+            if (tile == 0) {
+                st_release(p.tstat, TS_INCL | (all & TS_VAL));
+            } else {
+                st_release(p.tstat + tile, TS_AGG | (all & TS_VAL));
+                uint32_t prefix = S.id;                   // over tiles [t2, tile), earlier ones folded in front
+                for (int64_t t2 = tile - 1; t2 >= 0; --t2) {
+                    uint32_t v = 0;
+                    for (uint32_t it = 0; it < (1u << 24); ++it) {
+                        v = ld_acquire(p.tstat + t2);
+                        if (v & TS_FLAGS) break;
+                    }
+                    if (!(v & TS_FLAGS)) {
+                        if (p.err) raise_error(p.err, AMC_E_TIMEOUT);
+                        break;
+                    }
+                    prefix = seg_combine(v & TS_VAL, prefix, S.comp);
+                    if ((v & TS_INCL) || (v & 0x100u)) break;
+                }
+                st_release(p.tstat + tile, TS_INCL | (seg_combine(prefix, all, S.comp) & TS_VAL));
+                if (p.key[b - 1] == p.key[b]) carry = prefix & 31u;
+            }
+            s_carry = carry;
+        }
+        __syncthreads();
+        const uint32_t c = s_carry;
         uint32_t run = (ex & 0x100u) ? (ex & 31u) : S.comp[c * MAX_ELEMS + (ex & 31u)];
         const int64_t i0 = b + threadIdx.x * SE;
         const uint32_t after = (i0 + SE < n) ? p.key[i0 + SE] : NOKEY;
@@ -427,6 +410,7 @@ __global__ void __launch_bounds__(SNT) ss_seg_apply_kernel(const SegParams p)
             const uint32_t next = u + 1 < SE ? R.k[u + 1] : after;
             if (next != kv) p.fin[kv] = (uint8_t)post;
         }
+        __syncthreads();
     }
 }
 
@@ -483,7 +467,7 @@ int key_bits_of(int32_t n_vars)
 size_t sorted_check_scratch_bytes(int64_t cap)
 {
     const size_t nt = (size_t)((cap + ST - 1) / ST);
-    return align_up(4 * SRAD * nt, 256) + align_up(4 * SRAD, 256) + 2 * align_up(nt, 256);
+    return align_up(4 * SRAD * nt, 256) + align_up(4 * SRAD, 256) + align_up(4 * nt, 256) + 256;
 }
 
 int launch_ss_keys(const uint8_t* kind_side, const int32_t* var, int64_t n, int64_t n_after, int32_t n_vars,
@@ -519,9 +503,9 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     w += align_up(4 * SRAD * (size_t)tiles, 256);
     uint32_t* dtot = reinterpret_cast<uint32_t*>(w);
     w += align_up(4 * SRAD, 256);
-    uint8_t* tagg = w;
-    w += align_up((size_t)tiles, 256);
-    uint8_t* carry = w;
+    uint32_t* tstat = reinterpret_cast<uint32_t*>(w);
+    w += align_up(4 * (size_t)tiles, 256);
+    uint32_t* tile_counter = reinterpret_cast<uint32_t*>(w);
 
     const int kb = key_bits_of(C.n_vars);
     const int passes = (kb + SDIG - 1) / SDIG;
@@ -547,12 +531,13 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     p.vff = C.vff;
     p.ff = C.ff;
     p.offset = C.offset;
-    p.tagg = tagg;
-    p.carry = carry;
+    p.tstat = tstat;
+    p.tile_counter = tile_counter;
+    p.err = C.err;
     p.tab = host_tables();
-    ss_seg_reduce_kernel<<<grid(8), SNT, 0, s>>>(p);
-    ss_seg_carry_kernel<<<1, 1024, 0, s>>>(p);
-    ss_seg_apply_kernel<<<grid(8), SNT, 0, s>>>(p);
+    if (cudaMemsetAsync(tstat, 0, 4 * (size_t)tiles, s) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemsetAsync(tile_counter, 0, 4, s) != cudaSuccess) return AMC_E_CUDA;
+    ss_seg_kernel<<<grid(8), SNT, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 

@@ -556,6 +556,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     A.vff = L.vff;
     A.ff = L.first_fault;
     A.scratch = scratch;
+    A.err = L.err;
     rc = launch_sorted_check(A, s);
     if (rc) return rc;
 
@@ -618,6 +619,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         K.ff = L.first_fault;
         K.offset = e0;
         K.scratch = scratch;
+        K.err = L.err;
         rc = launch_sorted_check(K, s);
         if (rc) return rc;
         // fallback, gated on by an overflow: the single-pass scan over all the

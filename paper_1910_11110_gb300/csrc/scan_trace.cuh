@@ -125,6 +125,7 @@ struct SortedCheck {
     int64_t* ff = nullptr;
     int64_t offset = 0;
     void* scratch = nullptr;            // sorted_check_scratch_bytes(cap)
+    int* err = nullptr;                 // device error word (an expired bounded wait)
 };
 // 4-bit code of an op byte in a pair: kind (bits 0-2) and side (bit 3)
 __host__ __device__ __forceinline__ uint32_t sorted_code_of(uint32_t ks) { return (ks & 7u) | ((ks >> 1) & 8u); }
