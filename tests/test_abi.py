@@ -81,3 +81,24 @@ def test_workspace_sizes_at_the_bench_size(libamc):
     assert 18 * (1 << 25) < h < 48 * (1 << 25)
     assert libamc.amc_check_trace_host_workspace(n, v, 1 << 20) < h
     assert libamc.amc_check_trace_host_workspace(-1, v, 0) == 0
+
+
+def test_epoch_shape_follows_its_override(libamc, monkeypatch):
+    # the long-trace path's shape (first part, epochs) is host logic read per
+    # call: the workspace query follows AMC_SCAN_TAIL without a GPU (the query
+    # is the larger of the single-pass and the epoch path's needs)
+    libamc.amc_check_trace_workspace.restype = ctypes.c_size_t
+    libamc.amc_check_trace_workspace.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    ws = libamc.amc_check_trace_workspace
+    n, v = 3 << 20, 1 << 20
+    monkeypatch.delenv("AMC_SCAN_TAIL", raising=False)
+    plain, few = ws(n, v), ws(n, 16_384)     # below 2^29 ops: no epoch path
+    monkeypatch.setenv("AMC_SCAN_TAIL", "16,-2")
+    assert ws(n, v) > plain                  # forced: pairs for 2^16 ops, slots for epochs to 3 * 2^20
+    assert ws(n, 16_384) == few              # too few variables: the path is not taken
+    monkeypatch.setenv("AMC_SCAN_TAIL", "0")
+    assert ws(n, v) == plain                 # "0" switches the path off
+    monkeypatch.setenv("AMC_SCAN_TAIL", "30,-2")
+    assert ws(n, v) == plain                 # a first part beyond 2^27 ops is not accepted
+    monkeypatch.setenv("AMC_SCAN_TAIL", "16,-7")
+    assert ws(n, v) == plain                 # nor a growth beyond 2^4
