@@ -45,11 +45,13 @@ def lib():
         i64, i32 = ctypes.c_int64, ctypes.c_int32
         _lib.oracle_apply.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib.oracle_check_trace.argtypes = [P, P, i64, i32, P, P, P, P, P]
+        _lib.oracle_check_trace_shard.argtypes = [P, P, i64, i32, i32, i32, P, P, P, P]
         _lib.oracle_check_program.argtypes = [P, P, i64, i32, P, P, P, P]
         _lib.oracle_check_batch.argtypes = [P, P, P, P, P, i64, P, P, P]
         _lib.oracle_overlaps.argtypes = [P, P, i32, P, P, i64]
         _lib.oracle_vectorpu.argtypes = [P, P, i32, P, P, i64, P, P, ctypes.c_int,
                                          P, P, i64, P, P, P, P, P, P]
+        _lib.oracle_well_declared.argtypes = [P, i32, P, P, i64, P, P, P, P, P, P, P, P]
     return _lib
 
 
@@ -83,6 +85,36 @@ def check_trace(kind_side, var, n_vars, init_status=None):
     _check(lib().oracle_check_trace(_ptr(ks), _ptr(v), n, n_vars, _ptr(init),
                                     _ptr(step), _ptr(final), _ptr(vff), _ptr(ff)))
     return step, final, vff, int(ff[0])
+
+
+def check_trace_sharded(kind_side, var, n_vars, n_threads):
+    """Trace mode on n_threads host threads: thread t runs the oracle over the
+    whole trace for the variables v % n_threads == t (the ctypes calls release
+    the GIL).  Same outputs as check_trace with all-(V,I) initial statuses."""
+    import threading
+    ks = np.ascontiguousarray(kind_side, dtype=np.uint8)
+    v = np.ascontiguousarray(var, dtype=np.int32)
+    n = ks.shape[0]
+    step = np.empty(n, np.uint8)
+    final = np.empty(n_vars, np.uint8)
+    vff = np.empty(n_vars, np.int32)
+    ffs = np.empty(n_threads, np.int64)
+    rcs = [0] * n_threads
+    L = lib()
+
+    def run(t):
+        rcs[t] = L.oracle_check_trace_shard(_ptr(ks), _ptr(v), n, n_vars, n_threads, t, _ptr(step), _ptr(final),
+                                            _ptr(vff), ffs[t:].ctypes.data_as(ctypes.c_void_p))
+
+    th = [threading.Thread(target=run, args=(t,)) for t in range(n_threads)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    for rc in rcs:
+        _check(rc)
+    f = ffs[ffs >= 0]
+    return step, final, vff, int(f.min()) if f.size else -1
 
 
 def check_program(tok, payload, n_vars, init_mask=None):
@@ -164,3 +196,23 @@ def vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd_mode,
         return dict(kind_side=ks[:n].copy(), var=var[:n].copy(), step_status=step[:n].copy(),
                     call_first_op=cfo, final_status=final, var_first_fault=vff,
                     first_fault=int(ff[0]))
+
+
+def well_declared(arr_loc_off, loc_owner, call_tok_off, tok, payload, call_am_off, am_array, am_mode):
+    """Static well-declaredness of calls AM{S}.  Returns (violations uint32 [C],
+    first_bad int64 [C], first_unmet int32 [C]); see oracle.h."""
+    alo = np.ascontiguousarray(arr_loc_off, dtype=np.int64)
+    own = np.ascontiguousarray(loc_owner, dtype=np.int32)
+    cto = np.ascontiguousarray(call_tok_off, dtype=np.int64)
+    t = np.ascontiguousarray(tok, dtype=np.uint8)
+    p = np.ascontiguousarray(payload, dtype=np.int32)
+    cao = np.ascontiguousarray(call_am_off, dtype=np.int64)
+    aa = np.ascontiguousarray(am_array, dtype=np.int32)
+    am = np.ascontiguousarray(am_mode, dtype=np.uint8)
+    n_calls = cto.shape[0] - 1
+    viol = np.empty(n_calls, np.uint32)
+    bad = np.empty(n_calls, np.int64)
+    unmet = np.empty(n_calls, np.int32)
+    _check(lib().oracle_well_declared(_ptr(alo), alo.shape[0] - 1, _ptr(own), _ptr(cto), n_calls, _ptr(t), _ptr(p),
+                                      _ptr(cao), _ptr(aa), _ptr(am), _ptr(viol), _ptr(bad), _ptr(unmet)))
+    return viol, bad, unmet

@@ -186,6 +186,47 @@ int oracle_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_o
     return 0;
 }
 
+/* The same check restricted to the variables v with v % n_shards == shard:
+ * every op is read, ops on other variables are skipped (a variable's statuses
+ * depend only on its own ops, Fig. Opsem rules Effect / Remote Effect), and
+ * only the outputs of those variables are written: step_status at their
+ * positions, final_status / var_first_fault at their ids, *first_fault = the
+ * smallest of their first faults.  Used to run the oracle on several host
+ * threads at once; traces with GT are rejected (-1). */
+int oracle_check_trace_shard(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
+                             int32_t n_vars, int32_t n_shards, int32_t shard,
+                             uint8_t* step_status, uint8_t* final_status,
+                             int32_t* var_first_fault, int64_t* first_fault)
+{
+    if (n_ops < 0 || n_vars < 0 || n_ops > INT32_MAX || n_shards < 1 || shard < 0 || shard >= n_shards)
+        return -1;
+    uint8_t* st = (uint8_t*)malloc((size_t)(n_vars ? n_vars : 1));
+    if (!st) return -3;
+    for (int32_t v = shard; v < n_vars; v += n_shards) {
+        st[v] = (uint8_t)encode((pair_t){ V, I });                          /* sigma_0 */
+        var_first_fault[v] = -1;
+    }
+    int64_t ff = -1;
+    for (int64_t i = 0; i < n_ops; i++) {
+        const int32_t v = var[i];
+        if (v < 0 || v >= n_vars) { free(st); return -2; }
+        if (v % n_shards != shard) continue;
+        if (!valid_trace_byte(kind_side[i]) || (kind_side[i] & 15) > K_PW) { free(st); return -1; }
+        int k = kind_side[i] & 15, side = kind_side[i] >> 4;
+        int before = st[v], after = oracle_apply(k, side, before);
+        st[v] = (uint8_t)after;
+        step_status[i] = (uint8_t)after;
+        if (after == ST_F && before != ST_F) {
+            if (var_first_fault[v] < 0) var_first_fault[v] = (int32_t)i;
+            if (ff < 0) ff = i;
+        }
+    }
+    for (int32_t v = shard; v < n_vars; v += n_shards) final_status[v] = st[v];
+    *first_fault = ff;
+    free(st);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Relation mode: status sets, If = union of branches, While = closure       */
 /* ------------------------------------------------------------------------ */
@@ -548,4 +589,131 @@ int oracle_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_
     free(shadow);
     free(shadow_list);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Static well-declaredness (Section 3.3: Definitions "Occurs in all         */
+/* execution paths" and "Well-declared program"; Section 3.5: Definition     */
+/* "Well-declared program with array access").                               */
+/* ------------------------------------------------------------------------ */
+
+/* Whether the op "w on side `side` of location loc" occurs in all execution
+ * paths of the statement sequence [lo, hi).  Conditions are opaque, so every
+ * branch of an If and every iteration count of a While (zero included) is a
+ * path: a sequence has the op on all paths when one of its items has; an op
+ * item when it is that op; an If when both branches have; a While never (its
+ * body may run zero times).  Returns 1 / 0, or -1 on malformed tokens. */
+static int wd_must_write(const uint8_t* tok, const int32_t* payload, int64_t lo, int64_t hi,
+                         int32_t loc, int side, int depth)
+{
+    if (depth > ORACLE_MAX_DEPTH) return -1;
+    int found = 0;
+    int64_t i = lo;
+    while (i < hi) {
+        int k = tok[i] & 15, sd = (tok[i] >> 4) & 1;
+        if (k <= K_NOOP) {
+            if (k == K_W && sd == side && payload[i] == loc) found = 1;
+            i++;
+        } else if (k == T_IF) {
+            int64_t e = i + 1 + payload[i];
+            if (payload[i] < 0 || e >= hi || tok[e] != T_ELSE || sd) return -1;
+            int64_t end = e + 1 + payload[e];
+            if (payload[e] < 0 || end >= hi || tok[end] != T_END) return -1;
+            int a = wd_must_write(tok, payload, i + 1, e, loc, side, depth + 1);
+            int b = wd_must_write(tok, payload, e + 1, end, loc, side, depth + 1);
+            if (a < 0 || b < 0) return -1;
+            if (a && b) found = 1;
+            i = end + 1;
+        } else if (k == T_WHILE) {
+            int64_t end = i + 1 + payload[i];
+            if (payload[i] < 0 || end >= hi || tok[end] != T_END || sd) return -1;
+            int a = wd_must_write(tok, payload, i + 1, end, loc, side, depth + 1);   /* validates the body */
+            if (a < 0) return -1;
+            i = end + 1;
+        } else {
+            return -1;
+        }
+    }
+    return found;
+}
+
+int oracle_well_declared(const int64_t* arr_loc_off, int32_t n_arrays, const int32_t* loc_owner,
+                         const int64_t* call_tok_off, int64_t n_calls, const uint8_t* tok,
+                         const int32_t* payload, const int64_t* call_am_off, const int32_t* am_array,
+                         const uint8_t* am_mode, uint32_t* violations, int64_t* first_bad,
+                         int32_t* first_unmet)
+{
+    if (n_arrays < 0 || n_calls < 0) return -1;
+    const int64_t n_locs = arr_loc_off[n_arrays];
+    for (int32_t a = 0; a < n_arrays; a++) {
+        if (arr_loc_off[a + 1] < arr_loc_off[a]) return -1;
+        for (int64_t l = arr_loc_off[a]; l < arr_loc_off[a + 1]; l++)
+            if (loc_owner[l] != a) return -1;
+    }
+    for (int64_t c = 0; c < n_calls; c++) {
+        const int64_t t0 = call_tok_off[c], t1 = call_tok_off[c + 1];
+        const int64_t m0 = call_am_off[c], m1 = call_am_off[c + 1];
+        if (t1 < t0 || m1 < m0) return -1;
+        uint32_t viol = 0;
+        int64_t bad = -1;
+        int32_t unmet = -1;
+        if (wd_must_write(tok, payload, t0, t1, -1, 0, 0) < 0) return -1;   /* structure well formed */
+        /* the declarations: an array may appear once (Section 3.3, syntax of AM) */
+        for (int64_t j = m0; j < m1; j++) {
+            if (am_array[j] < 0 || am_array[j] >= n_arrays) return -2;
+            int md = am_mode[j] & 15;
+            if ((am_mode[j] & 0xE0) || md < 1 || md > 3) return -1;
+            for (int64_t j2 = m0; j2 < j; j2++)
+                if (am_array[j2] == am_array[j]) viol |= 16u;
+        }
+        /* every statement of the body against the declarations */
+        for (int64_t i = t0; i < t1; i++) {
+            int k = tok[i] & 15, sd = (tok[i] >> 4) & 1;
+            if (tok[i] & 0xE0) return -1;
+            if (k > K_NOOP) {
+                if (k == K_PW || k == K_GT || k == K_EN) return -1;   /* not statements of a body */
+                continue;                                           /* structure tokens */
+            }
+            if (k == K_NOOP) continue;
+            if (payload[i] < 0 || payload[i] >= n_locs) return -2;
+            uint32_t v = 0;
+            if (k == K_PUSH || k == K_PULL) {
+                v = 1u;                                   /* no Push / Pull in a function body */
+            } else {
+                const int32_t a = loc_owner[payload[i]];
+                int ok = 0;
+                for (int64_t j = m0; j < m1; j++) {
+                    if (am_array[j] != a || ((am_mode[j] >> 4) & 1) != sd) continue;
+                    int md = am_mode[j] & 15;
+                    if (k == K_W && (md == 2 || md == 3)) ok = 1;       /* W or RW */
+                    if (k == K_R && (md == 1 || md == 3)) ok = 1;       /* R or RW */
+                }
+                if (!ok) v = k == K_W ? 2u : 4u;
+            }
+            if (v) {
+                viol |= v;
+                if (bad < 0) bad = i - t0;
+            }
+        }
+        /* W obligations: every location of the array written, on the declared
+         * side, in all execution paths of the body */
+        for (int64_t j = m0; j < m1; j++) {
+            if ((am_mode[j] & 15) != 2) continue;
+            const int32_t a = am_array[j];
+            const int side = (am_mode[j] >> 4) & 1;
+            for (int64_t l = arr_loc_off[a]; l < arr_loc_off[a + 1]; l++) {
+                int r = wd_must_write(tok, payload, t0, t1, (int32_t)l, side, 0);
+                if (r < 0) return -1;
+                if (!r) {
+                    viol |= 8u;
+                    if (unmet < 0 || a < unmet) unmet = a;
+                    break;
+                }
+            }
+        }
+        violations[c] = viol;
+        first_bad[c] = bad;
+        first_unmet[c] = unmet;
+    }
+    return 0;
 }

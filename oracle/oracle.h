@@ -39,6 +39,13 @@ int oracle_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_o
                        uint8_t* step_status, uint8_t* final_status,
                        int32_t* var_first_fault, int64_t* first_fault);
 
+/* oracle_check_trace restricted to the variables v % n_shards == shard (core
+ * kinds only, initial statuses (V,I)); outputs written for those variables. */
+int oracle_check_trace_shard(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
+                             int32_t n_vars, int32_t n_shards, int32_t shard,
+                             uint8_t* step_status, uint8_t* final_status,
+                             int32_t* var_first_fault, int64_t* first_fault);
+
 /* Relation mode for one structured program (If = union, While = closure). */
 int oracle_check_program(const uint8_t* tok, const int32_t* payload, int64_t n_tok,
                          int32_t n_vars, const uint8_t* init_mask,
@@ -60,6 +67,26 @@ int oracle_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_
                     uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap, int64_t* out_n,
                     int64_t* call_first_op, uint8_t* step_status, uint8_t* final_status,
                     int32_t* var_first_fault, int64_t* first_fault);
+
+/* Static well-declaredness of VectorPU-style calls AM{S} (Section 3.3,
+ * Definitions "Occurs in all execution paths" and "Well-declared program";
+ * Section 3.5, "Well-declared program with array access").  Locations of
+ * array a are [arr_loc_off[a], arr_loc_off[a+1]) (loc_owner[l] = a; a scalar
+ * is an array of one location).  Call c has body tokens [call_tok_off[c],
+ * call_tok_off[c+1]) (ops r/w/Push/Pull/Noop on locations, IF/ELSE/WHILE/END
+ * as in relation mode) and declarations [call_am_off[c], call_am_off[c+1])
+ * (am_array, am_mode = mode (R 1, W 2, RW 3) | side << 4).  violations[c]:
+ * bit 0 Push / Pull in the body, bit 1 a write not declared W / RW on its
+ * side, bit 2 a read not declared R / RW on its side, bit 3 a W declaration
+ * whose array has a location not written on that side in all execution
+ * paths, bit 4 an array declared twice; first_bad[c] = call-relative token of
+ * the first bit 0-2 violation (-1 none); first_unmet[c] = smallest array id
+ * with a bit-3 violation (-1 none). */
+int oracle_well_declared(const int64_t* arr_loc_off, int32_t n_arrays, const int32_t* loc_owner,
+                         const int64_t* call_tok_off, int64_t n_calls, const uint8_t* tok,
+                         const int32_t* payload, const int64_t* call_am_off, const int32_t* am_array,
+                         const uint8_t* am_mode, uint32_t* violations, int64_t* first_bad,
+                         int32_t* first_unmet);
 
 #ifdef __cplusplus
 }

@@ -175,3 +175,17 @@ def test_uniform_workload_statistics(oracle_mod):
     step, final, vff, ff = oracle_mod.check_trace(ks, var, nv)
     assert 0.9 < np.mean(step == F) < 1.0
     assert ff >= 0
+
+
+@pytest.mark.parametrize("threads", [1, 3, 7])
+def test_sharded_driver_equals_whole(oracle_mod, threads):
+    # the multi-thread CPU baseline: each thread takes the variables v % T == t
+    # (statuses depend only on a variable's own ops); its outputs must be
+    # those of the one-thread check on every position and variable
+    rng = np.random.default_rng(31 + threads)
+    ks, var = workloads.trace_random(rng, 50_001, 997, zipf_s=1.05)
+    exp = oracle_mod.check_trace(ks, var, 997)
+    got = oracle_mod.check_trace_sharded(ks, var, 997, threads)
+    for e, g in zip(exp[:3], got[:3]):
+        assert np.array_equal(e, g)
+    assert exp[3] == got[3]

@@ -370,3 +370,30 @@ def test_dropped_annotations_can_fault(oracle_mod):
 def test_rejects_duplicate_operands(oracle_mod):
     with pytest.raises(oracle_mod.OracleError):
         run(oracle_mod, [(0, 4), (4, 4)], [(0, [(0, R), (0, W)])])
+
+
+@pytest.mark.parametrize("infer", [True, False])
+def test_abstract_variables_never_invalid_nor_stuck(oracle_mod, infer):
+    # Property Safety carried to the abstract variables of Section 3.5: only
+    # w x#, and the Pull / Push of a guard that found its side invalid, act on
+    # x#; w gives (V,I) or (I,V), and the guard's transfer runs only when the
+    # side is invalid, which from (V,I) / (I,V) / (V,V) means the other side
+    # is valid.  So no abstract variable reaches (I,I), and EN never gives F,
+    # with or without O(M) and whatever annotations are dropped (dropped ones
+    # add body accesses on real arrays only).  Overlapping arrays, drops at
+    # one in five.
+    rng = np.random.default_rng(81 if infer else 82)
+    A = 8
+    intervals = [(int(rng.integers(0, 200)), int(rng.integers(1, 80))) for _ in range(A)]
+    n_en = 0
+    for _ in range(20):
+        calls = random_calls(rng, A, 150, drop_p=0.2)
+        res = run(oracle_mod, intervals, calls, infer=infer)
+        abstract = res["var"] >= A
+        st = res["step_status"][abstract]
+        assert not np.isin(st, [II, F]).any()
+        en = (res["kind_side"] & 15) == K_EN
+        n_en += int(en.sum())
+        assert not (res["step_status"][en] == F).any()
+        assert not np.isin(res["final_status"][A:], [II, F]).any()
+    assert n_en > 100

@@ -17,6 +17,7 @@ Workloads (seeds fixed by the benchmark definition):
                   modes R/W/RW .5/.3/.2, 1e-4 dropped                    (seed 2)
   programs        100,000 If/While programs over 64-4,096 vars           (seed 3)
   serve_requests  Poisson arrivals of trace / program requests          (seed 4)
+  wd_calls        calls AM{S} for the static well-declaredness check    (seed 5)
 """
 from __future__ import annotations
 
@@ -54,6 +55,9 @@ def _clib():
         P = ctypes.c_void_p
         _lib.wl_program_sizes.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P]
         _lib.wl_program_fill.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, P, P, P]
+        _lib.wl_wd_sizes.argtypes = [P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, P, ctypes.c_double, P, P]
+        _lib.wl_wd_fill.argtypes = [P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, P, ctypes.c_double, P, P,
+                                    P, P, P, P]
     return _lib
 
 
@@ -197,6 +201,42 @@ def programs(n_progs: int = 100_000, seed: int = 3, first: int = 0, **kw):
     lib.wl_program_fill(_p(dp), _p(ip), seed, first, n_progs, _p(tok_off), _p(tok), _p(payload))
     return dict(tok=tok, payload=payload, prog_tok_off=tok_off, prog_nvars=n_vars,
                 n_leaf=n_leaf)
+
+
+# --------------------------------------------------------------------------
+# Calls AM{S} for the static well-declaredness check
+# --------------------------------------------------------------------------
+def wd_calls(n_calls: int = 1 << 20, n_arrays: int = 4096, len_range=(1, 64), seed: int = 5,
+             mode_p=(0.5, 0.3, 0.2), p_bad: float = 0.01):
+    """Arrays of len_range locations (uniform); per call one side, 1..4
+    declarations on distinct arrays (modes R / W / RW with mode_p) and a body
+    built from them (every location of a W array written, at top level or in
+    both branches of an If; 1..4 reads for R, reads and writes for RW, some in
+    a While; Noops); with probability p_bad one injected flaw (a W array
+    written in one branch or in a While only, an undeclared access, a read of
+    a W array, a Push).  Returns the CSR arrays of oracle.well_declared."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(len_range[0], len_range[1] + 1, n_arrays)
+    a_off = np.zeros(n_arrays + 1, np.int64)
+    np.cumsum(lens, out=a_off[1:])
+    owner = np.repeat(np.arange(n_arrays, dtype=np.int32), lens)
+    pm = np.array(mode_p, np.float64)
+    lib = _clib()
+    n_tok = np.empty(n_calls, np.int64)
+    n_decl = np.empty(n_calls, np.int32)
+    lib.wl_wd_sizes(_p(a_off), n_arrays, seed, n_calls, _p(pm), p_bad, _p(n_tok), _p(n_decl))
+    tok_off = np.zeros(n_calls + 1, np.int64)
+    np.cumsum(n_tok, out=tok_off[1:])
+    am_off = np.zeros(n_calls + 1, np.int64)
+    np.cumsum(n_decl, out=am_off[1:])
+    tok = np.empty(int(tok_off[-1]), np.uint8)
+    payload = np.empty(int(tok_off[-1]), np.int32)
+    am_array = np.empty(int(am_off[-1]), np.int32)
+    am_mode = np.empty(int(am_off[-1]), np.uint8)
+    lib.wl_wd_fill(_p(a_off), n_arrays, seed, n_calls, _p(pm), p_bad, _p(tok_off), _p(am_off), _p(tok), _p(payload),
+                   _p(am_array), _p(am_mode))
+    return dict(arr_loc_off=a_off, loc_owner=owner, call_tok_off=tok_off, tok=tok, payload=payload,
+                call_am_off=am_off, am_array=am_array, am_mode=am_mode)
 
 
 # --------------------------------------------------------------------------

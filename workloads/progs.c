@@ -167,3 +167,166 @@ void wl_program_fill(const double* params, const int64_t* iparams, uint64_t seed
         gen_program(&pp, seed, first + p, tok + tok_off[p], payload + tok_off[p], &nt, &nv, &nl);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Calls AM{S} for the static well-declaredness check: declarations over     */
+/* arrays of locations and a structured body built from them.               */
+/*   arrays: a owns locations [a_off[a], a_off[a+1]) (given by the caller)   */
+/*   per call (own SplitMix64 stream from (seed, call index)): one side; 1..4 */
+/*   declarations on distinct arrays, modes R / W / RW with p_mode[];        */
+/*   body items in a random order: for W, every location written, at top    */
+/*   level, or in both branches of an If; for R, 1..4 reads; for RW, reads   */
+/*   and writes; a Noop now and then.  With probability p_bad the call gets  */
+/*   one injected flaw: a W array written in one branch only, or inside a    */
+/*   While; a read or write of an undeclared array; a read of a W array; a   */
+/*   Push.                                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    rng_t rng;
+    uint8_t* tok;
+    int32_t* payload;
+    int64_t n;
+} wd_ctx;
+
+static void wput(wd_ctx* g, uint8_t t, int32_t p)
+{
+    if (g->tok) {
+        g->tok[g->n] = t;
+        g->payload[g->n] = p;
+    }
+    g->n++;
+}
+
+/* writes of every location of array a, in order */
+static void wd_write_all(wd_ctx* g, const int64_t* a_off, int32_t a, int side)
+{
+    for (int64_t l = a_off[a]; l < a_off[a + 1]; l++) wput(g, (uint8_t)(1 | side << 4), (int32_t)l);
+}
+
+static int64_t wd_call(wd_ctx* g, const int64_t* a_off, int32_t n_arrays, const double* p_mode, double p_bad,
+                       int32_t* am_array, uint8_t* am_mode)
+{
+    const int side = (int)uniform_int(&g->rng, 0, 1);
+    int nd = (int)uniform_int(&g->rng, 1, 4);
+    if (nd > n_arrays) nd = n_arrays;
+    int32_t arr[4];
+    int mode[4];
+    for (int i = 0; i < nd; i++) {
+        int32_t a;
+        int dup;
+        do {
+            a = (int32_t)uniform_int(&g->rng, 0, n_arrays - 1);
+            dup = 0;
+            for (int j = 0; j < i; j++) dup |= arr[j] == a;
+        } while (dup);
+        arr[i] = a;
+        double u = u01(&g->rng);
+        mode[i] = u < p_mode[0] ? 1 : (u < p_mode[0] + p_mode[1] ? 2 : 3);
+        if (am_array) {
+            am_array[i] = a;
+            am_mode[i] = (uint8_t)(mode[i] | side << 4);
+        }
+    }
+    const int bad = u01(&g->rng) < p_bad ? (int)uniform_int(&g->rng, 1, 5) : 0;
+    const int victim = (int)uniform_int(&g->rng, 0, nd - 1);
+    /* items in a random order: a permutation of the declarations */
+    int order[4] = {0, 1, 2, 3};
+    for (int i = nd - 1; i > 0; i--) {
+        int j = (int)uniform_int(&g->rng, 0, i);
+        int t = order[i];
+        order[i] = order[j];
+        order[j] = t;
+    }
+    for (int oi = 0; oi < nd; oi++) {
+        const int i = order[oi];
+        const int32_t a = arr[i];
+        const int64_t len = a_off[a + 1] - a_off[a];
+        if (mode[i] == 2) {
+            if (bad == 1 && i == victim) {               /* written in one branch only */
+                int64_t at = g->n;
+                wput(g, 8, 0);
+                int64_t b0 = g->n;
+                wd_write_all(g, a_off, a, side);
+                if (g->tok) g->payload[at] = (int32_t)(g->n - b0);
+                wput(g, 9, 1);
+                wput(g, (uint8_t)(4 | side << 4), (int32_t)a_off[a]);
+                wput(g, 11, 0);
+            } else if (bad == 2 && i == victim) {        /* written inside a While only */
+                int64_t at = g->n;
+                wput(g, 10, 0);
+                int64_t b0 = g->n;
+                wd_write_all(g, a_off, a, side);
+                if (g->tok) g->payload[at] = (int32_t)(g->n - b0);
+                wput(g, 11, 0);
+            } else if (u01(&g->rng) < 0.3) {             /* both branches write every location */
+                int64_t at = g->n;
+                wput(g, 8, 0);
+                int64_t b0 = g->n;
+                wd_write_all(g, a_off, a, side);
+                if (g->tok) g->payload[at] = (int32_t)(g->n - b0);
+                int64_t at2 = g->n;
+                wput(g, 9, 0);
+                int64_t b1 = g->n;
+                wd_write_all(g, a_off, a, side);
+                if (g->tok) g->payload[at2] = (int32_t)(g->n - b1);
+                wput(g, 11, 0);
+            } else {
+                wd_write_all(g, a_off, a, side);
+            }
+            if (bad == 3 && i == victim) wput(g, (uint8_t)(0 | side << 4), (int32_t)a_off[a]);   /* read under W */
+        } else {
+            const int nr = (int)uniform_int(&g->rng, 1, 4);
+            const int in_while = u01(&g->rng) < 0.2;
+            int64_t at = g->n;
+            if (in_while) wput(g, 10, 0);
+            int64_t b0 = g->n;
+            for (int r = 0; r < nr; r++) {
+                const int32_t l = (int32_t)(a_off[a] + uniform_int(&g->rng, 0, len - 1));
+                wput(g, (uint8_t)(0 | side << 4), l);
+                if (mode[i] == 3 && u01(&g->rng) < 0.5) wput(g, (uint8_t)(1 | side << 4), l);
+            }
+            if (in_while) {
+                if (g->tok) g->payload[at] = (int32_t)(g->n - b0);
+                wput(g, 11, 0);
+            }
+        }
+        if (u01(&g->rng) < 0.2) wput(g, (uint8_t)(4 | side << 4), (int32_t)a_off[a]);
+    }
+    if (bad == 4) {                                      /* an access to an undeclared array */
+        int32_t a;
+        int dup;
+        int tries = 0;
+        do {
+            a = (int32_t)uniform_int(&g->rng, 0, n_arrays - 1);
+            dup = 0;
+            for (int j = 0; j < nd; j++) dup |= arr[j] == a;
+        } while (dup && ++tries < 8);
+        wput(g, (uint8_t)((int)uniform_int(&g->rng, 0, 1) | side << 4), (int32_t)a_off[a]);
+    } else if (bad == 5) {
+        wput(g, (uint8_t)(2 | side << 4), (int32_t)a_off[arr[victim]]);          /* Push in a body */
+    }
+    return nd;
+}
+
+/* size pass: tokens and declarations per call */
+void wl_wd_sizes(const int64_t* a_off, int32_t n_arrays, uint64_t seed, int64_t n_calls, const double* p_mode,
+                 double p_bad, int64_t* n_tok, int32_t* n_decl)
+{
+    for (int64_t c = 0; c < n_calls; c++) {
+        wd_ctx g = {{seed * 0x9E3779B97F4A7C15ull + (uint64_t)c * 0xD1B54A32D192ED03ull}, NULL, NULL, 0};
+        n_decl[c] = (int32_t)wd_call(&g, a_off, n_arrays, p_mode, p_bad, NULL, NULL);
+        n_tok[c] = g.n;
+    }
+}
+
+/* fill pass, into CSR offsets computed from the size pass */
+void wl_wd_fill(const int64_t* a_off, int32_t n_arrays, uint64_t seed, int64_t n_calls, const double* p_mode,
+                double p_bad, const int64_t* tok_off, const int64_t* am_off, uint8_t* tok, int32_t* payload,
+                int32_t* am_array, uint8_t* am_mode)
+{
+    for (int64_t c = 0; c < n_calls; c++) {
+        wd_ctx g = {{seed * 0x9E3779B97F4A7C15ull + (uint64_t)c * 0xD1B54A32D192ED03ull}, tok + tok_off[c],
+                    payload + tok_off[c], 0};
+        wd_call(&g, a_off, n_arrays, p_mode, p_bad, am_array + am_off[c], am_mode + am_off[c]);
+    }
+}
