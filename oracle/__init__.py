@@ -52,6 +52,8 @@ def lib():
         _lib.oracle_vectorpu.argtypes = [P, P, i32, P, P, i64, P, P, ctypes.c_int,
                                          P, P, i64, P, P, P, P, P, P]
         _lib.oracle_well_declared.argtypes = [P, i32, P, P, i64, P, P, P, P, P, P, P, P]
+        _lib.oracle_apply_k.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        _lib.oracle_check_trace_k.argtypes = [P, P, i64, i32, i32, P, P, P, P, P]
     return _lib
 
 
@@ -115,6 +117,30 @@ def check_trace_sharded(kind_side, var, n_vars, n_threads):
         _check(rc)
     f = ffs[ffs >= 0]
     return step, final, vff, int(f.min()) if f.size else -1
+
+
+KL_F = 0x80  # stuck status of the k-location check
+
+
+def apply_k(op: int, status: int, k: int) -> int:
+    return lib().oracle_apply_k(op, status, k)
+
+
+def check_trace_k(op, var, n_vars, k, init_status=None):
+    """Traces over k memory locations.  Returns (step_status, final_status,
+    var_first_fault, first_fault); statuses are bit masks of valid locations,
+    0x80 = stuck."""
+    o = np.ascontiguousarray(op, dtype=np.uint8)
+    v = np.ascontiguousarray(var, dtype=np.int32)
+    n = o.shape[0]
+    init = None if init_status is None else np.ascontiguousarray(init_status, dtype=np.uint8)
+    step = np.empty(n, np.uint8)
+    final = np.empty(n_vars, np.uint8)
+    vff = np.empty(n_vars, np.int32)
+    ff = np.empty(1, np.int64)
+    _check(lib().oracle_check_trace_k(_ptr(o), _ptr(v), n, n_vars, k, _ptr(init), _ptr(step), _ptr(final),
+                                      _ptr(vff), _ptr(ff)))
+    return step, final, vff, int(ff[0])
 
 
 def check_program(tok, payload, n_vars, init_mask=None):

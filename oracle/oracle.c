@@ -717,3 +717,93 @@ int oracle_well_declared(const int64_t* arr_loc_off, int32_t n_arrays, const int
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* More than two memory locations (Section 3 states the results extend to    */
+/* many locations; the conclusion names it as future work).  The status of a */
+/* variable is a vector of k validity flags (location 0 = main memory, where */
+/* data starts, Section 3.2).  Each op runs at a location; the Section 3.1    */
+/* signatures, written for a vector instead of a pair:                       */
+/*   r at a:           flag a must be V; nothing changes                     */
+/*   w at a:           flag a becomes V, every other flag I                  */
+/*   copy a -> b:      flag a must be V; flag b becomes V (Push at a towards */
+/*                     b, or Pull at b from a; with k = 2, local 0 and       */
+/*                     remote 1: Push = copy 0->1, Pull = copy 1->0,         */
+/*                     rem Push = copy 1->0, rem Pull = copy 0->1)           */
+/*   Noop:             nothing changes                                       */
+/* A requirement that fails leaves the variable stuck (F), as in Property    */
+/* Progress.  Op byte: bits 0-1 kind (r 0, w 1, copy 2, Noop 3), bits 2-4   */
+/* location a, bits 5-7 location b (copy only; 0 otherwise, and a = 0 for    */
+/* Noop).  Status byte: bit i = flag of location i is V; F = 0x80; k <= 7.   */
+/* ------------------------------------------------------------------------ */
+enum { KL_R = 0, KL_W = 1, KL_COPY = 2, KL_NOOP = 3, KL_F = 0x80, KL_MAX = 7 };
+
+typedef struct { int valid[KL_MAX]; } kvec_t;
+
+static int kl_valid_byte(uint8_t op, int k)
+{
+    int kind = op & 3, a = (op >> 2) & 7, b = (op >> 5) & 7;
+    if (kind == KL_NOOP) return a == 0 && b == 0;
+    if (a >= k) return 0;
+    if (kind == KL_COPY) return b < k && b != a;
+    return b == 0;
+}
+
+/* status byte of applying op to status byte s (k locations) */
+int oracle_apply_k(int op, int s, int k)
+{
+    if (k < 1 || k > KL_MAX || !kl_valid_byte((uint8_t)op, k)) return -1;
+    if (s & KL_F) return KL_F;
+    kvec_t v = {{0}};
+    for (int i = 0; i < k; i++) v.valid[i] = (s >> i) & 1;
+    int kind = op & 3, a = (op >> 2) & 7, b = (op >> 5) & 7;
+    switch (kind) {
+    case KL_R:                                     /* (.., V_a, ..) -> same */
+        if (!v.valid[a]) return KL_F;
+        break;
+    case KL_W:                                     /* any -> V at a only */
+        for (int i = 0; i < k; i++) v.valid[i] = (i == a);
+        break;
+    case KL_COPY:                                  /* (.., V_a, ..) -> (.., V_b, ..) */
+        if (!v.valid[a]) return KL_F;
+        v.valid[b] = 1;
+        break;
+    default:                                       /* Noop */
+        break;
+    }
+    int out = 0;
+    for (int i = 0; i < k; i++) out |= v.valid[i] << i;
+    return out;
+}
+
+int oracle_check_trace_k(const uint8_t* op, const int32_t* var, int64_t n_ops, int32_t n_vars, int32_t k,
+                         const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                         int32_t* var_first_fault, int64_t* first_fault)
+{
+    if (n_ops < 0 || n_vars < 0 || k < 1 || k > KL_MAX) return -1;
+    for (int64_t i = 0; i < n_ops; i++) {
+        if (!kl_valid_byte(op[i], k)) return -1;
+        if (var[i] < 0 || var[i] >= n_vars) return -2;
+    }
+    uint8_t* st = (uint8_t*)malloc((size_t)(n_vars ? n_vars : 1));
+    if (!st) return -3;
+    for (int32_t v = 0; v < n_vars; v++) {
+        st[v] = init_status ? init_status[v] : (uint8_t)1;       /* valid in location 0 only */
+        if (st[v] != KL_F && (st[v] >> k)) { free(st); return -1; }
+        var_first_fault[v] = -1;
+    }
+    int64_t ff = -1;
+    for (int64_t i = 0; i < n_ops; i++) {
+        int v = var[i], before = st[v], after = oracle_apply_k(op[i], before, k);
+        st[v] = (uint8_t)after;
+        step_status[i] = (uint8_t)after;
+        if (after == KL_F && before != KL_F) {
+            if (var_first_fault[v] < 0) var_first_fault[v] = (int32_t)i;
+            if (ff < 0) ff = i;
+        }
+    }
+    for (int32_t v = 0; v < n_vars; v++) final_status[v] = st[v];
+    *first_fault = ff;
+    free(st);
+    return 0;
+}

@@ -88,6 +88,16 @@ int oracle_well_declared(const int64_t* arr_loc_off, int32_t n_arrays, const int
                          const uint8_t* am_mode, uint32_t* violations, int64_t* first_bad,
                          int32_t* first_unmet);
 
+/* Traces over k memory locations (k = 1..7): the Section 3.1 signatures on a
+ * vector of k validity flags.  Op byte: bits 0-1 kind (r 0, w 1, copy 2,
+ * Noop 3), bits 2-4 location a, bits 5-7 location b (copy a -> b only).
+ * Status byte: bit i = location i valid, 0x80 = F.  init_status NULL: valid
+ * in location 0 only.  Outputs as oracle_check_trace. */
+int oracle_apply_k(int op, int status, int k);
+int oracle_check_trace_k(const uint8_t* op, const int32_t* var, int64_t n_ops, int32_t n_vars, int32_t k,
+                         const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                         int32_t* var_first_fault, int64_t* first_fault);
+
 #ifdef __cplusplus
 }
 #endif
