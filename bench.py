@@ -1,17 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 access-mode consistency checker.
 
-One step = one amc_check_trace call over the 2^30-op, 2^20-variable Zipf(1.05)
-trace (kind mix r .40 / w .20 / Push .15 / Pull .15 / Noop .10, fair side,
-seed 1): every per-step status, final status and first fault.  Inputs (5.4 GB)
-are resident in HBM when the timed region starts and exceed L2, so no L2 flush
-is needed between steps.
+Headline step = one amc_check_trace call over the 2^30-op, 2^20-variable
+Zipf(1.05) trace (kind mix r .40 / w .20 / Push .15 / Pull .15 / Noop .10, fair
+side, seed 1): every per-step status, final status and first fault.  Inputs
+(5.4 GB) are resident in HBM when the timed region starts and exceed L2, so no
+L2 flush is needed between steps.
+
+The same JSON line carries, under "configs", the other workloads, each timed
+with CUDA events on its own stream with its clocks sampled and its oracle
+timed on the host cores beside it:
+  uniform_4096  16 variables, 4,096 uniform ops (seed 0): latency per check;
+  vectorpu      2^24 VectorPU calls over 4,096 overlapping arrays (seed 2):
+                translation + guarded check per step;
+  programs      100,000 If/While programs (seed 3): the batched persistent
+                launch (CUDA graph) against one launch per program;
+  serve         open-loop Poisson arrivals at 1k / 10k / 100k requests/s,
+                half traces and half programs, latency from the scheduled
+                arrival to the poll that sees the result.
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) each rank checks its own
 replica of the trace on its own GPU ("replicas only": the path has no exchange
-step); value = ops of all ranks / max time over ranks.
+step); value = ops of all ranks / max time over ranks; the sub-records run at
+N = 1 only.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload all|trace|uniform|vectorpu|programs|serve]
                   [--n-ops N] [--n-vars V] [--no-e2e] [--no-cpu]
 """
 from __future__ import annotations
@@ -44,12 +58,19 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=0, help="ops per chunk of the host-buffer check (0: 2^25)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=25.0)
-    ap.add_argument("--workload", default="trace", choices=["trace", "programs", "vectorpu", "serve"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "trace", "uniform", "programs", "vectorpu", "well_declared", "kloc", "serve"])
     ap.add_argument("--rates", default="1000,10000,100000")
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=10_000)
+    ap.add_argument("--serve-seconds", type=float, default=12.0, help="submission window per rate")
+    ap.add_argument("--serve-drain-seconds", type=float, default=20.0, help="wait for results after submitting")
     ap.add_argument("--n-progs", type=int, default=100_000, help="programs workload: number of programs")
-    ap.add_argument("--no-plain", action="store_true", help="programs workload: skip the one-launch-per-program run")
+    ap.add_argument("--plain-progs", type=int, default=2000,
+                    help="programs workload: programs timed with one launch each (0: none)")
+    ap.add_argument("--sub-steps", type=int, default=10, help="timed steps of each sub-record")
+    ap.add_argument("--sub-cpu-seconds", type=float, default=6.0)
+    ap.add_argument("--threads", type=int, default=0, help="host threads of the all-cores baseline (0: all)")
     return ap.parse_args()
 
 
@@ -179,6 +200,19 @@ def cpu_baseline(ks_host, var_host, n_vars, budget_s):
     what = "the whole trace" if m == len(ks_host) else f"the first {m} ops of the same trace"
     return {"value": reps * m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{what} ({m} ops), {reps} pass(es), single thread ({dt:.1f} s)"}
+
+
+def cpu_baseline_all(ks_host, var_host, n_vars, budget_s, threads):
+    """The oracle on `threads` host threads, each taking the variables
+    v % threads == t over the same prefix of the trace (every thread reads
+    every op), repeated for about budget_s seconds."""
+    import oracle
+    oracle.build()
+    m = min(len(ks_host), 1 << 28)
+    reps, dt = timed_calls(lambda: oracle.check_trace_sharded(ks_host[:m], var_host[:m], n_vars, threads), budget_s)
+    return {"value": reps * m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the first {m} ops of the same trace, {reps} pass(es), sharded by variable id modulo "
+                      f"{threads} over {threads} threads ({dt:.1f} s)"}
 
 
 def run_reference(args):
@@ -330,12 +364,13 @@ def run_ours(args):
     else:
         host_copy = None
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
         if host_copy is None:
             m = 1 << 26
             host_copy = (ks[:m].cpu().numpy(), var[:m].cpu().numpy())
         cpu = cpu_baseline(host_copy[0], host_copy[1], n_vars, args.cpu_seconds)
+        cpu_all = cpu_baseline_all(host_copy[0], host_copy[1], n_vars, args.cpu_seconds / 2, host_threads(args))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -351,11 +386,43 @@ def run_ours(args):
                              "kernel": trace_kernels(n_ops, n_vars)[0], "kernel_ms": k_ms,
                              "algorithmic_bytes": alg_bytes},
                 "gpu_launches": trace_kernels(n_ops, n_vars)[1] * args.steps,
-                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
-        print(json.dumps(line), flush=True)
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all}
     if world > 1:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         import torch.distributed as dist
         dist.destroy_process_group()
+        return
+    if args.workload == "all":
+        # the other workloads, after the trace's buffers are released
+        del ks, var, out, ws
+        if not args.no_e2e:
+            del ks_h, var_h, hout, hws
+        host_copy = None
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
+        line["configs"] = sub_records(args, amc, dev)
+    print(json.dumps(line), flush=True)
+
+
+def sub_records(args, amc, dev):
+    out = {}
+    for name, fn in (("uniform_4096", lambda: measure_uniform(args, amc, dev)),
+                     ("vectorpu", lambda: measure_vectorpu(args, amc, dev)),
+                     ("programs", lambda: measure_programs(args, amc, dev)),
+                     ("well_declared", lambda: measure_well_declared(args, amc, dev)),
+                     ("kloc", lambda: measure_kloc(args, amc, dev)),
+                     ("serve", lambda: measure_serve(args, amc, dev))):
+        import torch
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:            # one sub-record's failure does not hide the others
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    return out
 
 
 def ctypes_ptr(ev):
@@ -376,36 +443,191 @@ def timed(fn, steps, stream):
     return a.elapsed_time(b) / steps
 
 
-def base_line(args, value, ms, config, **extra):
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": config}
-    line.update(extra)
-    return line
+def host_threads(args):
+    return args.threads if args.threads > 0 else len(os.sched_getaffinity(0))
 
 
-def run_programs(args):
-    """Batched persistent launch (graph replay) vs one launch per program."""
+def roofline(alg_bytes, ms, note=None, bound="hbm"):
+    peak, kind = peaks()
+    ach = alg_bytes / (ms * 1e-3) / 1e9
+    r = {"bound": bound, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": kind,
+         "frac_of_8tbs": ach / 8000.0, "traffic": None, "algorithmic_bytes": int(alg_bytes)}
+    if note:
+        r["note"] = note
+    return r
+
+
+def timed_calls(fn, budget_s, min_calls=1):
+    """Calls fn() repeatedly for about budget_s seconds; returns (calls, seconds)."""
+    t0 = time.perf_counter()
+    fn()
+    one = max(time.perf_counter() - t0, 1e-6)
+    reps = max(min_calls, int(budget_s / one))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    return reps, time.perf_counter() - t0
+
+
+def measure_uniform(args, amc, dev):
+    """16 variables, 4,096 uniform ops (seed 0): latency of one check."""
     import numpy as np
     import torch
 
-    import paper_1910_11110_gb300 as amc
+    import oracle
     import workloads
-    torch.cuda.set_device(0)
-    amc.build()
+    ks_np, var_np, nv = workloads.trace_uniform(0)
+    n = len(ks_np)
+    ks, var = torch.from_numpy(ks_np).to(dev), torch.from_numpy(var_np).to(dev)
+    stream = torch.cuda.Stream()
+    out = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+               final_status=torch.empty(nv, dtype=torch.uint8, device=dev),
+               var_first_fault=torch.empty(nv, dtype=torch.int32, device=dev),
+               first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+    ws = torch.empty(amc.trace_workspace_bytes(n, nv) + 256, dtype=torch.uint8, device=dev)
+    ws = ws[(-ws.data_ptr()) % 256:]
+    step = lambda: amc.check_trace(ks, var, nv, out=out, workspace=ws, stream=stream)
+    for _ in range(20):
+        step()
+    assert amc.sync_status(stream) == 0
+    reps = 1000
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)          # us, each check alone on its stream
+    back = timed(step, reps, stream) * 1e3                          # us per check, back to back
+    clk = clocks.stop()
+    assert amc.sync_status(stream) == 0
+    exp = oracle.check_trace(ks_np, var_np, nv)
+    assert np.array_equal(out["step_status"].cpu().numpy(), exp[0]) and int(out["first_fault"].cpu()[0]) == exp[3]
+    # end to end: pinned host buffers, copies inside the call
+    ks_h, var_h = torch.from_numpy(ks_np).pin_memory(), torch.from_numpy(var_np).pin_memory()
+    hws = torch.empty(amc.trace_host_workspace_bytes(n, nv, 0) + 256, dtype=torch.uint8, device=dev)
+    hws = hws[(-hws.data_ptr()) % 256:]
+    e2e_step = lambda: (amc.check_trace_host(ks_h, var_h, nv, workspace=hws, stream=stream), stream.synchronize())
+    for _ in range(10):
+        e2e_step()
+    e_reps, e_s = timed_calls(e2e_step, 0.5, 100)
+    r_cpu, t_cpu = timed_calls(lambda: oracle.check_trace(ks_np, var_np, nv), 1.0, 100)
+    med = statistics.median(lat)
+    alg = 6 * n + 5 * nv
+    return {"workload": "uniform_trace", "n_ops": n, "n_vars": nv, "seed": 0,
+            "us_per_check_median": med, "us_per_check_best": lat[0], "us_per_check_p99": lat[int(0.99 * len(lat))],
+            "us_per_check_back_to_back": back, "checks": reps, "ops_per_s": n / (med * 1e-6),
+            "roofline": roofline(alg, med * 1e-3, bound="latency",
+                                 note="24,656 algorithmic bytes per check: latency-bound, the fraction is not "
+                                      "meaningful"),
+            "gpu_launches_per_check": trace_kernels(n, nv)[1],
+            "e2e": {"us_per_check": e_s / e_reps * 1e6, "api": "amc_check_trace_host",
+                    "h2d_bytes_per_step": 5 * n, "d2h_bytes_per_step": n + 5 * nv + 8,
+                    "mode": "pinned host buffers, call + stream synchronise per check"},
+            "cpu_baseline": {"value": r_cpu * n / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "us_per_check": t_cpu / r_cpu * 1e6,
+                             "sample": f"the whole trace, {r_cpu} passes, single thread"},
+            "clocks": clk}
+
+
+def measure_vectorpu(args, amc, dev):
+    """2^24 VectorPU calls (seed 2): translation + guarded check per step."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+    w = workloads.vectorpu_calls(seed=2)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in w.items()}
+    A = d["arr_start"].numel()
+    n_calls = d["call_side"].numel()
+    n_opnd = d["opnd_array"].numel()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        tr = amc.translate_vectorpu(d["arr_start"], d["arr_len"], d["call_side"], d["call_off"], d["opnd_array"],
+                                    d["opnd_mode"], stream=stream)
+        n = tr["n"]
+        tout = dict(kind_side=tr["kind_side"], var=tr["var"], call_first_op=tr["call_first_op"], n_dev=tr["n_dev"])
+        out = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+                   final_status=torch.empty(2 * A, dtype=torch.uint8, device=dev),
+                   var_first_fault=torch.empty(2 * A, dtype=torch.int32, device=dev),
+                   first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+        ws = torch.empty(amc.trace_workspace_bytes(n, 2 * A, guarded=True) + 256, dtype=torch.uint8, device=dev)
+        ws = ws[(-ws.data_ptr()) % 256:]
+
+        def step():
+            r = amc.translate_vectorpu(d["arr_start"], d["arr_len"], d["call_side"], d["call_off"],
+                                       d["opnd_array"], d["opnd_mode"], known_n=n, out=tout, stream=stream)
+            amc.check_trace(r["kind_side"], r["var"], 2 * A, guarded=True, out=out, workspace=ws, stream=stream)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        assert amc.sync_status(stream) == 0
+        clocks = ClockSampler(0)
+        clocks.start()
+        ms = timed(step, args.sub_steps, stream)
+        clk = clocks.stop()
+        assert amc.sync_status(stream) == 0
+        assert int(tout["n_dev"].item()) == n
+    # oracle: the first calls, about sub_cpu_seconds of one core
+    k = 1 << 14
+    while True:
+        sub = dict(w)
+        sub["call_side"] = w["call_side"][:k]
+        sub["call_off"] = w["call_off"][:k + 1]
+        m = int(w["call_off"][k])
+        sub["opnd_array"] = w["opnd_array"][:m]
+        sub["opnd_mode"] = w["opnd_mode"][:m]
+        t0 = time.perf_counter()
+        res = oracle.vectorpu(**sub)
+        dt = time.perf_counter() - t0
+        if dt > args.sub_cpu_seconds / 4 or k >= n_calls:
+            break
+        k = min(n_calls, k * 4)
+    # the oracle's statuses of those calls are the GPU's first statuses
+    ns = len(res["step_status"])
+    assert np.array_equal(out["step_status"][:ns].cpu().numpy(), res["step_status"])
+    alg = 8 * A + n_calls + 4 * (n_calls + 1) + 5 * n_opnd + n + 5 * 2 * A
+    return {"workload": "vectorpu_calls", "n_arrays": A, "n_calls": n_calls, "operands": n_opnd, "statements": n,
+            "seed": 2, "ms_per_step": ms, "statements_per_s": n / (ms * 1e-3), "calls_per_s": n_calls / (ms * 1e-3),
+            "roofline": roofline(alg, ms, note="algorithmic bytes: arrays, calls and operands in, one status per "
+                                               "translated statement and 5 B per variable out"),
+            "gpu_launches_per_step": vectorpu_launches(n, 2 * A),
+            "cpu_baseline": {"value": ns / dt, "unit": "statements/s", "calls_per_s": k / dt, "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"the first {k} calls ({ns} statements), single thread ({dt:.1f} s)"},
+            "clocks": clk}
+
+
+def measure_programs(args, amc, dev):
+    """100,000 programs (seed 3): the batched persistent launch (graph replay)
+    against one launch per program through the same entry point."""
+    import ctypes
+    import threading
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
     b = workloads.programs(n_progs=args.n_progs)
-    dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     tok, pay, off, nv = t(b["tok"]), t(b["payload"]), t(b["prog_tok_off"]), t(b["prog_nvars"])
     vo = torch.zeros(nv.numel() + 1, dtype=torch.int64, device=dev)
     torch.cumsum(nv.to(torch.int64), 0, out=vo[1:])
     n_tok = tok.numel()
     P = nv.numel()
+    total_vars = int(vo[-1])
+    leaf = int(b["n_leaf"].sum())
     out = dict(step_mask=torch.empty(n_tok, dtype=torch.uint8, device=dev),
-               final_mask=torch.empty(int(vo[-1]), dtype=torch.uint8, device=dev),
+               final_mask=torch.empty(total_vars, dtype=torch.uint8, device=dev),
                prog_first_fault=torch.empty(P, dtype=torch.int64, device=dev))
     stream = torch.cuda.Stream()
-    ws = torch.empty(amc.lib().amc_check_batch_workspace(n_tok, P, int(vo[-1])) + 256, dtype=torch.uint8, device=dev)
+    L = amc.lib()
+    ws = torch.empty(L.amc_check_batch_workspace(n_tok, P, total_vars) + 256, dtype=torch.uint8, device=dev)
     ws = ws[(-ws.data_ptr()) % 256:]
     with torch.cuda.stream(stream):
         batched = lambda: amc.check_batch(tok, pay, off, nv, vo, graph_capture=True, out=out, workspace=ws,
@@ -413,36 +635,289 @@ def run_programs(args):
         for _ in range(max(3, args.warmup)):
             batched()
         assert amc.sync_status(stream) == 0
-        ms_b = timed(batched, args.steps, stream)
-        # plain: one launch per program through the same entry point (no graph)
-        offs = b["prog_tok_off"]
-        L = amc.lib()
-        import ctypes
-        sp = ctypes.c_void_p(stream.cuda_stream)
-        P_ = lambda x: ctypes.c_void_p(x)
+        clocks = ClockSampler(0)
+        clocks.start()
+        ms_b = timed(batched, args.sub_steps, stream)
+        clk = clocks.stop()
+        assert amc.sync_status(stream) == 0
+        step_b = out["step_mask"].cpu().numpy()
+        plain = None
+        k = min(args.plain_progs, P)
+        if k > 0:
+            # one launch per program (no graph) over the first k programs; the
+            # CSR arrays are offset to the program, token and mask buffers stay whole
+            sp = ctypes.c_void_p(stream.cuda_stream)
+            V = lambda x: ctypes.c_void_p(x)
 
-        def plain():
-            # one launch per program: the CSR arrays are offset to the
-            # program, token and mask buffers stay whole (absolute offsets)
-            for i in range(P):
-                L.amc_check_batch(P_(tok.data_ptr()), P_(pay.data_ptr()), P_(off.data_ptr() + 8 * i),
-                                  P_(nv.data_ptr() + 4 * i), P_(vo.data_ptr() + 8 * i), 1, n_tok,
-                                  P_(out["step_mask"].data_ptr()), P_(out["final_mask"].data_ptr()),
-                                  P_(out["prog_first_fault"].data_ptr() + 8 * i), 0, P_(ws.data_ptr()), ws.numel(),
-                                  sp)
-        ms_p = None
-        if not args.no_plain:
-            plain()
+            def plain_run():
+                for i in range(k):
+                    L.amc_check_batch(V(tok.data_ptr()), V(pay.data_ptr()), V(off.data_ptr() + 8 * i),
+                                      V(nv.data_ptr() + 4 * i), V(vo.data_ptr() + 8 * i), 1, n_tok,
+                                      V(out["step_mask"].data_ptr()), V(out["final_mask"].data_ptr()),
+                                      V(out["prog_first_fault"].data_ptr() + 8 * i), 0, V(ws.data_ptr()), ws.numel(),
+                                      sp)
+
+            plain_run()
             assert amc.sync_status(stream) == 0
-            ms_p = timed(plain, 1, stream)
-    leaf = int(b["n_leaf"].sum())
-    line = base_line(args, n_tok / (ms_b * 1e-3), ms_b,
-                     {"workload": "programs", "n_progs": P, "tokens": n_tok, "leaf_ops": leaf, "seed": 3,
-                      "mode": "batched persistent launch, CUDA graph replay, longest-first queue"},
-                     plain=None if ms_p is None else {"value": n_tok / (ms_p * 1e-3), "ms_per_step": ms_p,
-                                                      "mode": "one launch per program, same kernel"},
-                     batched_over_plain=None if ms_p is None else ms_p / ms_b, gpu_launches=args.steps * 4)
-    print(json.dumps(line), flush=True)
+            ms_p = timed(plain_run, 1, stream)
+            assert amc.sync_status(stream) == 0
+            tk = int(b["prog_tok_off"][k])
+            assert np.array_equal(out["step_mask"][:tk].cpu().numpy(), step_b[:tk])
+            plain = {"programs": k, "tokens": tk, "ms": ms_p, "value": tk / (ms_p * 1e-3),
+                     "ms_per_program": ms_p / k,
+                     "mode": "one amc_check_batch launch per program (no graph), first programs of the batch, "
+                             "same stream"}
+    # oracle: programs sharded over the host threads, and one thread
+    T = host_threads(args)
+    to_np = b["prog_tok_off"]
+
+    def oracle_range(lo, hi):
+        a0, a1 = int(to_np[lo]), int(to_np[hi])
+        return oracle.check_batch(b["tok"][a0:a1], b["payload"][a0:a1], to_np[lo:hi + 1] - a0, b["prog_nvars"][lo:hi])
+
+    k1 = 256
+    while True:
+        t0 = time.perf_counter()
+        r1 = oracle_range(0, k1)
+        dt1 = time.perf_counter() - t0
+        if dt1 > args.sub_cpu_seconds / 4 or k1 >= P:
+            break
+        k1 = min(P, k1 * 4)
+    assert np.array_equal(r1[0], step_b[:int(to_np[k1])])
+    kT = min(P, k1 * T)
+    bounds = np.linspace(0, kT, T + 1).astype(int)
+    th = [threading.Thread(target=oracle_range, args=(int(bounds[i]), int(bounds[i + 1]))) for i in range(T)]
+    t0 = time.perf_counter()
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    dtT = time.perf_counter() - t0
+    tok1, tokT = int(to_np[k1]), int(to_np[kT])
+    alg = 5 * n_tok + n_tok + 8 * (P + 1) * 2 + 4 * P + total_vars + 8 * P
+    return {"workload": "programs", "n_progs": P, "tokens": n_tok, "leaf_ops": leaf, "seed": 3,
+            "ms_per_step": ms_b, "tokens_per_s": n_tok / (ms_b * 1e-3), "leaf_ops_per_s": leaf / (ms_b * 1e-3),
+            "mode": "batched persistent launch, CUDA graph replay",
+            "plain": plain, "batched_over_plain": None if plain is None else (n_tok / ms_b) / (plain["tokens"] / plain["ms"]),
+            "roofline": roofline(alg, ms_b, note="algorithmic bytes: 5 B per token in, 1 B per token out, CSR "
+                                                  "offsets, one mask per variable"),
+            "gpu_launches_per_step": 4,
+            "cpu_baseline": {"value": tok1 / dt1, "unit": "tokens/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the first {k1} programs ({tok1} tokens), single thread ({dt1:.1f} s)"},
+            "cpu_baseline_all_cores": {"value": tokT / dtT, "unit": "tokens/s", "cores": T, "kind": "oracle",
+                                       "sample": f"the first {kT} programs ({tokT} tokens) sharded by program over "
+                                                 f"{T} threads ({dtT:.1f} s)"},
+            "clocks": clk}
+
+
+def measure_well_declared(args, amc, dev):
+    """2^20 calls AM{S} (seed 5): the static well-declaredness check."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+    w = workloads.wd_calls()
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in w.items()}
+    C = d["call_tok_off"].numel() - 1
+    T = d["tok"].numel()
+    D = d["am_array"].numel()
+    stream = torch.cuda.Stream()
+    out = dict(violations=torch.empty(C, dtype=torch.int32, device=dev),
+               first_bad=torch.empty(C, dtype=torch.int64, device=dev),
+               first_unmet=torch.empty(C, dtype=torch.int32, device=dev))
+    step = lambda: amc.check_well_declared(d["arr_loc_off"], d["loc_owner"], d["call_tok_off"], d["tok"],
+                                           d["payload"], d["call_am_off"], d["am_array"], d["am_mode"], out=out,
+                                           stream=stream)
+    for _ in range(max(3, args.warmup)):
+        step()
+    assert amc.sync_status(stream) == 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = timed(step, args.sub_steps, stream)
+    clk = clocks.stop()
+    assert amc.sync_status(stream) == 0
+    reps, dt = timed_calls(lambda: oracle.well_declared(**w), args.sub_cpu_seconds, 1)
+    exp = oracle.well_declared(**w)
+    assert np.array_equal(out["violations"].cpu().numpy().astype(np.uint32), exp[0])
+    assert np.array_equal(out["first_bad"].cpu().numpy(), exp[1])
+    assert np.array_equal(out["first_unmet"].cpu().numpy(), exp[2])
+    alg = 5 * T + 5 * D + 16 * (C + 1) + 16 * C + 8 * w["arr_loc_off"].size + 4 * w["loc_owner"].size
+    return {"workload": "wd_calls", "n_calls": C, "tokens": T, "declarations": D, "seed": 5,
+            "ms_per_step": ms, "calls_per_s": C / (ms * 1e-3), "tokens_per_s": T / (ms * 1e-3),
+            "violating_calls": int((exp[0] != 0).sum()),
+            "roofline": roofline(alg, ms, note="algorithmic bytes: tokens, declarations and call offsets in, "
+                                               "three words per call out"),
+            "gpu_launches_per_step": 1,
+            "cpu_baseline": {"value": reps * C / dt, "unit": "calls/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the whole workload, {reps} pass(es), single thread ({dt:.1f} s)"},
+            "clocks": clk}
+
+
+def measure_kloc(args, amc, dev):
+    """Traces over k = 4 memory locations: 2^28 ops over 2^20 variables, Zipf
+    ids as the headline trace, kinds r .40 / w .20 / copy .30 / Noop .10 with
+    the locations drawn uniformly (seed 6)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+    k, n, nv = 4, 1 << 28, 1 << 20
+    g = torch.Generator(device=dev)
+    g.manual_seed(6)
+    ks, var = workloads.trace_zipf(n, nv, seed=6, device=dev)      # ids; the op bytes are redrawn below
+    del ks
+    u = torch.rand(n, device=dev, generator=g)
+    kind = torch.bucketize(u, torch.tensor([0.4, 0.6, 0.9], device=dev))
+    a = torch.randint(0, k, (n,), device=dev, generator=g)
+    b = (a + torch.randint(1, k, (n,), device=dev, generator=g)) % k
+    op = torch.where(kind == 3, torch.full_like(a, 3),
+                     torch.where(kind == 2, kind | a << 2 | b << 5, kind | a << 2)).to(torch.uint8)
+    del u, kind, a, b
+    stream = torch.cuda.Stream()
+    out = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+               final_status=torch.empty(nv, dtype=torch.uint8, device=dev),
+               var_first_fault=torch.empty(nv, dtype=torch.int32, device=dev),
+               first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+    ws = torch.empty(amc.lib().amc_check_trace_k_workspace(n, nv) + 256, dtype=torch.uint8, device=dev)
+    ws = ws[(-ws.data_ptr()) % 256:]
+    step = lambda: amc.check_trace_k(op, var, nv, k, out=out, workspace=ws, stream=stream)
+    for _ in range(max(3, args.warmup)):
+        step()
+    assert amc.sync_status(stream) == 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = timed(step, args.sub_steps, stream)
+    clk = clocks.stop()
+    assert amc.sync_status(stream) == 0
+    m = 1 << 24
+    op_h, var_h = op[:m].cpu().numpy(), var[:m].cpu().numpy()
+    reps, dt = timed_calls(lambda: oracle.check_trace_k(op_h, var_h, nv, k), args.sub_cpu_seconds, 1)
+    exp = oracle.check_trace_k(op_h, var_h, nv, k)
+    assert np.array_equal(out["step_status"][:m].cpu().numpy(), exp[0])
+    alg = 6 * n + 5 * nv
+    return {"workload": "kloc_trace", "k": k, "n_ops": n, "n_vars": nv, "seed": 6, "ms_per_step": ms,
+            "ops_per_s": n / (ms * 1e-3),
+            "roofline": roofline(alg, ms, note="algorithmic bytes: 5 B per op in, 1 B per op out, 5 B per variable"),
+            "gpu_launches_per_step": 13,
+            "cpu_baseline": {"value": reps * m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the first {m} ops, {reps} pass(es), single thread ({dt:.1f} s)"},
+            "clocks": clk}
+
+
+def measure_serve(args, amc, dev):
+    """Open-loop Poisson arrivals into the continuous-batching server.  Every
+    request is prepared before the clock starts: traces are slices of pinned op
+    pools, one per session size (var ids uniform over the session's variables),
+    submitted with AMC_REQ_BORROW; programs are generated in advance.  Latency
+    = poll-visible completion - scheduled arrival; submission stops after
+    --serve-seconds per rate and the requests not submitted by then are
+    counted."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import workloads
+    P = 1 << 24
+    grid = workloads.SERVE_NV_GRID
+    g = torch.Generator(device=dev)
+    g.manual_seed(4)
+    kcdf = torch.tensor(np.cumsum(workloads.KIND_MIX)[:-1], dtype=torch.float32, device=dev)
+    pools = {}
+    for nv in grid:
+        kind = torch.bucketize(torch.rand(P, device=dev, generator=g), kcdf, right=True)
+        side = torch.randint(0, 2, (P,), device=dev, generator=g)
+        ks = (kind | side << 4).to(torch.uint8).cpu().pin_memory()
+        var = torch.randint(0, nv, (P,), device=dev, generator=g, dtype=torch.int32).cpu().pin_memory()
+        pools[nv] = (ks, var)
+    results = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for rate in [float(x) for x in args.rates.split(",")]:
+        sch = workloads.serve_schedule(rate, n_requests=args.serve_requests, seed=4)
+        reqs = []
+        for i in range(len(sch["arrival"])):
+            nv = int(sch["nv"][i])
+            if sch["kind"][i] == 0:
+                a, n = int(sch["offset"][i]), int(sch["n_ops"][i])
+                ks, var = pools[nv]
+                reqs.append((int(sch["session"][i]), 0, nv, ks[a:a + n], var[a:a + n], True, float(sch["arrival"][i])))
+            else:
+                b = workloads.programs(1, seed=44, first=int(sch["prog_index"][i]), vars_lo=nv, vars_hi=nv)
+                reqs.append((int(sch["session"][i]), 1, nv, b["tok"], b["payload"], False, float(sch["arrival"][i])))
+        with amc.Server(mem_budget_bytes=32 << 30, max_slots=32) as srv:
+            tickets = {}
+            lat, errs = [], [0]
+            items = [0]
+            lock = threading.Lock()
+            done_flag = [False]
+            backp = [0]
+
+            def poller():
+                while True:
+                    with lock:
+                        pend = list(tickets.items())
+                        if done_flag[0] and not pend:
+                            return
+                    for tk, at in pend:
+                        r = srv.poll(tk)
+                        if r is not None:
+                            now = time.perf_counter()
+                            with lock:
+                                lat.append(now - (t0 + at))
+                                items[0] += len(r["status"])
+                                errs[0] += r["error"] != 0
+                                tickets.pop(tk)
+                    if time.perf_counter() > drain_deadline[0]:
+                        return
+                    time.sleep(2e-5)
+
+            drain_deadline = [float("inf")]
+            th = threading.Thread(target=poller)
+            t0 = time.perf_counter() + 0.05
+            th.start()
+            submitted = 0
+            last_submit = t0
+            for sid, kind, nv, a, bb, borrow, at in reqs:
+                while time.perf_counter() < t0 + at:
+                    pass
+                if time.perf_counter() - t0 > args.serve_seconds:
+                    break
+                while (tk := srv.submit(sid, kind, nv, a, bb, borrow=borrow)) is None:
+                    backp[0] += 1
+                    time.sleep(1e-5)
+                last_submit = time.perf_counter()
+                submitted += 1
+                with lock:
+                    tickets[tk] = at
+            drain_deadline[0] = time.perf_counter() + args.serve_drain_seconds
+            done_flag[0] = True
+            th.join()
+            wall = time.perf_counter() - t0
+            unfinished = len(tickets)
+        lat_ms = np.array(lat) * 1e3
+        span = reqs[submitted - 1][6] if submitted else 0.0
+        results[str(int(rate))] = {"p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
+                                   "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
+                                   "max_ms": float(lat_ms.max()) if len(lat) else None,
+                                   "requests": len(reqs), "submitted": submitted, "completed": len(lat),
+                                   "unfinished_at_deadline": unfinished, "errors": errs[0],
+                                   "offered_rate": submitted / span if span > 0 else None,
+                                   "achieved_submit_rate": submitted / max(last_submit - t0, 1e-9),
+                                   "backpressured_submits": backp[0],
+                                   "program_requests": sum(1 for x in reqs[:submitted] if x[1] == 1),
+                                   "items_per_s": items[0] / wall, "wall_s": wall}
+    clk = clocks.stop()
+    del pools
+    return {"workload": "serve", "rates_req_per_s": args.rates, "requests_per_rate": args.serve_requests,
+            "slots": 32, "budget_gb": 32, "seed": 4,
+            "sessions": "1-64 requests over n_vars drawn from 32 evenly spaced values in 64..4,032; kind drawn per "
+                        "request (half programs, half traces of 2^10-2^24 ops)",
+            "traces": "slices of pinned op pools (one per session size), submitted without a copy (AMC_REQ_BORROW)",
+            "latency": "poll-visible completion minus scheduled arrival (open loop)",
+            "by_rate": results, "clocks": clk}
 
 
 def vectorpu_launches(n_statements, n_vars):
@@ -455,122 +930,6 @@ def vectorpu_launches(n_statements, n_vars):
     if n_vars <= 16384 and n_statements >= (1 << 20) and os.environ.get("AMC_SCAN_DENSE", "") != "0":
         return 11 + 2 * (5 if n_vars <= 8192 else 3)
     return 11 + 1 + 2
-
-
-def run_vectorpu(args):
-    """Translation + guarded check of the 2^24-call VectorPU workload."""
-    import numpy as np
-    import torch
-
-    import paper_1910_11110_gb300 as amc
-    import workloads
-    torch.cuda.set_device(0)
-    amc.build()
-    w = workloads.vectorpu_calls(seed=2)
-    dev = torch.device("cuda")
-    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in w.items()}
-    A = d["arr_start"].numel()
-    stream = torch.cuda.current_stream()
-    tr = amc.translate_vectorpu(d["arr_start"], d["arr_len"], d["call_side"], d["call_off"], d["opnd_array"],
-                                d["opnd_mode"])
-    n = tr["n"]
-    cap = n
-    res = {}
-
-    def step():
-        r = amc.translate_vectorpu(d["arr_start"], d["arr_len"], d["call_side"], d["call_off"], d["opnd_array"],
-                                   d["opnd_mode"], out_cap=cap)
-        res["o"] = amc.check_trace(r["kind_side"], r["var"], 2 * A, guarded=True)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    assert amc.sync_status() == 0
-    ms = timed(step, args.steps, stream)
-    n_calls = d["call_side"].numel()
-    line = base_line(args, n / (ms * 1e-3), ms,
-                     {"workload": "vectorpu_calls", "n_arrays": A, "n_calls": n_calls, "statements": n, "seed": 2},
-                     calls_per_s=n_calls / (ms * 1e-3), gpu_launches=args.steps * vectorpu_launches(n, 2 * A))
-    print(json.dumps(line), flush=True)
-
-
-def run_serve(args):
-    """Open-loop Poisson arrivals into the continuous-batching server."""
-    import threading
-
-    import numpy as np
-    import torch
-
-    import paper_1910_11110_gb300 as amc
-    import workloads
-    torch.cuda.set_device(0)
-    amc.build()
-    rng = np.random.default_rng(4)
-    pool_n = 1 << 25
-    pool_ks = ((rng.choice(5, size=pool_n, p=workloads.KIND_MIX)) | (rng.integers(0, 2, pool_n) << 4)).astype(np.uint8)
-    pool_var = rng.integers(0, 1 << 30, pool_n).astype(np.int64)
-    results = {}
-    for rate in [float(x) for x in args.rates.split(",")]:
-        n_req = args.serve_requests
-        arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
-        # sessions of 1..64 requests over 64..4096 vars, typed by kind
-        sess = []
-        while sum(x[1] for x in sess) < n_req:
-            sess.append((len(sess), int(rng.integers(1, 65)), int(rng.integers(64, 4097)), int(rng.integers(0, 2))))
-        order = np.repeat(np.arange(len(sess)), [x[1] for x in sess])[:n_req]
-        rng.shuffle(order)
-        reqs = []
-        for k, si in enumerate(order):
-            sid, _, nv, kind = sess[si]
-            if kind == 0:
-                n = int(2 ** rng.uniform(10, 24))
-                a = int(rng.integers(0, pool_n - n))
-                reqs.append((sid, kind, nv, ("trace", a, n)))
-            else:
-                reqs.append((sid, kind, nv, ("prog", k)))
-        with amc.Server(mem_budget_bytes=32 << 30, max_slots=32) as srv:
-            tickets = {}
-            lat = []
-            ops = [0]
-            done_flag = [False]
-
-            def poller():
-                while not done_flag[0] or tickets:
-                    for t in list(tickets):
-                        r = srv.poll(t)
-                        if r is not None:
-                            lat.append(r["t_done"] - r["t_submit"])
-                            ops[0] += len(r["status"])
-                            tickets.pop(t)
-                    time.sleep(2e-5)
-
-            th = threading.Thread(target=poller)
-            th.start()
-            t0 = time.perf_counter()
-            for (sid, kind, nv, spec), at in zip(reqs, arr):
-                while time.perf_counter() - t0 < at:
-                    pass
-                if spec[0] == "trace":
-                    _, a, n = spec
-                    ks = pool_ks[a:a + n]
-                    var = (pool_var[a:a + n] % nv).astype(np.int32)
-                else:
-                    b = workloads.programs(1, seed=44, first=spec[1], vars_lo=nv, vars_hi=nv)
-                    ks, var = b["tok"], b["payload"]
-                while (t := srv.submit(sid, kind, nv, ks, var)) is None:
-                    time.sleep(1e-4)
-                tickets[t] = 1
-            done_flag[0] = True
-            th.join()
-            wall = time.perf_counter() - t0
-        lat = np.array(lat) * 1e3
-        results[str(int(rate))] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                                   "ops_per_s": ops[0] / wall, "requests": n_req, "wall_s": wall}
-    first = results[list(results)[0]]
-    line = base_line(args, first["ops_per_s"], None,
-                     {"workload": "serve", "rates_req_per_s": args.rates, "requests_per_rate": args.serve_requests,
-                      "slots": 32, "budget_gb": 32, "seed": 4},
-                     serve=results)
-    print(json.dumps(line), flush=True)
 
 
 def tail_epochs(n_ops):
@@ -590,11 +949,12 @@ def trace_kernels(n_ops, n_vars):
     bitmap seeded from its final statuses, the single-pass scan, the final
     statuses and the first-fault merge (7 kernels); from 2^29 ops the first
     2^22 ops as pairs sorted by variable (pairs, 3 radix passes of histogram,
-    scan and scatter, then the single-pass segmented scan: 11 kernels), then
-    per epoch the stuck bitmap, stream filter, block sums, chunk offsets,
-    gather, the candidates' sorted check (10), the gated fallback scan
-    (set-up, scan, final statuses) and the gated first-fault merge (19
-    kernels); else the scan and the final statuses."""
+    scan and scatter, then the single-pass segmented scan: 11 kernels) and the
+    stuck bitmap, then per epoch the stream filter, block sums, chunk offsets,
+    gather, the candidates' sorted check (10, which also marks the variables
+    that become stuck), the gated fallback scan (set-up, scan, final statuses)
+    and the gated first-fault merge and bitmap rebuild (18 kernels); else the
+    scan and the final statuses."""
     if os.environ.get("AMC_SCAN_DENSE", "") == "0":
         return "scan_trace_kernel", 2
     if n_vars <= 8192 and n_ops >= (1 << 20):
@@ -603,7 +963,7 @@ def trace_kernels(n_ops, n_vars):
         return "dense reduce + carry + apply kernels", 3
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 29) and os.environ.get("AMC_SCAN_TAIL", "") != "0":
         return ("first 2^22 ops: sorted check (radix sort by variable + segmented scan); epochs to 4x their "
-                "start: tail_filter_kernel + gather + sorted check of the candidates"), 11 + 19 * tail_epochs(n_ops)
+                "start: tail_filter_kernel + gather + sorted check of the candidates"), 12 + 18 * tail_epochs(n_ops)
     if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
         return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7
     return "scan_trace_kernel", 2
@@ -633,14 +993,20 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "programs":
-        run_programs(args)
-    elif args.workload == "vectorpu":
-        run_vectorpu(args)
-    elif args.workload == "serve":
-        run_serve(args)
-    else:
+    elif args.workload in ("all", "trace"):
         run_ours(args)
+    else:
+        import torch
+
+        import paper_1910_11110_gb300 as amc
+        torch.cuda.set_device(0)
+        amc.build()
+        dev = torch.device("cuda", 0)
+        fn = {"uniform": lambda: measure_uniform(args, amc, dev), "vectorpu": lambda: measure_vectorpu(args, amc, dev),
+              "well_declared": lambda: measure_well_declared(args, amc, dev),
+              "kloc": lambda: measure_kloc(args, amc, dev),
+              "programs": lambda: measure_programs(args, amc, dev), "serve": lambda: measure_serve(args, amc, dev)}
+        print(json.dumps(fn[args.workload]()), flush=True)
 
 
 if __name__ == "__main__":

@@ -204,6 +204,36 @@ AMC_API int amc_check_trace_host(const uint8_t* kind_side, const int32_t* var, i
                                  int32_t* var_first_fault, int64_t* first_fault, int64_t chunk_ops,
                                  void* workspace, size_t ws_bytes, void* stream);
 
+/* Traces over K memory locations (K = 1..AMC_K_MAX): the effects of Section
+ * 3.1 on a vector of K validity flags instead of a pair (Section 3 states that
+ * the results extend to multiple memory locations).  Location 0 is main
+ * memory, where every variable starts valid (Section 3.2).  An op runs at a
+ * location a:  r at a needs flag a valid and changes nothing; w at a makes a
+ * the only valid flag; copy a -> b (a Push at a towards b, or a Pull at b
+ * from a) needs flag a valid and makes flag b valid; Noop.  A failed need is
+ * the stuck status.  With K = 2, local = 0 and remote = 1, Push = copy 0->1,
+ * Pull = copy 1->0, rem Push = copy 1->0, rem Pull = copy 0->1.
+ *   op [n_ops]           bits 0-1 kind (0 r, 1 w, 2 copy, 3 Noop), bits 2-4
+ *                        location a, bits 5-7 location b (copy only, b != a;
+ *                        0 for r / w; a = b = 0 for Noop)
+ *   var [n_ops]          variable ids, 0 <= var < n_vars
+ *   init_status [n_vars] status bytes (bit i = location i valid, AMC_KL_F =
+ *                        stuck), or NULL for "valid in location 0 only"; must
+ *                        not be the final_status buffer
+ *   step_status, final_status, var_first_fault, first_fault: as for
+ *                        amc_check_trace, with status bytes of this encoding
+ * n_ops < 2^31.  Errors: host: AMC_E_INVALID for bad sizes, K out of range or
+ * aliased buffers, AMC_E_NOMEM for a small workspace; device (amc_sync_status):
+ * AMC_E_INVALID for a malformed op or initial status, AMC_E_RANGE for an id
+ * out of range. */
+#define AMC_K_MAX 7
+#define AMC_KL_F 0x80
+AMC_API size_t amc_check_trace_k_workspace(int64_t n_ops, int32_t n_vars);
+AMC_API int amc_check_trace_k(const uint8_t* op, const int32_t* var, int64_t n_ops, int32_t n_vars, int32_t k,
+                              const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                              int32_t* var_first_fault, int64_t* first_fault, void* workspace, size_t ws_bytes,
+                              void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* (2) VectorPU calls -> core trace -- Fig. sem-AM (translation of access    */
 /*     modes), Section 3.5 (one abstract status per array), Table            */
@@ -287,34 +317,94 @@ AMC_API int amc_check_batch(const uint8_t* tok_kind_side, const int32_t* tok_pay
                     int graph_capture, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* (3b) Static well-declaredness of calls AM{S} -- Section 3.3, Definitions   */
+/*      "Occurs in all execution paths" and "Well-declared program";         */
+/*      Section 3.5, "Well-declared program with array access".              */
+/* ------------------------------------------------------------------------ */
+
+/* Most declarations one call may have. */
+#define AMC_WD_MAX_DECLS 32
+
+/* Workspace bytes amc_check_well_declared needs (a work-queue counter). */
+AMC_API size_t amc_check_well_declared_workspace(int64_t n_calls);
+
+/* Checks n_calls calls AM{S}, each a function body S guarded by access-mode
+ * declarations AM, against the definition of a well-declared program.
+ * Locations: a scalar variable or one element of an array; array a owns the
+ * locations [arr_loc_off[a], arr_loc_off[a+1]) and is represented by one
+ * abstract variable (loc_owner[l] = the array owning location l).
+ *   arr_loc_off [n_arrays + 1], loc_owner [arr_loc_off[n_arrays]]
+ *   call_tok_off [n_calls + 1]  body tokens of call c: [off[c], off[c+1]) of
+ *                               tok / payload [n_tokens]: ops r / w / Push /
+ *                               Pull / Noop (kind | side << 4, payload = a
+ *                               location) and IF / ELSE / WHILE / END (payload
+ *                               = branch / body length, as in amc_check_batch),
+ *                               nested at most AMC_MAX_DEPTH deep
+ *   call_am_off [n_calls + 1]   declarations of call c: [off[c], off[c+1]) of
+ *                               am_array / am_mode [n_decls] (mode R 1, W 2,
+ *                               RW 3, | side << 4), at most AMC_WD_MAX_DECLS
+ * Outputs per call: violations[c] bit 0 a Push or Pull in the body (only the
+ * declarations may synchronise), bit 1 a write whose array has no W / RW
+ * declaration on the write's side, bit 2 a read without R / RW on its side,
+ * bit 3 a W declaration with a location of its array that is not written, on
+ * that side, in all execution paths of the body (conditions are opaque: both
+ * branches of an If, and zero or more runs of a While, are paths), bit 4 an
+ * array declared twice; first_bad[c] = call-relative index of the first token
+ * with a bit 0-2 violation (-1 none); first_unmet[c] = smallest array id with
+ * a bit-3 violation (-1 none).  A call is well-declared iff violations[c] = 0.
+ * Errors (via amc_sync_status): AMC_E_INVALID for malformed tokens (unbalanced
+ * or too deep constructs, pw / GT / EN in a body), bad modes or more than
+ * AMC_WD_MAX_DECLS declarations; AMC_E_RANGE for ids out of range. */
+AMC_API int amc_check_well_declared(const int64_t* arr_loc_off, int32_t n_arrays, const int32_t* loc_owner,
+                                    const int64_t* call_tok_off, int64_t n_calls, const uint8_t* tok,
+                                    const int32_t* payload, int64_t n_tokens, const int64_t* call_am_off,
+                                    const int32_t* am_array, const uint8_t* am_mode, int64_t n_decls,
+                                    uint32_t* violations, int64_t* first_bad, int32_t* first_unmet,
+                                    void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* (4) Serving -- continuous batching of check requests with per-session     */
 /*     variable statuses kept on the device between requests.                */
 /* ------------------------------------------------------------------------ */
 typedef struct amc_server amc_server;
 
 enum { AMC_REQ_TRACE = 0, AMC_REQ_PROGRAM = 1 };
+enum { AMC_REQ_BORROW = 1 };
 
-/* A request, described on the host.  Buffers are HOST pointers (copied by the
- * server when the request is admitted; they must stay valid until then).
- * TRACE: kind_side / var of n_items ops.  PROGRAM: kind_side / var hold the
- * token bytes and payloads of n_items tokens.  n_vars sizes the session on its
- * first request and must match afterwards. */
+/* A request, described on the host.  Buffers are HOST pointers, copied into
+ * the server's pinned staging before amc_serve_submit returns -- unless flags
+ * holds AMC_REQ_BORROW: then the server reads them when the request runs, and
+ * the caller keeps them valid and unchanged until amc_serve_poll reports the
+ * request done (page-locked buffers make that copy asynchronous).
+ * TRACE: kind_side / var of n_items ops, as for amc_check_trace; they are
+ * checked on the device (a bad byte or id is the request's `error`).
+ * PROGRAM: kind_side / var hold the token bytes and payloads of n_items
+ * tokens, checked at submission.  n_vars sizes the session on its first
+ * request and must match afterwards.  A session takes both kinds in any
+ * order: it keeps, per variable, the set of statuses the variable may have
+ * (every variable starts as {(V,I)}). */
 typedef struct {
     int kind;
     int32_t n_vars;
     int64_t n_items;
     const uint8_t* kind_side;
     const int32_t* var;
+    int flags;               /* 0 or AMC_REQ_BORROW */
 } amc_request;
 
-/* Result of a finished request.  `status` holds n_items host bytes: status
- * codes (TRACE) or masks (PROGRAM); valid until amc_serve_release(ticket). */
+/* Result of a finished request.  `status` holds n_items host bytes, valid
+ * until amc_serve_release(ticket): status masks (is_mask = 1) for a PROGRAM,
+ * and for a TRACE whose session has run a program with If / While before it
+ * (its variables may then hold sets of several statuses; the trace is checked
+ * in relation mode, first_fault as for amc_check_batch); else status codes
+ * (is_mask = 0, first_fault as for amc_check_trace). */
 typedef struct {
-    int error;               /* AMC_OK or a device-side error code */
+    int error;               /* AMC_OK, or the device-side error of this request's check */
     int64_t first_fault;     /* request-relative index, -1 none */
     int64_t n_items;
     const uint8_t* status;
     double t_submit, t_admit, t_done;   /* seconds, server clock */
+    int is_mask;             /* 1: `status` holds masks, 0: status codes */
 } amc_result;
 
 /* Creates a server on the current device that holds at most max_slots
@@ -325,12 +415,13 @@ AMC_API int amc_server_create(size_t mem_budget_bytes, int max_slots, amc_server
  * order; different sessions overlap on the device).  Returns AMC_E_AGAIN when
  * the queue is full. */
 AMC_API int amc_serve_submit(amc_server* srv, uint64_t session_id, const amc_request* req, uint64_t* ticket);
-/* Non-blocking: *done = 1 and *out filled once the request finished. */
+/* Non-blocking: *done = 1 and *out filled once the request finished.  A
+ * request that reports an error leaves its session's statuses unspecified. */
 AMC_API int amc_serve_poll(amc_server* srv, uint64_t ticket, int* done, amc_result* out);
 /* Frees a finished request's host result. */
 AMC_API int amc_serve_release(amc_server* srv, uint64_t ticket);
-/* Copies a session's current variable statuses (status codes for trace
- * sessions, masks for program sessions) to host memory. */
+/* Copies a session's current variable status sets (status masks, bit k set
+ * <=> status code k is possible) to host memory, after its queued requests. */
 AMC_API int amc_session_export(amc_server* srv, uint64_t session_id, uint8_t* host_status, int32_t n_vars);
 /* Waits for all queued requests, then frees the server. */
 AMC_API int amc_server_destroy(amc_server* srv);

@@ -58,6 +58,14 @@ def lib():
             L.amc_translate_vectorpu_workspace.argtypes = [i32, i64, i64]
             L.amc_translate_vectorpu.argtypes = [P, P, i32, P, P, i64, P, P, i64, ci,
                                                  P, P, i64, P, P, P, sz, P]
+        if hasattr(L, "amc_check_trace_k"):
+            L.amc_check_trace_k_workspace.restype = sz
+            L.amc_check_trace_k_workspace.argtypes = [i64, i32]
+            L.amc_check_trace_k.argtypes = [P, P, i64, i32, i32, P, P, P, P, P, P, sz, P]
+        if hasattr(L, "amc_check_well_declared"):
+            L.amc_check_well_declared_workspace.restype = sz
+            L.amc_check_well_declared_workspace.argtypes = [i64]
+            L.amc_check_well_declared.argtypes = [P, i32, P, P, i64, P, P, i64, P, P, P, i64, P, P, P, P, sz, P]
         if hasattr(L, "amc_check_batch"):
             L.amc_check_batch_workspace.restype = sz
             L.amc_check_batch_workspace.argtypes = [i64, i64, i64]
@@ -161,6 +169,31 @@ def check_trace(kind_side, var, n_vars, init_status=None, *, guarded=False, out=
     return out
 
 
+def check_trace_k(op, var, n_vars, k, init_status=None, *, out=None, workspace=None, stream=None):
+    """Trace check over k memory locations (amc_check_trace_k).  op uint8 /
+    var int32 CUDA tensors; statuses are bit masks of valid locations, 0x80 =
+    stuck.  Returns dict(step_status, final_status, var_first_fault,
+    first_fault)."""
+    _dev(op, torch.uint8, "op")
+    _dev(var, torch.int32, "var")
+    n = op.numel()
+    dev = op.device
+    if init_status is not None:
+        _dev(init_status, torch.uint8, "init_status")
+    if out is None:
+        out = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+                   final_status=torch.empty(max(n_vars, 0), dtype=torch.uint8, device=dev),
+                   var_first_fault=torch.empty(max(n_vars, 0), dtype=torch.int32, device=dev),
+                   first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+    L = lib()
+    ws = workspace if workspace is not None else _ws.get(L.amc_check_trace_k_workspace(n, n_vars), dev)
+    rc = L.amc_check_trace_k(_p(op), _p(var), n, n_vars, k, _p(init_status), _p(out["step_status"]),
+                             _p(out["final_status"]), _p(out["var_first_fault"]), _p(out["first_fault"]), _p(ws),
+                             ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_check_trace_k")
+    return out
+
+
 def _host(t, dtype, name):
     if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
         raise TypeError(f"{name} must be a CPU tensor")
@@ -214,11 +247,17 @@ def trace_host_workspace_bytes(n_ops: int, n_vars: int, chunk_ops: int = 0) -> i
 
 
 def translate_vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd_mode, *,
-                       infer_overlap=True, out_cap=None, stream=None):
+                       infer_overlap=True, out_cap=None, known_n=None, out=None, stream=None):
     """Translate VectorPU calls into a core trace over 2 * n_arrays variables
     (amc_translate_vectorpu).  All inputs are CUDA tensors (int32 / uint8).
-    Returns dict(kind_side, var, call_first_op, n).  When ``out_cap`` is too
-    small the call is repeated once with the exact size."""
+    Returns dict(kind_side, var, call_first_op, n, n_dev).  When ``out_cap`` is
+    too small the call is repeated once with the exact size.
+
+    ``known_n``: the statement count of an earlier translation of the same
+    calls; the call then reads nothing back (no host synchronisation) and
+    returns the outputs cut to known_n statements (``out`` may pass tensors
+    from an earlier call's result to reuse); a different count is reported by
+    sync_status (E_RANGE when larger)."""
     _dev(arr_start, torch.int32, "arr_start")
     _dev(arr_len, torch.int32, "arr_len")
     _dev(call_side, torch.uint8, "call_side")
@@ -230,6 +269,21 @@ def translate_vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd
     n_opnd = opnd_array.numel()
     dev = arr_start.device
     L = lib()
+    if known_n is not None:
+        n = int(known_n)
+        if out is None:
+            out = dict(kind_side=torch.empty(max(n, 1), dtype=torch.uint8, device=dev),
+                       var=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+                       call_first_op=torch.empty(n_calls + 1, dtype=torch.int64, device=dev),
+                       n_dev=torch.empty(1, dtype=torch.int64, device=dev))
+        ws = _ws.get(L.amc_translate_vectorpu_workspace(A, n_calls, n_opnd), dev)
+        rc = L.amc_translate_vectorpu(_p(arr_start), _p(arr_len), A, _p(call_side), _p(call_off), n_calls,
+                                      _p(opnd_array), _p(opnd_mode), n_opnd, int(bool(infer_overlap)),
+                                      _p(out["kind_side"]), _p(out["var"]), n, _p(out["n_dev"]),
+                                      _p(out["call_first_op"]), _p(ws), ws.numel(), _stream_ptr(stream))
+        _check(rc, "amc_translate_vectorpu")
+        return dict(kind_side=out["kind_side"][:n], var=out["var"][:n], call_first_op=out["call_first_op"], n=n,
+                    n_dev=out["n_dev"])
     if out_cap is None:
         out_cap = 48 * n_calls + 64
     first = torch.empty(n_calls + 1, dtype=torch.int64, device=dev)
@@ -245,7 +299,7 @@ def translate_vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd
         _check(rc, "amc_translate_vectorpu")
         n = int(out_n.item())
         if n <= out_cap:
-            return dict(kind_side=ks[:n], var=var[:n], call_first_op=first, n=n)
+            return dict(kind_side=ks[:n], var=var[:n], call_first_op=first, n=n, n_dev=out_n)
         code = sync_status(stream)
         if code not in (OK, E_RANGE):
             raise AmcError(code, "amc_translate_vectorpu")
@@ -286,6 +340,38 @@ def check_batch(tok, payload, prog_tok_off, prog_nvars, prog_var_off=None, *, gr
     return out
 
 
+def check_well_declared(arr_loc_off, loc_owner, call_tok_off, tok, payload, call_am_off, am_array, am_mode, *,
+                        out=None, stream=None):
+    """Static well-declaredness of calls AM{S} (amc_check_well_declared).
+
+    arr_loc_off int64 [A+1], loc_owner int32 [locations], call_tok_off int64
+    [C+1], tok uint8 / payload int32 [T], call_am_off int64 [C+1], am_array
+    int32 / am_mode uint8 [D], all CUDA tensors.  Returns dict(violations
+    uint32 -> int32 view, first_bad int64, first_unmet int32)."""
+    _dev(arr_loc_off, torch.int64, "arr_loc_off")
+    _dev(loc_owner, torch.int32, "loc_owner")
+    _dev(call_tok_off, torch.int64, "call_tok_off")
+    _dev(tok, torch.uint8, "tok")
+    _dev(payload, torch.int32, "payload")
+    _dev(call_am_off, torch.int64, "call_am_off")
+    _dev(am_array, torch.int32, "am_array")
+    _dev(am_mode, torch.uint8, "am_mode")
+    dev = tok.device
+    C = call_tok_off.numel() - 1
+    if out is None:
+        out = dict(violations=torch.empty(C, dtype=torch.int32, device=dev),
+                   first_bad=torch.empty(C, dtype=torch.int64, device=dev),
+                   first_unmet=torch.empty(C, dtype=torch.int32, device=dev))
+    L = lib()
+    ws = _ws.get(L.amc_check_well_declared_workspace(C), dev)
+    rc = L.amc_check_well_declared(_p(arr_loc_off), arr_loc_off.numel() - 1, _p(loc_owner), _p(call_tok_off), C,
+                                   _p(tok), _p(payload), tok.numel(), _p(call_am_off), _p(am_array), _p(am_mode),
+                                   am_array.numel(), _p(out["violations"]), _p(out["first_bad"]),
+                                   _p(out["first_unmet"]), _p(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_check_well_declared")
+    return out
+
+
 # --------------------------------------------------------------------------
 # Serving
 # --------------------------------------------------------------------------
@@ -294,13 +380,13 @@ REQ_TRACE, REQ_PROGRAM = 0, 1
 
 class _Request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n_vars", ctypes.c_int32), ("n_items", ctypes.c_int64),
-                ("kind_side", ctypes.c_void_p), ("var", ctypes.c_void_p)]
+                ("kind_side", ctypes.c_void_p), ("var", ctypes.c_void_p), ("flags", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
     _fields_ = [("error", ctypes.c_int), ("first_fault", ctypes.c_int64), ("n_items", ctypes.c_int64),
                 ("status", ctypes.c_void_p), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("is_mask", ctypes.c_int)]
 
 
 class Server:
@@ -308,7 +394,8 @@ class Server:
 
     Requests are numpy arrays on the host: op bytes (uint8) and var ids
     (int32) for traces; token bytes and payloads for programs.  A session's
-    variable statuses stay on the device between its requests."""
+    variable status sets stay on the device between its requests, which may
+    be of either kind."""
 
     def __init__(self, mem_budget_bytes: int = 32 << 30, max_slots: int = 16):
         import numpy as np  # noqa: F401
@@ -324,12 +411,24 @@ class Server:
         self._h = P()
         _check(L.amc_server_create(mem_budget_bytes, max_slots, ctypes.byref(self._h)), "amc_server_create")
 
-    def submit(self, session: int, kind: int, n_vars: int, kind_side, var):
-        """Queue a request; returns its ticket, or None when the server pushes back."""
+    def submit(self, session: int, kind: int, n_vars: int, kind_side, var, borrow: bool = False):
+        """Queue a request; returns its ticket, or None when the server pushes back.
+
+        kind_side / var: numpy arrays or CPU tensors.  borrow=True: the server
+        reads them when the request runs instead of copying them now; the
+        caller keeps them alive and unchanged until poll() reports the request
+        done (pinned tensors make the copy asynchronous)."""
         import numpy as np
-        ks = np.ascontiguousarray(kind_side, dtype=np.uint8)
-        v = np.ascontiguousarray(var, dtype=np.int32)
-        req = _Request(kind, n_vars, ks.shape[0], ks.ctypes.data, v.ctypes.data)
+        if isinstance(kind_side, torch.Tensor):
+            ks, v = kind_side, var
+            if ks.dtype != torch.uint8 or v.dtype != torch.int32 or not (ks.is_contiguous() and v.is_contiguous()):
+                raise TypeError("kind_side / var must be contiguous uint8 / int32 tensors")
+            n, pk, pv = ks.numel(), ks.data_ptr(), v.data_ptr()
+        else:
+            ks = np.ascontiguousarray(kind_side, dtype=np.uint8)
+            v = np.ascontiguousarray(var, dtype=np.int32)
+            n, pk, pv = ks.shape[0], ks.ctypes.data, v.ctypes.data
+        req = _Request(kind, n_vars, n, pk, pv, 1 if borrow else 0)
         t = ctypes.c_uint64()
         rc = self._L.amc_serve_submit(self._h, session, ctypes.byref(req), ctypes.byref(t))
         if rc == E_AGAIN:
@@ -338,7 +437,7 @@ class Server:
         return t.value
 
     def poll(self, ticket: int, release: bool = True):
-        """None while running; else dict(status, first_fault, error, t_submit, t_admit, t_done)."""
+        """None while running; else dict(status, is_mask, first_fault, error, t_submit, t_admit, t_done)."""
         import numpy as np
         done = ctypes.c_int()
         res = _Result()
@@ -348,8 +447,8 @@ class Server:
         n = res.n_items
         status = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(res.status)).copy() if n else \
             np.zeros(0, np.uint8)
-        out = dict(status=status, first_fault=res.first_fault, error=res.error, t_submit=res.t_submit,
-                   t_admit=res.t_admit, t_done=res.t_done)
+        out = dict(status=status, is_mask=bool(res.is_mask), first_fault=res.first_fault, error=res.error,
+                   t_submit=res.t_submit, t_admit=res.t_admit, t_done=res.t_done)
         if release:
             _check(self._L.amc_serve_release(self._h, ticket), "amc_serve_release")
         return out

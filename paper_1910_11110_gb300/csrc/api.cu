@@ -10,6 +10,8 @@
 #include "translate.cuh"
 #include "batch.cuh"
 #include "autotune.cuh"
+#include "wd.cuh"
+#include "kloc.cuh"
 
 using namespace amc;
 
@@ -330,6 +332,84 @@ int amc_check_batch(const uint8_t* tok_kind_side, const int32_t* tok_payload, co
     const cudaError_t le = cudaGraphLaunch(it->second, s);
     profile_end(s);
     return le == cudaSuccess ? AMC_OK : AMC_E_CUDA;
+}
+
+size_t amc_check_trace_k_workspace(int64_t n_ops, int32_t n_vars)
+{
+    if (n_ops < 0 || n_vars < 0) return 0;
+    return kloc_workspace_bytes(n_ops);
+}
+
+int amc_check_trace_k(const uint8_t* op, const int32_t* var, int64_t n_ops, int32_t n_vars, int32_t k,
+                      const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
+                      int32_t* var_first_fault, int64_t* first_fault, void* workspace, size_t ws_bytes,
+                      void* stream)
+{
+    if (k < 1 || k > AMC_K_MAX) return AMC_E_INVALID;
+    int rc = check_trace_args(op, var, n_ops, n_vars, step_status, final_status, var_first_fault, first_fault);
+    if (rc) return rc;
+    if (init_status && init_status == final_status) return AMC_E_INVALID;
+    if (!workspace || !aligned256(workspace) || ws_bytes < kloc_workspace_bytes(n_ops)) return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    KlocLaunch L;
+    L.op = op;
+    L.var = var;
+    L.n_ops = n_ops;
+    L.n_vars = n_vars;
+    L.k = k;
+    L.init = init_status;
+    L.step = step_status;
+    L.final_status = final_status;
+    L.vff = var_first_fault;
+    L.first_fault = first_fault;
+    L.workspace = workspace;
+    L.err = err;
+    L.profile = 3;
+    return launch_kloc(L, static_cast<cudaStream_t>(stream));
+}
+
+size_t amc_check_well_declared_workspace(int64_t n_calls)
+{
+    if (n_calls < 0) return 0;
+    return wd_workspace_bytes();
+}
+
+int amc_check_well_declared(const int64_t* arr_loc_off, int32_t n_arrays, const int32_t* loc_owner,
+                            const int64_t* call_tok_off, int64_t n_calls, const uint8_t* tok, const int32_t* payload,
+                            int64_t n_tokens, const int64_t* call_am_off, const int32_t* am_array,
+                            const uint8_t* am_mode, int64_t n_decls, uint32_t* violations, int64_t* first_bad,
+                            int32_t* first_unmet, void* workspace, size_t ws_bytes, void* stream)
+{
+    if (n_arrays < 0 || n_calls < 0 || n_tokens < 0 || n_decls < 0) return AMC_E_INVALID;
+    if (!arr_loc_off || !call_tok_off || !call_am_off) return AMC_E_INVALID;
+    if (n_calls > 0 && (!violations || !first_bad || !first_unmet)) return AMC_E_INVALID;
+    if (n_tokens > 0 && (!tok || !payload || !loc_owner)) return AMC_E_INVALID;
+    if (n_decls > 0 && (!am_array || !am_mode)) return AMC_E_INVALID;
+    if (!workspace || !aligned256(workspace) || ws_bytes < wd_workspace_bytes()) return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WdLaunch L;
+    L.arr_loc_off = arr_loc_off;
+    L.n_arrays = n_arrays;
+    L.loc_owner = loc_owner;
+    L.call_tok_off = call_tok_off;
+    L.n_calls = n_calls;
+    L.tok = tok;
+    L.payload = payload;
+    L.n_tokens = n_tokens;
+    L.call_am_off = call_am_off;
+    L.am_array = am_array;
+    L.am_mode = am_mode;
+    L.n_decls = n_decls;
+    L.violations = violations;
+    L.first_bad = first_bad;
+    L.first_unmet = first_unmet;
+    L.workspace = workspace;
+    L.err = err;
+    L.profile = 3;
+    return launch_well_declared(L, s);
 }
 
 }  // extern "C"

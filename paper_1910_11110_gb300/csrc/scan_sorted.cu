@@ -289,6 +289,7 @@ struct SegParams {
     uint32_t* tstat;            // [n_tiles] published scan value of each tile (zeroed before)
     uint32_t* tile_counter;     // tiles claimed so far (zeroed before)
     int* err;
+    uint32_t* bm;               // nullable: stuck bitmap, bits set for variables that end F
     Tables tab;
 };
 
@@ -408,7 +409,10 @@ __global__ void __launch_bounds__(SNT) ss_seg_kernel(const SegParams p)
                 }
             }
             const uint32_t next = u + 1 < SE ? R.k[u + 1] : after;
-            if (next != kv) p.fin[kv] = (uint8_t)post;
+            if (next != kv) {
+                p.fin[kv] = (uint8_t)post;
+                if (p.bm && post == ST_F) atomicOr(p.bm + (kv >> 5), 1u << (kv & 31));
+            }
         }
         __syncthreads();
     }
@@ -480,10 +484,9 @@ int launch_ss_keys(const uint8_t* kind_side, const int32_t* var, int64_t n, int6
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 
-int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
+int launch_ss_radix(uint32_t* const key[2], uint32_t* const val[2], const int64_t* n_dev, int64_t cap,
+                    int32_t n_vars, void* scratch, const int* gate, cudaStream_t s, int* passes_out)
 {
-    if (C.cap <= 0) return AMC_OK;
-    if (C.cap > ((int64_t)1 << 28)) return AMC_E_INVALID;        // set index << 4 must fit 32 bits
     static bool attr_done[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -496,6 +499,32 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
         if (dev < 64) attr_done[dev] = true;
     }
     const int n_sm = sm_count();
+    const int64_t tiles = (cap + ST - 1) / ST;
+    auto grid = [&](int per_sm) { return (int)(tiles < (int64_t)n_sm * per_sm ? tiles : (int64_t)n_sm * per_sm); };
+    uint8_t* w = static_cast<uint8_t*>(scratch);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(w);
+    w += align_up(4 * SRAD * (size_t)tiles, 256);
+    uint32_t* dtot = reinterpret_cast<uint32_t*>(w);
+    const int kb = key_bits_of(n_vars);
+    const int passes = (kb + SDIG - 1) / SDIG;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int src = ps & 1;
+        const int shift = ps * SDIG;
+        ss_hist_kernel<<<grid(8), SNT, 0, s>>>(key[src], n_dev, cap, shift, hist, gate);
+        ss_hscan_kernel<<<SRAD, 1024, 0, s>>>(hist, dtot, n_dev, cap, gate);
+        ss_scatter_kernel<<<grid(3), SNT, smem, s>>>(key[src], val[src], key[src ^ 1], val[src ^ 1], n_dev, cap, shift,
+                                                     hist, dtot, gate);
+        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
+    }
+    *passes_out = passes;
+    return AMC_OK;
+}
+
+int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
+{
+    if (C.cap <= 0) return AMC_OK;
+    if (C.cap > ((int64_t)1 << 28)) return AMC_E_INVALID;        // set index << 4 must fit 32 bits
+    const int n_sm = sm_count();
     const int64_t tiles = (C.cap + ST - 1) / ST;
     auto grid = [&](int per_sm) { return (int)(tiles < (int64_t)n_sm * per_sm ? tiles : (int64_t)n_sm * per_sm); };
     uint8_t* w = static_cast<uint8_t*>(C.scratch);
@@ -507,17 +536,9 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     w += align_up(4 * (size_t)tiles, 256);
     uint32_t* tile_counter = reinterpret_cast<uint32_t*>(w);
 
-    const int kb = key_bits_of(C.n_vars);
-    const int passes = (kb + SDIG - 1) / SDIG;
-    for (int ps = 0; ps < passes; ++ps) {
-        const int src = ps & 1;
-        const int shift = ps * SDIG;
-        ss_hist_kernel<<<grid(8), SNT, 0, s>>>(C.key[src], C.n_dev, C.cap, shift, hist, C.gate);
-        ss_hscan_kernel<<<SRAD, 1024, 0, s>>>(hist, dtot, C.n_dev, C.cap, C.gate);
-        ss_scatter_kernel<<<grid(3), SNT, smem, s>>>(C.key[src], C.val[src], C.key[src ^ 1], C.val[src ^ 1],
-                                                     C.n_dev, C.cap, shift, hist, dtot, C.gate);
-        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
-    }
+    int passes = 0;
+    const int rc = launch_ss_radix(C.key, C.val, C.n_dev, C.cap, C.n_vars, C.scratch, C.gate, s, &passes);
+    if (rc) return rc;
     SegParams p;
     p.key = C.key[passes & 1];
     p.val = C.val[passes & 1];
@@ -534,6 +555,7 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     p.tstat = tstat;
     p.tile_counter = tile_counter;
     p.err = C.err;
+    p.bm = C.bm;
     p.tab = host_tables();
     if (cudaMemsetAsync(tstat, 0, 4 * (size_t)tiles, s) != cudaSuccess) return AMC_E_CUDA;
     if (cudaMemsetAsync(tile_counter, 0, 4, s) != cudaSuccess) return AMC_E_CUDA;

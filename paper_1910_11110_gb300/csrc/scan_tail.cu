@@ -30,8 +30,10 @@ namespace amc {
 namespace {
 
 constexpr int TF_THREADS = 1024;          // filter CTA: one per SM (the bitmap fills shared memory)
-constexpr int TF_CHUNK = 4096;            // ops per warp chunk
-constexpr int TF_SLOTS = 1024;            // candidate slots per chunk (more: the epoch falls back)
+constexpr int TF_CHUNK = 4096;            // ops per warp chunk in epochs of 2^27 ops or more,
+constexpr int TF_CHUNK_SHORT = 1024;      // in shorter epochs (more warps busy)
+constexpr int64_t TF_LONG_CHUNKS_FROM = (int64_t)1 << 27;
+constexpr int TF_SLOT_DIV = 4;            // candidate slots per chunk: a quarter (more: the epoch falls back)
 constexpr int CAND_DIV = 4;               // candidate capacity: epoch ops / 4 (more: falls back)
 constexpr int64_t CAND_MAX = (int64_t)1 << 27;   // and at most 2^27 (set index << 4 fits 32 bits)
 constexpr int TF_PER = 16;                // ops per lane and step
@@ -74,6 +76,12 @@ bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh)
     return true;
 }
 
+// ops per filter chunk of an epoch of n ops
+int chunk_for(int64_t n) { return n < TF_LONG_CHUNKS_FROM ? TF_CHUNK_SHORT : TF_CHUNK; }
+int64_t chunks_of(int64_t n) { return (n + chunk_for(n) - 1) / chunk_for(n); }
+// candidate slots per chunk: a quarter of it
+int slots_for(int64_t n) { return chunk_for(n) / TF_SLOT_DIV; }
+
 int64_t epoch_end(const TailShape& sh, int64_t e0, int64_t n_ops)
 {
     const int64_t e1 = sh.grow ? (e0 << sh.grow) : e0 + sh.E;
@@ -115,7 +123,12 @@ TailLayout tail_layout(const TailShape& sh, int32_t n_vars, int64_t n_ops)
 {
     TailLayout t;
     const int64_t Emax = longest_epoch(sh, n_ops);
-    const size_t n_chunks = (size_t)((Emax + TF_CHUNK - 1) / TF_CHUNK);
+    size_t n_chunks = 0, n_slots = 0;          // most chunks, most slots of one epoch
+    for (int64_t e0 = sh.S; e0 < n_ops; e0 = epoch_end(sh, e0, n_ops)) {
+        const int64_t n = epoch_end(sh, e0, n_ops) - e0;
+        if ((size_t)chunks_of(n) > n_chunks) n_chunks = (size_t)chunks_of(n);
+        if ((size_t)(chunks_of(n) * slots_for(n)) > n_slots) n_slots = (size_t)(chunks_of(n) * slots_for(n));
+    }
     const int64_t C = cand_cap(Emax);
     t.K = C > sh.S ? C : sh.S;
     const size_t K = (size_t)t.K;
@@ -144,10 +157,9 @@ TailLayout tail_layout(const TailShape& sh, int32_t n_vars, int64_t n_ops)
     t.val1 = shared_at + align_up(4 * K, 256);
     const size_t second = 2 * align_up(4 * K, 256);
     t.sks = shared_at;
-    t.svar = t.sks + align_up(n_chunks * TF_SLOTS, 256);
-    t.spos = t.svar + align_up(4 * n_chunks * TF_SLOTS, 256);
-    const size_t slots = align_up(n_chunks * TF_SLOTS, 256) + align_up(4 * n_chunks * TF_SLOTS, 256) +
-                         align_up(2 * n_chunks * TF_SLOTS, 256);
+    t.svar = t.sks + align_up(n_slots, 256);
+    t.spos = t.svar + align_up(4 * n_slots, 256);
+    const size_t slots = align_up(n_slots, 256) + align_up(4 * n_slots, 256) + align_up(2 * n_slots, 256);
     r += second > slots ? second : slots;
     size_t reg = r;
     const size_t fallback = scan_workspace_bytes(Emax, n_vars, false);
@@ -174,7 +186,7 @@ struct FilterParams {
     const uint32_t* bm;         // stuck bitmap at the epoch's start
     int bm_words;
     uint8_t* step;              // the epoch's outputs
-    uint8_t* sks;               // candidate slots: TF_SLOTS per chunk
+    uint8_t* sks;               // candidate slots: a quarter of the chunk
     int32_t* svar;
     uint16_t* spos;             // position within the chunk
     uint32_t* cnt;              // candidates per chunk
@@ -183,13 +195,14 @@ struct FilterParams {
     int bulk_ok;
 };
 
-// Each warp takes chunks of TF_CHUNK ops in steps of 32 x 16 (lane L: ops
+// Each warp takes chunks of CHUNK ops in steps of 32 x 16 (lane L: ops
 // [16 L, 16 L + 16) of a step: one 16-byte load of op bytes and four of ids);
 // every position gets F (the candidates' statuses that are not F are written
 // after their check), the ops on variables outside the bitmap are staged in
 // the chunk's slots in position order.  Op bytes and ids are checked as in the
 // scan (malformed bytes, ids out of range, GT not followed by its EN); an id
 // out of range is staged as 0.
+template <int CHUNK>
 __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const FilterParams q)
 {
     extern __shared__ __align__(16) uint32_t sbm[];
@@ -197,11 +210,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    const int64_t n_chunks = (q.n + TF_CHUNK - 1) / TF_CHUNK;
+    const int64_t n_chunks = (q.n + CHUNK - 1) / CHUNK;
     for (int64_t c = (int64_t)blockIdx.x * (TF_THREADS / 32) + warp; c < n_chunks;
          c += (int64_t)gridDim.x * (TF_THREADS / 32)) {
-        const int64_t c0 = c * TF_CHUNK;
-        const int cn = (int)min((int64_t)TF_CHUNK, q.n - c0);
+        const int64_t c0 = c * CHUNK;
+        const int cn = (int)min((int64_t)CHUNK, q.n - c0);
         int wcount = 0;
         bool full = false;                                   // slots exhausted (warp-uniform)
         for (int s0 = 0; s0 < cn; s0 += 32 * TF_PER) {
@@ -313,13 +326,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1) tail_filter_kernel(const Filter
                 pre += __popc(bal & lt) << bit;
                 wtot += __popc(bal) << bit;
             }
-            if (wcount + wtot > TF_SLOTS) {
+            if (wcount + wtot > CHUNK / TF_SLOT_DIV) {
                 // more candidates than slots: the epoch is rechecked whole
                 if (lane == 0) atomicExch(q.ovf, 1);
                 full = true;
                 continue;
             }
-            int64_t idx = c * TF_SLOTS + wcount + pre;
+            int64_t idx = c * (CHUNK / TF_SLOT_DIV) + wcount + pre;
 #pragma unroll
             for (int u = 0; u < TF_PER; ++u) {
                 if (liveMask & (1u << u)) {
@@ -435,7 +448,8 @@ __global__ void __launch_bounds__(256) tail_gather_kernel(const uint8_t* __restr
                                                           const uint32_t* __restrict__ cnt,
                                                           const uint32_t* __restrict__ coff, int n_chunks,
                                                           uint32_t* __restrict__ ckey, uint32_t* __restrict__ cval,
-                                                          uint32_t* __restrict__ cpos, int G, const int* ovf)
+                                                          uint32_t* __restrict__ cpos, int G, int chunk, int slots,
+                                                          const int* ovf)
 {
     if (*ovf) return;
     const int lane = threadIdx.x & 31;
@@ -463,13 +477,39 @@ __global__ void __launch_bounds__(256) tail_gather_kernel(const uint8_t* __restr
             const uint32_t first = __shfl_sync(0xffffffffu, excl, k);
             if (idx < total) {
                 const int64_t ch = g * G + k;
-                const int64_t src = ch * TF_SLOTS + (idx - first);
+                const int64_t src = ch * slots + (idx - first);
                 const uint32_t o = base + idx;
                 ckey[o] = (uint32_t)svar[src];
                 cval[o] = o << 4 | sorted_code_of(sks[src]);
-                cpos[o] = (uint32_t)ch * (uint32_t)TF_CHUNK + spos[src];
+                cpos[o] = (uint32_t)ch * (uint32_t)chunk + spos[src];
             }
         }
+    }
+}
+
+// After an epoch's fallback scan (gated on by its overflow flag): the scan's
+// first faults folded into the trace's, the stuck bitmap rebuilt from the
+// statuses the scan wrote.
+__global__ void tail_post_kernel(const int* gate, const uint8_t* __restrict__ st, int32_t n_vars,
+                                 uint32_t* __restrict__ bm, int32_t* __restrict__ vff,
+                                 const int32_t* __restrict__ fvff, int64_t* __restrict__ ff,
+                                 const int64_t* __restrict__ fff, int64_t offset)
+{
+    if (*gate == 0) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_words = ((int64_t)n_vars + 31) / 32 * 32;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_words; v += stride) {
+        bool f = false;
+        if (v < n_vars) {
+            if (vff[v] == -1 && fvff[v] != -1) vff[v] = (int32_t)(fvff[v] + offset);
+            f = st[v] == ST_F;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, f);
+        if ((threadIdx.x & 31) == 0) bm[v >> 5] = m;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *fff != -1) {
+        const unsigned long long g = (unsigned long long)(*fff + offset);
+        atomicMin(reinterpret_cast<unsigned long long*>(ff), g);
     }
 }
 
@@ -524,8 +564,10 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     if ((int)fsmem > max_optin) return AMC_E_INVALID;
     static size_t attr_set[64] = {};
     if (dev >= 64 || attr_set[dev] < fsmem) {
-        if (cudaFuncSetAttribute(tail_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(tail_filter_kernel<TF_CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fsmem) != cudaSuccess ||
+            cudaFuncSetAttribute(tail_filter_kernel<TF_CHUNK_SHORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fsmem) != cudaSuccess)
             return AMC_E_CUDA;
         if (dev < 64) attr_set[dev] = fsmem;
     }
@@ -559,6 +601,10 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     A.err = L.err;
     rc = launch_sorted_check(A, s);
     if (rc) return rc;
+    // the stuck bitmap at the first epoch's start; later epochs add the
+    // variables that become stuck (the sorted checks set their bits, the
+    // fallback rebuilds it)
+    tail_bitmap_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(st[0], L.n_vars, bm);
 
     int cur = 0;
     for (int64_t e0 = sh.S; e0 < L.n_ops;) {
@@ -567,7 +613,8 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         const bool last = e1 >= L.n_ops;
         uint8_t* fin = (last && L.final_status) ? L.final_status : st[cur ^ 1];
         if (cudaMemsetAsync(ovf, 0, sizeof(int), s) != cudaSuccess) return AMC_E_CUDA;
-        tail_bitmap_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(st[cur], L.n_vars, bm);
+        const int chunk = chunk_for(n);
+        const int slots = slots_for(n);
         FilterParams q;
         q.kind_side = L.kind_side + e0;
         q.var = L.var + e0;
@@ -585,9 +632,12 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         q.err = L.err;
         q.bulk_ok = ((uintptr_t)q.kind_side % 16 == 0) && ((uintptr_t)q.var % 16 == 0) &&
                     ((uintptr_t)q.step % 16 == 0);
-        const int n_chunks = (int)((n + TF_CHUNK - 1) / TF_CHUNK);
+        const int n_chunks = (int)chunks_of(n);
         const int fgrid = (int)min((int64_t)n_sm, ((int64_t)n_chunks + TF_THREADS / 32 - 1) / (TF_THREADS / 32));
-        tail_filter_kernel<<<fgrid, TF_THREADS, fsmem, s>>>(q);
+        if (chunk == TF_CHUNK)
+            tail_filter_kernel<TF_CHUNK><<<fgrid, TF_THREADS, fsmem, s>>>(q);
+        else
+            tail_filter_kernel<TF_CHUNK_SHORT><<<fgrid, TF_THREADS, fsmem, s>>>(q);
         const int n_blocks = (n_chunks + 1023) / 1024;
         const int64_t C = cand_cap(n);
         tail_blocksum_kernel<<<n_blocks, 1024, 0, s>>>(cnt, n_chunks, bsum);
@@ -596,7 +646,8 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         while (G < 32 && n_chunks / (2 * G) >= 8192) G *= 2;
         const int64_t groups = ((int64_t)n_chunks + G - 1) / G;
         const int ggrid = (int)min((int64_t)n_sm * 8, (groups + 7) / 8);
-        tail_gather_kernel<<<ggrid, 256, 0, s>>>(sks, svar, spos, cnt, coff, n_chunks, key0, val0, cpos, G, ovf);
+        tail_gather_kernel<<<ggrid, 256, 0, s>>>(sks, svar, spos, cnt, coff, n_chunks, key0, val0, cpos, G, chunk, slots,
+                                                 ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // the candidates, at most C (count on the device), from the epoch's
         // start statuses; gated off when they overflowed
@@ -620,6 +671,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         K.offset = e0;
         K.scratch = scratch;
         K.err = L.err;
+        K.bm = bm;
         rc = launch_sorted_check(K, s);
         if (rc) return rc;
         // fallback, gated on by an overflow: the single-pass scan over all the
@@ -640,8 +692,8 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         F.profile = 0;
         rc = launch_scan_trace(F, s);
         if (rc) return rc;
-        rc = launch_merge_faults(L.vff, fvff, L.n_vars, L.first_fault, fff, e0, s, ovf);
-        if (rc) return rc;
+        tail_post_kernel<<<n_sm * 2, 256, 0, s>>>(ovf, fin, L.n_vars, bm, L.vff, fvff, L.first_fault, fff, e0);
+        if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         cur ^= 1;
         e0 = e1;
     }

@@ -1596,19 +1596,20 @@ __global__ void finalize_trace_kernel(int32_t* __restrict__ vff, const uint32_t*
                                       int32_t n_vars, uint8_t* __restrict__ final_status, const int* gate,
                                       int gate_on)
 {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n_vars) return;
     if (gate && ((*gate != 0) != (gate_on != 0))) return;     // gated off: the other launch writes
-    const uint32_t ff = (uint32_t)vff[v];
-    uint8_t f;
-    if (ff != 0xFFFFFFFFu) {
-        f = ST_F;
-        if (ff & VFF_BOUND) vff[v] = -1;       // stuck from the start: no fault inside the trace
-    } else {
-        const uint32_t h = head[v];
-        f = (h == NIL) ? (init ? init[v] : (uint8_t)AMC_ST_VI) : (uint8_t)(node_status[h] & 7u);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_vars; v += stride) {
+        const uint32_t ff = (uint32_t)vff[v];
+        uint8_t f;
+        if (ff != 0xFFFFFFFFu) {
+            f = ST_F;
+            if (ff & VFF_BOUND) vff[v] = -1;   // stuck from the start: no fault inside the trace
+        } else {
+            const uint32_t h = head[v];
+            f = (h == NIL) ? (init ? init[v] : (uint8_t)AMC_ST_VI) : (uint8_t)(node_status[h] & 7u);
+        }
+        if (final_status) final_status[v] = f;
     }
-    if (final_status) final_status[v] = f;
 }
 
 // Variables whose initial status is F are stuck before the first op: their
@@ -1817,7 +1818,11 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     if (L.gate) {
         // a gated launch (the epoch path's fallback) sets itself up on the device
         const int64_t nw = L.n_vars > (int64_t)(fbytes / 4) ? L.n_vars : (int64_t)(fbytes / 4);
-        const int nb = (int)((nw + 255) / 256 < 4096 ? (nw + 255) / 256 : 4096);
+        int n_sm = 0, dv = 0;
+        cudaGetDevice(&dv);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dv);
+        const int64_t cap = n_sm > 0 ? 4 * (int64_t)n_sm : 4096;       // grid-stride; a gated-off launch is cheap
+        const int nb = (int)((nw + 255) / 256 < cap ? (nw + 255) / 256 : cap);
         gated_init_kernel<<<nb > 0 ? nb : 1, 256, 0, s>>>(L.gate, L.gate_on, p.head, L.vff, L.n_vars,
                                                           L.first_fault, p.regbits, L.n_ops > 0 ? regbytes / 4 : 0,
                                                           p.fbits, L.n_ops > 0 ? p.fbits_words : 0, L.init,
@@ -1845,7 +1850,11 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     }
     {
         // final statuses (when asked for) and first-fault bounds cleared
-        const int nb = (int)((L.n_vars + 255) / 256);
+        int n_sm = 0, dv = 0;
+        cudaGetDevice(&dv);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dv);
+        const int64_t cap = n_sm > 0 ? 8 * (int64_t)n_sm : 4096;       // grid-stride
+        const int nb = (int)((L.n_vars + 255) / 256 < cap ? (L.n_vars + 255) / 256 : cap);
         if (nb > 0) {
             finalize_trace_kernel<<<nb, 256, 0, s>>>(L.vff, p.head, p.node_status, L.init, L.n_vars,
                                                      L.final_status, L.gate, L.gate_on);

@@ -126,11 +126,17 @@ struct SortedCheck {
     int64_t offset = 0;
     void* scratch = nullptr;            // sorted_check_scratch_bytes(cap)
     int* err = nullptr;                 // device error word (an expired bounded wait)
+    uint32_t* bm = nullptr;             // nullable: stuck bitmap; bits set for variables that end F
 };
 // 4-bit code of an op byte in a pair: kind (bits 0-2) and side (bit 3)
 __host__ __device__ __forceinline__ uint32_t sorted_code_of(uint32_t ks) { return (ks & 7u) | ((ks >> 1) & 8u); }
 size_t sorted_check_scratch_bytes(int64_t cap);
 int launch_sorted_check(const SortedCheck& C, cudaStream_t s);
+// The sort alone: stable LSD radix sort of the pairs key[0] / val[0] by key
+// (keys < n_vars), 7-bit digits, key[1] / val[1] as the second buffers; the
+// result is in buffer (*passes & 1).  scratch: sorted_check_scratch_bytes(cap).
+int launch_ss_radix(uint32_t* const key[2], uint32_t* const val[2], const int64_t* n_dev, int64_t cap,
+                    int32_t n_vars, void* scratch, const int* gate, cudaStream_t s, int* passes);
 // Ops [0, n) of a trace as pairs for launch_sorted_check, checked for bad
 // bytes, ids out of range and GT without its EN; F written to step[0, n).
 int launch_ss_keys(const uint8_t* kind_side, const int32_t* var, int64_t n, int64_t n_after, int32_t n_vars,

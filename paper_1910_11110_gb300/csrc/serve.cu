@@ -12,8 +12,13 @@
 // the per-op results come back to pinned memory, and an event marks the end.
 // The worker polls those events, hands results to amc_serve_poll, and frees
 // the slot and the request's pool space, which may admit the next requests.
-// Session tables stay on the device between requests (status codes for trace
-// sessions, status masks for program sessions).
+// A session's table stays on the device between requests and holds, per
+// variable, the SET of statuses it may have (a status mask), so that trace and
+// program requests can follow one another in a session.  Until the session has
+// run a program with an If or While every set is a singleton: a trace request
+// is then checked by the trace kernels on status codes (the table converted to
+// codes and back) and reports codes; after such a program a trace request is
+// checked in relation mode as a straight-line program and reports masks.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -102,11 +107,11 @@ private:
 };
 
 struct Session {
-    int kind = -1;
+    bool known = false;
+    bool det = true;                 // every set is a singleton (no If / While program has run)
     int32_t n_vars = 0;
-    size_t table_off = SIZE_MAX;     // status codes / masks, n_vars bytes (+ first-fault scratch)
+    size_t table_off = SIZE_MAX;     // status masks, n_vars bytes
     bool busy = false;
-    cudaEvent_t last = nullptr;
 };
 
 struct Request {
@@ -114,10 +119,14 @@ struct Request {
     int kind = 0;
     int32_t n_vars = 0;
     int64_t n = 0;
+    const uint8_t* src_ks = nullptr;   // borrowed inputs (AMC_REQ_BORROW), else staged copies
+    const int32_t* src_var = nullptr;
     size_t host_off = SIZE_MAX;      // pinned: op bytes [n], ids [4n] at 256-aligned offsets, results [n], small
     size_t host_bytes = 0;
     int64_t first_fault = -1;
     int error = AMC_OK;
+    bool has_struct = false;         // a program with If / While tokens
+    int is_mask = 0;                 // the result holds status masks
     int state = 0;                   // 0 queued, 1 running, 2 done
     int slot = -1;
     size_t off = SIZE_MAX, bytes = 0;
@@ -130,16 +139,17 @@ struct Slot {
     std::shared_ptr<Request> req;
 };
 
-// pinned layout of a request
+// pinned layout of a request: staged inputs (none when borrowed), results,
+// and a small block (first fault, error word, program offsets)
 struct HostLayout {
     size_t ks, var, out, small, total;
 };
-HostLayout host_layout(int64_t n)
+HostLayout host_layout(int64_t n, bool borrowed)
 {
     HostLayout L;
     L.ks = 0;
-    L.var = align_up((size_t)n, 256);
-    L.out = L.var + align_up(4 * (size_t)n, 256);
+    L.var = borrowed ? 0 : align_up((size_t)n, 256);
+    L.out = borrowed ? 0 : L.var + align_up(4 * (size_t)n, 256);
     L.small = L.out + align_up((size_t)n, 256);
     L.total = L.small + 256;
     return L;
@@ -167,20 +177,17 @@ struct amc_server {
 
 namespace {
 
-// Host-side validation of a request (so that device errors cannot occur).
-int validate(const amc_request* r)
+// Host-side validation of a request.  A trace is checked on the device by
+// the kernels themselves (op bytes, ids; the request's own error word); a
+// program's structure is checked here (its constructs decide how it runs).
+// *has_struct: the program has If / While tokens.
+int validate(const amc_request* r, bool* has_struct)
 {
+    *has_struct = false;
     if (!r || r->n_items < 0 || r->n_vars < 1 || (r->n_items > 0 && (!r->kind_side || !r->var))) return AMC_E_INVALID;
     if (r->kind != AMC_REQ_TRACE && r->kind != AMC_REQ_PROGRAM) return AMC_E_INVALID;
-    if (r->kind == AMC_REQ_TRACE) {
-        if (r->n_items > INT32_MAX) return AMC_E_RANGE;
-        for (int64_t i = 0; i < r->n_items; ++i) {
-            const uint8_t k = r->kind_side[i];
-            if ((k & 0xE0) || (k & 15) > AMC_K_PW) return AMC_E_INVALID;
-            if (r->var[i] < 0 || r->var[i] >= r->n_vars) return AMC_E_RANGE;
-        }
-        return AMC_OK;
-    }
+    if (r->flags & ~AMC_REQ_BORROW) return AMC_E_INVALID;
+    if (r->kind == AMC_REQ_TRACE) return r->n_items > INT32_MAX ? AMC_E_RANGE : AMC_OK;
     // programs: op tokens in range, constructs balanced and nested within AMC_MAX_DEPTH
     std::vector<int64_t> ends;
     std::vector<int> kinds;
@@ -194,6 +201,7 @@ int validate(const amc_request* r)
         }
         if (k & 0x10) return AMC_E_INVALID;
         if (kk == AMC_T_IF || kk == AMC_T_WHILE) {
+            *has_struct = true;
             const int64_t len = r->var[i];
             if (len < 0 || (int)ends.size() >= AMC_MAX_DEPTH) return AMC_E_INVALID;
             int64_t end;
@@ -225,18 +233,33 @@ size_t request_bytes(const Request& r)
 {
     const size_t n = (size_t)r.n;
     size_t b = align_up(n, 256) + align_up(4 * n, 256) + align_up(n, 256) + 512;   // ks, var, out, small
-    if (r.kind == AMC_REQ_TRACE)
-        b += scan_workspace_bytes(r.n, r.n_vars) + align_up(4 * (size_t)r.n_vars, 256);   // + vff
-    else
-        b += batch_workspace_bytes(r.n, 1) + 256;
-    return b;
+    size_t w = batch_workspace_bytes(r.n, 1) + 256;                  // relation mode
+    if (r.kind == AMC_REQ_TRACE) {
+        // trace kernels: workspace, first faults, the session's statuses as codes
+        const size_t t = scan_workspace_bytes(r.n, r.n_vars) + align_up(4 * (size_t)r.n_vars, 256) +
+                         align_up((size_t)r.n_vars, 256);
+        if (t > w) w = t;
+    }
+    return b + w;
+}
+
+// singleton masks <-> status codes
+__global__ void masks_to_codes_kernel(const uint8_t* __restrict__ m, uint8_t* __restrict__ c, int32_t n)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) c[v] = (uint8_t)(__ffs(m[v]) - 1);
+}
+__global__ void codes_to_masks_kernel(const uint8_t* __restrict__ c, uint8_t* __restrict__ m, int32_t n)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) m[v] = (uint8_t)(1u << (c[v] & 7u));
 }
 
 // Launch an admitted request on its slot (worker thread, lock held).
 int launch(amc_server* s, Slot& sl, Request& r, Session& ses)
 {
     const size_t n = (size_t)r.n;
-    const HostLayout H = host_layout(r.n);
+    const HostLayout H = host_layout(r.n, r.src_ks != nullptr);
     uint8_t* h = s->host.ptr(r.host_off);
     uint8_t* d = s->pool.ptr(r.off);
     uint8_t* d_ks = d;
@@ -247,26 +270,38 @@ int launch(amc_server* s, Slot& sl, Request& r, Session& ses)
     uint8_t* table = s->pool.ptr(ses.table_off);
     cudaStream_t st = sl.stream;
     if (n) {
-        if (cudaMemcpyAsync(d_ks, h + H.ks, n, cudaMemcpyHostToDevice, st) != cudaSuccess) return AMC_E_CUDA;
-        if (cudaMemcpyAsync(d_var, h + H.var, 4 * n, cudaMemcpyHostToDevice, st) != cudaSuccess) return AMC_E_CUDA;
+        const uint8_t* ks = r.src_ks ? r.src_ks : h + H.ks;
+        const void* vs = r.src_var ? static_cast<const void*>(r.src_var) : static_cast<const void*>(h + H.var);
+        if (cudaMemcpyAsync(d_ks, ks, n, cudaMemcpyHostToDevice, st) != cudaSuccess) return AMC_E_CUDA;
+        if (cudaMemcpyAsync(d_var, vs, 4 * n, cudaMemcpyHostToDevice, st) != cudaSuccess) return AMC_E_CUDA;
     }
     int64_t* d_ff = d_small;
+    int* d_err = reinterpret_cast<int*>(d_small + 7);      // this request's device-side error word
+    if (cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess) return AMC_E_CUDA;
     int rc;
-    if (r.kind == AMC_REQ_TRACE) {
+    const unsigned vb = (unsigned)((r.n_vars + 255) / 256);
+    if (r.kind == AMC_REQ_TRACE && ses.det) {
+        // every set is a singleton: the trace kernels on status codes
+        uint8_t* codes = d_ws + scan_workspace_bytes(r.n, r.n_vars) + align_up(4 * (size_t)r.n_vars, 256);
+        masks_to_codes_kernel<<<vb, 256, 0, st>>>(table, codes, r.n_vars);
         ScanLaunch L;
         L.kind_side = d_ks;
         L.var = d_var;
         L.n_ops = r.n;
         L.n_vars = r.n_vars;
-        L.init = table;
+        L.init = codes;
         L.step = d_out;
-        L.final_status = table;           // in place: read and written per variable by one thread
+        L.final_status = codes;           // in place: read and written per variable by one thread
         L.vff = reinterpret_cast<int32_t*>(d_ws + scan_workspace_bytes(r.n, r.n_vars));
         L.first_fault = d_ff;
-        L.err = s->err;
+        L.err = d_err;
         L.workspace = d_ws;
         rc = launch_scan_trace(L, st);
+        if (!rc) codes_to_masks_kernel<<<vb, 256, 0, st>>>(codes, table, r.n_vars);
+        r.is_mask = 0;
     } else {
+        // a program, or a trace over sets that may hold several statuses: a
+        // straight-line trace is a program without structure tokens
         // one program: token offsets {0, n}, var offsets {0, n_vars}, n_vars
         int64_t* hs = reinterpret_cast<int64_t*>(h + H.small);
         hs[1] = 0;
@@ -288,14 +323,16 @@ int launch(amc_server* s, Slot& sl, Request& r, Session& ses)
         B.step_mask = d_out;
         B.final_mask = table;
         B.prog_first_fault = d_ff;
-        B.err = s->err;
+        B.err = d_err;
         B.workspace = d_ws;
         B.longest_first = 0;
         rc = launch_batch(B, st);
+        r.is_mask = 1;
+        if (r.has_struct) ses.det = false;      // later requests see sets of several statuses
     }
     if (rc) return rc;
     if (n && cudaMemcpyAsync(h + H.out, d_out, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMC_E_CUDA;
-    if (cudaMemcpyAsync(h + H.small, d_ff, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMC_E_CUDA;
+    if (cudaMemcpyAsync(h + H.small, d_ff, 64, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMC_E_CUDA;
     if (cudaEventRecord(sl.done, st) != cudaSuccess) return AMC_E_CUDA;
     return AMC_OK;
 }
@@ -303,7 +340,11 @@ int launch(amc_server* s, Slot& sl, Request& r, Session& ses)
 void finish(amc_server* s, Slot& sl)
 {
     Request& r = *sl.req;
-    memcpy(&r.first_fault, s->host.ptr(r.host_off) + host_layout(r.n).small, 8);
+    const uint8_t* small = s->host.ptr(r.host_off) + host_layout(r.n, r.src_ks != nullptr).small;
+    memcpy(&r.first_fault, small, 8);
+    int e = 0;
+    memcpy(&e, small + 56, sizeof(int));
+    if (e) r.error = e;
     r.t_done = now_s();
     r.state = 2;
     s->pool.free(r.off, r.bytes);
@@ -398,37 +439,43 @@ int amc_server_create(size_t mem_budget_bytes, int max_slots, amc_server** out)
 int amc_serve_submit(amc_server* s, uint64_t session_id, const amc_request* req, uint64_t* ticket)
 {
     if (!s || !ticket) return AMC_E_INVALID;
-    const int v = validate(req);
+    bool has_struct = false;
+    const int v = validate(req, &has_struct);
     if (v) return v;
     auto r = std::make_shared<Request>();
+    r->has_struct = has_struct;
     r->session = session_id;
     r->kind = req->kind;
     r->n_vars = req->n_vars;
     r->n = req->n_items;
     r->bytes = request_bytes(*r);
-    const HostLayout H = host_layout(r->n);
+    const bool borrowed = (req->flags & AMC_REQ_BORROW) != 0;
+    if (borrowed) {
+        r->src_ks = req->kind_side;
+        r->src_var = req->var;
+    }
+    const HostLayout H = host_layout(r->n, borrowed);
     r->host_bytes = H.total;
     std::unique_lock<std::mutex> lock(s->mu);
     if (s->queue.size() >= s->max_queue) return AMC_E_AGAIN;
     Session& ses = s->sessions[session_id];
-    if (ses.kind >= 0 && (ses.kind != req->kind || ses.n_vars != req->n_vars))
-        return AMC_E_INVALID;            // sessions are typed by their first request
+    if (ses.known && ses.n_vars != req->n_vars) return AMC_E_INVALID;   // sized by its first request
     if (r->bytes + align_up((size_t)req->n_vars, 256) > s->pool.size() || H.total > s->host.size())
         return AMC_E_NOMEM;
     r->host_off = s->host.alloc(H.total);
     if (r->host_off == SIZE_MAX) return AMC_E_AGAIN;        // staging full: back-pressure
-    if (ses.kind < 0) {
-        // first request: the session's table (status codes or masks) lives in the pool
+    if (!ses.known) {
+        // first request: the session's table of status sets lives in the pool,
+        // every variable starting as {(V,I)} (Section 3.2)
         const size_t off = s->pool.alloc(align_up((size_t)req->n_vars, 256));
         if (off == SIZE_MAX) {
             s->host.free(r->host_off, H.total);
             return AMC_E_NOMEM;
         }
-        const uint8_t init = req->kind == AMC_REQ_TRACE ? (uint8_t)AMC_ST_VI : (uint8_t)(1u << AMC_ST_VI);
-        if (cudaMemsetAsync(s->pool.ptr(off), init, (size_t)req->n_vars, s->ctl) != cudaSuccess ||
+        if (cudaMemsetAsync(s->pool.ptr(off), (int)(1u << AMC_ST_VI), (size_t)req->n_vars, s->ctl) != cudaSuccess ||
             cudaStreamSynchronize(s->ctl) != cudaSuccess)
             return AMC_E_CUDA;
-        ses.kind = req->kind;
+        ses.known = true;
         ses.n_vars = req->n_vars;
         ses.table_off = off;
     }
@@ -437,7 +484,7 @@ int amc_serve_submit(amc_server* s, uint64_t session_id, const amc_request* req,
     r->t_submit = now_s();
     lock.unlock();
     // stage the inputs in pinned memory outside the lock (the slot is reserved)
-    if (r->n) {
+    if (r->n && !borrowed) {
         memcpy(h + H.ks, req->kind_side, (size_t)r->n);
         memcpy(h + H.var, req->var, 4 * (size_t)r->n);
     }
@@ -461,10 +508,11 @@ int amc_serve_poll(amc_server* s, uint64_t ticket, int* done, amc_result* out)
         out->error = r.error;
         out->first_fault = r.first_fault;
         out->n_items = r.n;
-        out->status = s->host.ptr(r.host_off) + host_layout(r.n).out;
+        out->status = s->host.ptr(r.host_off) + host_layout(r.n, r.src_ks != nullptr).out;
         out->t_submit = r.t_submit;
         out->t_admit = r.t_admit;
         out->t_done = r.t_done;
+        out->is_mask = r.is_mask;
     }
     return AMC_OK;
 }

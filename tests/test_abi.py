@@ -30,6 +30,7 @@ def libamc():
 def test_header_declares_entry_points():
     names = declared_functions()
     for n in ("amc_check_trace", "amc_check_guarded_trace", "amc_translate_vectorpu", "amc_check_batch",
+              "amc_check_well_declared", "amc_check_trace_k",
               "amc_serve_submit", "amc_serve_poll", "amc_sync_status"):
         assert n in names
 

@@ -1,7 +1,8 @@
 """GPU parity of the epoch path for long traces (the first part checked by
 sorting its ops by variable, then per epoch: stream filter on the stuck bitmap,
 the compacted candidates checked by sorting them by variable from the epoch's
-start statuses).
+start statuses, which also adds the variables that become stuck to the
+bitmap).
 
 Traces over 16,385 to 2^20 variables take it from 2^29 ops on (first part 2^22
 ops, each epoch ending at four times its start); AMC_SCAN_TAIL="s,e" forces a
@@ -164,3 +165,31 @@ def test_bad_input_in_the_first_part(amc, monkeypatch):
     amc.check_trace(ks, var, nv)
     assert amc.sync_status() == amc.E_INVALID
     assert amc.sync_status() == 0
+
+
+def test_many_long_lived_variables(amc, oracle_mod, monkeypatch):
+    # first part 2^16 ops, epochs of 2^18: a Zipf background over 40,000
+    # variables, plus 10,000 variables that only see CPU reads, writes and
+    # Noops (never stuck), 200 of them per epoch with 1..1,000 ops each, so
+    # runs of every length cross the sorted check's tiles at every offset;
+    # variable 49,999 gets 1,024 ops in the second epoch and 1,025 in the third
+    monkeypatch.setenv("AMC_SCAN_TAIL", "16,18")
+    rng = np.random.default_rng(96)
+    nv, n = 50_000, 1_200_000
+    ks, var = workloads.trace_random(rng, n, 40_000, zipf_s=1.05)
+    S, E = 1 << 16, 1 << 18
+    for j, e0 in enumerate(range(S, n, E)):
+        e1 = min(e0 + E, n)
+        ids = rng.choice(np.arange(40_000, 49_999), size=200, replace=False)
+        kk = rng.integers(1, 1001, size=200)
+        extra = {1: 1024, 2: 1025}.get(j, 0)
+        tot = int(kk.sum()) + extra
+        if tot > (e1 - e0) // 2:
+            kk = np.maximum(1, kk * ((e1 - e0) // 2) // max(tot, 1))
+            tot = int(kk.sum()) + extra
+        pos = e0 + rng.choice(e1 - e0, size=tot, replace=False)
+        who = np.concatenate([np.repeat(ids, kk), np.full(extra, 49_999)]).astype(np.int32)
+        rng.shuffle(who)
+        var[pos] = who
+        ks[pos] = rng.choice(np.array([0x00, 0x01, 0x04], np.uint8), size=tot)
+    check(amc, oracle_mod, ks, var, nv)

@@ -4,7 +4,8 @@ Each request's result is the same when it runs alone (one slot, requests
 submitted one at a time) and in the mix (many slots, all sessions submitted
 at once, their work overlapping on the GPU), and both equal the oracle run of
 the session's requests in order (the session's final statuses of one request
-are the initial statuses of the next)."""
+are the initial statuses of the next); so do the sessions' final status sets.
+Sessions mix trace and program requests."""
 import time
 
 import numpy as np
@@ -23,47 +24,67 @@ def amc():
 
 
 def make_sessions(seed=7, n_sessions=12):
+    """Sessions whose requests are traces or programs, drawn per request.
+    Sessions s % 3 == 0 start with a program holding If / While, so that their
+    later traces see sets of several statuses; sessions s % 3 == 1 mix traces
+    with straight-line programs (every set stays a singleton); sessions
+    s % 3 == 2 mix traces with programs holding If / While."""
     rng = np.random.default_rng(seed)
     sessions = []
     for s in range(n_sessions):
         nv = int(rng.integers(8, 300))
-        kind = s % 2                      # sessions are typed by their first request
         reqs = []
-        for r in range(int(rng.integers(1, 7))):
-            if kind == 0:
+        for r in range(int(rng.integers(2, 7))):
+            if (s % 3 == 0 and r == 0) or rng.random() < 0.4:
+                p = (0.0, 0.0) if s % 3 == 1 else (0.2, 0.1)
+                b = workloads.programs(1, seed=1000 + s, first=r, median=300.0, max_len=3000,
+                                       vars_lo=nv, vars_hi=nv, p_if=p[0], p_while=p[1])
+                reqs.append((1, b["tok"], b["payload"]))
+            else:
                 n = int(2 ** rng.uniform(3, 17))
                 ks, var = workloads.trace_random(rng, n, nv, p=[0.3, 0.35, 0.1, 0.1, 0.15])
-                reqs.append((ks, var))
-            else:
-                b = workloads.programs(1, seed=1000 + s, first=r, median=300.0, max_len=3000,
-                                       vars_lo=nv, vars_hi=nv)
-                reqs.append((b["tok"], b["payload"]))
-        sessions.append((s, kind, nv, reqs))
+                reqs.append((0, ks, var))
+        sessions.append((s, nv, reqs))
     return sessions
 
 
+def has_struct(tok):
+    return bool(np.isin(tok & 15, [8, 10]).any())
+
+
 def oracle_results(oracle_mod, sessions):
-    out = {}
-    for sid, kind, nv, reqs in sessions:
-        st = None
-        for i, (a, b) in enumerate(reqs):
-            if kind == 0:
-                step, st, vff, ff = oracle_mod.check_trace(a, b, nv, init_status=st)
-                out[(sid, i)] = (step, ff)
+    """Each session run in order on the oracle from all-{(V,I)} sets: a trace
+    while every set is a singleton is a trace check on status codes (results
+    are codes); a program, or a trace after a program with If / While, is a
+    relation-mode check (results are masks).  Returns the per-request results
+    and each session's final masks."""
+    out, finals = {}, {}
+    for sid, nv, reqs in sessions:
+        masks = np.full(nv, 1 << 1, np.uint8)
+        det = True
+        for i, (kind, a, b) in enumerate(reqs):
+            if kind == 0 and det:
+                codes = (np.log2(masks).astype(np.uint8))
+                step, st, vff, ff = oracle_mod.check_trace(a, b, nv, init_status=codes)
+                masks = (1 << st.astype(np.int64)).astype(np.uint8)
+                out[(sid, i)] = (step, ff, False)
             else:
-                step, st, ff = oracle_mod.check_program(a, b, nv, init_mask=st)
-                out[(sid, i)] = (step, ff)
-    return out
+                step, masks, ff = oracle_mod.check_program(a, b, nv, init_mask=masks)
+                out[(sid, i)] = (step, ff, True)
+                if kind == 1 and has_struct(a):
+                    det = False
+        finals[sid] = masks
+    return out, finals
 
 
 def run_server(amc, sessions, slots, one_at_a_time):
     res = {}
     with amc.Server(mem_budget_bytes=1 << 30, max_slots=slots) as srv:
         pending = {}
-        order = [(sid, kind, nv, i, r) for sid, kind, nv, reqs in sessions for i, r in enumerate(reqs)]
+        order = [(sid, nv, i, r) for sid, nv, reqs in sessions for i, r in enumerate(reqs)]
         if not one_at_a_time:      # interleave sessions: round robin by request index
-            order.sort(key=lambda x: (x[3], x[0]))
-        for sid, kind, nv, i, (a, b) in order:
+            order.sort(key=lambda x: (x[2], x[0]))
+        for sid, nv, i, (kind, a, b) in order:
             t = srv.submit(sid, kind, nv, a, b)
             assert t is not None
             pending[t] = (sid, i)
@@ -80,33 +101,68 @@ def run_server(amc, sessions, slots, one_at_a_time):
                     res[pending.pop(t)] = r
             time.sleep(1e-4)
         assert not pending
-        finals = {sid: srv.export(sid, nv) for sid, kind, nv, _ in sessions}
+        finals = {sid: srv.export(sid, nv) for sid, nv, _ in sessions}
     return res, finals
 
 
 def test_alone_equals_mix_equals_oracle(amc, oracle_mod):
     sessions = make_sessions()
-    exp = oracle_results(oracle_mod, sessions)
+    exp, exp_fin = oracle_results(oracle_mod, sessions)
+    assert any(m for (_, _, m) in exp.values()) and any(not m for (_, _, m) in exp.values())
     alone, fin_a = run_server(amc, sessions, slots=1, one_at_a_time=True)
     mix, fin_m = run_server(amc, sessions, slots=16, one_at_a_time=False)
-    for key, (step, ff) in exp.items():
+    for key, (step, ff, is_mask) in exp.items():
         for got in (alone[key], mix[key]):
             assert got["error"] == 0
+            assert got["is_mask"] == is_mask, key
             assert np.array_equal(got["status"], step), key
             assert got["first_fault"] == ff, key
-    for sid in fin_a:
-        assert np.array_equal(fin_a[sid], fin_m[sid])
+    for sid in exp_fin:
+        assert np.array_equal(fin_a[sid], exp_fin[sid]), sid
+        assert np.array_equal(fin_m[sid], exp_fin[sid]), sid
 
 
 def test_rejects_malformed_requests(amc):
     with amc.Server(mem_budget_bytes=1 << 26, max_slots=2) as srv:
-        with pytest.raises(amc.AmcError):
-            srv.submit(1, 0, 4, np.array([0, 1], np.uint8), np.array([0, 9], np.int32))
+        t = srv.submit(1, 0, 4, np.array([0, 1], np.uint8), np.array([0, 9], np.int32))   # checked on the device
+        while (r := srv.poll(t)) is None:
+            time.sleep(1e-4)
+        assert r["error"] == amc.E_RANGE
+        t = srv.submit(4, 0, 4, np.array([0, 0x21], np.uint8), np.array([0, 1], np.int32))
+        while (r := srv.poll(t)) is None:
+            time.sleep(1e-4)
+        assert r["error"] == amc.E_INVALID
         with pytest.raises(amc.AmcError):
             srv.submit(2, 1, 4, np.array([8, 0], np.uint8), np.array([1, 0], np.int32))
         t = srv.submit(3, 0, 4, np.array([1, 4], np.uint8), np.array([0, 0], np.int32))
         while (r := srv.poll(t)) is None:
             time.sleep(1e-4)
-        assert r["status"].tolist() == [1, 1] and r["first_fault"] == -1
-        with pytest.raises(amc.AmcError):           # a trace session cannot take a program
-            srv.submit(3, 1, 4, np.array([0], np.uint8), np.array([0], np.int32))
+        assert r["status"].tolist() == [1, 1] and r["first_fault"] == -1 and not r["is_mask"]
+        with pytest.raises(amc.AmcError):           # a session keeps its variable count
+            srv.submit(3, 1, 5, np.array([0], np.uint8), np.array([0], np.int32))
+        t = srv.submit(3, 1, 4, np.array([0], np.uint8), np.array([0], np.int32))   # a program after a trace
+        while (r := srv.poll(t)) is None:
+            time.sleep(1e-4)
+        assert r["status"].tolist() == [1 << 1] and r["is_mask"]
+        assert srv.export(3, 4).tolist() == [1 << 1] * 4
+
+
+def test_borrowed_buffers(amc, oracle_mod):
+    # AMC_REQ_BORROW: pinned tensors read when the request runs (no copy at
+    # submission); results as for copied requests and as the oracle's
+    import torch
+    rng = np.random.default_rng(8)
+    ks, var = workloads.trace_random(rng, 200_000, 500)
+    kt, vt = torch.from_numpy(ks).pin_memory(), torch.from_numpy(var).pin_memory()
+    with amc.Server(mem_budget_bytes=1 << 30, max_slots=4) as srv:
+        t1 = srv.submit(1, 0, 500, kt, vt, borrow=True)
+        t2 = srv.submit(2, 0, 500, ks, var)
+        res = {}
+        while len(res) < 2:
+            for t in (t1, t2):
+                if t not in res and (r := srv.poll(t)) is not None:
+                    res[t] = r
+            time.sleep(1e-4)
+    step, final, vff, ff = oracle_mod.check_trace(ks, var, 500)
+    for t in (t1, t2):
+        assert res[t]["error"] == 0 and np.array_equal(res[t]["status"], step) and res[t]["first_fault"] == ff

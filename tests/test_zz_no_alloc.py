@@ -1,11 +1,13 @@
 """amc_check_trace_noalloc, the allocation-free trace check, against the
-workspace entry point amc_check_trace.
+oracle and against the workspace entry point amc_check_trace.
 
 Some callers cannot allocate device memory themselves (their host owns every
 allocation, they are plug-ins handed only inputs and outputs, or an allocation
 would synchronise a latency-critical loop); this entry point takes its scratch
 from a fixed array inside the library.  The test calls it through the C ABI
-twice in a row, on different traces, and checks every output against
+three times in a row -- a 2^22-op Zipf trace over 2^20 variables (both
+limits), a 123,457-op trace with initial statuses that include F, and an
+empty trace -- and checks every output against the oracle and against
 amc_check_trace exactly (integer results: no tolerance).  It also checks that
 sizes above the documented limits are rejected before any GPU work.  This file
 is collected last so that a failure here does not hide any other test."""
@@ -50,18 +52,32 @@ def call_noalloc(amc, ks, var, n_vars, init, out):
                                             p(out["first_fault"]), stream)
 
 
-def test_noalloc_matches_workspace_entry_point(amc):
+def test_noalloc_matches_oracle_and_workspace_entry_point(amc, oracle_mod):
     dev = torch.device("cuda")
     rng = np.random.default_rng(17)
     ks1, var1 = workloads.trace_zipf(MAX_OPS, MAX_VARS, seed=23, device=dev)
     ks2_h, var2_h = workloads.trace_random(rng, 123_457, 1000, kinds=(0, 1, 2, 3, 4, 5, 7))
     ks2, var2 = torch.from_numpy(ks2_h).to(dev), torch.from_numpy(var2_h).to(dev)
-    init2 = torch.from_numpy(rng.integers(0, 5, 1000).astype(np.uint8)).to(dev)
-    cases = [(ks1, var1, MAX_VARS, None), (ks2, var2, 1000, init2)]
-    for ks, var, nv, init in cases:          # two calls in a row, different shapes
+    init2_h = rng.integers(0, 5, 1000).astype(np.uint8)
+    init2_h[:10] = 4                         # some variables stuck before the first op
+    init2 = torch.from_numpy(init2_h).to(dev)
+    init3 = torch.from_numpy(rng.integers(0, 5, 77).astype(np.uint8)).to(dev)
+    empty_ks = torch.zeros(0, dtype=torch.uint8, device=dev)
+    empty_var = torch.zeros(0, dtype=torch.int32, device=dev)
+    cases = [(ks1, var1, MAX_VARS, None), (ks2, var2, 1000, init2), (empty_ks, empty_var, 77, init3)]
+    for ks, var, nv, init in cases:          # three calls in a row, different shapes
         got = outputs(ks.numel(), nv, dev)
         assert call_noalloc(amc, ks, var, nv, init, got) == 0
         assert amc.sync_status() == 0
+        exp = oracle_mod.check_trace(ks.cpu().numpy(), var.cpu().numpy(), nv,
+                                     None if init is None else init.cpu().numpy())
+        assert np.array_equal(got["step_status"].cpu().numpy(), exp[0])
+        assert np.array_equal(got["final_status"].cpu().numpy(), exp[1])
+        assert np.array_equal(got["var_first_fault"].cpu().numpy(), exp[2])
+        assert int(got["first_fault"].cpu()[0]) == exp[3]
+        if ks.numel() == 0:
+            assert exp[3] == -1 and np.array_equal(exp[1], init.cpu().numpy())
+            continue
         ref = amc.check_trace(ks, var, nv, init)
         assert amc.sync_status() == 0
         for k in ref:

@@ -242,6 +242,36 @@ def wd_calls(n_calls: int = 1 << 20, n_arrays: int = 4096, len_range=(1, 64), se
 # --------------------------------------------------------------------------
 # Serving requests
 # --------------------------------------------------------------------------
+SERVE_NV_GRID = tuple(range(64, 4097, 128))        # 32 session sizes, 64 .. 4,032 variables
+
+
+def serve_schedule(rate: float, n_requests: int = 10_000, seed: int = 4, trace_log2=(10.0, 24.0),
+                   session_len=(1, 64), nv_grid=SERVE_NV_GRID, p_program: float = 0.5):
+    """The request stream of the serving workload without its data: open-loop
+    Poisson arrivals at ``rate`` req/s (exponential gaps); sessions of
+    session_len requests (uniform) whose variable count is drawn uniformly from
+    nv_grid; requests of all sessions interleaved at random; each request a
+    program (p_program) or a trace of floor(2^U(a, b)) ops.  Returns a dict of
+    numpy arrays: arrival (s), session, nv, kind (0 trace / 1 program), n_ops
+    (traces), offset (a uniform start in [0, 2^24 - n_ops], for slicing an op
+    pool), prog_index (programs: the generator index)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    lens, nvs = [], []
+    while sum(lens) < n_requests:
+        lens.append(min(int(rng.integers(session_len[0], session_len[1] + 1)), n_requests - sum(lens)))
+        nvs.append(int(rng.choice(nv_grid)))
+    order = np.repeat(np.arange(len(lens)), lens)
+    rng.shuffle(order)
+    kind = (rng.random(n_requests) < p_program).astype(np.int32)
+    n_ops = np.floor(2.0 ** rng.uniform(trace_log2[0], trace_log2[1], n_requests)).astype(np.int64)
+    offset = (rng.random(n_requests) * ((1 << 24) - n_ops + 1)).astype(np.int64)
+    prog_index = np.cumsum(kind) - 1
+    return dict(arrival=t, session=order.astype(np.int64), nv=np.array(nvs, np.int32)[order], kind=kind,
+                n_ops=np.where(kind == 0, n_ops, 0), offset=np.where(kind == 0, offset, 0),
+                prog_index=np.where(kind == 1, prog_index, -1))
+
+
 def serve_requests(rate: float, n_requests: int = 10_000, seed: int = 4,
                    trace_log2=(10.0, 24.0), session_len=(1, 64), vars_range=(64, 4096),
                    p_program: float = 0.5, **prog_kw):
