@@ -51,6 +51,8 @@ def lib():
         _lib.oracle_overlaps.argtypes = [P, P, i32, P, P, i64]
         _lib.oracle_vectorpu.argtypes = [P, P, i32, P, P, i64, P, P, ctypes.c_int,
                                          P, P, i64, P, P, P, P, P, P]
+        _lib.oracle_vectorpu_lifetimes.argtypes = [P, P, P, P, P, i32, P, P, i64, P, P, ctypes.c_int,
+                                                   P, P, i64, P, P, P, P, P, P, P]
         _lib.oracle_well_declared.argtypes = [P, i32, P, P, i64, P, P, P, P, P, P, P, P]
         _lib.oracle_apply_k.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib.oracle_check_trace_k.argtypes = [P, P, i64, i32, i32, P, P, P, P, P]
@@ -221,6 +223,50 @@ def vectorpu(arr_start, arr_len, call_side, call_off, opnd_array, opnd_mode,
         n = int(n_out[0])
         return dict(kind_side=ks[:n].copy(), var=var[:n].copy(), step_status=step[:n].copy(),
                     call_first_op=cfo, final_status=final, var_first_fault=vff,
+                    first_fault=int(ff[0]))
+
+
+def vectorpu_lifetimes(arr_start, arr_len, arr_parent, arr_born, arr_died, call_side, call_off, opnd_array,
+                       opnd_mode, infer_overlap=True, out_cap=None):
+    """VectorPU calls over pvectors with lifetimes and inherited statuses.
+
+    Returns the dict of vectorpu() plus arr_probe (int64 [A]: index of the
+    Noop v, Noop v# pair recording each pvector's creation, -1 for vectors).
+    """
+    s = np.ascontiguousarray(arr_start, dtype=np.int32)
+    ln = np.ascontiguousarray(arr_len, dtype=np.int32)
+    par = np.ascontiguousarray(arr_parent, dtype=np.int32)
+    bo = np.ascontiguousarray(arr_born, dtype=np.int32)
+    di = np.ascontiguousarray(arr_died, dtype=np.int32)
+    cs = np.ascontiguousarray(call_side, dtype=np.uint8)
+    co = np.ascontiguousarray(call_off, dtype=np.int32)
+    oa = np.ascontiguousarray(opnd_array, dtype=np.int32)
+    om = np.ascontiguousarray(opnd_mode, dtype=np.uint8)
+    A = s.shape[0]
+    n_calls = cs.shape[0]
+    if out_cap is None:
+        out_cap = int(5 * oa.shape[0] + 48 * n_calls + 2 * A + 64)
+    while True:
+        ks = np.empty(out_cap, np.uint8)
+        var = np.empty(out_cap, np.int32)
+        step = np.empty(out_cap, np.uint8)
+        n_out = np.empty(1, np.int64)
+        cfo = np.empty(n_calls + 1, np.int64)
+        probe = np.empty(A, np.int64)
+        final = np.empty(2 * A, np.uint8)
+        vff = np.empty(2 * A, np.int32)
+        ff = np.empty(1, np.int64)
+        rc = lib().oracle_vectorpu_lifetimes(_ptr(s), _ptr(ln), _ptr(par), _ptr(bo), _ptr(di), A, _ptr(cs),
+                                             _ptr(co), n_calls, _ptr(oa), _ptr(om), int(bool(infer_overlap)),
+                                             _ptr(ks), _ptr(var), out_cap, _ptr(n_out), _ptr(cfo), _ptr(probe),
+                                             _ptr(step), _ptr(final), _ptr(vff), _ptr(ff))
+        if rc == -4 and out_cap < (1 << 40):
+            out_cap *= 2
+            continue
+        _check(rc)
+        n = int(n_out[0])
+        return dict(kind_side=ks[:n].copy(), var=var[:n].copy(), step_status=step[:n].copy(),
+                    call_first_op=cfo, arr_probe=probe, final_status=final, var_first_fault=vff,
                     first_fault=int(ff[0]))
 
 

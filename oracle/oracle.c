@@ -592,6 +592,212 @@ int oracle_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_
 }
 
 /* ------------------------------------------------------------------------ */
+/* VectorPU calls over pvectors that are created and deleted during the run  */
+/* (Section 4.3: r_v is updated at pvector creations and deletions and       */
+/* queried at calls; a partial vector inherits the coherence state of its    */
+/* mother vector when it is declared, Section 5's description of VectorPU's  */
+/* partial vectors).                                                          */
+/*                                                                            */
+/* r_v is kept as the paper's "simple unordered list": the live arrays, with */
+/* every lookup a pass over all of them.  Array a is live at the calls       */
+/* born[a] <= c < died[a].  parent[a] = -1 for a vector (its elements are a  */
+/* fresh allocation: its statuses are those of the initial store), else the  */
+/* vector whose range holds a's range and whose lifetime holds a's lifetime. */
+/* Before call c, the pvectors born at c (ascending id) take their vector's  */
+/* real and abstract statuses; the translated trace records each creation as */
+/* Noop v, Noop v# (CPU side, no effect) at the head of call c's statements, */
+/* and arr_probe[a] is the index of the first of the two (-1 for vectors).   */
+/* The call's operands must be live; O(M), the shadows and the projections  */
+/* of body writes range over the live arrays only.                           */
+/* ------------------------------------------------------------------------ */
+static int cmp_i64_first(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+int oracle_vectorpu_lifetimes(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_parent,
+                              const int32_t* arr_born, const int32_t* arr_died, int32_t n_arrays,
+                              const uint8_t* call_side, const int32_t* call_off, int64_t n_calls,
+                              const int32_t* opnd_array, const uint8_t* opnd_mode, int infer_overlap,
+                              uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap, int64_t* out_n,
+                              int64_t* call_first_op, int64_t* arr_probe, uint8_t* step_status,
+                              uint8_t* final_status, int32_t* var_first_fault, int64_t* first_fault)
+{
+    if (n_arrays < 0 || n_arrays > (INT32_MAX / 2) || n_calls < 0 || n_calls > INT32_MAX || call_off[0] != 0)
+        return -1;
+    if (check_intervals(arr_start, arr_len, n_arrays)) return -1;
+    for (int32_t a = 0; a < n_arrays; a++) {
+        if (arr_born[a] < 0 || arr_born[a] >= arr_died[a] || arr_died[a] > n_calls) return -1;
+        int32_t p = arr_parent[a];
+        if (p == -1) continue;
+        if (p < 0 || p >= n_arrays) return -2;
+        if (p == a || arr_parent[p] != -1) return -1;                 /* a vector's own pvector */
+        if (!contains(arr_start[p], arr_len[p], arr_start[a], arr_len[a])) return -1;
+        if (arr_born[p] > arr_born[a] || arr_died[a] > arr_died[p]) return -1;
+    }
+    for (int64_t c = 0; c < n_calls; c++) {
+        if (call_off[c + 1] < call_off[c] || call_side[c] > 1) return -1;
+        for (int32_t k = call_off[c]; k < call_off[c + 1]; k++) {
+            uint8_t m = opnd_mode[k];
+            if ((m & 0x7C) || (m & 3) == 0) return -1;
+            if (opnd_array[k] < 0 || opnd_array[k] >= n_arrays) return -2;
+            int32_t x = opnd_array[k];
+            if (c < arr_born[x] || c >= arr_died[x]) return -1;       /* not live at this call */
+            for (int32_t j = call_off[c]; j < k; j++)
+                if (opnd_array[j] == x) return -1;
+        }
+    }
+    size_t An = (size_t)(n_arrays ? n_arrays : 1);
+    int32_t nv = 2 * n_arrays;
+    /* creation and deletion events ordered by call (then by id) */
+    int64_t* births = (int64_t*)malloc(sizeof(int64_t) * An);
+    int64_t* deaths = (int64_t*)malloc(sizeof(int64_t) * An);
+    int32_t* live = (int32_t*)malloc(sizeof(int32_t) * An);       /* r_v: unordered */
+    int32_t* live_pos = (int32_t*)malloc(sizeof(int32_t) * An);   /* index in live, -1 if dead */
+    uint8_t* opmode = (uint8_t*)calloc(An, 1);
+    uint8_t* eff = (uint8_t*)calloc(An, 1);
+    uint8_t* shadow = (uint8_t*)calloc(An, 1);
+    int32_t* list = (int32_t*)malloc(sizeof(int32_t) * An);
+    vp_ctx c;
+    c.n_arrays = n_arrays;
+    c.st = (uint8_t*)malloc((size_t)(nv ? nv : 1));
+    c.vff = var_first_fault;
+    c.ff = -1;
+    c.out_ks = out_kind_side;
+    c.out_var = out_var;
+    c.step = step_status;
+    c.n = 0;
+    c.cap = out_cap;
+    int rc = 0;
+    if (!births || !deaths || !live || !live_pos || !opmode || !eff || !shadow || !list || !c.st) rc = -3;
+    int32_t n_live = 0;
+    if (!rc) {
+        for (int32_t a = 0; a < n_arrays; a++) {
+            births[a] = ((int64_t)arr_born[a] << 32) | a;
+            deaths[a] = ((int64_t)arr_died[a] << 32) | a;
+            live_pos[a] = -1;
+            arr_probe[a] = -1;
+        }
+        qsort(births, (size_t)n_arrays, sizeof(int64_t), cmp_i64_first);
+        qsort(deaths, (size_t)n_arrays, sizeof(int64_t), cmp_i64_first);
+        for (int32_t v = 0; v < nv; v++) {
+            c.st[v] = (uint8_t)encode((pair_t){ V, I });   /* the initial store */
+            var_first_fault[v] = -1;
+        }
+    }
+    int32_t nb = 0, nd = 0;
+    for (int64_t call = 0; call < n_calls && !rc; call++) {
+        int side = call_side[call];
+        int32_t k0 = call_off[call], k1 = call_off[call + 1];
+        call_first_op[call] = c.n;
+        /* deletions: arrays whose lifetime ended before this call leave r_v */
+        while (nd < n_arrays && (deaths[nd] >> 32) <= call) {
+            int32_t a = (int32_t)(deaths[nd] & 0xFFFFFFFF);
+            int32_t i = live_pos[a];
+            if (i >= 0) {
+                live[i] = live[n_live - 1];
+                live_pos[live[i]] = i;
+                n_live--;
+                live_pos[a] = -1;
+            }
+            nd++;
+        }
+        /* creations: join r_v; a pvector takes its vector's statuses */
+        while (nb < n_arrays && (births[nb] >> 32) <= call && !rc) {
+            int32_t a = (int32_t)(births[nb] & 0xFFFFFFFF);
+            live_pos[a] = n_live;
+            live[n_live++] = a;
+            int32_t p = arr_parent[a];
+            if (p >= 0) {
+                arr_probe[a] = c.n;
+                rc = vp_op(&c, K_NOOP, 0, p);
+                if (!rc) rc = vp_op(&c, K_NOOP, 0, n_arrays + p);
+                c.st[a] = c.st[p];
+                c.st[n_arrays + a] = c.st[n_arrays + p];
+            }
+            nb++;
+        }
+        if (rc) break;
+        for (int32_t k = k0; k < k1; k++) {
+            opmode[opnd_array[k]] = opnd_mode[k];
+            eff[opnd_array[k]] = (opnd_mode[k] & M_DROPPED) ? 0 : (opnd_mode[k] & 3);
+        }
+        int32_t n_shadow = 0;
+        if (infer_overlap) {
+            /* O(M) against the live arrays, Table Overlap-ext-tab (declared set
+             * only, not applied again to what it adds) */
+            for (int32_t k = k0; k < k1; k++) {
+                int32_t x = opnd_array[k];
+                uint8_t mx = opnd_mode[k];
+                if ((mx & M_DROPPED) || !((mx & 3) & M_W)) continue;
+                for (int32_t i = 0; i < n_live; i++) {
+                    int32_t y = live[i];
+                    if (y == x || !overlap(arr_start[x], arr_len[x], arr_start[y], arr_len[y])) continue;
+                    if (opmode[y] == 0) {
+                        if (!shadow[y]) { shadow[y] = 1; list[n_shadow++] = y; }
+                    } else if (!(opmode[y] & M_DROPPED)) {
+                        if ((mx & 3) == M_RW || (opmode[y] & 3) != M_W) eff[y] = M_RW;
+                    }
+                }
+            }
+            qsort(list, (size_t)n_shadow, sizeof(int32_t), cmp_i32);
+        }
+        for (int32_t k = k0; k < k1 && !rc; k++) {
+            int32_t x = opnd_array[k];
+            int mo = opnd_mode[k] & 3;
+            if (!(opnd_mode[k] & M_DROPPED)) {
+                int me = eff[x];
+                if (me == M_R || me == M_RW) rc = vp_ensure(&c, side, x);
+                if (!rc && (me == M_W || me == M_RW)) rc = vp_op(&c, K_W, side, n_arrays + x);
+            }
+            if (!rc && (mo == M_R || mo == M_RW)) rc = vp_op(&c, K_R, side, x);
+            if (!rc && (mo == M_W || mo == M_RW)) rc = vp_op(&c, K_W, side, x);
+        }
+        for (int32_t s2 = 0; s2 < n_shadow && !rc; s2++) {
+            int32_t y = list[s2];
+            rc = vp_ensure(&c, side, y);
+            if (!rc) rc = vp_op(&c, K_W, side, n_arrays + y);
+        }
+        for (int32_t s2 = 0; s2 < n_shadow; s2++) shadow[list[s2]] = 0;
+        /* the body's writes reach the shared elements of the live arrays that
+         * overlap the operand, in ascending id */
+        for (int32_t k = k0; k < k1 && !rc; k++) {
+            int32_t x = opnd_array[k];
+            if (!((opnd_mode[k] & 3) & M_W)) continue;
+            int32_t n_ov = 0;
+            for (int32_t i = 0; i < n_live; i++) {
+                int32_t y = live[i];
+                if (y != x && overlap(arr_start[x], arr_len[x], arr_start[y], arr_len[y])) list[n_ov++] = y;
+            }
+            qsort(list, (size_t)n_ov, sizeof(int32_t), cmp_i32);
+            for (int32_t j = 0; j < n_ov && !rc; j++) {
+                int32_t y = list[j];
+                int whole = contains(arr_start[x], arr_len[x], arr_start[y], arr_len[y]);
+                rc = vp_op(&c, whole ? K_W : K_PW, side, y);
+            }
+        }
+        for (int32_t k = k0; k < k1; k++) { opmode[opnd_array[k]] = 0; eff[opnd_array[k]] = 0; }
+    }
+    if (!rc) {
+        call_first_op[n_calls] = c.n;
+        *out_n = c.n;
+        for (int32_t v = 0; v < nv; v++) final_status[v] = c.st[v];
+        *first_fault = c.ff;
+    }
+    free(births);
+    free(deaths);
+    free(live);
+    free(live_pos);
+    free(opmode);
+    free(eff);
+    free(shadow);
+    free(list);
+    free(c.st);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Static well-declaredness (Section 3.3: Definitions "Occurs in all         */
 /* execution paths" and "Well-declared program"; Section 3.5: Definition     */
 /* "Well-declared program with array access").                               */

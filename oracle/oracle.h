@@ -68,6 +68,24 @@ int oracle_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int32_t n_
                     int64_t* call_first_op, uint8_t* step_status, uint8_t* final_status,
                     int32_t* var_first_fault, int64_t* first_fault);
 
+/* oracle_vectorpu over pvectors with lifetimes (Section 4.3: r_v updated at
+ * creations and deletions; a pvector inherits its mother vector's coherence
+ * state when declared).  Array a is live at calls arr_born[a] <= c <
+ * arr_died[a] (0 <= born < died <= n_calls); arr_parent[a] = -1 for a vector,
+ * else the vector (parent -1) whose range and lifetime hold a's.  Before call
+ * c each pvector born at c (ascending id) takes its vector's real and
+ * abstract statuses, recorded as Noop v, Noop v# (CPU side) at the head of
+ * call c's statements; arr_probe[a] = index of the first (-1 for vectors).
+ * Operands must be live; O(M), shadows and write projections use the live
+ * arrays only. */
+int oracle_vectorpu_lifetimes(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_parent,
+                              const int32_t* arr_born, const int32_t* arr_died, int32_t n_arrays,
+                              const uint8_t* call_side, const int32_t* call_off, int64_t n_calls,
+                              const int32_t* opnd_array, const uint8_t* opnd_mode, int infer_overlap,
+                              uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap, int64_t* out_n,
+                              int64_t* call_first_op, int64_t* arr_probe, uint8_t* step_status,
+                              uint8_t* final_status, int32_t* var_first_fault, int64_t* first_fault);
+
 /* Static well-declaredness of VectorPU-style calls AM{S} (Section 3.3,
  * Definitions "Occurs in all execution paths" and "Well-declared program";
  * Section 3.5, "Well-declared program with array access").  Locations of
