@@ -923,50 +923,44 @@ def measure_serve(args, amc, dev):
 def vectorpu_launches(n_statements, n_vars):
     """Kernels of one translation + guarded check: 11 for the translation
     (two overlap passes, count, emit, total, two 3-kernel scans), then per
-    check pass the reduce / carry / apply path (traces over at most 16,384
-    variables from 2^20 ops on: 5 kernels up to 8,192 variables -- warp
+    check pass the reduce / carry / apply path where the size rule takes it
+    for a trace of that length (5 kernels up to 8,192 variables -- warp
     batches and a two-level carry -- else 3), or the scan kernel plus, in the
     second pass, the final-status kernel."""
-    if n_vars <= 16384 and n_statements >= (1 << 20) and os.environ.get("AMC_SCAN_DENSE", "") != "0":
-        return 11 + 2 * (5 if n_vars <= 8192 else 3)
+    import paper_1910_11110_gb300 as amc
+    path, n = amc.trace_plan(n_statements, n_vars)
+    if path in ("warp_dense", "dense"):
+        return 11 + 2 * n
     return 11 + 1 + 2
 
 
-def tail_epochs(n_ops):
-    """Epochs of the long-trace path at its default shape (first part 2^22
-    ops, each epoch ending at four times its start)."""
-    e0, k = 1 << 22, 0
-    while e0 < n_ops:
-        e0, k = min(e0 << 2, n_ops), k + 1
-    return k
+TRACE_PATH_TEXT = {
+    "small": "small_trace_kernel (one CTA: fold per warp stretch, carry per variable, apply)",
+    "warp_dense": "warp reduce + carry + apply kernels",
+    "dense": "dense reduce + carry + apply kernels",
+    "prefix": "prefix (dense reduce + carry + apply) + scan_trace_kernel",
+    "epochs": ("first part: sorted check (radix sort by variable + segmented scan); epochs to 4x their start: "
+               "tail_filter_kernel + gather + sorted check of the candidates"),
+    "scan": "scan_trace_kernel",
+}
 
 
-def trace_kernels(n_ops, n_vars):
-    """(what the timed span covers, kernels launched per check) for
-    amc_check_trace without initial statuses: the reduce / carry / apply path
-    over at most 16,384 variables from 2^20 ops; over more (at most 2^20)
-    variables from 2^24 ops that path on the first 2^22 ops, then the stuck
-    bitmap seeded from its final statuses, the single-pass scan, the final
-    statuses and the first-fault merge (7 kernels); from 2^29 ops the first
-    2^22 ops as pairs sorted by variable (pairs, 3 radix passes of histogram,
-    scan and scatter, then the single-pass segmented scan: 11 kernels) and the
-    stuck bitmap, then per epoch the stream filter, block sums, chunk offsets,
-    gather, the candidates' sorted check (10, which also marks the variables
-    that become stuck), the gated fallback scan (set-up, scan, final statuses)
-    and the gated first-fault merge and bitmap rebuild (18 kernels); else the
-    scan and the final statuses."""
-    if os.environ.get("AMC_SCAN_DENSE", "") == "0":
-        return "scan_trace_kernel", 2
-    if n_vars <= 8192 and n_ops >= (1 << 20):
-        return "warp reduce + carry + apply kernels", 5
-    if n_vars <= 16384 and n_ops >= (1 << 20):
-        return "dense reduce + carry + apply kernels", 3
-    if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 29) and os.environ.get("AMC_SCAN_TAIL", "") != "0":
-        return ("first 2^22 ops: sorted check (radix sort by variable + segmented scan); epochs to 4x their "
-                "start: tail_filter_kernel + gather + sorted check of the candidates"), 12 + 18 * tail_epochs(n_ops)
-    if 16384 < n_vars <= (1 << 20) and n_ops >= (1 << 24):
-        return "prefix (dense reduce + carry + apply) + scan_trace_kernel", 7
-    return "scan_trace_kernel", 2
+def trace_kernels(n_ops, n_vars, has_init=False):
+    """(what the timed span covers, kernels launched per check) for the next
+    amc_check_trace of these sizes, as the library reports it
+    (amc_check_trace_plan: the choice timed on the first call of the size
+    class, else the size rule).  The paths: one CTA (1 kernel); reduce / carry
+    / apply (5 kernels up to 8,192 variables, else 3); a reduce / carry / apply
+    prefix, the stuck bitmap, the single-pass scan, final statuses and the
+    first-fault merge (7); the epoch path (a sorted check of the first part --
+    pairs, three kernels per radix pass, segmented scan -- and the stuck
+    bitmap, then per epoch the stream filter, block sums, chunk offsets,
+    gather, the candidates' sorted check, the gated fallback scan's set-up,
+    scan and final statuses, and the gated merge with bitmap rebuild); or the
+    single-pass scan and the final statuses (2)."""
+    import paper_1910_11110_gb300 as amc
+    path, n = amc.trace_plan(n_ops, n_vars, has_init)
+    return TRACE_PATH_TEXT[path], n
 
 
 def scan_traffic(n_ops, n_vars):

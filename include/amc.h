@@ -121,16 +121,33 @@ AMC_API size_t amc_check_trace_workspace(int64_t n_ops, int32_t n_vars);
  * (-1 if none; a real execution stops there, Property Progress).
  *   kind_side   [n_ops]  op bytes (a GT is reported as AMC_E_INVALID)
  *   var         [n_ops]  int32 variable ids
- *   init_status [n_vars] initial status codes, or NULL for all (V,I)
+ *   init_status [n_vars] initial status codes, or NULL for all (V,I); must
+ *                        not overlap final_status (the first call of a size
+ *                        class may run the check once per launch shape to
+ *                        time them, each run reading init_status)
  *   step_status [n_ops], final_status [n_vars], var_first_fault [n_vars],
  *   first_fault [1]      outputs (int64)
- * Errors: AMC_E_INVALID for negative sizes or NULL buffers, AMC_E_NOMEM when
- * ws_bytes is too small.  Ids out of range or malformed op bytes are reported
- * through amc_sync_status (AMC_E_RANGE / AMC_E_INVALID). */
+ * Errors: AMC_E_INVALID for negative sizes, NULL or overlapping buffers,
+ * AMC_E_NOMEM when ws_bytes is too small.  Ids out of range or malformed op
+ * bytes are reported through amc_sync_status (AMC_E_RANGE / AMC_E_INVALID). */
 AMC_API int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_vars,
                     const uint8_t* init_status, uint8_t* step_status, uint8_t* final_status,
                     int32_t* var_first_fault, int64_t* first_fault,
                     void* workspace, size_t ws_bytes, void* stream);
+
+/* Which path the next amc_check_trace of these sizes takes and how many
+ * kernels it launches (profiling aid, no counterpart in the paper): the
+ * choice timed on the first call of the size class when one was made in this
+ * process, else the size rule.  Writes one of AMC_PATH_* to *path (nullable)
+ * and the kernel count to *launches (nullable).  Host only, no device work.
+ * Returns AMC_E_INVALID for negative sizes. */
+enum { AMC_PATH_SCAN = 0,        /* single-pass scan over linked runs */
+       AMC_PATH_SMALL = 1,       /* one CTA: at most 2^16 ops over at most 2,048 variables */
+       AMC_PATH_WARP_DENSE = 2,  /* reduce / carry / apply, warp-sequential chunks */
+       AMC_PATH_DENSE = 3,       /* reduce / carry / apply, sorted tiles */
+       AMC_PATH_PREFIX = 4,      /* a reduce / carry / apply prefix, then the scan */
+       AMC_PATH_EPOCHS = 5 };    /* first part sorted by variable, then filtered epochs */
+AMC_API int amc_check_trace_plan(int64_t n_ops, int32_t n_vars, int has_init, int32_t* path, int32_t* launches);
 
 /* Workspace bytes amc_check_guarded_trace needs. */
 AMC_API size_t amc_check_guarded_trace_workspace(int64_t n_ops, int32_t n_vars);

@@ -47,6 +47,7 @@ def lib():
         L.amc_check_trace_workspace.restype = sz
         L.amc_check_trace_workspace.argtypes = [i64, i32]
         L.amc_check_trace.argtypes = [P, P, i64, i32, P, P, P, P, P, P, sz, P]
+        L.amc_check_trace_plan.argtypes = [i64, i32, ci, P, P]
         L.amc_check_guarded_trace_workspace.restype = sz
         L.amc_check_guarded_trace_workspace.argtypes = [i64, i32]
         L.amc_check_guarded_trace.argtypes = [P, P, i64, i32, P, P, P, P, P, P, sz, P]
@@ -134,6 +135,20 @@ def trace_workspace_bytes(n_ops: int, n_vars: int, guarded: bool = False) -> int
     L = lib()
     f = L.amc_check_guarded_trace_workspace if guarded else L.amc_check_trace_workspace
     return int(f(n_ops, n_vars))
+
+
+TRACE_PATHS = ("scan", "small", "warp_dense", "dense", "prefix", "epochs")
+
+
+def trace_plan(n_ops, n_vars, has_init=False):
+    """(path name, kernels launched) of the next check_trace of these sizes
+    (amc_check_trace_plan): the timed choice for the size class if one was
+    made in this process, else the size rule."""
+    path, launches = ctypes.c_int32(-1), ctypes.c_int32(0)
+    rc = lib().amc_check_trace_plan(int(n_ops), int(n_vars), 1 if has_init else 0, ctypes.byref(path),
+                                    ctypes.byref(launches))
+    _check(rc, "amc_check_trace_plan")
+    return TRACE_PATHS[path.value], int(launches.value)
 
 
 def check_trace(kind_side, var, n_vars, init_status=None, *, guarded=False, out=None,

@@ -1,4 +1,5 @@
 // api.cu -- C ABI entry points: argument checks, workspace layout, launches.
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -109,6 +110,8 @@ int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
     int rc = check_trace_args(kind_side, var, n_ops, n_vars, step_status, final_status, var_first_fault,
                               first_fault);
     if (rc) return rc;
+    if (init_status && n_vars > 0 && init_status < final_status + n_vars && final_status < init_status + n_vars)
+        return AMC_E_INVALID;
     if (!workspace || !aligned256(workspace) || ws_bytes < scan_workspace_bytes(n_ops, n_vars))
         return AMC_E_NOMEM;
     int* err = device_error_word();
@@ -127,17 +130,52 @@ int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
     L.workspace = workspace;
     L.profile = 3;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // candidates: stuck bitmap read through L1 (three CTAs per SM), in shared
-    // memory (2^20 variables, one CTA per SM) or none, each with groups of up
-    // to 16 tiles per claim where few ops are live; or L1 and single tiles
-    static const int fb[4] = {-2, 1 << 20, -1, -2};
-    static const int grp[4] = {16, 16, 16, 1};
-    return autotune_run(shape_key("trace", n_ops, n_vars, 0), 4, 0, s, [&](int i) {
+    // candidates, timed on the first call of a shape bucket: the path by size
+    // with the single-pass scan's stuck bitmap read through L1 (three CTAs per
+    // SM), in shared memory (2^20 variables, one CTA per SM) or none, each with
+    // groups of up to 16 tiles per claim; or L1 and single tiles; the reduce /
+    // carry / apply path at any size; the epoch path at any size (else the
+    // single-pass scan alone)
+    static const int fb[6] = {-2, 1 << 20, -1, -2, -2, -2};
+    static const int grp[6] = {16, 16, 16, 1, 16, 16};
+    static const int dns[6] = {-1, -1, -1, -1, 1, 0};
+    static const int tl[6] = {-1, -1, -1, -1, 0, 1};
+    auto run = [&](int i) {
         ScanLaunch C = L;
         C.fb_max_bits = fb[i];
         C.group_max = grp[i];
+        C.dense = dns[i];
+        C.tail = tl[i];
         return launch_scan_trace(C, s);
-    });
+    };
+    if (const char* e = getenv("AMC_TRACE_CANDIDATE")) {        // test override: one candidate, untimed
+        const int i = atoi(e);
+        if (i >= 0 && i < 6) return run(i);
+    }
+    return autotune_run(shape_key("trace", n_ops, n_vars, init_status ? 1 : 0), 6, 0, s, run);
+}
+
+int amc_check_trace_plan(int64_t n_ops, int32_t n_vars, int has_init, int32_t* path, int32_t* launches)
+{
+    if (n_ops < 0 || n_vars < 0) return AMC_E_INVALID;
+    static const int dns[6] = {-1, -1, -1, -1, 1, 0};
+    static const int tl[6] = {-1, -1, -1, -1, 0, 1};
+    int pick = autotune_lookup(shape_key("trace", n_ops, n_vars, has_init ? 1 : 0));
+    if (const char* e = getenv("AMC_TRACE_CANDIDATE")) pick = atoi(e);
+    if (pick < 0 || pick >= 6) pick = 0;
+    ScanLaunch L;
+    L.n_ops = n_ops;
+    L.n_vars = n_vars;
+    static uint8_t stand_in = 0;                     // the plan only tests these against null
+    L.init = has_init ? &stand_in : nullptr;
+    L.final_status = &stand_in;
+    L.dense = dns[pick];
+    L.tail = tl[pick];
+    int n = 0;
+    const int p = scan_trace_plan(L, &n);
+    if (path) *path = p;
+    if (launches) *launches = n;
+    return AMC_OK;
 }
 
 size_t amc_check_guarded_trace_workspace(int64_t n_ops, int32_t n_vars)
@@ -179,12 +217,16 @@ int amc_check_guarded_trace(const uint8_t* kind_side, const int32_t* var, int64_
     A.err = err;
     A.workspace = workspace;
     A.profile = 1;          // the profiled span covers both scans
-    // the choice tuned for plain traces of this shape, if any
-    static const int fb[4] = {-2, 1 << 20, -1, -2};
-    static const int grp[4] = {16, 16, 16, 1};
-    const int pick = autotune_lookup(shape_key("trace", n_ops, n_vars, 0));
-    A.fb_max_bits = fb[pick >= 0 && pick < 4 ? pick : 0];
-    A.group_max = grp[pick >= 0 && pick < 4 ? pick : 0];
+    // the choice tuned for plain traces of this shape, if any (the epoch path
+    // does not take guards)
+    static const int fb[6] = {-2, 1 << 20, -1, -2, -2, -2};
+    static const int grp[6] = {16, 16, 16, 1, 16, 16};
+    static const int dns[6] = {-1, -1, -1, -1, 1, 0};
+    int pick = autotune_lookup(shape_key("trace", n_ops, n_vars, init_status ? 1 : 0));
+    if (pick < 0 || pick >= 6) pick = 0;
+    A.fb_max_bits = fb[pick];
+    A.group_max = grp[pick];
+    A.dense = dns[pick];
     rc = launch_scan_trace(A, s);
     if (rc) return rc;
     // pass 2: GT resolved from the pre-status of the EN that follows it

@@ -36,7 +36,7 @@ constexpr int DPOS = 12;                 // log2(DT): position bits of a key
 constexpr int DDIG = 7;                  // radix digit bits
 constexpr int DENSE_MAX_VARS = 16384;    // the dense vector lives in shared memory
 constexpr int DENSE_MAX_CHUNKS = 2048;
-constexpr int64_t DENSE_MIN_OPS = 1 << 20;
+constexpr int64_t DENSE_MIN_OPS = 1 << 10;
 
 __device__ __forceinline__ int dpad(int i) { return i + (i >> 5); }
 
@@ -764,7 +764,10 @@ bool scan_dense_eligible(int64_t n_ops, int32_t n_vars)
 {
     if (n_vars < 1 || n_vars > DENSE_MAX_VARS || n_ops < 1) return false;
     if (const char* e = getenv("AMC_SCAN_DENSE")) return e[0] == '1';   // tuning and test override
-    return n_ops >= DENSE_MIN_OPS;
+    int lv = 0, ln = 0;
+    while (lv < 31 && ((int64_t)1 << lv) < (int64_t)n_vars) ++lv;
+    while (ln < 62 && ((int64_t)1 << ln) < n_ops) ++ln;
+    return ln >= 15 + 2 * (12 - lv) && n_ops >= DENSE_MIN_OPS;
 }
 
 size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)

@@ -484,6 +484,8 @@ int launch_ss_keys(const uint8_t* kind_side, const int32_t* var, int64_t n, int6
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 
+int ss_radix_passes(int32_t n_vars) { return (key_bits_of(n_vars) + SDIG - 1) / SDIG; }
+
 int launch_ss_radix(uint32_t* const key[2], uint32_t* const val[2], const int64_t* n_dev, int64_t cap,
                     int32_t n_vars, void* scratch, const int* gate, cudaStream_t s, int* passes_out)
 {

@@ -52,7 +52,10 @@ struct TailShape {
 // AMC_SCAN_TAIL="s,e": first part 2^s ops, epochs of 2^e ops; "s,-g": first
 // part 2^s ops, each epoch ending at 2^g times its start; for every trace
 // longer than 2^s ops (test and tuning override); "0" disables.
-bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh)
+// force: -1 by size (from DEFAULT_MIN_OPS ops), 1 for every trace longer than
+// 2^22 ops (first part 2^22 ops from 2^24 ops on, else a quarter of the trace),
+// 0 never.
+bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh, int force)
 {
     if (guarded || n_vars < TAIL_MIN_VARS || n_vars > TAIL_MAX_VARS) return false;
     if (const char* e = getenv("AMC_SCAN_TAIL")) {
@@ -70,8 +73,11 @@ bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh)
             return true;
         }
     }
-    if (n_ops < DEFAULT_MIN_OPS) return false;
-    sh.S = (int64_t)1 << DEFAULT_FIRST_LOG2;
+    if (force == 0) return false;
+    if (force == 1 ? n_ops <= ((int64_t)1 << DEFAULT_FIRST_LOG2) : n_ops < DEFAULT_MIN_OPS) return false;
+    int lg = DEFAULT_FIRST_LOG2;
+    while (lg > 12 && ((int64_t)1 << (lg + 2)) > n_ops) --lg;      // first part at most a quarter
+    sh.S = (int64_t)1 << lg;
     sh.grow = DEFAULT_GROW;
     return true;
 }
@@ -518,21 +524,42 @@ __global__ void tail_post_kernel(const int* gate, const uint8_t* __restrict__ st
 bool scan_tail_eligible(const ScanLaunch& L)
 {
     TailShape sh;
-    return L.dense != 0 && !L.n_dev && !L.gate && !L.guard && !L.pre_mode &&
-           tail_shape(L.n_ops, L.n_vars, false, sh);
+    return (L.dense != 0 || L.tail == 1) && !L.n_dev && !L.gate && !L.guard && !L.pre_mode &&
+           tail_shape(L.n_ops, L.n_vars, false, sh, L.tail);
 }
 
 size_t scan_tail_workspace_bytes(int64_t n_ops, int32_t n_vars)
 {
+    TailShape sh;                          // the largest shape a launch may take (forced)
+    if (!tail_shape(n_ops, n_vars, false, sh, 1)) return 0;
+    size_t b = tail_layout(sh, n_vars, n_ops).total;
+    TailShape sd;
+    if (tail_shape(n_ops, n_vars, false, sd, -1)) {
+        const size_t d = tail_layout(sd, n_vars, n_ops).total;
+        if (d > b) b = d;
+    }
+    return b;
+}
+
+int scan_tail_launches(const ScanLaunch& L)
+{
     TailShape sh;
-    if (!tail_shape(n_ops, n_vars, false, sh)) return 0;
-    return tail_layout(sh, n_vars, n_ops).total;
+    if (!scan_tail_eligible(L) || !tail_shape(L.n_ops, L.n_vars, false, sh, L.tail)) return 0;
+    // a sorted check: three kernels per radix pass, segmented scan
+    const int sorted = 1 + 3 * ss_radix_passes(L.n_vars);
+    int epochs = 0;
+    for (int64_t e0 = sh.S; e0 < L.n_ops; e0 = epoch_end(sh, e0, L.n_ops)) ++epochs;
+    // first part: pairs, its sorted check, the stuck bitmap; per epoch filter,
+    // block sums, offsets, gather (which writes the pairs), the candidates'
+    // sorted check, gated set-up / scan / final statuses and the gated merge
+    // with bitmap rebuild
+    return 1 + sorted + 1 + epochs * (4 + sorted + 3 + 1);
 }
 
 int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
 {
     TailShape sh;
-    if (!tail_shape(L.n_ops, L.n_vars, false, sh)) return AMC_E_INVALID;
+    if (!tail_shape(L.n_ops, L.n_vars, false, sh, L.tail)) return AMC_E_INVALID;
     const TailLayout lay = tail_layout(sh, L.n_vars, L.n_ops);
     uint8_t* w = static_cast<uint8_t*>(L.workspace);
     uint8_t* st[2] = {w + lay.st0, w + lay.st1};

@@ -1746,8 +1746,35 @@ size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars, bool with_dense)
     return b;
 }
 
+int scan_trace_plan(const ScanLaunch& L, int* launches)
+{
+    int n = 2, path = AMC_PATH_SCAN;                        // scan, final statuses
+    const bool plain = !L.n_dev && !L.gate;
+    if (scan_small_eligible(L)) {
+        n = 1;
+        path = AMC_PATH_SMALL;
+    } else if (scan_tail_eligible(L)) {
+        n = scan_tail_launches(L);
+        path = AMC_PATH_EPOCHS;
+    } else if (L.dense != 0 && plain &&
+               ((L.dense == 1 && L.n_vars >= 1 && L.n_vars <= 16384 && L.n_ops >= 1) ||
+                scan_dense_eligible(L.n_ops, L.n_vars))) {
+        const char* e = getenv("AMC_SCAN_DENSE_SORT");
+        const bool warp = L.n_vars <= 8192 && !(e && e[0] == '1');
+        n = warp ? 5 : 3;                                   // chunk, reduce, carry, expand, chunk; or reduce, carry, apply
+        path = warp ? AMC_PATH_WARP_DENSE : AMC_PATH_DENSE;
+    } else if (L.dense != 0 && (L.prefix_log2 > 0 ? scan_forced_prefix(L)
+                                                  : plain && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr))) {
+        n = 7;                                              // prefix (3), bitmap seed, scan (2), merge
+        path = AMC_PATH_PREFIX;
+    }
+    if (launches) *launches = n;
+    return path;
+}
+
 int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
 {
+    if (scan_small_eligible(L)) return launch_scan_small(L, s);
     if (scan_tail_eligible(L)) return launch_scan_tail(L, s);
     ScanParams p{};
     p.kind_side = L.kind_side;
@@ -1796,7 +1823,9 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
     const bool plain = !L.n_dev && !L.gate;
-    if (L.dense != 0 && plain && scan_dense_eligible(L.n_ops, L.n_vars)) return launch_scan_dense(L, w + 256, s);
+    const bool dense_forced = L.dense == 1 && L.n_vars >= 1 && L.n_vars <= 16384 && L.n_ops >= 1;
+    if (L.dense != 0 && plain && (dense_forced || scan_dense_eligible(L.n_ops, L.n_vars)))
+        return launch_scan_dense(L, w + 256, s);
     if (L.dense != 0 && (L.prefix_log2 > 0 ? scan_forced_prefix(L)
                                            : plain && scan_prefix_eligible(L.n_ops, L.n_vars, L.init != nullptr)))
         return launch_scan_prefix(L, w + 256, s);

@@ -67,14 +67,19 @@ struct ScanLaunch {
                                         // size, initial statuses or device count (many variables)
     const int* gate = nullptr;          // device flag: the scan and its final-status pass do
     int gate_on = 0;                    // nothing unless (*gate != 0) == gate_on (single-pass only)
+    int tail = -1;                      // epoch path: -1 by size (2^29 ops or more), 1 whenever
+                                        // eligible (more than 2^22 ops), 0 never
 };
 
 int scan_tile_size();
 size_t scan_workspace_bytes(int64_t n_ops, int32_t n_vars, bool with_dense = true);
 int launch_scan_trace(const ScanLaunch& L, cudaStream_t s);
-// Traces over at most 16,384 variables and of 2^20 ops or more (or whenever
-// AMC_SCAN_DENSE=1; never when it is 0) take the reduce / carry / apply path
-// of scan_dense.cu; its scratch follows the single-pass workspace.
+// Traces over at most 16,384 variables take the reduce / carry / apply path of
+// scan_dense.cu by size (or whenever AMC_SCAN_DENSE=1 or the launch forces it;
+// never when AMC_SCAN_DENSE=0); its scratch follows the single-pass workspace.
+// By size: at least 1,024 ops and at least 2^(15 + 2 (12 - log2 n_vars)) ops (the crossover with the
+// single-pass scan measured on random traces with the Zipf workload's kind
+// mix: 2^11 ops at 2^14 variables, 2^15 at 2^12, 2^21 at 2^9).
 bool scan_dense_eligible(int64_t n_ops, int32_t n_vars);
 size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars);
 int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
@@ -100,8 +105,18 @@ int launch_merge_faults(int32_t* vff, const int32_t* vff_part, int32_t n_vars, i
 // the epoch's start statuses); its scratch replaces the single-pass workspace
 // (scan_workspace_bytes covers both).
 bool scan_tail_eligible(const ScanLaunch& L);
+// Traces of at most 2^16 ops over at most 2,048 variables, without a guard:
+// one CTA does the whole check (small.cu), no workspace.
+bool scan_small_eligible(const ScanLaunch& L);
+int launch_scan_small(const ScanLaunch& L, cudaStream_t s);
 size_t scan_tail_workspace_bytes(int64_t n_ops, int32_t n_vars);
 int launch_scan_tail(const ScanLaunch& L, cudaStream_t s);
+// Kernels one launch_scan_tail of L runs (0 when L does not take that path).
+int scan_tail_launches(const ScanLaunch& L);
+// Radix passes of a sort by variable id over n_vars variables.
+int ss_radix_passes(int32_t n_vars);
+// The path launch_scan_trace takes for L (AMC_PATH_*) and the kernels it runs.
+int scan_trace_plan(const ScanLaunch& L, int* launches);
 // A set of ops checked by sorting it by variable (scan_sorted.cu): the pairs
 // (variable id, set index << 4 | 4-bit code of the op byte) sit in key[0] /
 // val[0]; key[1] / val[1] are the sort's second buffers.  Writes the status of

@@ -103,3 +103,38 @@ def test_epoch_shape_follows_its_override(libamc, monkeypatch):
     assert ws(n, v) == plain                 # a first part beyond 2^27 ops is not accepted
     monkeypatch.setenv("AMC_SCAN_TAIL", "16,-7")
     assert ws(n, v) == plain                 # nor a growth beyond 2^4
+
+
+def test_trace_plan_follows_the_size_rule(monkeypatch):
+    # host logic only: which path a check of these sizes takes before any
+    # timing, and the kernels it launches
+    import paper_1910_11110_gb300 as amc
+    for k in ("AMC_SCAN_DENSE", "AMC_SCAN_TAIL", "AMC_SCAN_DENSE_SORT"):
+        monkeypatch.delenv(k, raising=False)
+    plan = amc.trace_plan
+    assert plan(4096, 16) == ("small", 1)
+    assert plan(1 << 16, 2048) == ("small", 1)
+    assert plan(1 << 16, 2048, has_init=True) == ("small", 1)
+    assert plan((1 << 16) + 1, 16)[0] == "scan"           # 16 variables: the scan at every length
+    assert plan(1 << 16, 4096) == ("warp_dense", 5)       # 2^12 variables from 2^15 ops
+    assert plan(1 << 14, 4096)[0] == "scan"
+    assert plan(1 << 21, 512) == ("warp_dense", 5)        # 2^9 variables from 2^21 ops
+    assert plan(1 << 20, 512)[0] == "scan"
+    assert plan(1 << 11, 16384) == ("dense", 3)           # 2^14 variables from 2^11 ops
+    assert plan(1 << 24, 1 << 20) == ("prefix", 7)
+    assert plan(1 << 24, 1 << 20, has_init=True)[0] == "scan"
+    # the epoch path from 2^29 ops: pairs + 3 radix passes (3 kernels each) +
+    # segmented scan + bitmap, then 18 kernels per epoch (2^22 -> 2^24 -> 2^26
+    # -> 2^28 -> 2^30)
+    assert plan(1 << 30, 1 << 20) == ("epochs", 12 + 18 * 4)
+    assert plan(1 << 29, 1 << 20) == ("epochs", 12 + 18 * 4)
+    monkeypatch.setenv("AMC_SCAN_TAIL", "0")
+    assert plan(1 << 30, 1 << 20) == ("prefix", 7)
+    monkeypatch.setenv("AMC_SCAN_DENSE", "0")
+    assert plan(1 << 16, 4096) == ("scan", 2)
+    monkeypatch.setenv("AMC_SCAN_DENSE", "1")
+    assert plan(1 << 20, 64) == ("warp_dense", 5)
+    monkeypatch.setenv("AMC_SCAN_DENSE_SORT", "1")
+    assert plan(1 << 20, 64) == ("dense", 3)
+    with pytest.raises(RuntimeError):
+        plan(-1, 16)

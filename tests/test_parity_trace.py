@@ -202,3 +202,40 @@ def test_shared_window_with_l1_bitmap(amc, oracle_mod, monkeypatch, group):
     assert_same(*run_both(amc, oracle_mod, ks, var, 1 << 16))
     init = rng.integers(0, 5, 1 << 16).astype(np.uint8)
     assert_same(*run_both(amc, oracle_mod, ks, var, 1 << 16, init))
+
+
+@pytest.mark.parametrize("n_ops,n_vars", [(0, 5), (1, 1), (31, 3), (32, 16), (33, 16), (4096, 16), (4097, 2048),
+                                          (65536, 2048), (65536, 1), (50_000, 700)])
+def test_small_traces_one_cta(amc, oracle_mod, n_ops, n_vars):
+    # traces of at most 2^16 ops over at most 2,048 variables are checked by
+    # one CTA; every kind incl. EN, initial statuses incl. (I,I) and F
+    rng = np.random.default_rng(n_ops * 7 + n_vars)
+    ks, var = workloads.trace_random(rng, n_ops, n_vars, kinds=(0, 1, 2, 3, 4, 5, 7))
+    init = rng.integers(0, 5, n_vars).astype(np.uint8)
+    for ini in (None, init):
+        exp = oracle_mod.check_trace(ks, var, n_vars, ini)
+        dev = torch.device("cuda")
+        out = amc.check_trace(torch.from_numpy(ks).to(dev), torch.from_numpy(var).to(dev), n_vars,
+                              None if ini is None else torch.from_numpy(ini).to(dev))
+        assert amc.sync_status() == 0
+        assert np.array_equal(out["step_status"].cpu().numpy(), exp[0])
+        assert np.array_equal(out["final_status"].cpu().numpy(), exp[1])
+        assert np.array_equal(out["var_first_fault"].cpu().numpy(), exp[2])
+        assert int(out["first_fault"].cpu()[0]) == exp[3]
+
+
+def test_small_trace_bad_input(amc):
+    dev = torch.device("cuda")
+    ks = torch.zeros(100, dtype=torch.uint8, device=dev)
+    var = torch.zeros(100, dtype=torch.int32, device=dev)
+    var[50] = 9
+    amc.check_trace(ks, var, 8)
+    assert amc.sync_status() == amc.E_RANGE
+    var[50] = 1
+    ks[7] = 6                                   # GT in a plain check
+    amc.check_trace(ks, var, 8)
+    assert amc.sync_status() == amc.E_INVALID
+    ks[7] = 0x48                                # malformed byte
+    amc.check_trace(ks, var, 8)
+    assert amc.sync_status() == amc.E_INVALID
+    assert amc.sync_status() == 0
