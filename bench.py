@@ -13,6 +13,12 @@ timed on the host cores beside it:
   uniform_4096  16 variables, 4,096 uniform ops (seed 0): latency per check;
   vectorpu      2^24 VectorPU calls over 4,096 overlapping arrays (seed 2):
                 translation + guarded check per step;
+  vectorpu_lifetimes  2^24 VectorPU calls over 16 vectors and 65,536
+                pvectors created and deleted during the run (seed 6):
+                translation with live overlap sets + check with inherited
+                statuses per step;
+  trace_sizes   the trace check on Zipf traces of 2^24, 2^26 and 2^28 ops
+                and on a 2^30-op low-fault trace;
   programs      100,000 If/While programs (seed 3): the batched persistent
                 launch (CUDA graph) against one launch per program;
   serve         open-loop Poisson arrivals at 1k / 10k / 100k requests/s,
@@ -25,7 +31,8 @@ step); value = ops of all ranks / max time over ranks; the sub-records run at
 N = 1 only.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload all|trace|uniform|vectorpu|programs|serve]
+                  [--workload all|trace|uniform|vectorpu|vectorpu_lifetimes|trace_sizes|
+                              programs|well_declared|kloc|serve]
                   [--n-ops N] [--n-vars V] [--no-e2e] [--no-cpu]
 """
 from __future__ import annotations
@@ -60,7 +67,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--workload", default="all",
-                    choices=["all", "trace", "uniform", "programs", "vectorpu", "well_declared", "kloc", "serve"])
+                    choices=["all", "trace", "uniform", "programs", "vectorpu", "vectorpu_lifetimes", "trace_sizes",
+                             "well_declared", "kloc", "serve"])
     ap.add_argument("--rates", default="1000,10000,100000")
     ap.add_argument("--serve-requests", type=int, default=10_000)
     ap.add_argument("--serve-seconds", type=float, default=12.0, help="submission window per rate")
@@ -410,6 +418,8 @@ def sub_records(args, amc, dev):
     out = {}
     for name, fn in (("uniform_4096", lambda: measure_uniform(args, amc, dev)),
                      ("vectorpu", lambda: measure_vectorpu(args, amc, dev)),
+                     ("vectorpu_lifetimes", lambda: measure_lifetimes(args, amc, dev)),
+                     ("trace_sizes", lambda: measure_sizes(args, amc, dev)),
                      ("programs", lambda: measure_programs(args, amc, dev)),
                      ("well_declared", lambda: measure_well_declared(args, amc, dev)),
                      ("kloc", lambda: measure_kloc(args, amc, dev)),
@@ -600,6 +610,133 @@ def measure_vectorpu(args, amc, dev):
                              "kind": "oracle",
                              "sample": f"the first {k} calls ({ns} statements), single thread ({dt:.1f} s)"},
             "clocks": clk}
+
+
+def measure_lifetimes(args, amc, dev):
+    """2^24 VectorPU calls over 16 vectors and 65,536 pvectors created and
+    deleted during the run (seed 6): translation with live overlap sets and
+    creation records, then the check with inherited statuses (two guarded
+    passes) per step."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+    w = workloads.vectorpu_lifetimes(seed=6)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in w.items()}
+    A = d["arr_start"].numel()
+    n_calls = d["call_side"].numel()
+    n_opnd = d["opnd_array"].numel()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        args_tr = (d["arr_start"], d["arr_len"], d["arr_parent"], d["arr_born"], d["arr_died"], d["call_side"],
+                   d["call_off"], d["opnd_array"], d["opnd_mode"])
+        tr = amc.translate_vectorpu_lifetimes(*args_tr, stream=stream)
+        n, pairs = tr["n"], tr["max_pairs"]
+        tout = dict(kind_side=tr["kind_side"], var=tr["var"], call_first_op=tr["call_first_op"],
+                    arr_probe=tr["arr_probe"], n_dev=tr["n_dev"])
+        out = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+                   final_status=torch.empty(2 * A, dtype=torch.uint8, device=dev),
+                   var_first_fault=torch.empty(2 * A, dtype=torch.int32, device=dev),
+                   first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+        L = amc.lib()
+        ws = torch.empty(L.amc_check_inherited_trace_workspace(n, A) + 256, dtype=torch.uint8, device=dev)
+        ws = ws[(-ws.data_ptr()) % 256:]
+
+        def step():
+            r = amc.translate_vectorpu_lifetimes(*args_tr, max_pairs=pairs, known_n=n, out=tout, stream=stream)
+            amc.check_inherited_trace(r["kind_side"], r["var"], A, d["arr_parent"], r["arr_probe"], out=out,
+                                      workspace=ws, stream=stream)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        assert amc.sync_status(stream) == 0
+        clocks = ClockSampler(0)
+        clocks.start()
+        ms = timed(step, args.sub_steps, stream)
+        clk = clocks.stop()
+        assert amc.sync_status(stream) == 0
+        assert int(tout["n_dev"].item()) == n
+    # oracle: the first k calls (lifetimes clipped to them), about
+    # sub_cpu_seconds of one core; its statuses before call k - 1 are the GPU's
+    k = 1 << 12
+    while True:
+        sub = dict(w)
+        sub["arr_born"] = np.minimum(w["arr_born"], k - 1).astype(np.int32)
+        sub["arr_died"] = np.maximum(np.minimum(w["arr_died"], k), sub["arr_born"] + 1).astype(np.int32)
+        sub["call_side"] = w["call_side"][:k]
+        sub["call_off"] = w["call_off"][:k + 1]
+        m = int(w["call_off"][k])
+        sub["opnd_array"] = w["opnd_array"][:m]
+        sub["opnd_mode"] = w["opnd_mode"][:m]
+        t0 = time.perf_counter()
+        res = oracle.vectorpu_lifetimes(**sub)
+        dt = time.perf_counter() - t0
+        if dt > args.sub_cpu_seconds / 4 or k >= n_calls:
+            break
+        k = min(n_calls, k * 4)
+    ns = int(res["call_first_op"][k - 1])
+    assert np.array_equal(out["step_status"][:ns].cpu().numpy(), res["step_status"][:ns])
+    alg = 20 * A + n_calls + 4 * (n_calls + 1) + 5 * n_opnd + n + 8 * A + 5 * 2 * A
+    return {"workload": "vectorpu_lifetimes", "n_vectors": 16, "n_pvectors": A - 16, "n_calls": n_calls,
+            "operands": n_opnd, "statements": n, "overlap_list_entries": pairs, "seed": 6, "ms_per_step": ms,
+            "statements_per_s": n / (ms * 1e-3), "calls_per_s": n_calls / (ms * 1e-3),
+            "roofline": roofline(alg, ms, note="algorithmic bytes: arrays (range, vector, lifetime), calls and "
+                                               "operands in; one status per translated statement, the creation "
+                                               "records and 5 B per variable out"),
+            "gpu_launches_per_step": lifetimes_launches(A, n_calls, n),
+            "cpu_baseline": {"value": ns / dt, "unit": "statements/s", "calls_per_s": k / dt, "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"the first {k} calls (lifetimes clipped to them; {ns} statements compared), "
+                                       f"single thread ({dt:.1f} s)"},
+            "clocks": clk}
+
+
+def measure_sizes(args, amc, dev):
+    """The trace check away from the headline size: Zipf(1.05) traces over
+    2^20 variables (the headline kind mix) of 2^24, 2^26 and 2^28 ops, and a
+    2^30-op low-fault trace (r .02 w .60 Push .05 Pull .05 Noop .28), each
+    timed over sub_steps checks after the first call of its size class has
+    timed the candidate paths."""
+    import torch
+
+    import workloads
+    nv = 1 << 20
+    cases = [("zipf_2p24", 1 << 24, workloads.KIND_MIX), ("zipf_2p26", 1 << 26, workloads.KIND_MIX),
+             ("zipf_2p28", 1 << 28, workloads.KIND_MIX), ("low_fault_2p30", 1 << 30, (0.02, 0.60, 0.05, 0.05, 0.28))]
+    out = {}
+    stream = torch.cuda.Stream()
+    for name, n, mix in cases:
+        with torch.cuda.stream(stream):
+            ks, var = workloads.trace_zipf(n, nv, seed=1, device=dev, kind_mix=mix)
+            res = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+                       final_status=torch.empty(nv, dtype=torch.uint8, device=dev),
+                       var_first_fault=torch.empty(nv, dtype=torch.int32, device=dev),
+                       first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+            ws = torch.empty(amc.trace_workspace_bytes(n, nv) + 256, dtype=torch.uint8, device=dev)
+            ws = ws[(-ws.data_ptr()) % 256:]
+            step = lambda: amc.check_trace(ks, var, nv, out=res, workspace=ws, stream=stream)
+            for _ in range(max(3, args.warmup)):
+                step()
+            assert amc.sync_status(stream) == 0
+            clocks = ClockSampler(0)
+            clocks.start()
+            ms = timed(step, args.sub_steps, stream)
+            clk = clocks.stop()
+            assert amc.sync_status(stream) == 0
+            stuck = int((res["step_status"] == 4).sum().item())
+            path, launches = amc.trace_plan(n, nv)
+            alg = 6 * n + 5 * nv
+            out[name] = {"n_ops": n, "n_vars": nv, "kind_mix": list(mix), "seed": 1, "ms_per_check": ms,
+                         "ops_per_s": n / (ms * 1e-3), "stuck_fraction": stuck / n, "path": path,
+                         "gpu_launches_per_check": launches,
+                         "roofline": roofline(alg, ms, note="6 B per op, 5 B per variable; the span of the "
+                                                            "whole check (every kernel)"),
+                         "l2": "inputs exceed L2" if 5 * n > (129 << 20) else "inputs fit in L2 (warm)",
+                         "clocks": clk}
+            del ks, var, res, ws
+            torch.cuda.empty_cache()
+    return out
 
 
 def measure_programs(args, amc, dev):
@@ -920,18 +1057,49 @@ def measure_serve(args, amc, dev):
             "by_rate": results, "clocks": clk}
 
 
-def vectorpu_launches(n_statements, n_vars):
-    """Kernels of one translation + guarded check: 11 for the translation
-    (two overlap passes, count, emit, total, two 3-kernel scans), then per
-    check pass the reduce / carry / apply path where the size rule takes it
-    for a trace of that length (5 kernels up to 8,192 variables -- warp
-    batches and a two-level carry -- else 3), or the scan kernel plus, in the
-    second pass, the final-status kernel."""
+def radix_passes(key_range):
+    """Passes of the library's 7-bit LSD radix sort for keys below key_range."""
+    kb = 1
+    while kb < 31 and (1 << kb) < key_range:
+        kb += 1
+    return (kb + 6) // 7
+
+
+def overlap_launches(n_arrays):
+    """Kernels that build the overlap lists: keys, the sort by range start
+    (three kernels per radix pass), the counting sweep, a three-kernel scan,
+    the total, the cursor reset, the filling sweep, two sorts of the pairs,
+    the copy and the overflow clear."""
+    return 1 + 3 * radix_passes(2 ** 31 - 1) + 1 + 3 + 1 + 1 + 1 + 2 * 3 * radix_passes(n_arrays) + 1 + 1
+
+
+def guarded_check_launches(n_statements, n_vars):
+    """Kernels of one guarded check (two scan passes): the reduce / carry /
+    apply path where the size rule takes it for a trace of that length (5
+    kernels up to 8,192 variables -- warp batches and a two-level carry --
+    else 3) in each pass, or the scan kernel plus, in the second pass, the
+    final-status kernel."""
     import paper_1910_11110_gb300 as amc
     path, n = amc.trace_plan(n_statements, n_vars)
     if path in ("warp_dense", "dense"):
-        return 11 + 2 * n
-    return 11 + 1 + 2
+        return 2 * n
+    return 1 + 2
+
+
+def vectorpu_launches(n_statements, n_vars):
+    """Kernels of one translation + guarded check: the overlap lists, counts,
+    a three-kernel scan, emission and the total, then the guarded check."""
+    return overlap_launches(n_vars // 2) + 1 + 3 + 1 + 1 + guarded_check_launches(n_statements, n_vars)
+
+
+def lifetimes_launches(n_arrays, n_calls, n_statements):
+    """Kernels of one lifetimes translation + inherited check: the overlap
+    lists, the lifetimes check and the sort by creation call, counts, scan,
+    emission and the total; then two guarded checks with the inheritance
+    kernel between them."""
+    births = 1 + 3 * radix_passes(n_calls + 1)
+    return (overlap_launches(n_arrays) + births + 1 + 3 + 1 + 1 +
+            2 * guarded_check_launches(n_statements, 2 * n_arrays) + 1)
 
 
 TRACE_PATH_TEXT = {
@@ -999,7 +1167,9 @@ def main():
         fn = {"uniform": lambda: measure_uniform(args, amc, dev), "vectorpu": lambda: measure_vectorpu(args, amc, dev),
               "well_declared": lambda: measure_well_declared(args, amc, dev),
               "kloc": lambda: measure_kloc(args, amc, dev),
-              "programs": lambda: measure_programs(args, amc, dev), "serve": lambda: measure_serve(args, amc, dev)}
+              "programs": lambda: measure_programs(args, amc, dev), "serve": lambda: measure_serve(args, amc, dev),
+              "vectorpu_lifetimes": lambda: measure_lifetimes(args, amc, dev),
+              "trace_sizes": lambda: measure_sizes(args, amc, dev)}
         print(json.dumps(fn[args.workload]()), flush=True)
 
 

@@ -262,7 +262,8 @@ AMC_API int amc_check_trace_k(const uint8_t* op, const int32_t* var, int64_t n_o
 #define AMC_MAX_OPERANDS 32
 
 /* Workspace bytes amc_translate_vectorpu needs (grows as n_arrays^2: the
- * overlap sets are stored as lists). */
+ * overlap lists are sized for every array overlapping every other; they are
+ * built by sorting the ranges by start and sweeping, in O(A log A + pairs)). */
 AMC_API size_t amc_translate_vectorpu_workspace(int32_t n_arrays, int64_t n_calls, int64_t n_operands);
 
 /* Translates n_calls component calls into a core trace over 2 * n_arrays
@@ -299,6 +300,64 @@ AMC_API int amc_translate_vectorpu(const int32_t* arr_start, const int32_t* arr_
                            int infer_overlap,
                            uint8_t* out_kind_side, int32_t* out_var, int64_t out_cap, int64_t* out_n,
                            int64_t* call_first_op, void* workspace, size_t ws_bytes, void* stream);
+
+/* pvectors created and deleted during the run -- Section 4.3 (r_v is
+ * initialised when a vector is declared, updated at pvector creations and
+ * deletions, queried at calls) and Section 5's account of VectorPU's partial
+ * vectors (a new pvector inherits the coherence state of its mother vector).
+ *   arr_parent [n_arrays]  -1 for a vector (its elements are a fresh
+ *                          allocation), else the id of the vector the pvector
+ *                          is a window of: a vector (parent -1), not the
+ *                          pvector itself, whose range holds its range
+ *   arr_born, arr_died     the array is live at calls born <= c < died
+ *                          (0 <= born < died <= n_calls); a pvector's lifetime
+ *                          lies within its vector's
+ * Overlap lists keep only the pairs whose lifetimes meet; at call c, O(M),
+ * the shadows and the projections of body writes take only the arrays live
+ * at c, and every operand must be live at c.  Before call c, each pvector
+ * created there (ascending id) takes its vector's real and abstract
+ * statuses; the translated trace records this at the head of call c's
+ * statements as Noop v, Noop v# (CPU side, no effect), and arr_probe[a]
+ * (device int64 [n_arrays]) = index of the first of the two (-1 for vectors).
+ *
+ * amc_vectorpu_overlap_pairs writes to *n_pairs (device int64) the number of
+ * list entries (overlapping pairs whose lifetimes meet, counted in both
+ * directions; with arr_born = arr_died = NULL every pair): the max_pairs the
+ * translation needs.  amc_translate_vectorpu_lifetimes is then
+ * amc_translate_vectorpu with those rules; more than max_pairs list entries
+ * give AMC_E_RANGE (device).  Feed its trace to amc_check_inherited_trace.
+ * Errors (device): AMC_E_INVALID for a malformed lifetime or vector link or an
+ * operand that is not live at its call, AMC_E_RANGE for a vector id out of
+ * range; the rest as amc_translate_vectorpu. */
+AMC_API size_t amc_vectorpu_overlap_pairs_workspace(int32_t n_arrays);
+AMC_API int amc_vectorpu_overlap_pairs(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_born,
+                                       const int32_t* arr_died, int32_t n_arrays, int64_t* n_pairs,
+                                       void* workspace, size_t ws_bytes, void* stream);
+AMC_API size_t amc_translate_vectorpu_lifetimes_workspace(int32_t n_arrays, int64_t n_calls, int64_t n_operands,
+                                                          int64_t max_pairs);
+AMC_API int amc_translate_vectorpu_lifetimes(const int32_t* arr_start, const int32_t* arr_len,
+                                             const int32_t* arr_parent, const int32_t* arr_born,
+                                             const int32_t* arr_died, int32_t n_arrays, const uint8_t* call_side,
+                                             const int32_t* call_off, int64_t n_calls, const int32_t* opnd_array,
+                                             const uint8_t* opnd_mode, int64_t n_operands, int infer_overlap,
+                                             int64_t max_pairs, uint8_t* out_kind_side, int32_t* out_var,
+                                             int64_t out_cap, int64_t* out_n, int64_t* call_first_op,
+                                             int64_t* arr_probe, void* workspace, size_t ws_bytes, void* stream);
+
+/* amc_check_guarded_trace of a trace with creation records (from
+ * amc_translate_vectorpu_lifetimes) over 2 * n_arrays variables: every
+ * variable starts from the initial store, except that each pvector starts
+ * from the statuses its vector has at its creation record.  Two passes: the
+ * first from the initial store gives every vector's statuses at the records
+ * (a vector's statuses never depend on a pvector's), the second runs from the
+ * inherited statuses and writes the outputs.  arr_parent and arr_probe as
+ * given to / written by the translation.  Errors: as amc_check_guarded_trace;
+ * AMC_E_INVALID (device) for a record that is not Noop v, Noop v#. */
+AMC_API size_t amc_check_inherited_trace_workspace(int64_t n_ops, int32_t n_arrays);
+AMC_API int amc_check_inherited_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_arrays,
+                                      const int32_t* arr_parent, const int64_t* arr_probe, uint8_t* step_status,
+                                      uint8_t* final_status, int32_t* var_first_fault, int64_t* first_fault,
+                                      void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* (3) Batches of structured programs, relation mode -- Fig. Opsem with      */

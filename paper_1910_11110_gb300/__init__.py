@@ -59,6 +59,17 @@ def lib():
             L.amc_translate_vectorpu_workspace.argtypes = [i32, i64, i64]
             L.amc_translate_vectorpu.argtypes = [P, P, i32, P, P, i64, P, P, i64, ci,
                                                  P, P, i64, P, P, P, sz, P]
+        if hasattr(L, "amc_translate_vectorpu_lifetimes"):
+            L.amc_vectorpu_overlap_pairs_workspace.restype = sz
+            L.amc_vectorpu_overlap_pairs_workspace.argtypes = [i32]
+            L.amc_vectorpu_overlap_pairs.argtypes = [P, P, P, P, i32, P, P, sz, P]
+            L.amc_translate_vectorpu_lifetimes_workspace.restype = sz
+            L.amc_translate_vectorpu_lifetimes_workspace.argtypes = [i32, i64, i64, i64]
+            L.amc_translate_vectorpu_lifetimes.argtypes = [P, P, P, P, P, i32, P, P, i64, P, P, i64, ci, i64,
+                                                           P, P, i64, P, P, P, P, sz, P]
+            L.amc_check_inherited_trace_workspace.restype = sz
+            L.amc_check_inherited_trace_workspace.argtypes = [i64, i32]
+            L.amc_check_inherited_trace.argtypes = [P, P, i64, i32, P, P, P, P, P, P, P, sz, P]
         if hasattr(L, "amc_check_trace_k"):
             L.amc_check_trace_k_workspace.restype = sz
             L.amc_check_trace_k_workspace.argtypes = [i64, i32]
@@ -182,6 +193,123 @@ def check_trace(kind_side, var, n_vars, init_status=None, *, guarded=False, out=
             _p(ws), ws.numel(), _stream_ptr(stream))
     _check(rc, "amc_check_trace")
     return out
+
+
+def vectorpu_overlap_pairs(arr_start, arr_len, arr_born=None, arr_died=None, *, out=None, stream=None):
+    """Overlap-list entries (overlapping pairs whose lifetimes meet, both
+    directions) of the arrays: the max_pairs translate_vectorpu_lifetimes
+    needs (amc_vectorpu_overlap_pairs).  Returns the device int64 [1] tensor
+    (``out`` if given); read it with .item()."""
+    _dev(arr_start, torch.int32, "arr_start")
+    _dev(arr_len, torch.int32, "arr_len")
+    if (arr_born is None) != (arr_died is None):
+        raise ValueError("arr_born and arr_died go together")
+    if arr_born is not None:
+        _dev(arr_born, torch.int32, "arr_born")
+        _dev(arr_died, torch.int32, "arr_died")
+    A = arr_start.numel()
+    dev = arr_start.device
+    L = lib()
+    n = out if out is not None else torch.empty(1, dtype=torch.int64, device=dev)
+    ws = _ws.get(L.amc_vectorpu_overlap_pairs_workspace(A), dev)
+    rc = L.amc_vectorpu_overlap_pairs(_p(arr_start), _p(arr_len), _p(arr_born), _p(arr_died), A, _p(n), _p(ws),
+                                      ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_vectorpu_overlap_pairs")
+    return n
+
+
+def translate_vectorpu_lifetimes(arr_start, arr_len, arr_parent, arr_born, arr_died, call_side, call_off,
+                                 opnd_array, opnd_mode, *, infer_overlap=True, max_pairs=None, out_cap=None,
+                                 known_n=None, out=None, stream=None):
+    """Translate VectorPU calls over pvectors with lifetimes
+    (amc_translate_vectorpu_lifetimes).  All inputs are CUDA tensors.  Returns
+    dict(kind_side, var, call_first_op, arr_probe, n, n_dev, max_pairs).
+    max_pairs None: counted first (amc_vectorpu_overlap_pairs, one host read).
+    known_n / out: as translate_vectorpu (no host read when max_pairs is
+    given too)."""
+    for t, dt, nm in ((arr_start, torch.int32, "arr_start"), (arr_len, torch.int32, "arr_len"),
+                      (arr_parent, torch.int32, "arr_parent"), (arr_born, torch.int32, "arr_born"),
+                      (arr_died, torch.int32, "arr_died"), (call_side, torch.uint8, "call_side"),
+                      (call_off, torch.int32, "call_off"), (opnd_array, torch.int32, "opnd_array"),
+                      (opnd_mode, torch.uint8, "opnd_mode")):
+        _dev(t, dt, nm)
+    A = arr_start.numel()
+    n_calls = call_side.numel()
+    n_opnd = opnd_array.numel()
+    dev = arr_start.device
+    L = lib()
+    if max_pairs is None:
+        max_pairs = int(vectorpu_overlap_pairs(arr_start, arr_len, arr_born, arr_died, stream=stream).item())
+    max_pairs = max(int(max_pairs), 1)
+    ws = _ws.get(L.amc_translate_vectorpu_lifetimes_workspace(A, n_calls, n_opnd, max_pairs), dev)
+
+    def call(ks, var, cap, n_dev, first, probe):
+        rc = L.amc_translate_vectorpu_lifetimes(_p(arr_start), _p(arr_len), _p(arr_parent), _p(arr_born),
+                                                _p(arr_died), A, _p(call_side), _p(call_off), n_calls,
+                                                _p(opnd_array), _p(opnd_mode), n_opnd, int(bool(infer_overlap)),
+                                                max_pairs, _p(ks), _p(var), cap, _p(n_dev), _p(first), _p(probe),
+                                                _p(ws), ws.numel(), _stream_ptr(stream))
+        _check(rc, "amc_translate_vectorpu_lifetimes")
+
+    if known_n is not None:
+        n = int(known_n)
+        if out is None:
+            out = dict(kind_side=torch.empty(max(n, 1), dtype=torch.uint8, device=dev),
+                       var=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+                       call_first_op=torch.empty(n_calls + 1, dtype=torch.int64, device=dev),
+                       arr_probe=torch.empty(max(A, 1), dtype=torch.int64, device=dev),
+                       n_dev=torch.empty(1, dtype=torch.int64, device=dev))
+        call(out["kind_side"], out["var"], n, out["n_dev"], out["call_first_op"], out["arr_probe"])
+        return dict(kind_side=out["kind_side"][:n], var=out["var"][:n], call_first_op=out["call_first_op"],
+                    arr_probe=out["arr_probe"][:A], n=n, n_dev=out["n_dev"], max_pairs=max_pairs)
+    if out_cap is None:
+        out_cap = 48 * n_calls + 2 * A + 64
+    first = torch.empty(n_calls + 1, dtype=torch.int64, device=dev)
+    probe = torch.empty(max(A, 1), dtype=torch.int64, device=dev)
+    out_n = torch.empty(1, dtype=torch.int64, device=dev)
+    for attempt in range(2):
+        ks = torch.empty(max(out_cap, 1), dtype=torch.uint8, device=dev)
+        var = torch.empty(max(out_cap, 1), dtype=torch.int32, device=dev)
+        call(ks, var, out_cap, out_n, first, probe)
+        n = int(out_n.item())
+        if n <= out_cap:
+            return dict(kind_side=ks[:n], var=var[:n], call_first_op=first, arr_probe=probe[:A], n=n, n_dev=out_n,
+                        max_pairs=max_pairs)
+        code = sync_status(stream)
+        if code not in (OK, E_RANGE):
+            raise AmcError(code, "amc_translate_vectorpu_lifetimes")
+        out_cap = n
+    raise AmcError(E_RANGE, "amc_translate_vectorpu_lifetimes")
+
+
+def check_inherited_trace(kind_side, var, n_arrays, arr_parent, arr_probe, *, out=None, workspace=None,
+                          stream=None):
+    """Check a translated trace with creation records over 2 * n_arrays
+    variables, pvectors starting from their vectors' statuses at creation
+    (amc_check_inherited_trace).  Returns dict(step_status, final_status,
+    var_first_fault, first_fault) of CUDA tensors."""
+    _dev(kind_side, torch.uint8, "kind_side")
+    _dev(var, torch.int32, "var")
+    _dev(arr_parent, torch.int32, "arr_parent")
+    _dev(arr_probe, torch.int64, "arr_probe")
+    n = kind_side.numel()
+    if var.numel() != n:
+        raise ValueError("kind_side and var differ in length")
+    dev = kind_side.device
+    nv = 2 * n_arrays
+    if out is None:
+        out = dict(step_status=torch.empty(max(n, 1), dtype=torch.uint8, device=dev),
+                   final_status=torch.empty(max(nv, 1), dtype=torch.uint8, device=dev),
+                   var_first_fault=torch.empty(max(nv, 1), dtype=torch.int32, device=dev),
+                   first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+    L = lib()
+    ws = workspace if workspace is not None else _ws.get(L.amc_check_inherited_trace_workspace(n, n_arrays), dev)
+    rc = L.amc_check_inherited_trace(_p(kind_side), _p(var), n, n_arrays, _p(arr_parent), _p(arr_probe),
+                                     _p(out["step_status"]), _p(out["final_status"]), _p(out["var_first_fault"]),
+                                     _p(out["first_fault"]), _p(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_check_inherited_trace")
+    return dict(step_status=out["step_status"][:n], final_status=out["final_status"][:nv],
+                var_first_fault=out["var_first_fault"][:nv], first_fault=out["first_fault"])
 
 
 def check_trace_k(op, var, n_vars, k, init_status=None, *, out=None, workspace=None, stream=None):

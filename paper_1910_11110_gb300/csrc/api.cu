@@ -288,6 +288,114 @@ int amc_translate_vectorpu(const int32_t* arr_start, const int32_t* arr_len, int
     return launch_translate(T, static_cast<cudaStream_t>(stream));
 }
 
+size_t amc_vectorpu_overlap_pairs_workspace(int32_t n_arrays)
+{
+    if (n_arrays < 0) return 0;
+    return overlap_count_workspace_bytes(n_arrays);
+}
+
+int amc_vectorpu_overlap_pairs(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_born,
+                               const int32_t* arr_died, int32_t n_arrays, int64_t* n_pairs, void* workspace,
+                               size_t ws_bytes, void* stream)
+{
+    if (n_arrays < 0 || !n_pairs || (n_arrays > 0 && (!arr_start || !arr_len)) || (!arr_born != !arr_died))
+        return AMC_E_INVALID;
+    if (!workspace || !aligned256(workspace) || ws_bytes < overlap_count_workspace_bytes(n_arrays))
+        return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    return launch_overlap_count(arr_start, arr_len, arr_born, arr_died, n_arrays, n_pairs, err, workspace,
+                                static_cast<cudaStream_t>(stream));
+}
+
+size_t amc_translate_vectorpu_lifetimes_workspace(int32_t n_arrays, int64_t n_calls, int64_t n_operands,
+                                                  int64_t max_pairs)
+{
+    if (n_arrays < 0 || n_calls < 0 || n_operands < 0 || max_pairs < 0) return 0;
+    return translate_lifetimes_workspace_bytes(n_arrays, n_calls, max_pairs);
+}
+
+int amc_translate_vectorpu_lifetimes(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_parent,
+                                     const int32_t* arr_born, const int32_t* arr_died, int32_t n_arrays,
+                                     const uint8_t* call_side, const int32_t* call_off, int64_t n_calls,
+                                     const int32_t* opnd_array, const uint8_t* opnd_mode, int64_t n_operands,
+                                     int infer_overlap, int64_t max_pairs, uint8_t* out_kind_side, int32_t* out_var,
+                                     int64_t out_cap, int64_t* out_n, int64_t* call_first_op, int64_t* arr_probe,
+                                     void* workspace, size_t ws_bytes, void* stream)
+{
+    if (n_arrays < 0 || n_arrays > INT32_MAX / 2 || n_calls < 0 || n_calls >= INT32_MAX || n_operands < 0 ||
+        out_cap < 0 || max_pairs < 0)
+        return AMC_E_INVALID;
+    if (!out_n || !call_first_op || !call_off) return AMC_E_INVALID;
+    if (n_arrays > 0 && (!arr_start || !arr_len || !arr_parent || !arr_born || !arr_died || !arr_probe))
+        return AMC_E_INVALID;
+    if (n_calls > 0 && !call_side) return AMC_E_INVALID;
+    if (n_operands > 0 && (!opnd_array || !opnd_mode)) return AMC_E_INVALID;
+    if (out_cap > 0 && (!out_kind_side || !out_var)) return AMC_E_INVALID;
+    if (!workspace || !aligned256(workspace) ||
+        ws_bytes < translate_lifetimes_workspace_bytes(n_arrays, n_calls, max_pairs))
+        return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    TranslateLaunch T;
+    T.arr_start = arr_start;
+    T.arr_len = arr_len;
+    T.n_arrays = n_arrays;
+    T.call_side = call_side;
+    T.call_off = call_off;
+    T.n_calls = n_calls;
+    T.opnd_array = opnd_array;
+    T.opnd_mode = opnd_mode;
+    T.n_operands = n_operands;
+    T.infer = infer_overlap ? 1 : 0;
+    T.out_ks = out_kind_side;
+    T.out_var = out_var;
+    T.out_cap = out_cap;
+    T.out_n = out_n;
+    T.call_first_op = call_first_op;
+    T.err = err;
+    T.workspace = workspace;
+    T.profile = 3;
+    T.arr_born = n_arrays > 0 ? arr_born : nullptr;
+    T.arr_died = arr_died;
+    T.arr_parent = arr_parent;
+    T.max_pairs = max_pairs;
+    T.arr_probe = arr_probe;
+    return launch_translate(T, static_cast<cudaStream_t>(stream));
+}
+
+size_t amc_check_inherited_trace_workspace(int64_t n_ops, int32_t n_arrays)
+{
+    if (n_ops < 0 || n_arrays < 0 || n_arrays > INT32_MAX / 2) return 0;
+    return amc_check_guarded_trace_workspace(n_ops, 2 * n_arrays) + align_up(2 * (size_t)n_arrays + 1, 256);
+}
+
+int amc_check_inherited_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops, int32_t n_arrays,
+                              const int32_t* arr_parent, const int64_t* arr_probe, uint8_t* step_status,
+                              uint8_t* final_status, int32_t* var_first_fault, int64_t* first_fault,
+                              void* workspace, size_t ws_bytes, void* stream)
+{
+    if (n_arrays < 0 || n_arrays > INT32_MAX / 2 || n_ops < 0) return AMC_E_INVALID;
+    if (n_arrays > 0 && (!arr_parent || !arr_probe)) return AMC_E_INVALID;
+    const size_t gws = amc_check_guarded_trace_workspace(n_ops, 2 * n_arrays);
+    if (!workspace || !aligned256(workspace) || ws_bytes < amc_check_inherited_trace_workspace(n_ops, n_arrays))
+        return AMC_E_NOMEM;
+    int* err = device_error_word();
+    if (!err) return AMC_E_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* init = static_cast<uint8_t*>(workspace) + gws;
+    // pass 1 from the initial store: the vectors' statuses at every creation
+    // record (a vector's ops do not depend on any pvector's statuses)
+    int rc = amc_check_guarded_trace(kind_side, var, n_ops, 2 * n_arrays, nullptr, step_status, final_status,
+                                     var_first_fault, first_fault, workspace, gws, stream);
+    if (rc) return rc;
+    rc = launch_inherit(var, n_ops, n_arrays, arr_parent, arr_probe, step_status, init, err, s);
+    if (rc) return rc;
+    // pass 2 from the inherited statuses
+    return amc_check_guarded_trace(kind_side, var, n_ops, 2 * n_arrays, n_arrays > 0 ? init : nullptr, step_status,
+                                   final_status, var_first_fault, first_fault, workspace, gws, stream);
+}
+
 size_t amc_check_batch_workspace(int64_t n_tokens, int64_t n_progs, int64_t total_vars)
 {
     if (n_tokens < 0 || n_progs < 0 || total_vars < 0) return 0;
@@ -322,13 +430,11 @@ int amc_check_batch(const uint8_t* tok_kind_side, const int32_t* tok_payload, co
     B.workspace = workspace;
     B.profile = 3;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // candidates: longest-first queue or input order, one or two waves of CTAs
-    int n_sm = 0, dev0 = 0;
-    cudaGetDevice(&dev0);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev0);
+    // candidates: longest-first queue or input order; registers fitted to
+    // six or four CTAs per SM
     auto shape = [&](BatchLaunch X, int i) {
         X.longest_first = (i & 1) ? 0 : 1;
-        X.max_ctas = (i & 2) ? n_sm : 0;
+        X.regs_capped = (i & 2) ? 0 : 1;
         return X;
     };
     const std::string key = shape_key("batch", n_tokens, n_progs, 0);

@@ -8,8 +8,8 @@
 // A program's "first fault" is the smallest token of an op whose possible
 // pre-statuses include a non-stuck status that the op makes stuck.
 //
-// Work is split by op count.  A program longer than SPLIT tokens (with at
-// most SPLIT_VARS variables) is cut into segments of about SPLIT tokens at
+// Work is split by op count.  A program longer than the split length (with at
+// most SPLIT_VARS variables) is cut into segments of about that length at
 // top-level boundaries (never inside an If or While); every other program is
 // one segment.  Per variable, a segment maps the set its variable enters with
 // to the set it leaves with through a relation over the five statuses (a 5x5
@@ -39,6 +39,8 @@
 // below the new fixpoint and the iteration still ends on it, in fewer passes.
 // Sets live in shared memory for programs of at most SMEM_VARS variables,
 // else in the final_mask output; the image and fault tables in shared memory.
+#include <cstdlib>
+
 #include "amc_internal.cuh"
 #include "batch.cuh"
 
@@ -49,10 +51,25 @@ namespace {
 constexpr int SMEM_VARS = 4096;
 constexpr int BWARPS = 8;                  // warps per CTA
 constexpr uint32_t MAX_WHILE_PASSES = 32;
-constexpr int64_t SPLIT = 16384;           // segment length of split programs (tokens)
+constexpr int64_t SPLIT_DEFAULT = 65536;   // segment length of split programs (tokens)
 constexpr int32_t SPLIT_VARS = 4096;       // programs with more variables are not split
-constexpr int64_t SEG_MAX = 2 * SPLIT;     // longest segment a reduce pass takes (else the program is not split)
-constexpr int RED_CTAS = 512;              // CTAs of the reduce phase: each warp has its own save / alt rows
+constexpr int RED_CTAS = 64;               // CTAs of the reduce phase: each warp has its own save / alt rows
+
+// Segment length (AMC_BATCH_SPLIT overrides it, 1,024 .. 2^30 tokens).  A
+// program is split when one warp would take longer on it alone than the rest
+// of the batch takes on all of them; at the measured rate of a lone warp that
+// is far beyond the longest programs of the 100,000-program workload.
+int64_t batch_split()
+{
+    int64_t v = SPLIT_DEFAULT;
+    if (const char* e = getenv("AMC_BATCH_SPLIT")) {
+        const long long x = atoll(e);
+        if (x >= 1024 && x <= (1ll << 30)) v = x;
+    }
+    return v;
+}
+// longest segment a reduce pass takes (else the program is not split)
+__host__ __device__ __forceinline__ int64_t seg_max_of(int64_t split) { return split + split / 2; }
 
 __device__ __forceinline__ bool is_op(uint32_t ks) { return (ks & 0xE0u) == 0 && (ks & 15u) <= AMC_K_PW; }
 
@@ -75,7 +92,7 @@ struct Unit {
     int last;                     // apply: the program's last segment (writes final sets)
     const uint8_t* entry;         // apply of a later segment: entry sets (nv bytes); else null
     uint32_t* rel;                // reduce: relation row of the segment (nv words)
-    uint8_t* rsave;               // reduce: the warp's save / alt rows ([AMC_MAX_DEPTH][SEG_MAX] each)
+    uint8_t* rsave;               // reduce: the warp's save / alt rows ([AMC_MAX_DEPTH][seg_max] each)
     uint8_t* ralt;
 };
 
@@ -111,10 +128,10 @@ __device__ void run_unit(const BatchParams& p, const Unit& u, WarpSmem& S, const
     // token of the segment in the warp's own rows (the five passes of a
     // segment run at once on different warps)
     auto save_at = [&](int d, int64_t q) -> uint8_t* {
-        return apply ? p.save + (int64_t)d * p.n_tokens + q : u.rsave + (int64_t)d * SEG_MAX + (q - t0);
+        return apply ? p.save + (int64_t)d * p.n_tokens + q : u.rsave + (int64_t)d * seg_max_of(p.split) + (q - t0);
     };
     auto alt_at = [&](int d, int64_t q) -> uint8_t* {
-        return apply ? p.alt + (int64_t)d * p.n_tokens + q : u.ralt + (int64_t)d * SEG_MAX + (q - t0);
+        return apply ? p.alt + (int64_t)d * p.n_tokens + q : u.ralt + (int64_t)d * seg_max_of(p.split) + (q - t0);
     };
     auto range_end = [&]() -> int64_t { return depth ? fpos[(depth - 1) * 3 + 2] : t1; };
     // parallel helper over the op tokens of (a, b)
@@ -285,13 +302,13 @@ struct Plan {
     int64_t* seg_t0;              // [slots]
     uint8_t* E;                   // [slots][SPLIT_VARS] entry sets
     uint32_t* R;                  // [slots][SPLIT_VARS] relations
-    uint8_t* rsave;               // [reduce warps][2][AMC_MAX_DEPTH][SEG_MAX] reduce-pass copies
+    uint8_t* rsave;               // [reduce warps][2][AMC_MAX_DEPTH][seg_max] reduce-pass copies
     int64_t* ord_off;             // [P + 1] apply units before the k-th program of the queue order
 };
 
-__device__ __forceinline__ int64_t split_slots(int64_t len, int32_t nv)
+__device__ __forceinline__ int64_t split_slots(int64_t len, int32_t nv, int64_t split)
 {
-    return (len > SPLIT && nv >= 0 && nv <= SPLIT_VARS) ? (len + SPLIT - 1) / SPLIT : 0;
+    return (len > split && nv >= 0 && nv <= SPLIT_VARS) ? (len + split - 1) / split : 0;
 }
 
 // largest p in [0, n) with off[p] <= i (off ascending, off[0] = 0)
@@ -323,7 +340,11 @@ __device__ __forceinline__ bool segment_of(const BatchParams& p, const Plan& pl,
 
 // phase 0: reduce passes, unit i = (slot i / 5, entry status i % 5);
 // phase 1: apply, unit i of program find_owner(unit_off, P, i)
-__global__ void __launch_bounds__(BWARPS * 32, 6) batch_kernel(const BatchParams p, const Plan pl, int phase)
+// MINB: resident CTAs per SM the register budget is fitted to (6: 40
+// registers with a few spills, 48 warps per SM; 4: 64 registers, 32 warps)
+// -- the tuner times both
+template <int MINB>
+__global__ void __launch_bounds__(BWARPS * 32, MINB) batch_kernel(const BatchParams p, const Plan pl, int phase)
 {
     __shared__ WarpSmem smem[BWARPS];
     __shared__ TabSmem tab;
@@ -334,8 +355,9 @@ __global__ void __launch_bounds__(BWARPS * 32, 6) batch_kernel(const BatchParams
     if (threadIdx.x < 16) tab.flt[threadIdx.x] = p.tab.flt[threadIdx.x];
     __syncthreads();
     const int64_t wid = (int64_t)blockIdx.x * BWARPS + w;
-    uint8_t* rsave = pl.rsave + wid * 2 * (int64_t)AMC_MAX_DEPTH * SEG_MAX;
-    uint8_t* ralt = rsave + (int64_t)AMC_MAX_DEPTH * SEG_MAX;
+    const int64_t sm = seg_max_of(p.split);
+    uint8_t* rsave = pl.rsave + wid * 2 * (int64_t)AMC_MAX_DEPTH * sm;
+    uint8_t* ralt = rsave + (int64_t)AMC_MAX_DEPTH * sm;
     const int64_t n_slots = pl.slot_off[p.n_progs];
     const int64_t n_units = pl.unit_off[p.n_progs];
     for (;;) {
@@ -410,7 +432,7 @@ __global__ void __launch_bounds__(1024) plan_offsets_kernel(const int64_t* __res
                                                             const int32_t* __restrict__ nvars, int64_t P,
                                                             int64_t* __restrict__ slot_off,
                                                             int64_t* __restrict__ unit_off,
-                                                            int64_t* __restrict__ prog_ff)
+                                                            int64_t* __restrict__ prog_ff, int64_t split)
 {
     __shared__ unsigned long long tmp_s[32], tmp_u[32];
     __shared__ unsigned long long carry_s, carry_u;
@@ -424,7 +446,7 @@ __global__ void __launch_bounds__(1024) plan_offsets_kernel(const int64_t* __res
         const int64_t pr = b0 + threadIdx.x;
         unsigned long long ns = 0, nu = 0;
         if (pr < P) {
-            ns = (unsigned long long)split_slots(tok_off[pr + 1] - tok_off[pr], nvars[pr]);
+            ns = (unsigned long long)split_slots(tok_off[pr + 1] - tok_off[pr], nvars[pr], split);
             nu = ns ? ns : 1ull;
             prog_ff[pr] = -1;
         }
@@ -466,13 +488,13 @@ __global__ void __launch_bounds__(1024) plan_offsets_kernel(const int64_t* __res
 }
 
 // Warp per split program: the segment starts.  Slot j's segment starts at the
-// first top-level token boundary at or after the program start + j * SPLIT
+// first top-level token boundary at or after the program start + j * split
 // (slot 0 at the program start); a slot whose stretch has no such boundary
 // before the next slot's target is left empty (-1).  Depth is tracked with a
 // warp prefix sum of +1 (IF, WHILE) / -1 (END) over 32 tokens at a time.
 __global__ void plan_cuts_kernel(const uint8_t* __restrict__ tok, const int64_t* __restrict__ tok_off,
                                  const int32_t* __restrict__ nvars, int64_t P, const int64_t* __restrict__ slot_off,
-                                 int64_t* __restrict__ seg_t0)
+                                 int64_t* __restrict__ seg_t0, int64_t split)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -504,11 +526,11 @@ __global__ void plan_cuts_kernel(const uint8_t* __restrict__ tok, const int64_t*
             while (cand && next < s1 - s0) {
                 const int L = __ffs(cand) - 1;
                 const int64_t qq = q0 + L;
-                const int64_t target = t0 + next * SPLIT;
+                const int64_t target = t0 + next * split;
                 if (qq >= target) {
-                    // the stretch of slot `next` is [target, target + SPLIT); later slots whose
+                    // the stretch of slot `next` is [target, target + split); later slots whose
                     // targets this boundary passes stay empty
-                    while (next < s1 - s0 && t0 + (next + 1) * SPLIT <= qq) ++next;
+                    while (next < s1 - s0 && t0 + (next + 1) * split <= qq) ++next;
                     if (lane == 0) seg_t0[s0 + next] = qq;
                     ++next;
                 }
@@ -516,7 +538,7 @@ __global__ void plan_cuts_kernel(const uint8_t* __restrict__ tok, const int64_t*
             }
             depth += __shfl_sync(0xffffffffu, incl, 31);
         }
-        // a reduce pass keeps its construct copies for SEG_MAX tokens: with a
+        // a reduce pass keeps its construct copies for seg_max tokens: with a
         // longer segment before the last, the program runs as one segment
         __syncwarp();
         bool too_long = false;
@@ -524,7 +546,7 @@ __global__ void plan_cuts_kernel(const uint8_t* __restrict__ tok, const int64_t*
         for (int64_t s = s0 + 1; s < s1; ++s) {
             const int64_t b = seg_t0[s];
             if (b < 0) continue;
-            too_long |= b - prev > SEG_MAX;
+            too_long |= b - prev > seg_max_of(split);
             prev = b;
         }
         __syncwarp();
@@ -645,11 +667,11 @@ struct BatchLayout {
     int64_t red_ctas;             // CTAs of the reduce phase (each warp owns construct-copy rows)
 };
 
-BatchLayout layout(int64_t n_tokens, int64_t n_progs)
+BatchLayout layout(int64_t n_tokens, int64_t n_progs, int64_t split)
 {
     BatchLayout L;
-    // a split program of length len has ceil(len / SPLIT) <= 2 len / SPLIT slots
-    L.max_slots = 2 * (n_tokens / SPLIT) + 1;
+    // a split program of length len has ceil(len / split) <= 2 len / split slots
+    L.max_slots = 2 * (n_tokens / split) + 1;
     size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o += align_up(b, 256); return at; };
     L.save = take((size_t)AMC_MAX_DEPTH * (size_t)n_tokens + 1);
@@ -660,9 +682,9 @@ BatchLayout layout(int64_t n_tokens, int64_t n_progs)
     L.E = take((size_t)L.max_slots * SPLIT_VARS);
     L.R = take(4 * (size_t)L.max_slots * SPLIT_VARS);
     // reduce-pass copies: one warp per reduce unit at most (five per slot)
-    L.red_ctas = n_tokens > SPLIT ? (5 * L.max_slots + BWARPS - 1) / BWARPS : 0;
+    L.red_ctas = n_tokens > split ? (5 * L.max_slots + BWARPS - 1) / BWARPS : 0;
     if (L.red_ctas > RED_CTAS) L.red_ctas = RED_CTAS;
-    L.rsave = take((size_t)L.red_ctas * BWARPS * 2 * AMC_MAX_DEPTH * SEG_MAX);
+    L.rsave = take((size_t)L.red_ctas * BWARPS * 2 * AMC_MAX_DEPTH * (size_t)seg_max_of(split));
     L.order = take(4 * (size_t)n_progs + 4);
     L.ord_off = take(8 * ((size_t)n_progs + 1));
     L.counts = take(256);
@@ -674,7 +696,10 @@ BatchLayout layout(int64_t n_tokens, int64_t n_progs)
 
 }  // namespace
 
-size_t batch_workspace_bytes(int64_t n_tokens, int64_t n_progs) { return layout(n_tokens, n_progs).total; }
+size_t batch_workspace_bytes(int64_t n_tokens, int64_t n_progs)
+{
+    return layout(n_tokens, n_progs, batch_split()).total;
+}
 
 int launch_batch(const BatchLaunch& B, cudaStream_t s)
 {
@@ -692,7 +717,8 @@ int launch_batch(const BatchLaunch& B, cudaStream_t s)
     p.prog_first_fault = B.prog_first_fault;
     p.err = B.err;
     p.tab = host_set_tables();
-    const BatchLayout L = layout(B.n_tokens, B.n_progs);
+    p.split = batch_split();
+    const BatchLayout L = layout(B.n_tokens, B.n_progs, p.split);
     uint8_t* w = static_cast<uint8_t*>(B.workspace);
     p.save = w + L.save;
     p.alt = w + L.alt;
@@ -713,15 +739,17 @@ int launch_batch(const BatchLaunch& B, cudaStream_t s)
     int dev = 0, n_sm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, BWARPS * 32, 0);
+    auto kern = B.regs_capped ? batch_kernel<6> : batch_kernel<4>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BWARPS * 32, 0);
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)n_sm * per_sm;
     if (B.max_ctas > 0 && grid > B.max_ctas) grid = B.max_ctas;
     if (B.profile & 1) profile_begin(s);
     plan_offsets_kernel<<<1, 1024, 0, s>>>(B.prog_tok_off, B.prog_nvars, B.n_progs,
                                            const_cast<int64_t*>(pl.slot_off), const_cast<int64_t*>(pl.unit_off),
-                                           B.prog_first_fault);
-    plan_cuts_kernel<<<n_sm * 4, 256, 0, s>>>(B.tok, B.prog_tok_off, B.prog_nvars, B.n_progs, pl.slot_off, pl.seg_t0);
+                                           B.prog_first_fault, p.split);
+    plan_cuts_kernel<<<n_sm * 4, 256, 0, s>>>(B.tok, B.prog_tok_off, B.prog_nvars, B.n_progs, pl.slot_off, pl.seg_t0,
+                                              p.split);
     zero_rel_kernel<<<n_sm * 4, 256, 0, s>>>(p, pl);
     if (B.longest_first) {
         if (cudaMemsetAsync(counts, 0, 256, s) != cudaSuccess) return AMC_E_CUDA;
@@ -734,10 +762,10 @@ int launch_batch(const BatchLaunch& B, cudaStream_t s)
     }
     if (cudaMemsetAsync(p.queue_head, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
     const int64_t rgrid = grid < L.red_ctas ? grid : L.red_ctas;
-    if (rgrid > 0) batch_kernel<<<(unsigned)rgrid, BWARPS * 32, 0, s>>>(p, pl, 0);      // reduce
+    if (rgrid > 0) kern<<<(unsigned)rgrid, BWARPS * 32, 0, s>>>(p, pl, 0);      // reduce
     carry_kernel<<<n_sm * 4, 256, 0, s>>>(p, pl);
     if (cudaMemsetAsync(p.queue_head, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
-    batch_kernel<<<(unsigned)grid, BWARPS * 32, 0, s>>>(p, pl, 1);       // apply
+    kern<<<(unsigned)grid, BWARPS * 32, 0, s>>>(p, pl, 1);       // apply
     if (B.profile & 2) profile_end(s);
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }

@@ -22,6 +22,7 @@ struct BatchParams {
     const int32_t* order;          // nullable: program queue order
     uint64_t* queue_head;
     int* err;
+    int64_t split;                 // segment length of split programs
     SetTables tab;
 };
 
@@ -41,6 +42,7 @@ struct BatchLaunch {
     void* workspace = nullptr;
     int longest_first = 1;
     int max_ctas = 0;
+    int regs_capped = 1;           // registers fitted to 6 CTAs per SM (else to 4)
     int profile = 0;
 };
 

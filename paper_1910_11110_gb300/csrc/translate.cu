@@ -15,10 +15,21 @@
 //   - shadows RW(y) in ascending order: GT y, EN y#, w y#;
 //   - every body write of x also writes the shared elements of each array y
 //     overlapping x: w y when y lies inside x, otherwise pw y.
-// Kernels: overlap sets r_v (count / fill, one warp per array), per-call
-// statement counts, device-wide exclusive scan of the counts, emission.
+// With lifetimes (pvectors created and deleted during the run, Section 4.3:
+// r_v is updated at creations and deletions): array a is live at the calls
+// born[a] <= c < died[a]; operands must be live; O(M), the shadows and the
+// projections of body writes take only the arrays live at the call; and each
+// pvector created before call c (ascending id) is recorded at the head of
+// call c's statements as Noop v, Noop v# (CPU side) on its vector v, the
+// point where it takes v's statuses (arr_probe[a] = index of the first).
+// Kernels: overlap sets r_v (sort and sweep, overlap.cu; with lifetimes only
+// the pairs whose lifetimes meet), the pvectors sorted by creation call,
+// per-call statement counts, device-wide exclusive scan of the counts,
+// emission.
 #include "amc_internal.cuh"
 #include "dscan.cuh"
+#include "overlap.cuh"
+#include "scan_trace.cuh"
 #include "translate.cuh"
 
 namespace amc {
@@ -44,41 +55,67 @@ struct TrParams {
     int64_t* out_n;
     int64_t* call_first_op;
     const int64_t* ov_off;
-    int32_t* ov_idx;
-    int32_t* ov_cnt;
+    const int32_t* ov_idx;
     int32_t* call_cnt;
     int* err;
+    // lifetimes (born == nullptr: every array live throughout)
+    const int32_t* born;
+    const int32_t* died;
+    const int32_t* parent;
+    const uint32_t* b_key;        // creation call of each pvector, ascending (n_calls for vectors)
+    const uint32_t* b_id;         // the pvector ids in that order
+    int64_t* arr_probe;
 };
 
-__device__ __forceinline__ bool iv_overlap(int32_t s1, int32_t l1, int32_t s2, int32_t l2)
+__device__ __forceinline__ bool live_at(const TrParams& p, int32_t a, int64_t c)
 {
-    return (int64_t)s1 < (int64_t)s2 + l2 && (int64_t)s2 < (int64_t)s1 + l1;
+    return !p.born || (c >= p.born[a] && c < p.died[a]);
 }
+
+// [*lo, *hi): the pvectors created before call c
+__device__ __forceinline__ void births_of(const TrParams& p, int64_t c, int32_t* lo, int32_t* hi)
+{
+    int32_t a = 0, b = p.n_arrays;
+    while (a < b) {
+        const int32_t m = (a + b) >> 1;
+        if ((int64_t)p.b_key[m] < c) a = m + 1;
+        else b = m;
+    }
+    *lo = a;
+    b = p.n_arrays;
+    while (a < b) {
+        const int32_t m = (a + b) >> 1;
+        if ((int64_t)p.b_key[m] <= c) a = m + 1;
+        else b = m;
+    }
+    *hi = a;
+}
+
 __device__ __forceinline__ bool iv_contains(int32_t so, int32_t lo, int32_t si, int32_t li)
 {
     return so <= si && (int64_t)si + li <= (int64_t)so + lo;
 }
 
-// One warp per array: count (FILL = false) or list (FILL = true) the arrays
-// overlapping it, in ascending id order.
-template <bool FILL>
-__global__ void overlap_kernel(const TrParams p)
+// The creation records at the head of call c: Noop v, Noop v# (CPU side)
+// for every pvector created before it, ascending id.  Returns the count.
+template <bool EMIT>
+__device__ __forceinline__ int64_t put_births(const TrParams& p, int64_t c, int64_t o)
 {
-    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (a >= p.n_arrays) return;
-    const int32_t sa = p.arr_start[a], la = p.arr_len[a];
-    if (!FILL && lane == 0 && (sa < 0 || la < 1 || (int64_t)sa + la > INT32_MAX)) raise_error(p.err, AMC_E_INVALID);
-    int64_t run = FILL ? p.ov_off[a] : 0;
-    const uint32_t lt = lanemask_lt();
-    for (int32_t b0 = 0; b0 < p.n_arrays; b0 += 32) {
-        const int32_t b = b0 + lane;
-        const bool ov = b < p.n_arrays && b != a && iv_overlap(sa, la, p.arr_start[b], p.arr_len[b]);
-        const uint32_t m = __ballot_sync(0xffffffffu, ov);
-        if (FILL && ov) p.ov_idx[run + __popc(m & lt)] = b;
-        run += __popc(m);
+    int32_t lo, hi;
+    births_of(p, c, &lo, &hi);
+    for (int32_t k = lo; k < hi; ++k) {
+        if (EMIT) {
+            const int32_t y = (int32_t)p.b_id[k];
+            const int32_t v = p.parent[y];
+            p.arr_probe[y] = o;
+            p.out_ks[o] = (uint8_t)AMC_K_NOOP;
+            p.out_var[o] = v;
+            p.out_ks[o + 1] = (uint8_t)AMC_K_NOOP;
+            p.out_var[o + 1] = p.n_arrays + v;
+        }
+        o += 2;
     }
-    if (!FILL && lane == 0) p.ov_cnt[a] = (int32_t)run;
+    return 2 * (int64_t)(hi - lo);
 }
 
 // Statements of call c.  EMIT = false only counts; EMIT = true writes them at
@@ -114,6 +151,10 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
             if (!EMIT) raise_error(p.err, AMC_E_RANGE);
             return -1;
         }
+        if (!live_at(p, arr[i], c)) {       // not live at this call
+            if (!EMIT) raise_error(p.err, AMC_E_INVALID);
+            return -1;
+        }
         bool dup = false;
 #pragma unroll
         for (int j = 0; j < NMAX; ++j) dup |= j < i && arr[j] == arr[i];
@@ -137,6 +178,7 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
             const bool x_rw = (mode[i] & 3) == AMC_MODE_RW;
             for (int64_t q = p.ov_off[arr[i]]; q < p.ov_off[arr[i] + 1]; ++q) {
                 const int32_t y = p.ov_idx[q];
+                if (!live_at(p, y, c)) continue;
 #pragma unroll
                 for (int j = 0; j < NMAX; ++j)
                     if (j < n && arr[j] == y && !(mode[j] & AMC_MODE_DROPPED) && (x_rw || (mode[j] & 3) != AMC_MODE_W))
@@ -153,6 +195,7 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
         }
         ++o;
     };
+    if (p.b_key) o += put_births<EMIT>(p, c, o);
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
         if (i >= n) break;
@@ -187,7 +230,7 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
 #pragma unroll
             for (int l = 0; l < NMAX; ++l)
                 if (cur[l] < end[l] && p.ov_idx[cur[l]] == y) ++cur[l];
-            if (is_arg(y)) continue;
+            if (is_arg(y) || !live_at(p, y, c)) continue;
             put(AMC_K_GT, y);
             put(AMC_K_EN, A + y);
             put(AMC_K_W, A + y);
@@ -201,6 +244,7 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
         const int32_t sx = p.arr_start[x], lx = p.arr_len[x];
         for (int64_t q = p.ov_off[x]; q < p.ov_off[x + 1]; ++q) {
             const int32_t y = p.ov_idx[q];
+            if (!live_at(p, y, c)) continue;
             put(iv_contains(sx, lx, p.arr_start[y], p.arr_len[y]) ? AMC_K_W : AMC_K_PW, y);
         }
     }
@@ -232,6 +276,10 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
             if (!EMIT) raise_error(p.err, AMC_E_RANGE);
             return -1;
         }
+        if (!live_at(p, arr[i], c)) {
+            if (!EMIT) raise_error(p.err, AMC_E_INVALID);
+            return -1;
+        }
         for (int j = 0; j < i; ++j)
             if (arr[j] == arr[i]) {       // one declaration per variable (Section 3.3)
                 if (!EMIT) raise_error(p.err, AMC_E_INVALID);
@@ -248,6 +296,7 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
         for (int i = 0; i < n; ++i) {
             if ((mode[i] & AMC_MODE_DROPPED) || !(mode[i] & AMC_MODE_W)) continue;
             for (int64_t q = p.ov_off[arr[i]]; q < p.ov_off[arr[i] + 1]; ++q) {
+                if (!live_at(p, p.ov_idx[q], c)) continue;
                 const int j = find(p.ov_idx[q]);
                 if (j < 0 || (mode[j] & AMC_MODE_DROPPED)) continue;
                 if ((mode[i] & 3) == AMC_MODE_RW || (mode[j] & 3) != AMC_MODE_W) eff[j] = AMC_MODE_RW;
@@ -263,6 +312,7 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
         }
         ++o;
     };
+    if (p.b_key) o += put_births<EMIT>(p, c, o);
     for (int i = 0; i < n; ++i) {
         const int32_t x = arr[i];
         const int me = eff[i], mo = mode[i] & 3;
@@ -292,7 +342,7 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
             if (y == INT32_MAX) break;
             for (int l = 0; l < nl; ++l)
                 if (cur[l] < end[l] && p.ov_idx[cur[l]] == y) ++cur[l];
-            if (find(y) >= 0) continue;
+            if (find(y) >= 0 || !live_at(p, y, c)) continue;
             put(AMC_K_GT, y);
             put(AMC_K_EN, A + y);
             put(AMC_K_W, A + y);
@@ -304,6 +354,7 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
         const int32_t sx = p.arr_start[x], lx = p.arr_len[x];
         for (int64_t q = p.ov_off[x]; q < p.ov_off[x + 1]; ++q) {
             const int32_t y = p.ov_idx[q];
+            if (!live_at(p, y, c)) continue;
             put(iv_contains(sx, lx, p.arr_start[y], p.arr_len[y]) ? AMC_K_W : AMC_K_PW, y);
         }
     }
@@ -348,24 +399,53 @@ __global__ void total_kernel(const TrParams p)
     if (total > p.out_cap) raise_error(p.err, AMC_E_RANGE);
 }
 
+// pvector lifetimes: 0 <= born < died <= n_calls; a pvector's vector is a
+// vector (parent -1) other than itself whose range and lifetime hold its own.
+// Sort keys: the creation call of each pvector, n_calls for vectors.
+__global__ void lifetimes_kernel(const TrParams p, uint32_t* __restrict__ key, uint32_t* __restrict__ val)
+{
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= p.n_arrays) return;
+    p.arr_probe[a] = -1;
+    const int32_t b = p.born[a], d = p.died[a], v = p.parent[a];
+    bool ok = b >= 0 && b < d && (int64_t)d <= p.n_calls;
+    if (v != -1) {
+        if (v < 0 || v >= p.n_arrays) {
+            raise_error(p.err, AMC_E_RANGE);
+            ok = true;                        // reported
+        } else {
+            ok = ok && v != a && p.parent[v] == -1 && p.born[v] <= b && d <= p.died[v] &&
+                 iv_contains(p.arr_start[v], p.arr_len[v], p.arr_start[a], p.arr_len[a]);
+        }
+    }
+    if (!ok) raise_error(p.err, AMC_E_INVALID);
+    key[a] = (v >= 0 && v < p.n_arrays && b >= 0 && b < p.n_calls) ? (uint32_t)b : (uint32_t)p.n_calls;
+    val[a] = (uint32_t)a;
+}
+
 struct TrLayout {
-    size_t ov_cnt, ov_off, ov_idx, call_cnt, scan, total;
+    size_t ov_off, ov_idx, ovws, bk0, bv0, bk1, bv1, bscr, call_cnt, scan, total;
+    int64_t cap;
 };
 
-TrLayout layout(int32_t A, int64_t n_calls)
+TrLayout layout(int32_t A, int64_t n_calls, int64_t max_pairs, bool lifetimes)
 {
     TrLayout L;
     size_t o = 0;
-    L.ov_cnt = o;
-    o += align_up(4 * (size_t)A, 256);
-    L.ov_off = o;
-    o += align_up(8 * ((size_t)A + 1), 256);
-    L.ov_idx = o;
-    o += align_up(4 * (size_t)A * (size_t)(A > 0 ? A - 1 : 0) + 4, 256);
-    L.call_cnt = o;
-    o += align_up(4 * (size_t)n_calls + 4, 256);
-    L.scan = o;
-    o += dscan_workspace_bytes(n_calls > A ? n_calls : A);
+    auto take = [&](size_t b) { const size_t at = o; o += align_up(b, 256); return at; };
+    // without lifetimes every array may overlap every other
+    L.cap = lifetimes ? max_pairs : (int64_t)A * (A > 0 ? A - 1 : 0);
+    L.ov_off = take(8 * ((size_t)A + 1));
+    L.ov_idx = take(4 * (size_t)(L.cap > 0 ? L.cap : 1));
+    L.ovws = take(overlap_workspace_bytes(A, L.cap));
+    const size_t a4 = lifetimes ? 4 * (size_t)(A > 0 ? A : 1) : 0;
+    L.bk0 = take(a4);
+    L.bv0 = take(a4);
+    L.bk1 = take(a4);
+    L.bv1 = take(a4);
+    L.bscr = take(lifetimes ? sorted_check_scratch_bytes(A > 0 ? A : 1) : 0);
+    L.call_cnt = take(4 * (size_t)n_calls + 4);
+    L.scan = take(dscan_workspace_bytes(n_calls > 0 ? n_calls : 1));
     L.total = o;
     return L;
 }
@@ -374,11 +454,40 @@ TrLayout layout(int32_t A, int64_t n_calls)
 
 size_t translate_workspace_bytes(int32_t n_arrays, int64_t n_calls)
 {
-    return layout(n_arrays, n_calls).total;
+    return layout(n_arrays, n_calls, 0, false).total;
+}
+
+size_t translate_lifetimes_workspace_bytes(int32_t n_arrays, int64_t n_calls, int64_t max_pairs)
+{
+    return layout(n_arrays, n_calls, max_pairs, true).total;
+}
+
+size_t overlap_count_workspace_bytes(int32_t n_arrays)
+{
+    return align_up(8 * ((size_t)n_arrays + 1), 256) + overlap_workspace_bytes(n_arrays, 0);
+}
+
+int launch_overlap_count(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_born,
+                         const int32_t* arr_died, int32_t n_arrays, int64_t* n_pairs, int* err, void* workspace,
+                         cudaStream_t s)
+{
+    OverlapBuild O;
+    O.arr_start = arr_start;
+    O.arr_len = arr_len;
+    O.arr_born = arr_born;
+    O.arr_died = arr_died;
+    O.n_arrays = n_arrays;
+    O.cap = 0;
+    O.ov_off = static_cast<int64_t*>(workspace);
+    O.n_pairs = n_pairs;
+    O.err = err;
+    O.workspace = static_cast<uint8_t*>(workspace) + align_up(8 * ((size_t)n_arrays + 1), 256);
+    return launch_overlaps(O, s);
 }
 
 int launch_translate(const TranslateLaunch& T, cudaStream_t s)
 {
+    const bool lifetimes = T.arr_born != nullptr;
     TrParams p{};
     p.arr_start = T.arr_start;
     p.arr_len = T.arr_len;
@@ -396,24 +505,41 @@ int launch_translate(const TranslateLaunch& T, cudaStream_t s)
     p.out_n = T.out_n;
     p.call_first_op = T.call_first_op;
     p.err = T.err;
-    const TrLayout L = layout(T.n_arrays, T.n_calls);
+    p.born = T.arr_born;
+    p.died = T.arr_died;
+    p.parent = T.arr_parent;
+    p.arr_probe = T.arr_probe;
+    const TrLayout L = layout(T.n_arrays, T.n_calls, T.max_pairs, lifetimes);
     uint8_t* w = static_cast<uint8_t*>(T.workspace);
-    p.ov_cnt = reinterpret_cast<int32_t*>(w + L.ov_cnt);
     int64_t* ov_off = reinterpret_cast<int64_t*>(w + L.ov_off);
     p.ov_off = ov_off;
     p.ov_idx = reinterpret_cast<int32_t*>(w + L.ov_idx);
     p.call_cnt = reinterpret_cast<int32_t*>(w + L.call_cnt);
     void* scan_ws = w + L.scan;
 
-    if (T.n_arrays > 0) {
-        const int64_t threads = (int64_t)T.n_arrays * 32;
-        const unsigned blocks = (unsigned)((threads + 255) / 256);
-        overlap_kernel<false><<<blocks, 256, 0, s>>>(p);
-        int rc = dscan_exclusive(p.ov_cnt, ov_off, T.n_arrays, scan_ws, s);
+    OverlapBuild O;
+    O.arr_start = T.arr_start;
+    O.arr_len = T.arr_len;
+    O.arr_born = T.arr_born;
+    O.arr_died = T.arr_died;
+    O.n_arrays = T.n_arrays;
+    O.cap = L.cap > 0 ? L.cap : 1;
+    O.ov_off = ov_off;
+    O.ov_idx = reinterpret_cast<uint32_t*>(w + L.ov_idx);
+    O.err = T.err;
+    O.workspace = w + L.ovws;
+    int rc = launch_overlaps(O, s);
+    if (rc) return rc;
+    if (lifetimes && T.n_arrays > 0) {
+        uint32_t* bk[2] = {reinterpret_cast<uint32_t*>(w + L.bk0), reinterpret_cast<uint32_t*>(w + L.bk1)};
+        uint32_t* bv[2] = {reinterpret_cast<uint32_t*>(w + L.bv0), reinterpret_cast<uint32_t*>(w + L.bv1)};
+        lifetimes_kernel<<<(unsigned)((T.n_arrays + 255) / 256), 256, 0, s>>>(p, bk[0], bv[0]);
+        int passes = 0;
+        const int64_t kr = T.n_calls + 1 < INT32_MAX ? T.n_calls + 1 : INT32_MAX;
+        rc = launch_ss_radix(bk, bv, nullptr, T.n_arrays, (int32_t)kr, w + L.bscr, nullptr, s, &passes);
         if (rc) return rc;
-        overlap_kernel<true><<<blocks, 256, 0, s>>>(p);
-    } else if (cudaMemsetAsync(ov_off, 0, 8, s) != cudaSuccess) {
-        return AMC_E_CUDA;
+        p.b_key = bk[passes & 1];
+        p.b_id = bv[passes & 1];
     }
     if (T.n_calls > 0) {
         const unsigned blocks = (unsigned)((T.n_calls + 255) / 256);
@@ -427,6 +553,46 @@ int launch_translate(const TranslateLaunch& T, cudaStream_t s)
         return AMC_E_CUDA;
     }
     total_kernel<<<1, 1, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
+}
+
+}  // namespace amc
+
+namespace amc {
+
+namespace {
+
+// Initial statuses of the second check pass: a vector's are those of the
+// initial store, (V,I); a pvector's real and abstract statuses are its
+// vector's at its creation record (the statuses the first pass gave the two
+// Noops there).
+__global__ void inherit_kernel(const int32_t* __restrict__ var, int64_t n_ops, int32_t A,
+                               const int32_t* __restrict__ parent, const int64_t* __restrict__ probe,
+                               const uint8_t* __restrict__ step, uint8_t* __restrict__ init, int* err)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= 2 * (int64_t)A) return;
+    const int32_t a = (int32_t)(v < A ? v : v - A);
+    const int32_t pv = parent[a];
+    uint8_t st = (uint8_t)AMC_ST_VI;
+    if (pv != -1) {
+        const int64_t q = probe[a];
+        const bool ok = pv >= 0 && pv < A && q >= 0 && q + 1 < n_ops && var[q] == pv && var[q + 1] == A + pv;
+        if (ok) st = step[q + (v < A ? 0 : 1)];
+        else raise_error(err, AMC_E_INVALID);
+    }
+    init[v] = st;
+}
+
+}  // namespace
+
+int launch_inherit(const int32_t* var, int64_t n_ops, int32_t n_arrays, const int32_t* arr_parent,
+                   const int64_t* arr_probe, const uint8_t* step, uint8_t* init, int* err, cudaStream_t s)
+{
+    if (n_arrays <= 0) return AMC_OK;
+    const int64_t n = 2 * (int64_t)n_arrays;
+    inherit_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(var, n_ops, n_arrays, arr_parent, arr_probe, step,
+                                                                init, err);
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 

@@ -93,7 +93,13 @@ def _concat(progs):
     return dict(tok=tok, payload=pay, prog_tok_off=off, prog_nvars=nv)
 
 
-def test_split_programs(amc, oracle_mod):
+@pytest.fixture
+def split8k(monkeypatch):
+    # segments of 8,192 tokens (the default splits only far longer programs)
+    monkeypatch.setenv("AMC_BATCH_SPLIT", "8192")
+
+
+def test_split_programs(amc, oracle_mod, split8k):
     # programs longer than one segment (8,192 tokens) are cut at top-level
     # boundaries and checked as segments (relations of the earlier segments,
     # carried entry sets); lengths 8,193 .. 60,000 tokens, dense constructs so
@@ -115,7 +121,7 @@ def test_split_programs(amc, oracle_mod):
     compare(amc, oracle_mod, b, graph=True)
 
 
-def test_split_program_without_boundaries(amc, oracle_mod):
+def test_split_program_without_boundaries(amc, oracle_mod, split8k):
     # one While around 20,000 tokens: no top-level boundary after the first
     # token, so every slot but the first stays empty and the program runs as one
     # segment; then the same body after 9,000 top-level ops (one cut)
@@ -130,7 +136,7 @@ def test_split_program_without_boundaries(amc, oracle_mod):
     compare(amc, oracle_mod, _concat([(whole_t, whole_p, 50), (second_t, second_p, 50)]))
 
 
-def test_initial_masks_with_split_programs(amc, oracle_mod):
+def test_initial_masks_with_split_programs(amc, oracle_mod, split8k):
     # through the server, whose program requests start from the session's
     # sets: a short structured program leaves sets of several statuses, then a
     # 30,000-token program (split into segments) starts from them

@@ -18,6 +18,8 @@ Workloads (seeds fixed by the benchmark definition):
   programs        100,000 If/While programs over 64-4,096 vars           (seed 3)
   serve_requests  Poisson arrivals of trace / program requests          (seed 4)
   wd_calls        calls AM{S} for the static well-declaredness check    (seed 5)
+  vectorpu_lifetimes  16 vectors of 2^20 elements, 65,536 pvectors created
+                  and deleted during 2^24 calls (about 4,096 live at a time) (seed 6)
 """
 from __future__ import annotations
 
@@ -58,6 +60,11 @@ def _clib():
         _lib.wl_wd_sizes.argtypes = [P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, P, ctypes.c_double, P, P]
         _lib.wl_wd_fill.argtypes = [P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, P, ctypes.c_double, P, P,
                                     P, P, P, P]
+        _lib.wl_lifetimes_arrays.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             P, P, P, P, P]
+        _lib.wl_lifetimes_calls.argtypes = [ctypes.c_uint64, ctypes.c_int32, P, P, ctypes.c_int64, ctypes.c_int32, P,
+                                            ctypes.c_double, P, P, P, P, P]
     return _lib
 
 
@@ -237,6 +244,45 @@ def wd_calls(n_calls: int = 1 << 20, n_arrays: int = 4096, len_range=(1, 64), se
                    _p(am_array), _p(am_mode))
     return dict(arr_loc_off=a_off, loc_owner=owner, call_tok_off=tok_off, tok=tok, payload=payload,
                 call_am_off=am_off, am_array=am_array, am_mode=am_mode)
+
+
+def vectorpu_lifetimes(seed: int = 6, n_vectors: int = 16, vec_len: int = 1 << 20, n_pvectors: int = 65536,
+                       n_calls: int = 1 << 24, len_log2=(8.0, 16.0), mean_life: float | None = None,
+                       max_opnds: int = 4, mode_p=(0.5, 0.3, 0.2), drop_p: float = 1e-4):
+    """VectorPU calls over pvectors that are created and deleted during the
+    run: n_vectors vectors of vec_len elements side by side (ids 0..), live
+    throughout; n_pvectors pvectors (ids after them), each a sub-range of a
+    uniformly drawn vector (start uniform in it, length floor(2^U(a, b))
+    clipped to its end), created before a uniform call and live for an
+    exponential number of calls of mean mean_life (default n_calls / 16, so
+    that about n_pvectors / 16 are live at a time); calls with a fair side and
+    1..max_opnds distinct operands drawn from the arrays live at the call,
+    modes R / W / RW with mode_p, annotations dropped with drop_p.  Returns
+    the inputs of oracle.vectorpu_lifetimes."""
+    A = n_vectors + n_pvectors
+    life = float(n_calls) / 16.0 if mean_life is None else float(mean_life)
+    lib = _clib()
+    start = np.empty(A, np.int32)
+    length = np.empty(A, np.int32)
+    parent = np.empty(A, np.int32)
+    born = np.empty(A, np.int32)
+    died = np.empty(A, np.int32)
+    lib.wl_lifetimes_arrays(seed, n_vectors, vec_len, A, n_calls, len_log2[0], len_log2[1], life, _p(start),
+                            _p(length), _p(parent), _p(born), _p(died))
+    side = np.empty(n_calls, np.uint8)
+    cnt = np.empty(n_calls, np.int32)
+    pm = np.array(mode_p, np.float64)
+    if lib.wl_lifetimes_calls(seed, A, _p(born), _p(died), n_calls, max_opnds, _p(pm), drop_p, _p(side), _p(cnt),
+                              None, None, None) != 0:
+        raise MemoryError("workload generator")
+    call_off = np.zeros(n_calls + 1, np.int64)
+    np.cumsum(cnt, out=call_off[1:])
+    opnd_array = np.empty(int(call_off[-1]), np.int32)
+    opnd_mode = np.empty(int(call_off[-1]), np.uint8)
+    lib.wl_lifetimes_calls(seed, A, _p(born), _p(died), n_calls, max_opnds, _p(pm), drop_p, _p(side), _p(cnt),
+                           _p(call_off), _p(opnd_array), _p(opnd_mode))
+    return dict(arr_start=start, arr_len=length, arr_parent=parent, arr_born=born, arr_died=died, call_side=side,
+                call_off=call_off.astype(np.int32), opnd_array=opnd_array, opnd_mode=opnd_mode)
 
 
 # --------------------------------------------------------------------------

@@ -15,6 +15,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 typedef struct { uint64_t s; } rng_t;
@@ -329,4 +330,132 @@ void wl_wd_fill(const int64_t* a_off, int32_t n_arrays, uint64_t seed, int64_t n
                     payload + tok_off[c], 0};
         wd_call(&g, a_off, n_arrays, p_mode, p_bad, am_array + am_off[c], am_mode + am_off[c]);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* VectorPU calls over pvectors with lifetimes.  Arrays [0, n_vectors) are   */
+/* vectors (parent -1, live for the whole run); the rest are pvectors of a   */
+/* uniformly drawn vector: a sub-range of it (start uniform in the vector,   */
+/* length floor(2^U(len_lo, len_hi)) clipped to the vector's end), created   */
+/* before a uniformly drawn call and deleted after floor(mean_life * E) more */
+/* calls (E exponential, at least one call, clipped to the run).  Each call  */
+/* has a fair side and 1..max_opnds distinct operands drawn uniformly from   */
+/* the arrays live at that call (creations and deletions happen between      */
+/* calls), modes R / W / RW with p_mode and annotations dropped with p_drop. */
+/* One stream for the arrays and one for the calls, both SplitMix64.         */
+/* ------------------------------------------------------------------------ */
+static void wl_sort_events(int64_t* ev, int32_t n)                /* ascending, heap sort */
+{
+    for (int32_t i = n / 2 - 1; i >= 0; i--) {
+        for (int32_t r = i;;) {
+            int32_t c = 2 * r + 1;
+            if (c >= n) break;
+            if (c + 1 < n && ev[c + 1] > ev[c]) c++;
+            if (ev[r] >= ev[c]) break;
+            int64_t t = ev[r]; ev[r] = ev[c]; ev[c] = t; r = c;
+        }
+    }
+    for (int32_t e = n - 1; e > 0; e--) {
+        int64_t t = ev[0]; ev[0] = ev[e]; ev[e] = t;
+        for (int32_t r = 0;;) {
+            int32_t c = 2 * r + 1;
+            if (c >= e) break;
+            if (c + 1 < e && ev[c + 1] > ev[c]) c++;
+            if (ev[r] >= ev[c]) break;
+            t = ev[r]; ev[r] = ev[c]; ev[c] = t; r = c;
+        }
+    }
+}
+
+void wl_lifetimes_arrays(uint64_t seed, int32_t n_vectors, int32_t vec_len, int32_t n_arrays, int64_t n_calls,
+                         double len_lo, double len_hi, double mean_life, int32_t* start, int32_t* len,
+                         int32_t* parent, int32_t* born, int32_t* died)
+{
+    rng_t r = {seed * 0x9E3779B97F4A7C15ull + 0x5851F42D4C957F2Dull};
+    for (int32_t a = 0; a < n_arrays; a++) {
+        if (a < n_vectors) {
+            start[a] = a * vec_len;
+            len[a] = vec_len;
+            parent[a] = -1;
+            born[a] = 0;
+            died[a] = (int32_t)n_calls;
+            continue;
+        }
+        int32_t v = (int32_t)uniform_int(&r, 0, n_vectors - 1);
+        int32_t off = (int32_t)uniform_int(&r, 0, vec_len - 1);
+        double l = floor(pow(2.0, len_lo + (len_hi - len_lo) * u01(&r)));
+        int64_t ln = (int64_t)l < 1 ? 1 : (int64_t)l;
+        if (ln > vec_len - off) ln = vec_len - off;
+        start[a] = v * vec_len + off;
+        len[a] = (int32_t)ln;
+        parent[a] = v;
+        int64_t b = uniform_int(&r, 0, n_calls - 1);
+        double u = u01(&r);
+        int64_t life = (int64_t)floor(-mean_life * log(u < 1e-300 ? 1e-300 : u));
+        if (life < 1) life = 1;
+        int64_t d = b + life > n_calls ? n_calls : b + life;
+        born[a] = (int32_t)b;
+        died[a] = (int32_t)d;
+    }
+}
+
+/* calls; counts[c] = operands of call c when opnd_array is NULL (size pass),
+ * else the operands are written at call_off[c] */
+int wl_lifetimes_calls(uint64_t seed, int32_t n_arrays, const int32_t* born, const int32_t* died, int64_t n_calls,
+                       int32_t max_opnds, const double* p_mode, double p_drop, uint8_t* side, int32_t* counts,
+                       const int64_t* call_off, int32_t* opnd_array, uint8_t* opnd_mode)
+{
+    rng_t r = {seed * 0xD1B54A32D192ED03ull + 0x2545F4914F6CDD1Dull};
+    int64_t* births = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_arrays ? n_arrays : 1));
+    int64_t* deaths = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_arrays ? n_arrays : 1));
+    int32_t* live = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_arrays ? n_arrays : 1));
+    int32_t* pos = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_arrays ? n_arrays : 1));
+    if (!births || !deaths || !live || !pos) {
+        free(births); free(deaths); free(live); free(pos);
+        return -3;
+    }
+    for (int32_t a = 0; a < n_arrays; a++) {
+        births[a] = ((int64_t)born[a] << 32) | a;
+        deaths[a] = ((int64_t)died[a] << 32) | a;
+        pos[a] = -1;
+    }
+    wl_sort_events(births, n_arrays);
+    wl_sort_events(deaths, n_arrays);
+    int32_t n_live = 0, nb = 0, nd = 0;
+    int32_t pick[64];
+    for (int64_t c = 0; c < n_calls; c++) {
+        while (nd < n_arrays && (deaths[nd] >> 32) <= c) {
+            int32_t a = (int32_t)(deaths[nd++] & 0xFFFFFFFF);
+            int32_t i = pos[a];
+            if (i >= 0) { live[i] = live[--n_live]; pos[live[i]] = i; pos[a] = -1; }
+        }
+        while (nb < n_arrays && (births[nb] >> 32) <= c) {
+            int32_t a = (int32_t)(births[nb++] & 0xFFFFFFFF);
+            pos[a] = n_live;
+            live[n_live++] = a;
+        }
+        side[c] = (uint8_t)(next_u64(&r) & 1);
+        int32_t k = (int32_t)uniform_int(&r, 1, max_opnds);
+        if (k > n_live) k = n_live;
+        if (k > 64) k = 64;
+        for (int32_t j = 0; j < k; j++) {
+            int32_t a, dup;
+            do {
+                a = live[uniform_int(&r, 0, n_live - 1)];
+                dup = 0;
+                for (int32_t i = 0; i < j; i++) dup |= pick[i] == a;
+            } while (dup);
+            pick[j] = a;
+            double u = u01(&r);
+            uint8_t m = u < p_mode[0] ? 1 : (u < p_mode[0] + p_mode[1] ? 2 : 3);
+            if (u01(&r) < p_drop) m |= 0x80;
+            if (opnd_array) {
+                opnd_array[call_off[c] + j] = a;
+                opnd_mode[call_off[c] + j] = m;
+            }
+        }
+        counts[c] = k;
+    }
+    free(births); free(deaths); free(live); free(pos);
+    return 0;
 }
