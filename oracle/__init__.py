@@ -51,6 +51,8 @@ def lib():
         _lib.oracle_overlaps.argtypes = [P, P, i32, P, P, i64]
         _lib.oracle_vectorpu.argtypes = [P, P, i32, P, P, i64, P, P, ctypes.c_int,
                                          P, P, i64, P, P, P, P, P, P]
+        _lib.oracle_check_program_guarded.argtypes = [P, P, i64, i32, i32, P, P, P, P]
+        _lib.oracle_check_batch_guarded.argtypes = [P, P, P, P, P, P, i64, P, P, P]
         _lib.oracle_vectorpu_lifetimes.argtypes = [P, P, P, P, P, i32, P, P, i64, P, P, ctypes.c_int,
                                                    P, P, i64, P, P, P, P, P, P, P]
         _lib.oracle_well_declared.argtypes = [P, i32, P, P, i64, P, P, P, P, P, P, P, P]
@@ -172,6 +174,38 @@ def check_batch(tok, payload, prog_tok_off, prog_nvars):
     _check(lib().oracle_check_batch(_ptr(t), _ptr(p), _ptr(to), _ptr(nv), _ptr(vo),
                                     nv.shape[0], _ptr(step), _ptr(final), _ptr(pff)))
     return step, final, pff
+
+
+def check_program_guarded(tok, payload, n_vars, guard, init_mask=None):
+    """Path-sensitive relation mode for one program (conditions on the guard
+    variable `guard`, -1 none).  Returns (step_mask, final_mask, first_fault)."""
+    t = np.ascontiguousarray(tok, dtype=np.uint8)
+    p = np.ascontiguousarray(payload, dtype=np.int32)
+    init = None if init_mask is None else np.ascontiguousarray(init_mask, dtype=np.uint8)
+    step = np.zeros(t.shape[0], np.uint8)
+    final = np.empty(max(n_vars, 1), np.uint8)
+    ff = np.empty(1, np.int64)
+    _check(lib().oracle_check_program_guarded(_ptr(t), _ptr(p), t.shape[0], n_vars, int(guard), _ptr(init),
+                                              _ptr(step), _ptr(final), _ptr(ff)))
+    return step, final[:n_vars], int(ff[0])
+
+
+def check_batch_guarded(tok, payload, prog_tok_off, prog_nvars, prog_guard):
+    """Path-sensitive relation mode over a CSR batch.  Returns (step_mask,
+    final_mask, prog_first_fault)."""
+    t = np.ascontiguousarray(tok, dtype=np.uint8)
+    p = np.ascontiguousarray(payload, dtype=np.int32)
+    to = np.ascontiguousarray(prog_tok_off, dtype=np.int64)
+    nv = np.ascontiguousarray(prog_nvars, dtype=np.int32)
+    gd = np.ascontiguousarray(prog_guard, dtype=np.int32)
+    vo = np.zeros(nv.shape[0] + 1, np.int64)
+    np.cumsum(nv, out=vo[1:])
+    step = np.zeros(t.shape[0], np.uint8)
+    final = np.empty(max(int(vo[-1]), 1), np.uint8)
+    pff = np.empty(nv.shape[0], np.int64)
+    _check(lib().oracle_check_batch_guarded(_ptr(t), _ptr(p), _ptr(to), _ptr(nv), _ptr(vo), _ptr(gd), nv.shape[0],
+                                            _ptr(step), _ptr(final), _ptr(pff)))
+    return step, final[:int(vo[-1])], pff
 
 
 def overlaps(arr_start, arr_len):

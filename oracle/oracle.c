@@ -365,6 +365,222 @@ int oracle_check_batch(const uint8_t* tok, const int32_t* payload, const int64_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* Path-sensitive relation mode: the conditions isValid g and remIsValid g   */
+/* of Fig. Opsem (rules valid / invalid / rem-valid / rem-invalid) evaluated  */
+/* on one guard variable g per program, other conditions (x (+) y) opaque.   */
+/* The state at a program point is, for every variable x other than g, the   */
+/* set of reachable pairs (status of g, status of x) -- a 5x5 bit matrix,    */
+/* bit 5 i + j for g = i, x = j -- and the set of reachable statuses of g.   */
+/* Control flow depends on g alone, so these pair sets are exactly the       */
+/* projections of the reachable stores (each variable's F absorbing and not  */
+/* stopping the others, as in the opaque relation mode).  A condition on g   */
+/* keeps, on each branch, the pairs whose g status makes it true / false; a  */
+/* stuck g satisfies neither rule, so its paths end there.  While: the pairs */
+/* at the loop head are the least X with X = entry U body(X restricted to    */
+/* the condition); the loop leaves with X restricted to its negation.  Token */
+/* byte of IF / WHILE: bits 4-5 = condition (0 opaque, 1 isValid g,         */
+/* 2 remIsValid g).                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const uint8_t* tok;
+    const int32_t* payload;
+    int32_t n_vars, g;
+    uint8_t* step_mask;
+    int64_t first_fault;
+    int depth;
+} ps_ctx;
+
+typedef struct {
+    uint8_t G;                     /* statuses of g */
+    uint32_t* J;                   /* [n_vars] pair sets (unused at g) */
+} ps_state;
+
+/* g statuses for which the condition holds (then) and fails (else) */
+static void ps_rows(int cond, uint8_t* t_rows, uint8_t* e_rows)
+{
+    if (cond == 0) { *t_rows = *e_rows = 31; return; }       /* opaque: both, every path */
+    uint8_t t = 0, e = 0;
+    for (int s = 0; s < ST_F; s++) {                         /* F: no rule applies */
+        if (is_valid_on(cond == 1 ? 0 : 1, s)) t |= (uint8_t)(1u << s);
+        else e |= (uint8_t)(1u << s);
+    }
+    *t_rows = t;
+    *e_rows = e;
+}
+
+static uint32_t ps_keep_rows(uint32_t J, uint8_t rows)
+{
+    uint32_t out = 0;
+    for (int i = 0; i <= ST_F; i++)
+        if (rows & (1u << i)) out |= J & (31u << (5 * i));
+    return out;
+}
+
+static uint8_t ps_proj(uint32_t J)
+{
+    uint8_t m = 0;
+    for (int i = 0; i <= ST_F; i++) m |= (uint8_t)((J >> (5 * i)) & 31u);
+    return m;
+}
+
+static int ps_alloc(const ps_ctx* c, ps_state* d, const ps_state* src)
+{
+    d->J = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(c->n_vars ? c->n_vars : 1));
+    if (!d->J) return -3;
+    d->G = src->G;
+    memcpy(d->J, src->J, sizeof(uint32_t) * (size_t)c->n_vars);
+    return 0;
+}
+
+static void ps_restrict(const ps_ctx* c, ps_state* st, uint8_t rows)
+{
+    st->G &= rows;
+    for (int32_t x = 0; x < c->n_vars; x++)
+        if (x != c->g) st->J[x] = ps_keep_rows(st->J[x], rows);
+}
+
+static int ps_eval(ps_ctx* c, int64_t lo, int64_t hi, ps_state* st)
+{
+    if (++c->depth > ORACLE_MAX_DEPTH) return -1;
+    int64_t i = lo;
+    while (i < hi) {
+        int k = c->tok[i] & 15, hb = c->tok[i] >> 4;
+        if (k <= K_PW) {
+            if (hb > 1) return -1;
+            int side = hb;
+            int32_t v = c->payload[i];
+            if (v < 0 || v >= c->n_vars) return -2;
+            uint8_t pre, post;
+            if (v == c->g) {
+                /* an op on g moves every pair's first component */
+                pre = st->G;
+                post = image(k, side, pre);
+                for (int32_t x = 0; x < c->n_vars; x++) {
+                    if (x == c->g) continue;
+                    uint32_t out = 0;
+                    for (int gi = 0; gi <= ST_F; gi++) {
+                        uint32_t row = (st->J[x] >> (5 * gi)) & 31u;
+                        if (row) out |= row << (5 * oracle_apply(k, side, gi));
+                    }
+                    st->J[x] = out;
+                }
+                st->G = post;
+            } else {
+                pre = ps_proj(st->J[v]);
+                uint32_t out = 0;
+                for (int gi = 0; gi <= ST_F; gi++)
+                    out |= (uint32_t)image(k, side, (uint8_t)((st->J[v] >> (5 * gi)) & 31u)) << (5 * gi);
+                st->J[v] = out;
+                post = ps_proj(out);
+            }
+            for (int s = 0; s < ST_F; s++)
+                if ((pre & (1u << s)) && oracle_apply(k, side, s) == ST_F) {
+                    if (c->first_fault < 0 || i < c->first_fault) c->first_fault = i;
+                    break;
+                }
+            c->step_mask[i] = post;
+            i++;
+        } else if (k == T_IF) {
+            if (hb > 2 || (hb && c->g < 0)) return -1;
+            int64_t lt = c->payload[i], e = i + 1 + lt;
+            if (lt < 0 || e >= hi || c->tok[e] != T_ELSE) return -1;
+            int64_t le = c->payload[e], end = e + 1 + le;
+            if (le < 0 || end >= hi || c->tok[end] != T_END) return -1;
+            uint8_t tr, er;
+            ps_rows(hb, &tr, &er);
+            ps_state other;
+            int rc = ps_alloc(c, &other, st);
+            if (rc) return rc;
+            ps_restrict(c, st, tr);                          /* IF-True paths */
+            ps_restrict(c, &other, er);                      /* IF-False paths */
+            rc = ps_eval(c, i + 1, e, st);
+            if (!rc) rc = ps_eval(c, e + 1, end, &other);
+            if (!rc) {
+                st->G |= other.G;
+                for (int32_t x = 0; x < c->n_vars; x++) st->J[x] |= other.J[x];
+            }
+            free(other.J);
+            if (rc) return rc;
+            c->step_mask[i] = c->step_mask[e] = c->step_mask[end] = 0;
+            i = end + 1;
+        } else if (k == T_WHILE) {
+            if (hb > 2 || (hb && c->g < 0)) return -1;
+            int64_t lb = c->payload[i], end = i + 1 + lb;
+            if (lb < 0 || end >= hi || c->tok[end] != T_END) return -1;
+            uint8_t tr, er;
+            ps_rows(hb, &tr, &er);
+            /* loop head: least X with X = entry U body(X on While-True paths) */
+            for (;;) {
+                ps_state y;
+                int rc = ps_alloc(c, &y, st);
+                if (rc) return rc;
+                ps_restrict(c, &y, tr);
+                rc = ps_eval(c, i + 1, end, &y);
+                if (rc) { free(y.J); return rc; }
+                int changed = (uint8_t)(st->G | y.G) != st->G;
+                st->G |= y.G;
+                for (int32_t x = 0; x < c->n_vars; x++) {
+                    uint32_t u = st->J[x] | y.J[x];
+                    if (u != st->J[x]) { st->J[x] = u; changed = 1; }
+                }
+                free(y.J);
+                if (!changed) break;
+            }
+            ps_restrict(c, st, er);                          /* While-False: the loop is left */
+            c->step_mask[i] = c->step_mask[end] = 0;
+            i = end + 1;
+        } else {
+            return -1;
+        }
+    }
+    c->depth--;
+    return 0;
+}
+
+int oracle_check_program_guarded(const uint8_t* tok, const int32_t* payload, int64_t n_tok, int32_t n_vars,
+                                 int32_t guard, const uint8_t* init_mask, uint8_t* step_mask,
+                                 uint8_t* final_mask, int64_t* first_fault)
+{
+    if (n_tok < 0 || n_vars < 0 || guard < -1 || guard >= n_vars) return -1;
+    ps_ctx c = { tok, payload, n_vars, guard, step_mask, -1, 0 };
+    ps_state st;
+    st.J = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n_vars ? n_vars : 1));
+    if (!st.J) return -3;
+    uint8_t vi = (uint8_t)(1u << encode((pair_t){ V, I }));
+    st.G = guard >= 0 ? (init_mask ? init_mask[guard] : vi) : 1;       /* no guard: one row */
+    int rc = 0;
+    for (int32_t x = 0; x < n_vars && !rc; x++) {
+        uint8_t m = init_mask ? init_mask[x] : vi;
+        if (m >> 5) rc = -1;
+        st.J[x] = 0;
+        for (int gi = 0; gi <= ST_F; gi++)
+            if (st.G & (1u << gi)) st.J[x] |= (uint32_t)m << (5 * gi);
+    }
+    if (!rc) rc = ps_eval(&c, 0, n_tok, &st);
+    if (!rc) {
+        for (int32_t x = 0; x < n_vars; x++) final_mask[x] = x == guard ? st.G : ps_proj(st.J[x]);
+        *first_fault = c.first_fault;
+    }
+    free(st.J);
+    return rc;
+}
+
+int oracle_check_batch_guarded(const uint8_t* tok, const int32_t* payload, const int64_t* prog_tok_off,
+                               const int32_t* prog_nvars, const int64_t* prog_var_off, const int32_t* prog_guard,
+                               int64_t n_progs, uint8_t* step_mask, uint8_t* final_mask, int64_t* prog_first_fault)
+{
+    if (n_progs < 0 || prog_tok_off[0] != 0 || prog_var_off[0] != 0) return -1;
+    for (int64_t p = 0; p < n_progs; p++) {
+        int64_t t0 = prog_tok_off[p], t1 = prog_tok_off[p + 1];
+        if (t1 < t0 || prog_var_off[p + 1] - prog_var_off[p] != prog_nvars[p]) return -1;
+        int rc = oracle_check_program_guarded(tok + t0, payload + t0, t1 - t0, prog_nvars[p], prog_guard[p], NULL,
+                                              step_mask + t0, final_mask + prog_var_off[p], &prog_first_fault[p]);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* VectorPU calls over possibly overlapping arrays                           */
 /* ------------------------------------------------------------------------ */
 static int overlap(int32_t s1, int32_t l1, int32_t s2, int32_t l2)

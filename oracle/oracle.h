@@ -56,6 +56,19 @@ int oracle_check_batch(const uint8_t* tok, const int32_t* payload, const int64_t
                        const int32_t* prog_nvars, const int64_t* prog_var_off, int64_t n_progs,
                        uint8_t* step_mask, uint8_t* final_mask, int64_t* prog_first_fault);
 
+/* Path-sensitive relation mode: IF / WHILE token bits 4-5 = condition
+ * (0 opaque x (+) y, 1 isValid g, 2 remIsValid g) on the program's guard
+ * variable g (guard = -1: none, every condition opaque).  Pair sets (status
+ * of g, status of x) per variable; a stuck g satisfies no condition rule (the
+ * path ends).  Outputs as oracle_check_program (step_mask = statuses of the
+ * op's variable after it, 0 when the op is unreachable). */
+int oracle_check_program_guarded(const uint8_t* tok, const int32_t* payload, int64_t n_tok, int32_t n_vars,
+                                 int32_t guard, const uint8_t* init_mask, uint8_t* step_mask,
+                                 uint8_t* final_mask, int64_t* first_fault);
+int oracle_check_batch_guarded(const uint8_t* tok, const int32_t* payload, const int64_t* prog_tok_off,
+                               const int32_t* prog_nvars, const int64_t* prog_var_off, const int32_t* prog_guard,
+                               int64_t n_progs, uint8_t* step_mask, uint8_t* final_mask, int64_t* prog_first_fault);
+
 /* Overlap sets of half-open intervals [start, start+len): CSR, ascending ids. */
 int oracle_overlaps(const int32_t* arr_start, const int32_t* arr_len, int32_t n_arrays,
                     int64_t* ov_off, int32_t* ov_idx, int64_t ov_cap);
