@@ -21,6 +21,8 @@ timed on the host cores beside it:
                 and on a 2^30-op low-fault trace;
   programs      100,000 If/While programs (seed 3): the batched persistent
                 launch (CUDA graph) against one launch per program;
+  programs_guarded  20,000 programs whose If conditions test a guard
+                variable (seed 7): the path-sensitive relation mode;
   serve         open-loop Poisson arrivals at 1k / 10k / 100k requests/s,
                 half traces and half programs, latency from the scheduled
                 arrival to the poll that sees the result.
@@ -67,8 +69,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--workload", default="all",
-                    choices=["all", "trace", "uniform", "programs", "vectorpu", "vectorpu_lifetimes", "trace_sizes",
-                             "well_declared", "kloc", "serve"])
+                    choices=["all", "trace", "uniform", "programs", "programs_guarded", "vectorpu",
+                             "vectorpu_lifetimes", "trace_sizes", "well_declared", "kloc", "serve"])
     ap.add_argument("--rates", default="1000,10000,100000")
     ap.add_argument("--serve-requests", type=int, default=10_000)
     ap.add_argument("--serve-seconds", type=float, default=12.0, help="submission window per rate")
@@ -421,6 +423,7 @@ def sub_records(args, amc, dev):
                      ("vectorpu_lifetimes", lambda: measure_lifetimes(args, amc, dev)),
                      ("trace_sizes", lambda: measure_sizes(args, amc, dev)),
                      ("programs", lambda: measure_programs(args, amc, dev)),
+                     ("programs_guarded", lambda: measure_guarded(args, amc, dev)),
                      ("well_declared", lambda: measure_well_declared(args, amc, dev)),
                      ("kloc", lambda: measure_kloc(args, amc, dev)),
                      ("serve", lambda: measure_serve(args, amc, dev))):
@@ -838,12 +841,80 @@ def measure_programs(args, amc, dev):
             "plain": plain, "batched_over_plain": None if plain is None else (n_tok / ms_b) / (plain["tokens"] / plain["ms"]),
             "roofline": roofline(alg, ms_b, note="algorithmic bytes: 5 B per token in, 1 B per token out, CSR "
                                                   "offsets, one mask per variable"),
-            "gpu_launches_per_step": 4,
+            "gpu_launches_per_step": batch_launches(n_tok),
             "cpu_baseline": {"value": tok1 / dt1, "unit": "tokens/s", "cores": 1, "kind": "oracle",
                              "sample": f"the first {k1} programs ({tok1} tokens), single thread ({dt1:.1f} s)"},
             "cpu_baseline_all_cores": {"value": tokT / dtT, "unit": "tokens/s", "cores": T, "kind": "oracle",
                                        "sample": f"the first {kT} programs ({tokT} tokens) sharded by program over "
                                                  f"{T} threads ({dtT:.1f} s)"},
+            "clocks": clk}
+
+
+def batch_launches(n_tokens):
+    """Kernels of one batched relation-mode check (longest-first queue):
+    bucket count, scan and order; when the batch is longer than the split
+    length (so that some program may be split) also the slot offsets, the
+    cuts, the relation reset, the ordered unit offsets, the reduce phase and
+    the carry; then the apply phase."""
+    split = int(os.environ.get("AMC_BATCH_SPLIT", "65536"))
+    return 3 + 1 if n_tokens <= split else 3 + 3 + 1 + 1 + 1 + 1
+
+
+def measure_guarded(args, amc, dev):
+    """20,000 programs over 16-256 variables whose If conditions test a guard
+    variable (seed 7): the path-sensitive relation mode, one launch sequence
+    per step."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+    b = workloads.programs_guarded()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    tok, pay, off, nv, gd = t(b["tok"]), t(b["payload"]), t(b["prog_tok_off"]), t(b["prog_nvars"]), t(b["prog_guard"])
+    vo = torch.zeros(nv.numel() + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(nv.to(torch.int64), 0, out=vo[1:])
+    n_tok, P, total_vars = tok.numel(), nv.numel(), int(vo[-1])
+    out = dict(step_mask=torch.empty(n_tok, dtype=torch.uint8, device=dev),
+               final_mask=torch.empty(total_vars, dtype=torch.uint8, device=dev),
+               prog_first_fault=torch.empty(P, dtype=torch.int64, device=dev))
+    L = amc.lib()
+    ws = torch.empty(L.amc_check_batch_guarded_workspace(n_tok, P, total_vars) + 256, dtype=torch.uint8, device=dev)
+    ws = ws[(-ws.data_ptr()) % 256:]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        step = lambda: amc.check_batch_guarded(tok, pay, off, nv, gd, vo, out=out, workspace=ws, stream=stream)
+        for _ in range(max(3, args.warmup)):
+            step()
+        assert amc.sync_status(stream) == 0
+        clocks = ClockSampler(0)
+        clocks.start()
+        ms = timed(step, args.sub_steps, stream)
+        clk = clocks.stop()
+        assert amc.sync_status(stream) == 0
+        got = out["step_mask"].cpu().numpy()
+    to_np = b["prog_tok_off"]
+    k1 = 256
+    while True:
+        a1 = int(to_np[k1])
+        t0 = time.perf_counter()
+        r1 = oracle.check_batch_guarded(b["tok"][:a1], b["payload"][:a1], to_np[:k1 + 1], b["prog_nvars"][:k1],
+                                        b["prog_guard"][:k1])
+        dt1 = time.perf_counter() - t0
+        if dt1 > args.sub_cpu_seconds / 4 or k1 >= P:
+            break
+        k1 = min(P, k1 * 4)
+    assert np.array_equal(r1[0], got[:a1])
+    ops = (b["tok"] & 15) <= 5
+    alg = 5 * n_tok + n_tok + 8 * (P + 1) * 2 + 8 * P + total_vars + 8 * P
+    return {"workload": "programs_guarded", "n_progs": P, "tokens": n_tok, "seed": 7, "ms_per_step": ms,
+            "tokens_per_s": n_tok / (ms * 1e-3),
+            "unreachable_op_fraction": float(((got == 0) & ops).sum() / max(1, ops.sum())),
+            "roofline": roofline(alg, ms, note="algorithmic bytes: 5 B per token in, 1 B per token out, CSR "
+                                               "offsets and guards, one mask per variable"),
+            "gpu_launches_per_step": 4,
+            "cpu_baseline": {"value": a1 / dt1, "unit": "tokens/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the first {k1} programs ({a1} tokens), single thread ({dt1:.1f} s)"},
             "clocks": clk}
 
 
@@ -943,6 +1014,24 @@ def measure_kloc(args, amc, dev):
             "clocks": clk}
 
 
+def phase_summary(phases):
+    """Median / p99 of the server's queue wait (submit to admission) and service
+    time (admission to done) in ms, for results as status codes (traces on
+    sessions of single statuses) and as masks (programs, and traces after a
+    program with constructs)."""
+    import numpy as np
+    out = {}
+    for kind, name in ((0, "code_results"), (1, "mask_results")):
+        q = np.array([p[0] for p in phases if p[2] == kind]) * 1e3
+        sv = np.array([p[1] for p in phases if p[2] == kind]) * 1e3
+        n = np.array([p[3] for p in phases if p[2] == kind])
+        if q.size:
+            out[name] = {"queue_p50": float(np.percentile(q, 50)), "queue_p99": float(np.percentile(q, 99)),
+                         "service_p50": float(np.percentile(sv, 50)), "service_p99": float(np.percentile(sv, 99)),
+                         "service_sum_s": float(sv.sum() / 1e3), "items": int(n.sum()), "requests": int(q.size)}
+    return out
+
+
 def measure_serve(args, amc, dev):
     """Open-loop Poisson arrivals into the continuous-batching server.  Every
     request is prepared before the clock starts: traces are slices of pinned op
@@ -955,6 +1044,9 @@ def measure_serve(args, amc, dev):
 
     import numpy as np
     import torch
+
+    # the submitter and the poller share the interpreter: switch often
+    sys.setswitchinterval(1e-4)
 
     import workloads
     P = 1 << 24
@@ -992,21 +1084,27 @@ def measure_serve(args, amc, dev):
             done_flag = [False]
             backp = [0]
 
+            phases = []
+
             def poller():
+                # the server reports what finished; only those are read (a
+                # ticket can finish before the submitter has recorded it)
+                early = {}
                 while True:
                     with lock:
-                        pend = list(tickets.items())
-                        if done_flag[0] and not pend:
+                        if done_flag[0] and not tickets:
                             return
-                    for tk, at in pend:
+                    for tk in srv.completed():
                         r = srv.poll(tk)
-                        if r is not None:
-                            now = time.perf_counter()
-                            with lock:
-                                lat.append(now - (t0 + at))
-                                items[0] += len(r["status"])
-                                errs[0] += r["error"] != 0
-                                tickets.pop(tk)
+                        early[tk] = (time.perf_counter(), len(r["status"]), r["error"] != 0)
+                        phases.append((r["t_admit"] - r["t_submit"], r["t_done"] - r["t_admit"],
+                                       1 if r["is_mask"] else 0, len(r["status"])))
+                    with lock:
+                        for tk in [t for t in early if t in tickets]:
+                            now, n_items, bad = early.pop(tk)
+                            lat.append(now - (t0 + tickets.pop(tk)))
+                            items[0] += n_items
+                            errs[0] += bad
                     if time.perf_counter() > drain_deadline[0]:
                         return
                     time.sleep(2e-5)
@@ -1018,8 +1116,9 @@ def measure_serve(args, amc, dev):
             submitted = 0
             last_submit = t0
             for sid, kind, nv, a, bb, borrow, at in reqs:
-                while time.perf_counter() < t0 + at:
-                    pass
+                # wait for the scheduled arrival without holding the interpreter
+                while (wait := t0 + at - time.perf_counter()) > 0:
+                    time.sleep(wait if wait > 2e-4 else 0)
                 if time.perf_counter() - t0 > args.serve_seconds:
                     break
                 while (tk := srv.submit(sid, kind, nv, a, bb, borrow=borrow)) is None:
@@ -1045,7 +1144,8 @@ def measure_serve(args, amc, dev):
                                    "achieved_submit_rate": submitted / max(last_submit - t0, 1e-9),
                                    "backpressured_submits": backp[0],
                                    "program_requests": sum(1 for x in reqs[:submitted] if x[1] == 1),
-                                   "items_per_s": items[0] / wall, "wall_s": wall}
+                                   "items_per_s": items[0] / wall, "wall_s": wall,
+                                   "server_phases_ms": phase_summary(phases)}
     clk = clocks.stop()
     del pools
     return {"workload": "serve", "rates_req_per_s": args.rates, "requests_per_rate": args.serve_requests,
@@ -1169,6 +1269,7 @@ def main():
               "kloc": lambda: measure_kloc(args, amc, dev),
               "programs": lambda: measure_programs(args, amc, dev), "serve": lambda: measure_serve(args, amc, dev),
               "vectorpu_lifetimes": lambda: measure_lifetimes(args, amc, dev),
+              "programs_guarded": lambda: measure_guarded(args, amc, dev),
               "trace_sizes": lambda: measure_sizes(args, amc, dev)}
         print(json.dumps(fn[args.workload]()), flush=True)
 

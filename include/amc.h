@@ -320,18 +320,21 @@ AMC_API int amc_translate_vectorpu(const int32_t* arr_start, const int32_t* arr_
  * statements as Noop v, Noop v# (CPU side, no effect), and arr_probe[a]
  * (device int64 [n_arrays]) = index of the first of the two (-1 for vectors).
  *
+ * The overlap lists are kept per time bucket (up to 256 stretches of equal
+ * length of the n_calls calls): a pair of overlapping arrays is listed, for
+ * each of the two, in every bucket their lifetimes share.
  * amc_vectorpu_overlap_pairs writes to *n_pairs (device int64) the number of
- * list entries (overlapping pairs whose lifetimes meet, counted in both
- * directions; with arr_born = arr_died = NULL every pair): the max_pairs the
+ * list entries for a run of n_calls calls (with arr_born = arr_died = NULL:
+ * every overlapping pair, both directions, one bucket): the max_pairs the
  * translation needs.  amc_translate_vectorpu_lifetimes is then
  * amc_translate_vectorpu with those rules; more than max_pairs list entries
  * give AMC_E_RANGE (device).  Feed its trace to amc_check_inherited_trace.
  * Errors (device): AMC_E_INVALID for a malformed lifetime or vector link or an
  * operand that is not live at its call, AMC_E_RANGE for a vector id out of
  * range; the rest as amc_translate_vectorpu. */
-AMC_API size_t amc_vectorpu_overlap_pairs_workspace(int32_t n_arrays);
+AMC_API size_t amc_vectorpu_overlap_pairs_workspace(int32_t n_arrays, int64_t n_calls);
 AMC_API int amc_vectorpu_overlap_pairs(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_born,
-                                       const int32_t* arr_died, int32_t n_arrays, int64_t* n_pairs,
+                                       const int32_t* arr_died, int32_t n_arrays, int64_t n_calls, int64_t* n_pairs,
                                        void* workspace, size_t ws_bytes, void* stream);
 AMC_API size_t amc_translate_vectorpu_lifetimes_workspace(int32_t n_arrays, int64_t n_calls, int64_t n_operands,
                                                           int64_t max_pairs);
@@ -438,6 +441,27 @@ AMC_API int amc_check_well_declared(const int64_t* arr_loc_off, int32_t n_arrays
                                     uint32_t* violations, int64_t* first_bad, int32_t* first_unmet,
                                     void* workspace, size_t ws_bytes, void* stream);
 
+/* Path-sensitive relation mode -- Fig. Opsem with the conditions of Section
+ * 3.2 evaluated (rules valid / invalid / rem-valid / rem-invalid): IF and
+ * WHILE token bits 4-5 give the condition, 0 = opaque (x (+) y, both
+ * outcomes), 1 = isValid g, 2 = remIsValid g, on the program's guard
+ * variable g = prog_guard[p] (-1: none, every condition must be opaque).
+ * For every variable x other than g the set of reachable pairs (status of g,
+ * status of x) is tracked (exact, as control flow depends on g alone); a
+ * stuck g satisfies no condition rule, so its paths end at the next
+ * condition; each variable's F is absorbing and does not stop the others.
+ * Outputs as amc_check_batch: step_mask[token] = statuses the op's variable
+ * may have after the op (0 for structure tokens and for ops no path reaches),
+ * final_mask, prog_first_fault.  Errors (device): AMC_E_INVALID for
+ * malformed tokens, a condition without a guard, a guard out of range or
+ * depth > AMC_MAX_DEPTH; AMC_E_RANGE for a variable id out of range. */
+AMC_API size_t amc_check_batch_guarded_workspace(int64_t n_tokens, int64_t n_progs, int64_t total_vars);
+AMC_API int amc_check_batch_guarded(const uint8_t* tok_kind_side, const int32_t* tok_payload,
+                                    const int64_t* prog_tok_off, const int32_t* prog_nvars,
+                                    const int64_t* prog_var_off, const int32_t* prog_guard, int64_t n_progs,
+                                    int64_t n_tokens, int64_t total_vars, uint8_t* step_mask, uint8_t* final_mask,
+                                    int64_t* prog_first_fault, void* workspace, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* (4) Serving -- continuous batching of check requests with per-session     */
 /*     variable statuses kept on the device between requests.                */
@@ -494,6 +518,10 @@ AMC_API int amc_serve_submit(amc_server* srv, uint64_t session_id, const amc_req
 /* Non-blocking: *done = 1 and *out filled once the request finished.  A
  * request that reports an error leaves its session's statuses unspecified. */
 AMC_API int amc_serve_poll(amc_server* srv, uint64_t ticket, int* done, amc_result* out);
+/* Non-blocking: writes to tickets[0..*n) up to cap tickets of requests that
+ * finished since the previous call (each reported once, in finishing order),
+ * so that a client polls only what is done. */
+AMC_API int amc_serve_completed(amc_server* srv, uint64_t* tickets, int32_t cap, int32_t* n);
 /* Frees a finished request's host result. */
 AMC_API int amc_serve_release(amc_server* srv, uint64_t ticket);
 /* Copies a session's current variable status sets (status masks, bit k set

@@ -61,8 +61,8 @@ def lib():
                                                  P, P, i64, P, P, P, sz, P]
         if hasattr(L, "amc_translate_vectorpu_lifetimes"):
             L.amc_vectorpu_overlap_pairs_workspace.restype = sz
-            L.amc_vectorpu_overlap_pairs_workspace.argtypes = [i32]
-            L.amc_vectorpu_overlap_pairs.argtypes = [P, P, P, P, i32, P, P, sz, P]
+            L.amc_vectorpu_overlap_pairs_workspace.argtypes = [i32, i64]
+            L.amc_vectorpu_overlap_pairs.argtypes = [P, P, P, P, i32, i64, P, P, sz, P]
             L.amc_translate_vectorpu_lifetimes_workspace.restype = sz
             L.amc_translate_vectorpu_lifetimes_workspace.argtypes = [i32, i64, i64, i64]
             L.amc_translate_vectorpu_lifetimes.argtypes = [P, P, P, P, P, i32, P, P, i64, P, P, i64, ci, i64,
@@ -78,6 +78,10 @@ def lib():
             L.amc_check_well_declared_workspace.restype = sz
             L.amc_check_well_declared_workspace.argtypes = [i64]
             L.amc_check_well_declared.argtypes = [P, i32, P, P, i64, P, P, i64, P, P, P, i64, P, P, P, P, sz, P]
+        if hasattr(L, "amc_check_batch_guarded"):
+            L.amc_check_batch_guarded_workspace.restype = sz
+            L.amc_check_batch_guarded_workspace.argtypes = [i64, i64, i64]
+            L.amc_check_batch_guarded.argtypes = [P, P, P, P, P, P, i64, i64, i64, P, P, P, P, sz, P]
         if hasattr(L, "amc_check_batch"):
             L.amc_check_batch_workspace.restype = sz
             L.amc_check_batch_workspace.argtypes = [i64, i64, i64]
@@ -195,11 +199,12 @@ def check_trace(kind_side, var, n_vars, init_status=None, *, guarded=False, out=
     return out
 
 
-def vectorpu_overlap_pairs(arr_start, arr_len, arr_born=None, arr_died=None, *, out=None, stream=None):
-    """Overlap-list entries (overlapping pairs whose lifetimes meet, both
-    directions) of the arrays: the max_pairs translate_vectorpu_lifetimes
-    needs (amc_vectorpu_overlap_pairs).  Returns the device int64 [1] tensor
-    (``out`` if given); read it with .item()."""
+def vectorpu_overlap_pairs(arr_start, arr_len, arr_born=None, arr_died=None, n_calls=0, *, out=None, stream=None):
+    """Overlap-list entries of the arrays for a run of n_calls calls (one per
+    time bucket each overlapping pair's lifetimes share, both directions; every
+    overlapping pair when the lifetimes are left out): the max_pairs
+    translate_vectorpu_lifetimes needs (amc_vectorpu_overlap_pairs).  Returns
+    the device int64 [1] tensor (``out`` if given); read it with .item()."""
     _dev(arr_start, torch.int32, "arr_start")
     _dev(arr_len, torch.int32, "arr_len")
     if (arr_born is None) != (arr_died is None):
@@ -211,9 +216,9 @@ def vectorpu_overlap_pairs(arr_start, arr_len, arr_born=None, arr_died=None, *, 
     dev = arr_start.device
     L = lib()
     n = out if out is not None else torch.empty(1, dtype=torch.int64, device=dev)
-    ws = _ws.get(L.amc_vectorpu_overlap_pairs_workspace(A), dev)
-    rc = L.amc_vectorpu_overlap_pairs(_p(arr_start), _p(arr_len), _p(arr_born), _p(arr_died), A, _p(n), _p(ws),
-                                      ws.numel(), _stream_ptr(stream))
+    ws = _ws.get(L.amc_vectorpu_overlap_pairs_workspace(A, int(n_calls)), dev)
+    rc = L.amc_vectorpu_overlap_pairs(_p(arr_start), _p(arr_len), _p(arr_born), _p(arr_died), A, int(n_calls), _p(n),
+                                      _p(ws), ws.numel(), _stream_ptr(stream))
     _check(rc, "amc_vectorpu_overlap_pairs")
     return n
 
@@ -239,7 +244,8 @@ def translate_vectorpu_lifetimes(arr_start, arr_len, arr_parent, arr_born, arr_d
     dev = arr_start.device
     L = lib()
     if max_pairs is None:
-        max_pairs = int(vectorpu_overlap_pairs(arr_start, arr_len, arr_born, arr_died, stream=stream).item())
+        max_pairs = int(vectorpu_overlap_pairs(arr_start, arr_len, arr_born, arr_died, n_calls,
+                                               stream=stream).item())
     max_pairs = max(int(max_pairs), 1)
     ws = _ws.get(L.amc_translate_vectorpu_lifetimes_workspace(A, n_calls, n_opnd, max_pairs), dev)
 
@@ -483,6 +489,39 @@ def check_batch(tok, payload, prog_tok_off, prog_nvars, prog_var_off=None, *, gr
     return out
 
 
+def check_batch_guarded(tok, payload, prog_tok_off, prog_nvars, prog_guard, prog_var_off=None, *, out=None,
+                        workspace=None, stream=None):
+    """Path-sensitive relation mode over a batch (amc_check_batch_guarded):
+    IF / WHILE bits 4-5 = condition (0 opaque, 1 isValid g, 2 remIsValid g)
+    on each program's guard variable prog_guard[p] (int32, -1 none).  Other
+    arguments and the returned dict as check_batch."""
+    _dev(tok, torch.uint8, "tok")
+    _dev(payload, torch.int32, "payload")
+    _dev(prog_tok_off, torch.int64, "prog_tok_off")
+    _dev(prog_nvars, torch.int32, "prog_nvars")
+    _dev(prog_guard, torch.int32, "prog_guard")
+    dev = tok.device
+    P = prog_nvars.numel()
+    if prog_var_off is None:
+        prog_var_off = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(prog_nvars.to(torch.int64), 0, out=prog_var_off[1:])
+    _dev(prog_var_off, torch.int64, "prog_var_off")
+    n_tok = tok.numel()
+    total_vars = int(prog_var_off[-1].item()) if P > 0 else 0
+    if out is None:
+        out = dict(step_mask=torch.empty(n_tok, dtype=torch.uint8, device=dev),
+                   final_mask=torch.empty(total_vars, dtype=torch.uint8, device=dev),
+                   prog_first_fault=torch.empty(P, dtype=torch.int64, device=dev))
+    L = lib()
+    nbytes = L.amc_check_batch_guarded_workspace(n_tok, P, total_vars)
+    ws = workspace if workspace is not None else _ws.get(nbytes, dev)
+    rc = L.amc_check_batch_guarded(_p(tok), _p(payload), _p(prog_tok_off), _p(prog_nvars), _p(prog_var_off),
+                                   _p(prog_guard), P, n_tok, total_vars, _p(out["step_mask"]), _p(out["final_mask"]),
+                                   _p(out["prog_first_fault"]), _p(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "amc_check_batch_guarded")
+    return out
+
+
 def check_well_declared(arr_loc_off, loc_owner, call_tok_off, tok, payload, call_am_off, am_array, am_mode, *,
                         out=None, stream=None):
     """Static well-declaredness of calls AM{S} (amc_check_well_declared).
@@ -548,6 +587,7 @@ class Server:
         L.amc_serve_submit.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]
         L.amc_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_Result)]
         L.amc_serve_release.argtypes = [P, ctypes.c_uint64]
+        L.amc_serve_completed.argtypes = [P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.amc_session_export.argtypes = [P, ctypes.c_uint64, P, ctypes.c_int32]
         L.amc_server_destroy.argtypes = [P]
         self._L = L
@@ -595,6 +635,14 @@ class Server:
         if release:
             _check(self._L.amc_serve_release(self._h, ticket), "amc_serve_release")
         return out
+
+    def completed(self, cap: int = 4096):
+        """Tickets of the requests finished since the last call (amc_serve_completed)."""
+        buf = (ctypes.c_uint64 * cap)()
+        n = ctypes.c_int32()
+        _check(self._L.amc_serve_completed(self._h, ctypes.cast(buf, ctypes.c_void_p), cap, ctypes.byref(n)),
+               "amc_serve_completed")
+        return list(buf[:n.value])
 
     def export(self, session: int, n_vars: int):
         import numpy as np

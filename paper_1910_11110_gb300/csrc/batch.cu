@@ -94,6 +94,7 @@ struct Unit {
     uint32_t* rel;                // reduce: relation row of the segment (nv words)
     uint8_t* rsave;               // reduce: the warp's save / alt rows ([AMC_MAX_DEPTH][seg_max] each)
     uint8_t* ralt;
+    int whole;                    // apply of a whole program under the simple plan
 };
 
 // Runs one unit on the calling warp.
@@ -194,7 +195,7 @@ __device__ void run_unit(const BatchParams& p, const Unit& u, WarpSmem& S, const
                 end = pos + 1 + len;
             }
             if ((ks0 >> 4) || len < 0 || end <= pos || end >= lim || (p.tok[end] & 0xEFu) != AMC_T_END ||
-                (p.tok[end] >> 4) || depth >= AMC_MAX_DEPTH) {
+                (p.tok[end] >> 4) || depth >= p.save_rows) {
                 bad = true;
                 break;
             }
@@ -281,8 +282,12 @@ __device__ void run_unit(const BatchParams& p, const Unit& u, WarpSmem& S, const
         // program first fault: min over lanes, then over the program's segments
 #pragma unroll
         for (int o = 16; o; o >>= 1) ff = min(ff, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)ff, o));
-        if (lane == 0 && ff != INT64_MAX)
-            atomicMin(reinterpret_cast<unsigned long long*>(p.prog_first_fault + prog), (unsigned long long)ff);
+        if (lane == 0) {
+            if (u.whole)                    // the only segment: the program's first fault
+                p.prog_first_fault[prog] = ff == INT64_MAX ? -1 : ff;
+            else if (ff != INT64_MAX)
+                atomicMin(reinterpret_cast<unsigned long long*>(p.prog_first_fault + prog), (unsigned long long)ff);
+        }
         if (SMEM && u.last)
             for (int32_t v = lane; v < nv; v += 32) gM[v] = M[v];
     } else {
@@ -304,6 +309,7 @@ struct Plan {
     uint32_t* R;                  // [slots][SPLIT_VARS] relations
     uint8_t* rsave;               // [reduce warps][2][AMC_MAX_DEPTH][seg_max] reduce-pass copies
     int64_t* ord_off;             // [P + 1] apply units before the k-th program of the queue order
+    int simple;                   // no program can be split: one unit per program, no planning
 };
 
 __device__ __forceinline__ int64_t split_slots(int64_t len, int32_t nv, int64_t split)
@@ -358,8 +364,9 @@ __global__ void __launch_bounds__(BWARPS * 32, MINB) batch_kernel(const BatchPar
     const int64_t sm = seg_max_of(p.split);
     uint8_t* rsave = pl.rsave + wid * 2 * (int64_t)AMC_MAX_DEPTH * sm;
     uint8_t* ralt = rsave + (int64_t)AMC_MAX_DEPTH * sm;
-    const int64_t n_slots = pl.slot_off[p.n_progs];
-    const int64_t n_units = pl.unit_off[p.n_progs];
+    // without any split program (simple plan) unit i is program i of the queue
+    const int64_t n_slots = pl.simple ? 0 : pl.slot_off[p.n_progs];
+    const int64_t n_units = pl.simple ? p.n_progs : pl.unit_off[p.n_progs];
     for (;;) {
         int64_t i = 0;
         if (lane == 0) i = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(p.queue_head), 1ull);
@@ -376,6 +383,7 @@ __global__ void __launch_bounds__(BWARPS * 32, MINB) batch_kernel(const BatchPar
             u.t1 = b;
             u.mode = 1 + (int)(i % 5);
             u.last = 0;
+            u.whole = 0;
             u.entry = nullptr;
             u.rel = pl.R + slot * (int64_t)SPLIT_VARS;
             u.rsave = rsave;
@@ -383,7 +391,10 @@ __global__ void __launch_bounds__(BWARPS * 32, MINB) batch_kernel(const BatchPar
         } else {
             if (i >= n_units) break;
             int64_t prog, j;
-            if (p.order) {                  // programs longest first, their units in order
+            if (pl.simple) {
+                prog = p.order ? p.order[i] : i;
+                j = 0;
+            } else if (p.order) {           // programs longest first, their units in order
                 const int64_t k = find_owner(pl.ord_off, p.n_progs, i);
                 prog = p.order[k];
                 j = i - pl.ord_off[k];
@@ -391,11 +402,12 @@ __global__ void __launch_bounds__(BWARPS * 32, MINB) batch_kernel(const BatchPar
                 prog = find_owner(pl.unit_off, p.n_progs, i);
                 j = i - pl.unit_off[prog];
             }
-            const int64_t ns = pl.slot_off[prog + 1] - pl.slot_off[prog];
+            const int64_t ns = pl.simple ? 0 : pl.slot_off[prog + 1] - pl.slot_off[prog];
             u.prog = prog;
             u.mode = 0;
             u.rel = nullptr;
             u.rsave = u.ralt = nullptr;
+            u.whole = pl.simple;
             if (ns == 0) {
                 u.t0 = p.prog_tok_off[prog];
                 u.t1 = p.prog_tok_off[prog + 1];
@@ -667,15 +679,15 @@ struct BatchLayout {
     int64_t red_ctas;             // CTAs of the reduce phase (each warp owns construct-copy rows)
 };
 
-BatchLayout layout(int64_t n_tokens, int64_t n_progs, int64_t split)
+BatchLayout layout(int64_t n_tokens, int64_t n_progs, int64_t split, int save_rows)
 {
     BatchLayout L;
     // a split program of length len has ceil(len / split) <= 2 len / split slots
     L.max_slots = 2 * (n_tokens / split) + 1;
     size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o += align_up(b, 256); return at; };
-    L.save = take((size_t)AMC_MAX_DEPTH * (size_t)n_tokens + 1);
-    L.alt = take((size_t)AMC_MAX_DEPTH * (size_t)n_tokens + 1);
+    L.save = take((size_t)save_rows * (size_t)n_tokens + 1);
+    L.alt = take((size_t)save_rows * (size_t)n_tokens + 1);
     L.slot_off = take(8 * ((size_t)n_progs + 1));
     L.unit_off = take(8 * ((size_t)n_progs + 1));
     L.seg_t0 = take(8 * (size_t)L.max_slots);
@@ -696,9 +708,17 @@ BatchLayout layout(int64_t n_tokens, int64_t n_progs, int64_t split)
 
 }  // namespace
 
+// no_split: programs are never split (a split length past any program)
+int64_t split_of(bool no_split) { return no_split ? (int64_t)1 << 60 : batch_split(); }
+
 size_t batch_workspace_bytes(int64_t n_tokens, int64_t n_progs)
 {
-    return layout(n_tokens, n_progs, batch_split()).total;
+    return layout(n_tokens, n_progs, batch_split(), AMC_MAX_DEPTH).total;
+}
+
+size_t batch_workspace_bytes(int64_t n_tokens, int64_t n_progs, bool no_split, int save_rows)
+{
+    return layout(n_tokens, n_progs, split_of(no_split), save_rows).total;
 }
 
 int launch_batch(const BatchLaunch& B, cudaStream_t s)
@@ -717,8 +737,9 @@ int launch_batch(const BatchLaunch& B, cudaStream_t s)
     p.prog_first_fault = B.prog_first_fault;
     p.err = B.err;
     p.tab = host_set_tables();
-    p.split = batch_split();
-    const BatchLayout L = layout(B.n_tokens, B.n_progs, p.split);
+    p.split = split_of(B.no_split != 0);
+    p.save_rows = B.save_rows < 0 ? 0 : (B.save_rows > AMC_MAX_DEPTH ? AMC_MAX_DEPTH : B.save_rows);
+    const BatchLayout L = layout(B.n_tokens, B.n_progs, p.split, p.save_rows);
     uint8_t* w = static_cast<uint8_t*>(B.workspace);
     p.save = w + L.save;
     p.alt = w + L.alt;
@@ -744,26 +765,36 @@ int launch_batch(const BatchLaunch& B, cudaStream_t s)
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)n_sm * per_sm;
     if (B.max_ctas > 0 && grid > B.max_ctas) grid = B.max_ctas;
+    // no program longer than the split length: one unit per program, no planning
+    pl.simple = B.n_tokens <= p.split ? 1 : 0;
+    if (pl.simple) {
+        const int64_t need = (B.n_progs + BWARPS - 1) / BWARPS;
+        if (grid > need) grid = need;
+    }
     if (B.profile & 1) profile_begin(s);
-    plan_offsets_kernel<<<1, 1024, 0, s>>>(B.prog_tok_off, B.prog_nvars, B.n_progs,
-                                           const_cast<int64_t*>(pl.slot_off), const_cast<int64_t*>(pl.unit_off),
-                                           B.prog_first_fault, p.split);
-    plan_cuts_kernel<<<n_sm * 4, 256, 0, s>>>(B.tok, B.prog_tok_off, B.prog_nvars, B.n_progs, pl.slot_off, pl.seg_t0,
-                                              p.split);
-    zero_rel_kernel<<<n_sm * 4, 256, 0, s>>>(p, pl);
+    if (!pl.simple) {
+        plan_offsets_kernel<<<1, 1024, 0, s>>>(B.prog_tok_off, B.prog_nvars, B.n_progs,
+                                               const_cast<int64_t*>(pl.slot_off), const_cast<int64_t*>(pl.unit_off),
+                                               B.prog_first_fault, p.split);
+        plan_cuts_kernel<<<n_sm * 4, 256, 0, s>>>(B.tok, B.prog_tok_off, B.prog_nvars, B.n_progs, pl.slot_off,
+                                                  pl.seg_t0, p.split);
+        zero_rel_kernel<<<n_sm * 4, 256, 0, s>>>(p, pl);
+    }
     if (B.longest_first) {
         if (cudaMemsetAsync(counts, 0, 256, s) != cudaSuccess) return AMC_E_CUDA;
         bucket_count_kernel<<<128, 256, 0, s>>>(B.prog_tok_off, B.n_progs, counts);
         bucket_scan_kernel<<<1, 32, 0, s>>>(counts, boff);
         order_kernel<<<(unsigned)((B.n_progs + 255) / 256), 256, 0, s>>>(B.prog_tok_off, B.n_progs, boff, counts,
                                                                            order);
-        order_units_kernel<<<1, 1024, 0, s>>>(order, pl.unit_off, B.n_progs, pl.ord_off);
+        if (!pl.simple) order_units_kernel<<<1, 1024, 0, s>>>(order, pl.unit_off, B.n_progs, pl.ord_off);
         p.order = order;
     }
-    if (cudaMemsetAsync(p.queue_head, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
-    const int64_t rgrid = grid < L.red_ctas ? grid : L.red_ctas;
-    if (rgrid > 0) kern<<<(unsigned)rgrid, BWARPS * 32, 0, s>>>(p, pl, 0);      // reduce
-    carry_kernel<<<n_sm * 4, 256, 0, s>>>(p, pl);
+    if (!pl.simple) {
+        if (cudaMemsetAsync(p.queue_head, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
+        const int64_t rgrid = grid < L.red_ctas ? grid : L.red_ctas;
+        if (rgrid > 0) kern<<<(unsigned)rgrid, BWARPS * 32, 0, s>>>(p, pl, 0);      // reduce
+        carry_kernel<<<n_sm * 4, 256, 0, s>>>(p, pl);
+    }
     if (cudaMemsetAsync(p.queue_head, 0, 8, s) != cudaSuccess) return AMC_E_CUDA;
     kern<<<(unsigned)grid, BWARPS * 32, 0, s>>>(p, pl, 1);       // apply
     if (B.profile & 2) profile_end(s);

@@ -23,6 +23,7 @@ struct BatchParams {
     uint64_t* queue_head;
     int* err;
     int64_t split;                 // segment length of split programs
+    int save_rows;                 // construct levels the save / alt rows hold (deeper: AMC_E_INVALID)
     SetTables tab;
 };
 
@@ -43,10 +44,13 @@ struct BatchLaunch {
     int longest_first = 1;
     int max_ctas = 0;
     int regs_capped = 1;           // registers fitted to 6 CTAs per SM (else to 4)
+    int no_split = 0;              // never split a program (no reduce-pass scratch)
+    int save_rows = AMC_MAX_DEPTH; // construct levels with save / alt rows (0: straight-line only)
     int profile = 0;
 };
 
 size_t batch_workspace_bytes(int64_t n_tokens, int64_t n_progs);
+size_t batch_workspace_bytes(int64_t n_tokens, int64_t n_progs, bool no_split, int save_rows);
 int launch_batch(const BatchLaunch& B, cudaStream_t s);
 
 }  // namespace amc

@@ -770,9 +770,41 @@ bool scan_dense_eligible(int64_t n_ops, int32_t n_vars)
     return ln >= 15 + 2 * (12 - lv) && n_ops >= DENSE_MIN_OPS;
 }
 
+// The whole trace over more than 16,384 (at most 2^20) variables with global
+// per-chunk rows: where nothing gets stuck (a well-declared program's guarded
+// trace) every op stays live and the single-pass kernel's lists are long and
+// contended.  Taken when the launch forces it (the tuner times it) on traces
+// of at least GV_MIN_OPS ops; chunk count from the row budget (about 2^28
+// row bytes, 256 .. 1,024 chunks).
+constexpr int64_t GV_MIN_OPS = (int64_t)1 << 20;
+constexpr int32_t GV_MAX_VARS = 1 << 20;
+
+int gv_chunks(int32_t n_vars)
+{
+    int64_t c = ((int64_t)1 << 28) / (n_vars > 0 ? n_vars : 1);
+    return (int)(c < 256 ? 256 : (c > 1024 ? 1024 : c));
+}
+
+bool dense_forced_ok(int64_t n_ops, int32_t n_vars)
+{
+    if (n_vars < 1 || n_ops < 1) return false;
+    return n_vars <= DENSE_MAX_VARS || (n_vars <= GV_MAX_VARS && n_ops >= GV_MIN_OPS);
+}
+
 size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars)
 {
     int n_tiles, n_chunks, tpc;
+    if (n_vars > DENSE_MAX_VARS && n_vars <= GV_MAX_VARS && n_ops >= GV_MIN_OPS) {
+        dense_shape(n_ops, gv_chunks(n_vars), n_tiles, n_chunks, tpc);
+        size_t b = 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256);
+        if (const int64_t P = prefix_ops(n_ops, n_vars, false)) {
+            dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
+            const size_t pb = 2 * align_up((size_t)n_chunks * (size_t)n_vars, 256) + align_up(4 * (size_t)n_vars, 256) +
+                              256 + align_up((size_t)n_vars, 256) + 256;
+            if (pb > b) b = pb;
+        }
+        return b;
+    }
     if (const int64_t P = prefix_ops(n_ops, n_vars, false)) {   // the larger workspace
         // prefix rows, then the suffix's first faults and the prefix's final statuses
         dense_shape(P, PREFIX_CHUNKS, n_tiles, n_chunks, tpc);
@@ -873,9 +905,11 @@ int launch_scan_prefix(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 
 int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s)
 {
-    // up to 8,192 variables: warp-sequential batches; else tile sorts
+    // up to 8,192 variables: warp-sequential batches; else tile sorts (rows
+    // in shared memory up to 16,384 variables, in global memory above)
     const char* e = getenv("AMC_SCAN_DENSE_SORT");                // test override: the sorted variant
     if (L.n_vars <= WARP_MAX_VARS && !(e && e[0] == '1')) return launch_warp_dense(L, ws, s);
+    if (L.n_vars > DENSE_MAX_VARS) return launch_dense_range(L, gv_chunks(L.n_vars), L.n_ops, ws, s);
     return launch_dense_range(L, DENSE_MAX_CHUNKS, L.n_ops, ws, s);
 }
 

@@ -1757,8 +1757,7 @@ int scan_trace_plan(const ScanLaunch& L, int* launches)
         n = scan_tail_launches(L);
         path = AMC_PATH_EPOCHS;
     } else if (L.dense != 0 && plain &&
-               ((L.dense == 1 && L.n_vars >= 1 && L.n_vars <= 16384 && L.n_ops >= 1) ||
-                scan_dense_eligible(L.n_ops, L.n_vars))) {
+               ((L.dense == 1 && dense_forced_ok(L.n_ops, L.n_vars)) || scan_dense_eligible(L.n_ops, L.n_vars))) {
         const char* e = getenv("AMC_SCAN_DENSE_SORT");
         const bool warp = L.n_vars <= 8192 && !(e && e[0] == '1');
         n = warp ? 5 : 3;                                   // chunk, reduce, carry, expand, chunk; or reduce, carry, apply
@@ -1823,7 +1822,7 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s)
     p.tile_counter = reinterpret_cast<uint32_t*>(w);
     p.front = p.tile_counter + 1;
     const bool plain = !L.n_dev && !L.gate;
-    const bool dense_forced = L.dense == 1 && L.n_vars >= 1 && L.n_vars <= 16384 && L.n_ops >= 1;
+    const bool dense_forced = L.dense == 1 && dense_forced_ok(L.n_ops, L.n_vars);
     if (L.dense != 0 && plain && (dense_forced || scan_dense_eligible(L.n_ops, L.n_vars)))
         return launch_scan_dense(L, w + 256, s);
     if (L.dense != 0 && (L.prefix_log2 > 0 ? scan_forced_prefix(L)

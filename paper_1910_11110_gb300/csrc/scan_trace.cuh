@@ -81,6 +81,9 @@ int launch_scan_trace(const ScanLaunch& L, cudaStream_t s);
 // single-pass scan measured on random traces with the Zipf workload's kind
 // mix: 2^11 ops at 2^14 variables, 2^15 at 2^12, 2^21 at 2^9).
 bool scan_dense_eligible(int64_t n_ops, int32_t n_vars);
+// Whether a launch may force the reduce / carry / apply path on these sizes
+// (at most 16,384 variables; up to 2^20 with global rows from 2^20 ops on).
+bool dense_forced_ok(int64_t n_ops, int32_t n_vars);
 size_t scan_dense_workspace_bytes(int64_t n_ops, int32_t n_vars);
 int launch_scan_dense(const ScanLaunch& L, uint8_t* ws, cudaStream_t s);
 // Traces over more than 16,384 (at most 2^20) variables and of 2^24 ops or

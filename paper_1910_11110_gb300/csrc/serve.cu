@@ -137,6 +137,7 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     std::shared_ptr<Request> req;
+    bool launching = false;          // the worker is enqueueing its work (outside the lock)
 };
 
 // pinned layout of a request: staged inputs (none when borrowed), results,
@@ -167,6 +168,7 @@ struct amc_server {
     std::deque<std::shared_ptr<Request>> queue;
     std::map<uint64_t, std::shared_ptr<Request>> reqs;
     std::map<uint64_t, Session> sessions;
+    std::deque<uint64_t> finished;   // tickets finished since the last amc_serve_completed
     uint64_t next_ticket = 1;
     size_t max_queue = 1 << 20;
     std::atomic<bool> stop{false};
@@ -233,7 +235,9 @@ size_t request_bytes(const Request& r)
 {
     const size_t n = (size_t)r.n;
     size_t b = align_up(n, 256) + align_up(4 * n, 256) + align_up(n, 256) + 512;   // ks, var, out, small
-    size_t w = batch_workspace_bytes(r.n, 1) + 256;                  // relation mode
+    // relation mode, one program, never split; construct rows only when the
+    // request has constructs
+    size_t w = batch_workspace_bytes(r.n, 1, true, r.has_struct ? AMC_MAX_DEPTH : 0) + 256;
     if (r.kind == AMC_REQ_TRACE) {
         // trace kernels: workspace, first faults, the session's statuses as codes
         const size_t t = scan_workspace_bytes(r.n, r.n_vars) + align_up(4 * (size_t)r.n_vars, 256) +
@@ -326,6 +330,8 @@ int launch(amc_server* s, Slot& sl, Request& r, Session& ses)
         B.err = d_err;
         B.workspace = d_ws;
         B.longest_first = 0;
+        B.no_split = 1;
+        B.save_rows = r.has_struct ? AMC_MAX_DEPTH : 0;
         rc = launch_batch(B, st);
         r.is_mask = 1;
         if (r.has_struct) ses.det = false;      // later requests see sets of several statuses
@@ -349,18 +355,23 @@ void finish(amc_server* s, Slot& sl)
     r.state = 2;
     s->pool.free(r.off, r.bytes);
     s->sessions[r.session].busy = false;
+    s->finished.push_back(r.ticket);
     sl.req.reset();
 }
 
+// The worker: under the lock it retires finished slots and admits queued
+// requests (memory, slot, session); it enqueues their copies and kernels with
+// the lock released, so that submit and poll never wait for CUDA calls.
 void worker_loop(amc_server* s)
 {
     cudaSetDevice(s->device);
+    std::vector<Slot*> batch;
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
         bool progress = false;
         bool running = false;
         for (Slot& sl : s->slots) {
-            if (!sl.req) continue;
+            if (!sl.req || sl.launching) continue;
             running = true;
             if (cudaEventQuery(sl.done) == cudaSuccess) {
                 finish(s, sl);
@@ -368,6 +379,7 @@ void worker_loop(amc_server* s)
             }
         }
         // admission in arrival order; a request waits if its session is busy
+        batch.clear();
         for (auto it = s->queue.begin(); it != s->queue.end();) {
             Slot* free_slot = nullptr;
             for (Slot& sl : s->slots)
@@ -383,19 +395,36 @@ void worker_loop(amc_server* s)
             r.state = 1;
             ses.busy = true;
             free_slot->req = *it;
-            const int rc = launch(s, *free_slot, r, ses);
-            if (rc) {
-                cudaStreamSynchronize(free_slot->stream);
-                r.error = rc;
-                r.t_done = now_s();
-                r.state = 2;
-                s->pool.free(r.off, r.bytes);
-                ses.busy = false;
-                free_slot->req.reset();
-            }
+            free_slot->launching = true;
+            batch.push_back(free_slot);
             it = s->queue.erase(it);
             progress = true;
             running = true;
+        }
+        if (!batch.empty()) {
+            // sessions and requests of admitted slots are touched by no one
+            // else until their slot is retired
+            std::vector<std::pair<Request*, Session*>> work;
+            for (Slot* sl : batch) work.emplace_back(sl->req.get(), &s->sessions[sl->req->session]);
+            lock.unlock();
+            std::vector<int> rcs(batch.size());
+            for (size_t k = 0; k < batch.size(); ++k) rcs[k] = launch(s, *batch[k], *work[k].first, *work[k].second);
+            lock.lock();
+            for (size_t k = 0; k < batch.size(); ++k) {
+                Slot& sl = *batch[k];
+                sl.launching = false;
+                if (rcs[k]) {
+                    cudaStreamSynchronize(sl.stream);
+                    Request& r = *sl.req;
+                    r.error = rcs[k];
+                    r.t_done = now_s();
+                    r.state = 2;
+                    s->pool.free(r.off, r.bytes);
+                    s->sessions[r.session].busy = false;
+                    s->finished.push_back(r.ticket);
+                    sl.req.reset();
+                }
+            }
         }
         if (s->stop && s->queue.empty() && !running) break;
         if (!progress) {
@@ -514,6 +543,19 @@ int amc_serve_poll(amc_server* s, uint64_t ticket, int* done, amc_result* out)
         out->t_done = r.t_done;
         out->is_mask = r.is_mask;
     }
+    return AMC_OK;
+}
+
+int amc_serve_completed(amc_server* s, uint64_t* tickets, int32_t cap, int32_t* n)
+{
+    if (!s || !n || cap < 0 || (cap > 0 && !tickets)) return AMC_E_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    int32_t k = 0;
+    while (k < cap && !s->finished.empty()) {
+        tickets[k++] = s->finished.front();
+        s->finished.pop_front();
+    }
+    *n = k;
     return AMC_OK;
 }
 

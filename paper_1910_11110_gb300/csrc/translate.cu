@@ -54,8 +54,10 @@ struct TrParams {
     int64_t out_cap;
     int64_t* out_n;
     int64_t* call_first_op;
-    const int64_t* ov_off;
+    const int64_t* ov_off;        // [n_arrays * nb + 1]: list (a, bucket)
     const int32_t* ov_idx;
+    int32_t nb;                   // time buckets of the lists (1 without lifetimes)
+    int64_t bl;                   // calls per bucket
     int32_t* call_cnt;
     int* err;
     // lifetimes (born == nullptr: every array live throughout)
@@ -66,6 +68,16 @@ struct TrParams {
     const uint32_t* b_id;         // the pvector ids in that order
     int64_t* arr_probe;
 };
+
+// overlap list of array a read at call c (its time bucket's list)
+__device__ __forceinline__ int64_t list_lo(const TrParams& p, int32_t a, int64_t c)
+{
+    return p.ov_off[(int64_t)a * p.nb + (p.nb > 1 ? c / p.bl : 0)];
+}
+__device__ __forceinline__ int64_t list_hi(const TrParams& p, int32_t a, int64_t c)
+{
+    return p.ov_off[(int64_t)a * p.nb + (p.nb > 1 ? c / p.bl : 0) + 1];
+}
 
 __device__ __forceinline__ bool live_at(const TrParams& p, int32_t a, int64_t c)
 {
@@ -176,7 +188,7 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
             if (i >= n) break;
             if ((mode[i] & AMC_MODE_DROPPED) || !(mode[i] & AMC_MODE_W)) continue;
             const bool x_rw = (mode[i] & 3) == AMC_MODE_RW;
-            for (int64_t q = p.ov_off[arr[i]]; q < p.ov_off[arr[i] + 1]; ++q) {
+            for (int64_t q = list_lo(p, arr[i], c); q < list_hi(p, arr[i], c); ++q) {
                 const int32_t y = p.ov_idx[q];
                 if (!live_at(p, y, c)) continue;
 #pragma unroll
@@ -217,8 +229,8 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
         for (int l = 0; l < NMAX; ++l) {
             cur[l] = end[l] = 0;
             if (l < n && !(mode[l] & AMC_MODE_DROPPED) && (mode[l] & AMC_MODE_W)) {
-                cur[l] = p.ov_off[arr[l]];
-                end[l] = p.ov_off[arr[l] + 1];
+                cur[l] = list_lo(p, arr[l], c);
+                end[l] = list_hi(p, arr[l], c);
             }
         }
         for (;;) {
@@ -242,7 +254,7 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
         if (!(mode[i] & AMC_MODE_W)) continue;           // the body writes x (declared or not)
         const int32_t x = arr[i];
         const int32_t sx = p.arr_start[x], lx = p.arr_len[x];
-        for (int64_t q = p.ov_off[x]; q < p.ov_off[x + 1]; ++q) {
+        for (int64_t q = list_lo(p, x, c); q < list_hi(p, x, c); ++q) {
             const int32_t y = p.ov_idx[q];
             if (!live_at(p, y, c)) continue;
             put(iv_contains(sx, lx, p.arr_start[y], p.arr_len[y]) ? AMC_K_W : AMC_K_PW, y);
@@ -295,7 +307,7 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
     if (p.infer) {
         for (int i = 0; i < n; ++i) {
             if ((mode[i] & AMC_MODE_DROPPED) || !(mode[i] & AMC_MODE_W)) continue;
-            for (int64_t q = p.ov_off[arr[i]]; q < p.ov_off[arr[i] + 1]; ++q) {
+            for (int64_t q = list_lo(p, arr[i], c); q < list_hi(p, arr[i], c); ++q) {
                 if (!live_at(p, p.ov_idx[q], c)) continue;
                 const int j = find(p.ov_idx[q]);
                 if (j < 0 || (mode[j] & AMC_MODE_DROPPED)) continue;
@@ -331,8 +343,8 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
         int nl = 0;
         for (int i = 0; i < n; ++i) {
             if ((mode[i] & AMC_MODE_DROPPED) || !(mode[i] & AMC_MODE_W)) continue;
-            cur[nl] = p.ov_off[arr[i]];
-            end[nl] = p.ov_off[arr[i] + 1];
+            cur[nl] = list_lo(p, arr[i], c);
+            end[nl] = list_hi(p, arr[i], c);
             ++nl;
         }
         for (;;) {
@@ -352,7 +364,7 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
         if (!(mode[i] & AMC_MODE_W)) continue;           // the body writes x (declared or not)
         const int32_t x = arr[i];
         const int32_t sx = p.arr_start[x], lx = p.arr_len[x];
-        for (int64_t q = p.ov_off[x]; q < p.ov_off[x + 1]; ++q) {
+        for (int64_t q = list_lo(p, x, c); q < list_hi(p, x, c); ++q) {
             const int32_t y = p.ov_idx[q];
             if (!live_at(p, y, c)) continue;
             put(iv_contains(sx, lx, p.arr_start[y], p.arr_len[y]) ? AMC_K_W : AMC_K_PW, y);
@@ -426,6 +438,7 @@ __global__ void lifetimes_kernel(const TrParams p, uint32_t* __restrict__ key, u
 struct TrLayout {
     size_t ov_off, ov_idx, ovws, bk0, bv0, bk1, bv1, bscr, call_cnt, scan, total;
     int64_t cap;
+    int32_t nb;
 };
 
 TrLayout layout(int32_t A, int64_t n_calls, int64_t max_pairs, bool lifetimes)
@@ -435,9 +448,10 @@ TrLayout layout(int32_t A, int64_t n_calls, int64_t max_pairs, bool lifetimes)
     auto take = [&](size_t b) { const size_t at = o; o += align_up(b, 256); return at; };
     // without lifetimes every array may overlap every other
     L.cap = lifetimes ? max_pairs : (int64_t)A * (A > 0 ? A - 1 : 0);
-    L.ov_off = take(8 * ((size_t)A + 1));
+    L.nb = overlap_buckets(n_calls, lifetimes);
+    L.ov_off = take(8 * ((size_t)A * L.nb + 1));
     L.ov_idx = take(4 * (size_t)(L.cap > 0 ? L.cap : 1));
-    L.ovws = take(overlap_workspace_bytes(A, L.cap));
+    L.ovws = take(overlap_workspace_bytes(A, L.nb, L.cap));
     const size_t a4 = lifetimes ? 4 * (size_t)(A > 0 ? A : 1) : 0;
     L.bk0 = take(a4);
     L.bv0 = take(a4);
@@ -462,14 +476,15 @@ size_t translate_lifetimes_workspace_bytes(int32_t n_arrays, int64_t n_calls, in
     return layout(n_arrays, n_calls, max_pairs, true).total;
 }
 
-size_t overlap_count_workspace_bytes(int32_t n_arrays)
+size_t overlap_count_workspace_bytes(int32_t n_arrays, int64_t n_calls, bool lifetimes)
 {
-    return align_up(8 * ((size_t)n_arrays + 1), 256) + overlap_workspace_bytes(n_arrays, 0);
+    const int32_t nb = overlap_buckets(n_calls, lifetimes);
+    return align_up(8 * ((size_t)n_arrays * nb + 1), 256) + overlap_workspace_bytes(n_arrays, nb, 0);
 }
 
 int launch_overlap_count(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_born,
-                         const int32_t* arr_died, int32_t n_arrays, int64_t* n_pairs, int* err, void* workspace,
-                         cudaStream_t s)
+                         const int32_t* arr_died, int32_t n_arrays, int64_t n_calls, int64_t* n_pairs, int* err,
+                         void* workspace, cudaStream_t s)
 {
     OverlapBuild O;
     O.arr_start = arr_start;
@@ -477,11 +492,13 @@ int launch_overlap_count(const int32_t* arr_start, const int32_t* arr_len, const
     O.arr_born = arr_born;
     O.arr_died = arr_died;
     O.n_arrays = n_arrays;
+    O.n_buckets = overlap_buckets(n_calls, arr_born != nullptr);
+    O.bucket_len = overlap_bucket_len(n_calls, O.n_buckets);
     O.cap = 0;
     O.ov_off = static_cast<int64_t*>(workspace);
     O.n_pairs = n_pairs;
     O.err = err;
-    O.workspace = static_cast<uint8_t*>(workspace) + align_up(8 * ((size_t)n_arrays + 1), 256);
+    O.workspace = static_cast<uint8_t*>(workspace) + align_up(8 * ((size_t)n_arrays * O.n_buckets + 1), 256);
     return launch_overlaps(O, s);
 }
 
@@ -523,6 +540,10 @@ int launch_translate(const TranslateLaunch& T, cudaStream_t s)
     O.arr_born = T.arr_born;
     O.arr_died = T.arr_died;
     O.n_arrays = T.n_arrays;
+    O.n_buckets = L.nb;
+    O.bucket_len = overlap_bucket_len(T.n_calls, L.nb);
+    p.nb = L.nb;
+    p.bl = O.bucket_len;
     O.cap = L.cap > 0 ? L.cap : 1;
     O.ov_off = ov_off;
     O.ov_idx = reinterpret_cast<uint32_t*>(w + L.ov_idx);

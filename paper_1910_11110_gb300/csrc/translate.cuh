@@ -35,16 +35,17 @@ struct TranslateLaunch {
 size_t translate_workspace_bytes(int32_t n_arrays, int64_t n_calls);
 size_t translate_lifetimes_workspace_bytes(int32_t n_arrays, int64_t n_calls, int64_t max_pairs);
 int launch_translate(const TranslateLaunch& T, cudaStream_t s);
-// The listed overlap pairs (both directions) whose lifetimes meet, into
-// *n_pairs (device): the max_pairs a lifetimes translation needs.
 // Initial statuses (2 n_arrays) of the second pass of a check of a trace with
 // creation records: (V,I) for vectors, for a pvector the statuses step gives
 // the Noop v, Noop v# of its record (its vector's at its creation).
 int launch_inherit(const int32_t* var, int64_t n_ops, int32_t n_arrays, const int32_t* arr_parent,
                    const int64_t* arr_probe, const uint8_t* step, uint8_t* init, int* err, cudaStream_t s);
-size_t overlap_count_workspace_bytes(int32_t n_arrays);
+// The overlap-list entries (both directions, one per time bucket two
+// lifetimes share) into *n_pairs (device): the max_pairs a lifetimes
+// translation of n_calls calls needs.
+size_t overlap_count_workspace_bytes(int32_t n_arrays, int64_t n_calls, bool lifetimes);
 int launch_overlap_count(const int32_t* arr_start, const int32_t* arr_len, const int32_t* arr_born,
-                         const int32_t* arr_died, int32_t n_arrays, int64_t* n_pairs, int* err, void* workspace,
-                         cudaStream_t s);
+                         const int32_t* arr_died, int32_t n_arrays, int64_t n_calls, int64_t* n_pairs, int* err,
+                         void* workspace, cudaStream_t s);
 
 }  // namespace amc

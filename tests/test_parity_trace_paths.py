@@ -49,8 +49,8 @@ PATHS = {  # candidate -> path it takes for each shape (by size / forced)
     "small_ragged": ["small"] * 4 + ["small", "scan"],
     "mid_64": ["scan"] * 4 + ["warp_dense", "scan"],
     "mid_4096": ["warp_dense"] * 4 + ["warp_dense", "scan"],
-    "wide_20000": ["scan"] * 4 + ["scan", "scan"],
-    "long_wide": ["scan"] * 4 + ["scan", "epochs"],
+    "wide_20000": ["scan"] * 4 + ["dense", "scan"],      # rows in global memory
+    "long_wide": ["scan"] * 4 + ["dense", "epochs"],
 }
 
 
@@ -81,3 +81,24 @@ def test_first_call_tunes_and_reports(amc, oracle_mod, monkeypatch):
     path, launches = amc.trace_plan(n, nv)
     assert path in amc.TRACE_PATHS and launches >= 1
     check(amc, oracle_mod, ks, var, nv, None)
+
+
+@pytest.mark.parametrize("cand", [0, 1])
+def test_guarded_check_candidates(amc, oracle_mod, monkeypatch, cand):
+    # amc_check_guarded_trace times two candidates: the plain choice and both
+    # passes on the reduce / carry / apply path, which over 20,000 variables
+    # keeps its per-chunk rows in global memory
+    monkeypatch.setenv("AMC_GUARDED_CANDIDATE", str(cand))
+    w = workloads.vectorpu_calls(seed=95, n_arrays=10_000, space=1 << 20, n_calls=60_000, len_log2=(4.0, 10.0))
+    exp = oracle_mod.vectorpu(**w)
+    n = exp["kind_side"].size
+    assert n >= 1 << 20
+    A = w["arr_start"].size
+    dev = torch.device("cuda")
+    out = amc.check_trace(torch.from_numpy(exp["kind_side"]).to(dev), torch.from_numpy(exp["var"]).to(dev), 2 * A,
+                          guarded=True)
+    assert amc.sync_status() == 0
+    assert np.array_equal(out["step_status"].cpu().numpy(), exp["step_status"])
+    assert np.array_equal(out["final_status"].cpu().numpy(), exp["final_status"])
+    assert np.array_equal(out["var_first_fault"].cpu().numpy(), exp["var_first_fault"])
+    assert int(out["first_fault"].cpu()[0]) == exp["first_fault"]

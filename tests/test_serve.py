@@ -166,3 +166,34 @@ def test_borrowed_buffers(amc, oracle_mod):
     step, final, vff, ff = oracle_mod.check_trace(ks, var, 500)
     for t in (t1, t2):
         assert res[t]["error"] == 0 and np.array_equal(res[t]["status"], step) and res[t]["first_fault"] == ff
+
+
+def test_completed_reports_each_ticket_once(amc, oracle_mod):
+    # amc_serve_completed: every finished ticket exactly once, results as the
+    # oracle's, many sessions in flight at once
+    rng = np.random.default_rng(9)
+    reqs = []
+    with amc.Server(mem_budget_bytes=1 << 30, max_slots=8) as srv:
+        for i in range(60):
+            n = int(rng.integers(1, 50_000))
+            ks, var = workloads.trace_random(rng, n, 300)
+            while (t := srv.submit(100 + i % 13, 0, 300, ks, var)) is None:
+                time.sleep(1e-4)
+            reqs.append((t, i % 13, ks, var))
+        seen, res = [], {}
+        deadline = time.time() + 60
+        while len(seen) < len(reqs) and time.time() < deadline:
+            for t in srv.completed(cap=7):
+                seen.append(t)
+                res[t] = srv.poll(t)
+            time.sleep(1e-4)
+        assert sorted(seen) == sorted(t for t, *_ in reqs)
+        assert srv.completed() == []
+    # per session, requests chain from the previous statuses
+    for sess in range(13):
+        mine = [r for r in reqs if r[1] == sess]
+        ks = np.concatenate([r[2] for r in mine])
+        var = np.concatenate([r[3] for r in mine])
+        step, *_ = oracle_mod.check_trace(ks, var, 300)
+        got = np.concatenate([res[r[0]]["status"] for r in mine])
+        assert np.array_equal(got, step)

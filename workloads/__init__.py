@@ -20,6 +20,8 @@ Workloads (seeds fixed by the benchmark definition):
   wd_calls        calls AM{S} for the static well-declaredness check    (seed 5)
   vectorpu_lifetimes  16 vectors of 2^20 elements, 65,536 pvectors created
                   and deleted during 2^24 calls (about 4,096 live at a time) (seed 6)
+  programs_guarded  20,000 programs over 16-256 vars whose conditions test a
+                  guard variable (isValid / remIsValid) or are opaque    (seed 7)
 """
 from __future__ import annotations
 
@@ -213,6 +215,35 @@ def programs(n_progs: int = 100_000, seed: int = 3, first: int = 0, **kw):
 # --------------------------------------------------------------------------
 # Calls AM{S} for the static well-declaredness check
 # --------------------------------------------------------------------------
+def programs_guarded(n_progs: int = 20_000, seed: int = 7, p_cond=(1 / 3, 1 / 3, 1 / 3), **kw):
+    """Structured programs (programs(), seed 7, 16-256 variables and a median
+    of 2,000 tokens unless given) with a guard variable g drawn uniformly per
+    program: each If's condition is drawn from opaque / isValid g /
+    remIsValid g with probabilities p_cond (bits 4-5 of the token); Whiles
+    keep opaque conditions (a While on g whose body leaves g alone would never
+    end); the ops on g become writes or Noops (kind w .7 / Noop .3, side
+    unchanged), so that g flips between its sides and is never stuck.
+    Returns the dict of programs() plus prog_guard (int32)."""
+    kw.setdefault("vars_lo", 16)
+    kw.setdefault("vars_hi", 256)
+    kw.setdefault("median", 2000.0)
+    b = programs(n_progs, seed=seed, **kw)
+    rng = np.random.default_rng(seed)
+    tok, pay, off = b["tok"], b["payload"], b["prog_tok_off"]
+    nv = b["prog_nvars"].astype(np.int64)
+    guard = np.floor(rng.random(nv.size) * nv).astype(np.int32)
+    k = tok & 15
+    ifs = np.nonzero(k == 8)[0]
+    c = rng.choice(3, size=ifs.size, p=np.asarray(p_cond, np.float64))
+    tok[ifs] = (tok[ifs] & 15) | (c.astype(np.uint8) << 4)
+    prog_of = np.repeat(np.arange(nv.size), np.diff(off))
+    on_g = np.nonzero((k <= 4) & (pay == guard[prog_of]))[0]
+    kind = np.where(rng.random(on_g.size) < 0.7, 1, 4).astype(np.uint8)
+    tok[on_g] = (tok[on_g] & 0x10) | kind
+    b["prog_guard"] = guard
+    return b
+
+
 def wd_calls(n_calls: int = 1 << 20, n_arrays: int = 4096, len_range=(1, 64), seed: int = 5,
              mode_p=(0.5, 0.3, 0.2), p_bad: float = 0.01):
     """Arrays of len_range locations (uniform); per call one side, 1..4
