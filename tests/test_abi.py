@@ -91,11 +91,13 @@ def test_epoch_shape_follows_its_override(libamc, monkeypatch):
     libamc.amc_check_trace_workspace.restype = ctypes.c_size_t
     libamc.amc_check_trace_workspace.argtypes = [ctypes.c_int64, ctypes.c_int32]
     ws = libamc.amc_check_trace_workspace
-    n, v = 3 << 20, 1 << 20
+    # (below 2^20 ops, where the global-row reduce / carry / apply scratch that
+    # a tuner candidate may take is not part of the query)
+    n, v = 3 << 18, 1 << 20
     monkeypatch.delenv("AMC_SCAN_TAIL", raising=False)
     plain, few = ws(n, v), ws(n, 16_384)     # below 2^29 ops: no epoch path
     monkeypatch.setenv("AMC_SCAN_TAIL", "16,-2")
-    assert ws(n, v) > plain                  # forced: pairs for 2^16 ops, slots for epochs to 3 * 2^20
+    assert ws(n, v) > plain                  # forced: pairs for 2^16 ops, slots for epochs to 3 * 2^18
     assert ws(n, 16_384) == few              # too few variables: the path is not taken
     monkeypatch.setenv("AMC_SCAN_TAIL", "0")
     assert ws(n, v) == plain                 # "0" switches the path off
