@@ -239,12 +239,63 @@ size_t request_bytes(const Request& r)
     // request has constructs
     size_t w = batch_workspace_bytes(r.n, 1, true, r.has_struct ? AMC_MAX_DEPTH : 0) + 256;
     if (r.kind == AMC_REQ_TRACE) {
-        // trace kernels: workspace, first faults, the session's statuses as codes
+        // trace kernels: workspace, first faults, the session's statuses as
+        // codes; for sessions of status sets also one pass's statuses, the
+        // final sets and the passes' first faults
         const size_t t = scan_workspace_bytes(r.n, r.n_vars) + align_up(4 * (size_t)r.n_vars, 256) +
-                         align_up((size_t)r.n_vars, 256);
+                         align_up((size_t)r.n_vars, 256) + align_up(n, 256) + align_up((size_t)r.n_vars, 256) + 256;
         if (t > w) w = t;
     }
     return b + w;
+}
+
+// A straight-line trace over status sets (Section 3.2's semantics on every
+// member of the entry set, as relation mode computes it): each op is a
+// function of the status, so the set after a prefix is the image of the entry
+// set, the union of the members' trajectories.  Pass k checks the trace from
+// the k-th member of every variable's set (its last member when the set has
+// fewer); the step sets, final sets and first fault are the union / minimum
+// over the five passes.  Sets are never empty (every op maps a status to a
+// status).
+constexpr int SET_PASSES = 5;
+
+__global__ void member_codes_kernel(const uint8_t* __restrict__ m, uint8_t* __restrict__ c, int32_t n, int k)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    uint32_t x = m[v] & 31u, pick = 0;
+    for (int j = 0; x; ++j, x &= x - 1) {
+        pick = (uint32_t)(__ffs(x) - 1);
+        if (j == k) break;
+    }
+    c[v] = (uint8_t)pick;
+}
+
+// out[i] |= 1 << step[i] (the first pass sets out[i]); the same for the
+// final sets; *ff = min over the passes
+__global__ void merge_pass_kernel(const uint8_t* __restrict__ step, uint8_t* __restrict__ out, int64_t n,
+                                  const uint8_t* __restrict__ fin, uint8_t* __restrict__ fset, int32_t nv,
+                                  const int64_t* __restrict__ ff_pass, int64_t* __restrict__ ff, int first)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint8_t b = (uint8_t)(1u << (step[i] & 7u));
+        out[i] = first ? b : (uint8_t)(out[i] | b);
+    }
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+        const uint8_t b = (uint8_t)(1u << (fin[v] & 7u));
+        fset[v] = first ? b : (uint8_t)(fset[v] | b);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t a = *ff_pass, cur = first ? -1 : *ff;
+        *ff = a < 0 ? cur : (cur < 0 || a < cur ? a : cur);
+    }
+}
+
+__global__ void copy_sets_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, int32_t n)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) dst[v] = src[v];
 }
 
 // singleton masks <-> status codes
@@ -303,10 +354,40 @@ int launch(amc_server* s, Slot& sl, Request& r, Session& ses)
         rc = launch_scan_trace(L, st);
         if (!rc) codes_to_masks_kernel<<<vb, 256, 0, st>>>(codes, table, r.n_vars);
         r.is_mask = 0;
+    } else if (r.kind == AMC_REQ_TRACE) {
+        // a trace over sets of several statuses: one trace check per member
+        uint8_t* after = d_ws + scan_workspace_bytes(r.n, r.n_vars);
+        int32_t* vff = reinterpret_cast<int32_t*>(after);
+        uint8_t* codes = after + align_up(4 * (size_t)r.n_vars, 256);
+        uint8_t* step_k = codes + align_up((size_t)r.n_vars, 256);
+        uint8_t* fset = step_k + align_up(n, 256);
+        int64_t* ff_k = reinterpret_cast<int64_t*>(fset + align_up((size_t)r.n_vars, 256));
+        const unsigned mb = (unsigned)((n > (size_t)r.n_vars ? n : (size_t)r.n_vars) + 255) / 256;
+        const unsigned mgrid = mb < 4096 ? (mb ? mb : 1) : 4096;
+        rc = AMC_OK;
+        for (int k = 0; k < SET_PASSES && !rc; ++k) {
+            member_codes_kernel<<<vb, 256, 0, st>>>(table, codes, r.n_vars, k);
+            ScanLaunch L;
+            L.kind_side = d_ks;
+            L.var = d_var;
+            L.n_ops = r.n;
+            L.n_vars = r.n_vars;
+            L.init = codes;
+            L.step = step_k;
+            L.final_status = codes;       // in place, as above
+            L.vff = vff;
+            L.first_fault = ff_k;
+            L.err = d_err;
+            L.workspace = d_ws;
+            rc = launch_scan_trace(L, st);
+            if (!rc)
+                merge_pass_kernel<<<mgrid, 256, 0, st>>>(step_k, d_out, (int64_t)n, codes, fset, r.n_vars, ff_k, d_ff,
+                                                         k == 0);
+        }
+        if (!rc) copy_sets_kernel<<<vb, 256, 0, st>>>(fset, table, r.n_vars);
+        r.is_mask = 1;
     } else {
-        // a program, or a trace over sets that may hold several statuses: a
-        // straight-line trace is a program without structure tokens
-        // one program: token offsets {0, n}, var offsets {0, n_vars}, n_vars
+        // a program: token offsets {0, n}, var offsets {0, n_vars}, n_vars
         int64_t* hs = reinterpret_cast<int64_t*>(h + H.small);
         hs[1] = 0;
         hs[2] = (int64_t)r.n;
