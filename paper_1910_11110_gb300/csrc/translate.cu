@@ -79,6 +79,14 @@ __device__ __forceinline__ int64_t list_hi(const TrParams& p, int32_t a, int64_t
     return p.ov_off[(int64_t)a * p.nb + (p.nb > 1 ? c / p.bl : 0) + 1];
 }
 
+// Where statement o goes: ks[o - base], var[o - base] (the output itself, or
+// a warp's staging buffer in shared memory)
+struct Out {
+    uint8_t* ks;
+    int32_t* var;
+    int64_t base;
+};
+
 __device__ __forceinline__ bool live_at(const TrParams& p, int32_t a, int64_t c)
 {
     return !p.born || (c >= p.born[a] && c < p.died[a]);
@@ -111,7 +119,7 @@ __device__ __forceinline__ bool iv_contains(int32_t so, int32_t lo, int32_t si, 
 // The creation records at the head of call c: Noop v, Noop v# (CPU side)
 // for every pvector created before it, ascending id.  Returns the count.
 template <bool EMIT>
-__device__ __forceinline__ int64_t put_births(const TrParams& p, int64_t c, int64_t o)
+__device__ __forceinline__ int64_t put_births(const TrParams& p, int64_t c, int64_t o, const Out& out)
 {
     int32_t lo, hi;
     births_of(p, c, &lo, &hi);
@@ -120,10 +128,10 @@ __device__ __forceinline__ int64_t put_births(const TrParams& p, int64_t c, int6
             const int32_t y = (int32_t)p.b_id[k];
             const int32_t v = p.parent[y];
             p.arr_probe[y] = o;
-            p.out_ks[o] = (uint8_t)AMC_K_NOOP;
-            p.out_var[o] = v;
-            p.out_ks[o + 1] = (uint8_t)AMC_K_NOOP;
-            p.out_var[o + 1] = p.n_arrays + v;
+            out.ks[o - out.base] = (uint8_t)AMC_K_NOOP;
+            out.var[o - out.base] = v;
+            out.ks[o + 1 - out.base] = (uint8_t)AMC_K_NOOP;
+            out.var[o + 1 - out.base] = p.n_arrays + v;
         }
         o += 2;
     }
@@ -137,7 +145,8 @@ __device__ __forceinline__ int64_t put_births(const TrParams& p, int64_t c, int6
 // found by comparing against all slots), so for small NMAX they stay in
 // registers.  The statements and their order are the same for every NMAX.
 template <bool EMIT, int NMAX>
-__device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_base, const int32_t k0, const int n,
+__device__ int64_t translate_call_n(const TrParams& p, const Out& out, int64_t c, int64_t out_base, const int32_t k0,
+                                    const int n,
                                     const uint32_t side)
 {
     const int32_t A = p.n_arrays;
@@ -202,12 +211,12 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
     const uint8_t sb = (uint8_t)(side << 4);
     auto put = [&](uint32_t kind, int32_t v) {
         if (EMIT) {
-            p.out_ks[o] = (uint8_t)(kind | sb);
-            p.out_var[o] = v;
+            out.ks[o - out.base] = (uint8_t)(kind | sb);
+            out.var[o - out.base] = v;
         }
         ++o;
     };
-    if (p.b_key) o += put_births<EMIT>(p, c, o);
+    if (p.b_key) o += put_births<EMIT>(p, c, o, out);
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
         if (i >= n) break;
@@ -265,7 +274,7 @@ __device__ int64_t translate_call_n(const TrParams& p, int64_t c, int64_t out_ba
 
 // Calls with more than 8 operands (rare): the same statements, arrays in local memory.
 template <bool EMIT>
-__device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c, int64_t out_base)
+__device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, const Out& out, int64_t c, int64_t out_base)
 {
     const uint32_t side = p.call_side[c];
     const int32_t k0 = p.call_off[c], k1 = p.call_off[c + 1];
@@ -319,12 +328,12 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
     const uint8_t sb = (uint8_t)(side << 4);
     auto put = [&](uint32_t kind, int32_t v) {
         if (EMIT) {
-            p.out_ks[o] = (uint8_t)(kind | sb);
-            p.out_var[o] = v;
+            out.ks[o - out.base] = (uint8_t)(kind | sb);
+            out.var[o - out.base] = v;
         }
         ++o;
     };
-    if (p.b_key) o += put_births<EMIT>(p, c, o);
+    if (p.b_key) o += put_births<EMIT>(p, c, o, out);
     for (int i = 0; i < n; ++i) {
         const int32_t x = arr[i];
         const int me = eff[i], mo = mode[i] & 3;
@@ -374,7 +383,7 @@ __device__ __noinline__ int64_t translate_call_dyn(const TrParams& p, int64_t c,
 }
 
 template <bool EMIT>
-__device__ int64_t translate_call(const TrParams& p, int64_t c, int64_t out_base)
+__device__ int64_t translate_call(const TrParams& p, const Out& out, int64_t c, int64_t out_base)
 {
     const uint32_t side = p.call_side[c];
     const int32_t k0 = p.call_off[c], k1 = p.call_off[c + 1];
@@ -383,25 +392,44 @@ __device__ int64_t translate_call(const TrParams& p, int64_t c, int64_t out_base
         return -1;
     }
     const int n = k1 - k0;
-    if (n <= 4) return translate_call_n<EMIT, 4>(p, c, out_base, k0, n, side);
-    if (n <= 8) return translate_call_n<EMIT, 8>(p, c, out_base, k0, n, side);
-    return translate_call_dyn<EMIT>(p, c, out_base);
+    if (n <= 4) return translate_call_n<EMIT, 4>(p, out, c, out_base, k0, n, side);
+    if (n <= 8) return translate_call_n<EMIT, 8>(p, out, c, out_base, k0, n, side);
+    return translate_call_dyn<EMIT>(p, out, c, out_base);
 }
 
 __global__ void count_kernel(const TrParams p)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.n_calls) return;
-    const int64_t k = translate_call<false>(p, c, 0);
+    const int64_t k = translate_call<false>(p, Out{nullptr, nullptr, 0}, c, 0);
     p.call_cnt[c] = k < 0 ? 0 : (int32_t)k;
 }
 
-__global__ void emit_kernel(const TrParams p)
+// Emission: a thread per call writes its statements in order; a warp whose 32
+// calls emit at most EMIT_STAGE statements writes them to shared memory first
+// and then copies them out with consecutive lanes on consecutive statements.
+constexpr int EMIT_STAGE = 1536;
+
+__global__ void __launch_bounds__(256) emit_kernel(const TrParams p)
 {
+    __shared__ uint8_t sks[8][EMIT_STAGE];
+    __shared__ int32_t svar[8][EMIT_STAGE];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= p.n_calls) return;
-    if (p.call_first_op[p.n_calls] > p.out_cap) return;     // nothing but out_n is written
-    translate_call<true>(p, c, p.call_first_op[c]);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c0 = c - lane;
+    if (c0 >= p.n_calls) return;                                // whole warp
+    if (p.call_first_op[p.n_calls] > p.out_cap) return;         // nothing but out_n is written
+    const int64_t lo = p.call_first_op[c0];
+    const int64_t hi = p.call_first_op[min(c0 + 32, p.n_calls)];
+    const bool staged = hi - lo <= EMIT_STAGE;
+    const Out out = staged ? Out{sks[w], svar[w], lo} : Out{p.out_ks, p.out_var, 0};
+    if (c < p.n_calls) translate_call<true>(p, out, c, p.call_first_op[c]);
+    if (!staged) return;
+    __syncwarp();
+    for (int64_t i = lane; i < hi - lo; i += 32) {
+        p.out_ks[lo + i] = sks[w][i];
+        p.out_var[lo + i] = svar[w][i];
+    }
 }
 
 __global__ void total_kernel(const TrParams p)
