@@ -405,31 +405,15 @@ __global__ void count_kernel(const TrParams p)
     p.call_cnt[c] = k < 0 ? 0 : (int32_t)k;
 }
 
-// Emission: a thread per call writes its statements in order; a warp whose 32
-// calls emit at most EMIT_STAGE statements writes them to shared memory first
-// and then copies them out with consecutive lanes on consecutive statements.
-constexpr int EMIT_STAGE = 1536;
-
-__global__ void __launch_bounds__(256) emit_kernel(const TrParams p)
+// Emission: a thread per call writes its statements in order.  (Staging a
+// warp's statements in shared memory to coalesce the stores cost more in
+// occupancy than it saved: 37.4 -> 42.0 ms per VectorPU step.)
+__global__ void emit_kernel(const TrParams p)
 {
-    __shared__ uint8_t sks[8][EMIT_STAGE];
-    __shared__ int32_t svar[8][EMIT_STAGE];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t c0 = c - lane;
-    if (c0 >= p.n_calls) return;                                // whole warp
-    if (p.call_first_op[p.n_calls] > p.out_cap) return;         // nothing but out_n is written
-    const int64_t lo = p.call_first_op[c0];
-    const int64_t hi = p.call_first_op[min(c0 + 32, p.n_calls)];
-    const bool staged = hi - lo <= EMIT_STAGE;
-    const Out out = staged ? Out{sks[w], svar[w], lo} : Out{p.out_ks, p.out_var, 0};
-    if (c < p.n_calls) translate_call<true>(p, out, c, p.call_first_op[c]);
-    if (!staged) return;
-    __syncwarp();
-    for (int64_t i = lane; i < hi - lo; i += 32) {
-        p.out_ks[lo + i] = sks[w][i];
-        p.out_var[lo + i] = svar[w][i];
-    }
+    if (c >= p.n_calls) return;
+    if (p.call_first_op[p.n_calls] > p.out_cap) return;     // nothing but out_n is written
+    translate_call<true>(p, Out{p.out_ks, p.out_var, 0}, c, p.call_first_op[c]);
 }
 
 __global__ void total_kernel(const TrParams p)
