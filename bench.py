@@ -51,6 +51,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+PLAIN_STREAMS = 32      # concurrent streams of the per-program launches
 METRIC = "checked ops/s + HBM GB/s vs peak, batched vs plain, bit-exact; serve p99 ms"
 UNIT = "checked ops/s"
 
@@ -784,29 +785,50 @@ def measure_programs(args, amc, dev):
         plain = None
         k = min(args.plain_progs, P)
         if k > 0:
-            # one launch per program (no graph) over the first k programs; the
-            # CSR arrays are offset to the program, token and mask buffers stay whole
-            sp = ctypes.c_void_p(stream.cuda_stream)
+            # one launch per program (no graph) over the first k programs, each
+            # program rebased to its own tokens (offsets [0, len]) with its own
+            # small workspace, launched round-robin on PLAIN_STREAMS streams so
+            # that up to that many programs run at once
+            sp = [torch.cuda.Stream() for _ in range(PLAIN_STREAMS)]
             V = lambda x: ctypes.c_void_p(x)
+            offs = b["prog_tok_off"]
+            lens = np.diff(offs[:k + 1]).astype(np.int64)
+            rel = np.zeros((k, 2), np.int64)
+            rel[:, 1] = lens
+            rel_d = t(rel.reshape(-1))
+            wsz = int(L.amc_check_batch_workspace(int(lens.max()), 1, int(b["prog_nvars"][:k].max())))
+            wss = []
+            for _ in range(PLAIN_STREAMS):
+                w1 = torch.empty(wsz + 256, dtype=torch.uint8, device=dev)
+                wss.append(w1[(-w1.data_ptr()) % 256:])
+            sm_p, fm_p, pf_p = out["step_mask"].data_ptr(), out["final_mask"].data_ptr(), \
+                out["prog_first_fault"].data_ptr()
 
             def plain_run():
+                for x in sp:
+                    x.wait_stream(stream)
                 for i in range(k):
-                    L.amc_check_batch(V(tok.data_ptr()), V(pay.data_ptr()), V(off.data_ptr() + 8 * i),
-                                      V(nv.data_ptr() + 4 * i), V(vo.data_ptr() + 8 * i), 1, n_tok,
-                                      V(out["step_mask"].data_ptr()), V(out["final_mask"].data_ptr()),
-                                      V(out["prog_first_fault"].data_ptr() + 8 * i), 0, V(ws.data_ptr()), ws.numel(),
-                                      sp)
+                    j = i % PLAIN_STREAMS
+                    a0 = int(offs[i])
+                    rc = L.amc_check_batch(V(tok.data_ptr() + a0), V(pay.data_ptr() + 4 * a0), V(rel_d.data_ptr() + 16 * i),
+                                           V(nv.data_ptr() + 4 * i), V(vo.data_ptr() + 8 * i), 1, int(lens[i]),
+                                           V(sm_p + a0), V(fm_p), V(pf_p + 8 * i), 0, V(wss[j].data_ptr()), wsz,
+                                           V(sp[j].cuda_stream))
+                    assert rc == 0, rc
+                for x in sp:
+                    stream.wait_stream(x)
 
             plain_run()
             assert amc.sync_status(stream) == 0
             ms_p = timed(plain_run, 1, stream)
             assert amc.sync_status(stream) == 0
-            tk = int(b["prog_tok_off"][k])
+            tk = int(offs[k])
             assert np.array_equal(out["step_mask"][:tk].cpu().numpy(), step_b[:tk])
             plain = {"programs": k, "tokens": tk, "ms": ms_p, "value": tk / (ms_p * 1e-3),
-                     "ms_per_program": ms_p / k,
-                     "mode": "one amc_check_batch launch per program (no graph), first programs of the batch, "
-                             "same stream"}
+                     "ms_per_program": ms_p / k, "streams": PLAIN_STREAMS,
+                     "mode": f"one amc_check_batch launch per program (no graph), the first {k} programs of the "
+                             f"batch, each rebased to its own tokens with its own workspace, round-robin on "
+                             f"{PLAIN_STREAMS} streams"}
     # oracle: programs sharded over the host threads, and one thread
     T = host_threads(args)
     to_np = b["prog_tok_off"]
@@ -1221,7 +1243,8 @@ def trace_kernels(n_ops, n_vars, has_init=False):
     / apply (5 kernels up to 8,192 variables, else 3); a reduce / carry / apply
     prefix, the stuck bitmap, the single-pass scan, final statuses and the
     first-fault merge (7); the epoch path (a sorted check of the first part --
-    pairs, three kernels per radix pass, segmented scan -- and the stuck
+    pairs, three kernels per radix pass, the segmented scan's reduce, carry
+    and apply -- and the stuck
     bitmap, then per epoch the stream filter, block sums, chunk offsets,
     gather, the candidates' sorted check, the gated fallback scan's set-up,
     scan and final statuses, and the gated merge with bitmap rebuild); or the

@@ -32,17 +32,13 @@ namespace amc {
 
 namespace {
 
-constexpr int ST = 4096;                 // pairs per tile
+constexpr int ST = 2048;                 // pairs per tile
 constexpr int SNT = 256;                 // threads per CTA
 constexpr int SE = ST / SNT;             // pairs per thread (blocked)
 constexpr int SDIG = 7;                  // digit bits
 constexpr int SRAD = 1 << SDIG;
-constexpr int CROWS = SRAD / 2;          // counter rows: digit d and d + 64 share a word (16-bit halves)
-constexpr int CWORDS = CROWS * SNT;      // logical counter words
-constexpr int CPHYS = CWORDS + CWORDS / 64;   // one pad word per 64: conflict-free row scans
 constexpr uint32_t NOKEY = 0xFFFFFFFFu;  // no variable id equals it
 
-__device__ __forceinline__ int cphys(int l) { return l + (l >> 6); }
 
 __device__ __forceinline__ int64_t set_count(const int64_t* n_dev, int64_t cap)
 {
@@ -136,88 +132,109 @@ __global__ void __launch_bounds__(1024) ss_hscan_kernel(uint32_t* __restrict__ h
     if (threadIdx.x == 0) dtot[blockIdx.x] = (uint32_t)total;
 }
 
-// (3) stable scatter of one pass.  Counters: thread t's count of digit d sits
-// in the 16-bit half (d >> 6) of logical word (d & 63) * 256 + t; an exclusive
-// scan of the words in logical order, plus the low halves' total added to the
-// high halves, gives every (digit, thread) its first rank in the tile.
-__global__ void __launch_bounds__(SNT, 3) ss_scatter_kernel(const uint32_t* __restrict__ kin,
+// (3) stable scatter of one pass, ranked warp by warp: warp w holds pairs
+// [256 w, 256 w + 256) of the tile, lane L pair 256 w + 32 r + L in round r
+// (loads coalesce).  In each round the lanes with equal digits find each
+// other (one ballot per digit bit); the lowest of them adds the group's size
+// to the warp's counter of that digit, and each lane's rank within the warp
+// is the counter's old value plus the group's lanes below it.  Ranks follow
+// (warp, round, lane), i.e. the pairs' order in the tile, so the pass is
+// stable.  Per digit an exclusive sum over the warps' counters and over the
+// digits' tile totals turns warp ranks into tile ranks; the tile is staged in
+// shared memory in digit order, so the stores of each digit's run coalesce.
+constexpr int SCT = 256;                       // scatter threads per CTA
+constexpr int SCW = SCT / 32;                  // its warps
+constexpr int SWR = ST / SCW / 32;             // rounds per warp (8)
+
+__global__ void __launch_bounds__(SCT, 5) ss_scatter_kernel(const uint32_t* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin,
                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                          const int64_t* n_dev, int64_t cap, int shift,
                                                          const uint32_t* __restrict__ hist,
                                                          const uint32_t* __restrict__ dtot, const int* gate)
 {
-    extern __shared__ __align__(16) uint32_t sm[];          // CPHYS counter words, then the staged tile
+    __shared__ __align__(16) uint32_t sk[ST];
+    __shared__ __align__(16) uint32_t sv[ST];
+    __shared__ uint32_t wcnt[SCW][SRAD];                    // per-warp digit counters, then their prefixes
     __shared__ uint32_t gbase[SRAD];
     __shared__ uint32_t dpre[SRAD];                         // pairs of all tiles with a smaller digit
-    __shared__ int tmp[SNT / 32 + 1];
+    __shared__ uint32_t dstart[SRAD];                       // first rank of each digit in the tile
+    __shared__ int tmp[SCT / 32 + 1];
     if (gated(gate)) return;
     const int64_t n = set_count(n_dev, cap);
     const int64_t nt = (n + ST - 1) / ST;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t lt = lanemask_lt();
     {
         const int x = t < SRAD ? (int)dtot[t] : 0;
-        const int e = block_excl_sum<SNT>(x, tmp, nullptr);
+        const int e = block_excl_sum<SCT>(x, tmp, nullptr);
         if (t < SRAD) dpre[t] = (uint32_t)e;
     }
     for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         const int64_t b = tile * ST;
         const int m = (int)(n - b < ST ? n - b : ST);
-        uint32_t k[SE], v[SE], r[SE];           // r: rank among the thread's own digit, then in the tile
-        load_blocked(kin, b, m, k, NOKEY);
-        load_blocked(vin, b, m, v, 0u);
-        for (int i = t; i < CPHYS / 4; i += SNT) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+        // the tile's first pair of each digit among all tiles: its row entry (loaded early)
+        const uint32_t hrow = t < SRAD ? hist[(int64_t)t * nt + tile] : 0u;
+        uint32_t k[SWR], r[SWR];
+        const int w0 = warp * (ST / SCW);
+#pragma unroll
+        for (int u = 0; u < SWR; ++u) {
+            const int i = w0 + 32 * u + lane;
+            const bool ok = i < m;
+            k[u] = ok ? kin[b + i] : NOKEY;
+            sv[i] = ok ? vin[b + i] : 0u;                   // values wait in shared memory
+        }
+        for (int i = t; i < SCW * SRAD; i += SCT) (&wcnt[0][0])[i] = 0;
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < SE; ++u) {
-            if (k[u] == NOKEY) continue;
+        for (int u = 0; u < SWR; ++u) {
+            const bool ok = k[u] != NOKEY;
             const uint32_t d = (k[u] >> shift) & (SRAD - 1);
-            const int p = cphys((int)(d & (CROWS - 1)) * SNT + t);
-            const uint32_t sh = (d >> 6) * 16;
-            r[u] = (sm[p] >> sh) & 0xFFFFu;
-            sm[p] += 1u << sh;
-        }
-        __syncthreads();
-        // thread t scans logical words [64 t, 64 t + 64): physical 65 t + i
-        uint32_t s = 0;
-#pragma unroll 8
-        for (int i = 0; i < 64; ++i) s += sm[65 * t + i];
-        int total = 0;
-        uint32_t run = (uint32_t)block_excl_sum<SNT>((int)s, tmp, &total);
-#pragma unroll 8
-        for (int i = 0; i < 64; ++i) {
-            const uint32_t x = sm[65 * t + i];
-            sm[65 * t + i] = run;
-            run += x;
-        }
-        const uint32_t low_total = (uint32_t)total & 0xFFFFu;       // pairs with digits 0..63
-        __syncthreads();
+            const uint32_t valid = __ballot_sync(0xffffffffu, ok);
+            uint32_t peers = ok ? valid : ~valid;
 #pragma unroll
-        for (int u = 0; u < SE; ++u) {
-            if (k[u] == NOKEY) continue;
-            const uint32_t d = (k[u] >> shift) & (SRAD - 1);
-            const int p = cphys((int)(d & (CROWS - 1)) * SNT + t);
-            const uint32_t sh = (d >> 6) * 16;
-            r[u] += ((sm[p] >> sh) & 0xFFFFu) + (sh ? low_total : 0u);
+            for (int bit = 0; bit < SDIG; ++bit) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+                peers &= ((d >> bit) & 1u) ? bal : ~bal;
+            }
+            const int lead = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (ok && lane == lead) {
+                old = wcnt[warp][d];
+                wcnt[warp][d] = old + (uint32_t)__popc(peers);
+            }
+            old = __shfl_sync(0xffffffffu, old, lead);
+            r[u] = old + (uint32_t)__popc(peers & lt);
         }
+        __syncthreads();
+        uint32_t cnt = 0;
         if (t < SRAD) {
-            const uint32_t d = (uint32_t)t;
-            const int p = cphys((int)(d & (CROWS - 1)) * SNT);
-            const uint32_t sh = (d >> 6) * 16;
-            const uint32_t dstart = ((sm[p] >> sh) & 0xFFFFu) + (sh ? low_total : 0u);
-            gbase[t] = dpre[t] + hist[(int64_t)t * nt + tile] - dstart;
-        }
-        __syncthreads();
-        uint32_t* sk = sm;
-        uint32_t* sv = sm + ST;
 #pragma unroll
-        for (int u = 0; u < SE; ++u) {
+            for (int w = 0; w < SCW; ++w) {
+                const uint32_t x = wcnt[w][t];
+                wcnt[w][t] = cnt;
+                cnt += x;
+            }
+        }
+        const uint32_t ds = (uint32_t)block_excl_sum<SCT>((int)cnt, tmp, nullptr);
+        if (t < SRAD) {
+            dstart[t] = ds;
+            gbase[t] = dpre[t] + hrow - ds;
+        }
+        uint32_t v[SWR];
+#pragma unroll
+        for (int u = 0; u < SWR; ++u) v[u] = sv[w0 + 32 * u + lane];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < SWR; ++u) {
             if (k[u] == NOKEY) continue;
-            sk[r[u]] = k[u];
-            sv[r[u]] = v[u];
+            const uint32_t d = (k[u] >> shift) & (SRAD - 1);
+            const uint32_t rr = r[u] + wcnt[warp][d] + dstart[d];
+            sk[rr] = k[u];
+            sv[rr] = v[u];
         }
         __syncthreads();
-        for (int i = t; i < m; i += SNT) {
+        for (int i = t; i < m; i += SCT) {
             const uint32_t kk = sk[i];
             const uint32_t o = gbase[(kk >> shift) & (SRAD - 1)] + (uint32_t)i;
             kout[o] = kk;
@@ -286,12 +303,13 @@ struct SegParams {
     int32_t* vff;
     int64_t* ff;
     int64_t offset;
-    uint32_t* tstat;            // [n_tiles] published scan value of each tile (zeroed before)
-    uint32_t* tile_counter;     // tiles claimed so far (zeroed before)
+    uint32_t* tstat;            // [n_tiles] each tile's scan value, then the value before it
     int* err;
     uint32_t* bm;               // nullable: stuck bitmap, bits set for variables that end F
     Tables tab;
 };
+
+constexpr uint32_t TS_VAL = 0x1FFu;      // a scan value: element (bits 0-4), "a run starts inside" (bit 8)
 
 // Per thread: its 16 sorted pairs, run starts and the fold of its pairs.
 struct ThreadRun {
@@ -324,68 +342,113 @@ __device__ __forceinline__ void thread_run(const SegParams& p, const SegTables& 
     R.agg = a;
 }
 
-// (4) every pair's prefix, applied to its variable's entry status, in one
-// pass: CTAs claim tiles in order; a tile publishes its aggregate (the fold of
-// its trailing run, and whether a run starts inside), then looks back over the
-// earlier tiles' published values until one that covers everything before it
-// (an inclusive value, or an aggregate in which a run starts), publishes its
-// inclusive value and carries the exclusive one into its leading run.  A
-// claimed tile belongs to a running CTA that publishes its aggregate before it
-// waits on anything, so every look-back ends; the wait is bounded all the same
-// (AMC_E_TIMEOUT).
-constexpr uint32_t TS_AGG = 1u << 30, TS_INCL = 2u << 30, TS_FLAGS = 3u << 30, TS_VAL = 0x1FFu;
-
-__global__ void __launch_bounds__(SNT) ss_seg_kernel(const SegParams p)
+// (4) every pair's prefix, applied to its variable's entry status, as
+// reduce / carry / apply over the sorted tiles (no CTA waits on another):
+//   (a) each tile's value: the fold of its trailing run, bit 8 set when a run
+//       starts inside (what a later tile needs from it);
+//   (b) one CTA folds the tile values into exclusive prefixes in place (the
+//       value of everything before the tile: the fold of the run that the
+//       tile's first pair may continue);
+//   (c) each tile carries that prefix into its leading run (when the run
+//       continues across the boundary) and composes every pair's prefix;
+//       each pair's entry status and output position are loaded before the
+//       tile's scan so that their latency overlaps it.
+__global__ void __launch_bounds__(SNT, 6) ss_red_kernel(const SegParams p)
 {
     __shared__ SegTables S;
     __shared__ uint32_t wtot[SNT / 32];
-    __shared__ uint32_t s_tile, s_carry;
     if (gated(p.gate)) return;
     load_seg_tables(S, p.tab);
     __syncthreads();
     const int64_t n = set_count(p.n_dev, p.cap);
     const int64_t nt = (n + ST - 1) / ST;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(p.tile_counter, 1u);
-        __syncthreads();
-        const int64_t tile = s_tile;
-        if (tile >= nt) break;
+    for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         const int64_t b = tile * ST;
         const int m = (int)(n - b < ST ? n - b : ST);
         ThreadRun R;
         thread_run(p, S, n, b, m, R);
         uint32_t all;
-        const uint32_t ex = seg_block_excl(R.agg, S.id, S.comp, wtot, &all);
-        if (threadIdx.x == 0) {
-            uint32_t carry = S.id;
-            if (tile == 0) {
-                st_release(p.tstat, TS_INCL | (all & TS_VAL));
-            } else {
-                st_release(p.tstat + tile, TS_AGG | (all & TS_VAL));
-                uint32_t prefix = S.id;                   // over tiles [t2, tile), earlier ones folded in front
-                for (int64_t t2 = tile - 1; t2 >= 0; --t2) {
-                    uint32_t v = 0;
-                    for (uint32_t it = 0; it < (1u << 24); ++it) {
-                        v = ld_acquire(p.tstat + t2);
-                        if (v & TS_FLAGS) break;
-                    }
-                    if (!(v & TS_FLAGS)) {
-                        if (p.err) raise_error(p.err, AMC_E_TIMEOUT);
-                        break;
-                    }
-                    prefix = seg_combine(v & TS_VAL, prefix, S.comp);
-                    if ((v & TS_INCL) || (v & 0x100u)) break;
-                }
-                st_release(p.tstat + tile, TS_INCL | (seg_combine(prefix, all, S.comp) & TS_VAL));
-                if (p.key[b - 1] == p.key[b]) carry = prefix & 31u;
-            }
-            s_carry = carry;
+        seg_block_excl(R.agg, S.id, S.comp, wtot, &all);
+        if (threadIdx.x == 0) p.tstat[tile] = all & TS_VAL;
+    }
+}
+
+constexpr int CNT = 1024;                  // threads of the carry CTA
+
+__global__ void __launch_bounds__(CNT) ss_carry_kernel(const SegParams p)
+{
+    __shared__ uint8_t comp[MAX_ELEMS * MAX_ELEMS];
+    __shared__ uint32_t wtot[CNT / 32];
+    __shared__ uint8_t s_id;
+    if (gated(p.gate)) return;
+    for (int i = threadIdx.x; i < MAX_ELEMS * MAX_ELEMS; i += CNT) comp[i] = p.tab.comp[i];
+    if (threadIdx.x == 0) s_id = p.tab.identity;
+    __syncthreads();
+    const uint32_t id = s_id;
+    const int64_t n = set_count(p.n_dev, p.cap);
+    const int64_t nt = (n + ST - 1) / ST;
+    const int64_t per = (nt + CNT - 1) / CNT;
+    const int64_t lo = threadIdx.x * per, hi = lo + per < nt ? lo + per : nt;
+    uint32_t a = id;
+    for (int64_t i = lo; i < hi; ++i) a = seg_combine(a, p.tstat[i], comp);
+    // exclusive segmented scan of the threads' folds
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = a;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl = seg_combine(y, incl, comp);
+    }
+    uint32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) ex = id;
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    uint32_t pre = id;
+    for (int w = 0; w < warp; ++w) pre = seg_combine(pre, wtot[w], comp);
+    uint32_t run = seg_combine(pre, ex, comp);
+    for (int64_t i = lo; i < hi; ++i) {
+        const uint32_t x = p.tstat[i];
+        p.tstat[i] = run;
+        run = seg_combine(run, x, comp);
+    }
+}
+
+__global__ void __launch_bounds__(SNT, 4) ss_apply_kernel(const SegParams p)
+{
+    __shared__ SegTables S;
+    __shared__ uint32_t wtot[SNT / 32];
+    if (gated(p.gate)) return;
+    load_seg_tables(S, p.tab);
+    __syncthreads();
+    const int64_t n = set_count(p.n_dev, p.cap);
+    const int64_t nt = (n + ST - 1) / ST;
+    const uint8_t* __restrict__ init = p.init;
+    const uint32_t* __restrict__ posm = p.pos;
+    for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const int64_t b = tile * ST;
+        const int m = (int)(n - b < ST ? n - b : ST);
+        const uint32_t before_tile = p.tstat[tile];
+        const bool cont = tile > 0 && p.key[b - 1] == p.key[b];
+        ThreadRun R;
+        thread_run(p, S, n, b, m, R);
+        // entry statuses (3 bits each, packed) and positions of the thread's pairs
+        uint32_t s0lo = 0, s0hi = 0;
+        uint32_t posv[SE];
+#pragma unroll
+        for (int u = 0; u < SE; ++u) {
+            const bool ok = R.k[u] != NOKEY;
+            const uint32_t s0 = (init && ok) ? (init[R.k[u]] & 7u) : (uint32_t)AMC_ST_VI;
+            if (u < 8) s0lo |= s0 << (3 * u);
+            else s0hi |= s0 << (3 * (u - 8));
+            const uint32_t j = R.v[u] >> 4;
+            posv[u] = (posm && ok) ? posm[j] : j;
         }
-        __syncthreads();
-        const uint32_t c = s_carry;
+        const uint32_t ex = seg_block_excl(R.agg, S.id, S.comp, wtot, nullptr);
+        const uint32_t c = cont ? (before_tile & 31u) : S.id;
         uint32_t run = (ex & 0x100u) ? (ex & 31u) : S.comp[c * MAX_ELEMS + (ex & 31u)];
         const int64_t i0 = b + threadIdx.x * SE;
         const uint32_t after = (i0 + SE < n) ? p.key[i0 + SE] : NOKEY;
+        unsigned long long gmin = ~0ull;
 #pragma unroll
         for (int u = 0; u < SE; ++u) {
             const uint32_t kv = R.k[u];
@@ -393,19 +456,17 @@ __global__ void __launch_bounds__(SNT) ss_seg_kernel(const SegParams p)
             const uint32_t e = S.elem[R.v[u] & 15u];
             const uint32_t before = (R.heads >> u) & 1u ? S.id : run;
             run = (R.heads >> u) & 1u ? e : S.comp[run * MAX_ELEMS + e];
-            const uint32_t s0 = p.init ? (p.init[kv] & 7u) : (uint32_t)AMC_ST_VI;
+            const uint32_t s0 = ((u < 8 ? s0lo : s0hi) >> (3 * (u & 7))) & 7u;
             const uint32_t pre = S.app[before * 8 + s0];
             const uint32_t post = S.app[run * 8 + s0];
-            const uint32_t j = R.v[u] >> 4;
             if (post != ST_F || pre != ST_F) {
-                const int64_t pos = p.pos ? (int64_t)p.pos[j] : (int64_t)j;
+                const int64_t pos = (int64_t)posv[u];
                 if (post != ST_F) {
                     p.step[pos] = (uint8_t)post;
                 } else {
                     const int64_t g = p.offset + pos;
                     p.vff[kv] = (int32_t)g;
-                    if ((unsigned long long)g < *reinterpret_cast<volatile unsigned long long*>(p.ff))
-                        atomicMin(reinterpret_cast<unsigned long long*>(p.ff), (unsigned long long)g);
+                    if ((unsigned long long)g < gmin) gmin = (unsigned long long)g;
                 }
             }
             const uint32_t next = u + 1 < SE ? R.k[u + 1] : after;
@@ -414,6 +475,221 @@ __global__ void __launch_bounds__(SNT) ss_seg_kernel(const SegParams p)
                 if (p.bm && post == ST_F) atomicOr(p.bm + (kv >> 5), 1u << (kv & 31));
             }
         }
+        // the warp's smallest first fault, one atomic per warp
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, gmin, d);
+            if (o < gmin) gmin = o;
+        }
+        if ((threadIdx.x & 31) == 0 && gmin != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(p.ff), gmin);
+        __syncthreads();
+    }
+}
+
+// (5) A set over many variables whose ops spread evenly over the variable
+// ids (an epoch's candidates), checked per bucket of ids: one stable radix
+// pass on the top seven bits of the id groups the pairs into 128 buckets of
+// 2^shift consecutive ids, each still in position order; then one CTA per
+// bucket does the whole check of its bucket, as a reduce / carry / apply
+// over its warps' stretches (no CTA waits on another):
+//   (a) warp w folds its stretch of the bucket, 32 pairs at a time (lanes with
+//       the same variable grouped by match.any, the group's first lane
+//       composing them in order), into one function per variable of the
+//       bucket (a row of 2^shift bytes in shared memory);
+//   (b) a thread per variable carries the entry status through the warps'
+//       functions: every stretch's entry statuses, the final status and the
+//       stuck bitmap's word;
+//   (c) each warp re-runs its stretch from those entry statuses, writing the
+//       statuses that are not F (the caller wrote F everywhere) and the first
+//       faults.
+constexpr int BKW = 16;                   // warps of a bucket CTA
+constexpr int BK_MAX_SHIFT = 13;          // buckets of at most 8,192 ids: 128 KB of rows
+constexpr int BKU = 16;                   // batches of 32 pairs loaded at once
+
+struct BucketParams {
+    const uint32_t* key;        // grouped by bucket, position order inside
+    const uint32_t* val;
+    const int64_t* n_dev;
+    int64_t cap;
+    const int* gate;
+    const uint32_t* dtot;       // pairs per bucket
+    int shift;                  // bucket b: ids [b << shift, (b + 1) << shift)
+    int32_t n_vars;
+    const uint32_t* pos;        // set index -> position in the epoch
+    const uint8_t* init;        // nullable: all (V,I)
+    uint8_t* step;
+    uint8_t* fin;
+    int32_t* vff;
+    int64_t* ff;
+    int64_t offset;
+    uint32_t* bm;               // nullable: stuck bitmap (whole words written per bucket)
+    Tables tab;
+};
+
+// Duplicate test of a batch without match.any (slow on this part): each lane
+// sets its variable's bit in the warp's bitmap; a bit already set means that
+// an earlier lane of the batch has the same variable.  The bits are cleared
+// after the batch.
+__device__ __forceinline__ bool seen_before(uint32_t* seen, uint32_t lv)
+{
+    const uint32_t bit = 1u << (lv & 31);
+    return (atomicOr(seen + (lv >> 5), bit) & bit) != 0;
+}
+__device__ __forceinline__ void forget(uint32_t* seen, uint32_t lv) { atomicAnd(seen + (lv >> 5), ~(1u << (lv & 31))); }
+
+__global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketParams p)
+{
+    extern __shared__ __align__(16) uint8_t rows[];        // [BKW][1 << shift], then seen bits [BKW][1 << shift >> 5]
+    __shared__ uint8_t comp[MAX_ELEMS * MAX_ELEMS];
+    __shared__ uint8_t app[MAX_ELEMS * 8];
+    __shared__ uint8_t elem[16];
+    __shared__ uint8_t mb[BKW][32];
+    __shared__ uint32_t bstart[SRAD];
+    __shared__ int tmp[BKW + 1];
+    if (gated(p.gate)) return;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    for (int i = tid; i < MAX_ELEMS * MAX_ELEMS; i += BKW * 32) comp[i] = p.tab.comp[i];
+    for (int i = tid; i < MAX_ELEMS * 8; i += BKW * 32) app[i] = p.tab.app[i];
+    if (tid < 16) {
+        const uint32_t m = p.tab.elem_of[byte_of(tid)];
+        elem[tid] = (uint8_t)(m < MAX_ELEMS ? m : p.tab.identity);
+    }
+    {
+        const int x = tid < SRAD ? (int)p.dtot[tid] : 0;
+        const int e = block_excl_sum<BKW * 32>(x, tmp, nullptr);
+        if (tid < SRAD) bstart[tid] = (uint32_t)e;
+    }
+    const uint32_t ID = p.tab.identity;
+    const int W = 1 << p.shift;
+    const int64_t n = set_count(p.n_dev, p.cap);
+    uint32_t* const seen_all = reinterpret_cast<uint32_t*>(rows + (size_t)BKW * W);
+    uint32_t* const seen = seen_all + w * (W >> 5);       // this warp's bits
+    for (int i = tid; i < BKW * (W >> 5); i += BKW * 32) seen_all[i] = 0;
+    __syncthreads();
+    for (int b = blockIdx.x; b < SRAD; b += gridDim.x) {
+        const int64_t v0 = (int64_t)b << p.shift;
+        if (v0 >= p.n_vars) break;
+        const int nv = (int)min((int64_t)W, (int64_t)p.n_vars - v0);
+        const int64_t lo_b = bstart[b];
+        const int64_t hi_b = min(n, lo_b + (int64_t)p.dtot[b]);
+        const int64_t per = (hi_b - lo_b + BKW - 1) / BKW;
+        const int64_t lo = min(hi_b, lo_b + w * per), hi = min(hi_b, lo + per);
+        uint8_t* row = rows + (size_t)w * W;
+        for (int v = lane; v < nv; v += 32) row[v] = (uint8_t)ID;
+        __syncwarp();
+        // (a) fold the stretch per variable; BKU batches of 32 pairs are
+        // loaded at once (their loads overlap), then folded one by one
+        for (int64_t g0 = lo; g0 < hi; g0 += 32 * BKU) {
+            uint32_t kk[BKU], vv[BKU];
+#pragma unroll
+            for (int u = 0; u < BKU; ++u) {
+                const int64_t i = g0 + 32 * u + lane;
+                kk[u] = i < hi ? p.key[i] - (uint32_t)v0 : 0xFFFFFFFFu;
+                vv[u] = i < hi ? p.val[i] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < BKU; ++u) {
+                if (g0 + 32 * u >= hi) break;
+                const uint32_t lv = kk[u];
+                const bool ok = lv != 0xFFFFFFFFu;
+                const uint32_t m = ok ? elem[vv[u] & 15u] : ID;
+                if (!__ballot_sync(0xffffffffu, ok && seen_before(seen, lv))) {
+                    // every variable once in the batch: each lane composes alone
+                    if (ok) row[lv] = comp[row[lv] * MAX_ELEMS + m];
+                } else {
+                    mb[w][lane] = (uint8_t)m;
+                    const uint32_t peers = __match_any_sync(0xffffffffu, lv);
+                    __syncwarp();
+                    if (ok && lane == __ffs(peers) - 1) {
+                        uint32_t acc = row[lv];
+                        for (uint32_t r = peers; r; r &= r - 1) acc = comp[acc * MAX_ELEMS + mb[w][__ffs(r) - 1]];
+                        row[lv] = (uint8_t)acc;
+                    }
+                }
+                if (ok) forget(seen, lv);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // (b) carry: entry statuses of every stretch, final statuses, bitmap words
+        for (int v = tid; v < ((nv + 31) & ~31); v += BKW * 32) {
+            bool stuck = false;
+            if (v < nv) {
+                uint32_t st = p.init ? (uint32_t)(p.init[v0 + v] & 7u) : (uint32_t)AMC_ST_VI;
+                for (int k = 0; k < BKW; ++k) {
+                    uint8_t* r = rows + (size_t)k * W + v;
+                    const uint32_t e = *r;
+                    *r = (uint8_t)st;
+                    st = app[e * 8 + st];
+                }
+                p.fin[v0 + v] = (uint8_t)st;
+                stuck = st == ST_F;
+            }
+            const uint32_t word = __ballot_sync(0xffffffffu, stuck);
+            if (p.bm && lane == 0) p.bm[(v0 + v) >> 5] = word;
+        }
+        __syncthreads();
+        // (c) every pair's status from its stretch's entry statuses
+        unsigned long long gmin = ~0ull;
+        for (int64_t g0 = lo; g0 < hi; g0 += 32 * BKU) {
+            uint32_t kk[BKU], vv[BKU], pp[BKU];
+#pragma unroll
+            for (int u = 0; u < BKU; ++u) {
+                const int64_t i = g0 + 32 * u + lane;
+                kk[u] = i < hi ? p.key[i] - (uint32_t)v0 : 0xFFFFFFFFu;
+                vv[u] = i < hi ? p.val[i] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < BKU; ++u) pp[u] = kk[u] != 0xFFFFFFFFu ? p.pos[vv[u] >> 4] : 0u;
+#pragma unroll
+            for (int u = 0; u < BKU; ++u) {
+                if (g0 + 32 * u >= hi) break;
+                const uint32_t lv = kk[u];
+                const bool ok = lv != 0xFFFFFFFFu;
+                const uint32_t m = ok ? elem[vv[u] & 15u] : ID;
+                const uint32_t posi = pp[u];
+                // pre / post: the variable's status before / after the pair
+                uint32_t pre = 0, post = 0;
+                if (!__ballot_sync(0xffffffffu, ok && seen_before(seen, lv))) {
+                    if (ok) {
+                        pre = row[lv];
+                        post = app[m * 8 + pre];
+                        row[lv] = (uint8_t)post;
+                    }
+                } else {
+                    mb[w][lane] = (uint8_t)m;
+                    const uint32_t peers = __match_any_sync(0xffffffffu, lv);
+                    __syncwarp();
+                    const uint32_t cur = ok ? row[lv] : 0u;
+                    __syncwarp();
+                    if (ok) {
+                        uint32_t acc = ID;
+                        for (uint32_t r = peers & lt; r; r &= r - 1) acc = comp[acc * MAX_ELEMS + mb[w][__ffs(r) - 1]];
+                        pre = app[acc * 8 + cur];
+                        post = app[comp[acc * MAX_ELEMS + m] * 8 + cur];
+                        if (lane == 31 - __clz(peers)) row[lv] = (uint8_t)post;
+                    }
+                }
+                if (ok) {
+                    forget(seen, lv);
+                    if (post != ST_F) {
+                        p.step[posi] = (uint8_t)post;
+                    } else if (pre != ST_F) {
+                        const int64_t g = p.offset + (int64_t)posi;
+                        p.vff[v0 + lv] = (int32_t)g;
+                        if ((unsigned long long)g < gmin) gmin = (unsigned long long)g;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, gmin, d);
+            if (o < gmin) gmin = o;
+        }
+        if (lane == 0 && gmin != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(p.ff), gmin);
         __syncthreads();
     }
 }
@@ -489,17 +765,6 @@ int ss_radix_passes(int32_t n_vars) { return (key_bits_of(n_vars) + SDIG - 1) / 
 int launch_ss_radix(uint32_t* const key[2], uint32_t* const val[2], const int64_t* n_dev, int64_t cap,
                     int32_t n_vars, void* scratch, const int* gate, cudaStream_t s, int* passes_out)
 {
-    static bool attr_done[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const size_t smem = (size_t)CPHYS * 4;
-    static_assert(CPHYS >= 2 * ST, "the staged tile reuses the counter words");
-    if (dev >= 64 || !attr_done[dev]) {
-        if (cudaFuncSetAttribute(ss_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return AMC_E_CUDA;
-        if (dev < 64) attr_done[dev] = true;
-    }
     const int n_sm = sm_count();
     const int64_t tiles = (cap + ST - 1) / ST;
     auto grid = [&](int per_sm) { return (int)(tiles < (int64_t)n_sm * per_sm ? tiles : (int64_t)n_sm * per_sm); };
@@ -514,7 +779,7 @@ int launch_ss_radix(uint32_t* const key[2], uint32_t* const val[2], const int64_
         const int shift = ps * SDIG;
         ss_hist_kernel<<<grid(8), SNT, 0, s>>>(key[src], n_dev, cap, shift, hist, gate);
         ss_hscan_kernel<<<SRAD, 1024, 0, s>>>(hist, dtot, n_dev, cap, gate);
-        ss_scatter_kernel<<<grid(3), SNT, smem, s>>>(key[src], val[src], key[src ^ 1], val[src ^ 1], n_dev, cap, shift,
+        ss_scatter_kernel<<<grid(5), SCT, 0, s>>>(key[src], val[src], key[src ^ 1], val[src ^ 1], n_dev, cap, shift,
                                                      hist, dtot, gate);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
     }
@@ -529,14 +794,9 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     const int n_sm = sm_count();
     const int64_t tiles = (C.cap + ST - 1) / ST;
     auto grid = [&](int per_sm) { return (int)(tiles < (int64_t)n_sm * per_sm ? tiles : (int64_t)n_sm * per_sm); };
-    uint8_t* w = static_cast<uint8_t*>(C.scratch);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(w);
-    w += align_up(4 * SRAD * (size_t)tiles, 256);
-    uint32_t* dtot = reinterpret_cast<uint32_t*>(w);
-    w += align_up(4 * SRAD, 256);
+    // scratch: the sort's digit rows and totals, then the tile values
+    uint8_t* w = static_cast<uint8_t*>(C.scratch) + align_up(4 * SRAD * (size_t)tiles, 256) + align_up(4 * SRAD, 256);
     uint32_t* tstat = reinterpret_cast<uint32_t*>(w);
-    w += align_up(4 * (size_t)tiles, 256);
-    uint32_t* tile_counter = reinterpret_cast<uint32_t*>(w);
 
     int passes = 0;
     const int rc = launch_ss_radix(C.key, C.val, C.n_dev, C.cap, C.n_vars, C.scratch, C.gate, s, &passes);
@@ -555,13 +815,68 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     p.ff = C.ff;
     p.offset = C.offset;
     p.tstat = tstat;
-    p.tile_counter = tile_counter;
     p.err = C.err;
     p.bm = C.bm;
     p.tab = host_tables();
-    if (cudaMemsetAsync(tstat, 0, 4 * (size_t)tiles, s) != cudaSuccess) return AMC_E_CUDA;
-    if (cudaMemsetAsync(tile_counter, 0, 4, s) != cudaSuccess) return AMC_E_CUDA;
-    ss_seg_kernel<<<grid(8), SNT, 0, s>>>(p);
+    ss_red_kernel<<<grid(6), SNT, 0, s>>>(p);
+    ss_carry_kernel<<<1, CNT, 0, s>>>(p);
+    ss_apply_kernel<<<grid(4), SNT, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
+}
+
+int bucket_check_shift(int32_t n_vars)
+{
+    const int kb = key_bits_of(n_vars);
+    return kb > SDIG ? kb - SDIG : 0;
+}
+
+bool bucket_check_ok(int32_t n_vars) { return bucket_check_shift(n_vars) <= BK_MAX_SHIFT; }
+
+int launch_bucket_check(const SortedCheck& C, cudaStream_t s)
+{
+    if (C.cap <= 0) return AMC_OK;
+    if (C.cap > ((int64_t)1 << 28) || !C.pos || !bucket_check_ok(C.n_vars)) return AMC_E_INVALID;
+    const int shift = bucket_check_shift(C.n_vars);
+    const size_t smem = ((size_t)BKW << shift) + ((size_t)BKW << shift >> 3);
+    static size_t attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || attr_set[dev] < smem) {
+        if (cudaFuncSetAttribute(ss_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return AMC_E_CUDA;
+        if (dev < 64) attr_set[dev] = smem;
+    }
+    const int n_sm = sm_count();
+    const int64_t tiles = (C.cap + ST - 1) / ST;
+    auto grid = [&](int per_sm) { return (int)(tiles < (int64_t)n_sm * per_sm ? tiles : (int64_t)n_sm * per_sm); };
+    uint8_t* w = static_cast<uint8_t*>(C.scratch);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(w);
+    uint32_t* dtot = reinterpret_cast<uint32_t*>(w + align_up(4 * SRAD * (size_t)tiles, 256));
+    ss_hist_kernel<<<grid(8), SNT, 0, s>>>(C.key[0], C.n_dev, C.cap, shift, hist, C.gate);
+    ss_hscan_kernel<<<SRAD, 1024, 0, s>>>(hist, dtot, C.n_dev, C.cap, C.gate);
+    ss_scatter_kernel<<<grid(5), SCT, 0, s>>>(C.key[0], C.val[0], C.key[1], C.val[1], C.n_dev, C.cap, shift, hist,
+                                              dtot, C.gate);
+    BucketParams p;
+    p.key = C.key[1];
+    p.val = C.val[1];
+    p.n_dev = C.n_dev;
+    p.cap = C.cap;
+    p.gate = C.gate;
+    p.dtot = dtot;
+    p.shift = shift;
+    p.n_vars = C.n_vars;
+    p.pos = C.pos;
+    p.init = C.init;
+    p.step = C.step;
+    p.fin = C.fin;
+    p.vff = C.vff;
+    p.ff = C.ff;
+    p.offset = C.offset;
+    p.bm = C.bm;
+    p.tab = host_tables();
+    const int buckets = (int)(((int64_t)C.n_vars + ((int64_t)1 << shift) - 1) >> shift);
+    ss_bucket_kernel<<<buckets < SRAD ? buckets : SRAD, BKW * 32, smem, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 

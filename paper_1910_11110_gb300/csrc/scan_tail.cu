@@ -57,7 +57,7 @@ struct TailShape {
 // 0 never.
 bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh, int force)
 {
-    if (guarded || n_vars < TAIL_MIN_VARS || n_vars > TAIL_MAX_VARS) return false;
+    if (guarded || n_vars < TAIL_MIN_VARS || n_vars > TAIL_MAX_VARS || !bucket_check_ok(n_vars)) return false;
     if (const char* e = getenv("AMC_SCAN_TAIL")) {
         if (e[0] == '0' && e[1] == 0) return false;
         int a = 0, b = 0;
@@ -545,15 +545,17 @@ int scan_tail_launches(const ScanLaunch& L)
 {
     TailShape sh;
     if (!scan_tail_eligible(L) || !tail_shape(L.n_ops, L.n_vars, false, sh, L.tail)) return 0;
-    // a sorted check: three kernels per radix pass, segmented scan
-    const int sorted = 1 + 3 * ss_radix_passes(L.n_vars);
+    // a sorted check: three kernels per radix pass, then the segmented scan's
+    // reduce, carry and apply; a bucket check: one radix pass, the bucket kernel
+    const int sorted = 3 + 3 * ss_radix_passes(L.n_vars);
+    const int bucketed = 3 + 1;
     int epochs = 0;
     for (int64_t e0 = sh.S; e0 < L.n_ops; e0 = epoch_end(sh, e0, L.n_ops)) ++epochs;
     // first part: pairs, its sorted check, the stuck bitmap; per epoch filter,
     // block sums, offsets, gather (which writes the pairs), the candidates'
     // sorted check, gated set-up / scan / final statuses and the gated merge
     // with bitmap rebuild
-    return 1 + sorted + 1 + epochs * (4 + sorted + 3 + 1);
+    return 1 + sorted + 1 + epochs * (4 + bucketed + 3 + 1);
 }
 
 int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
@@ -677,9 +679,8 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
                                                  ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // the candidates, at most C (count on the device), from the epoch's
-        // start statuses; gated off when they overflowed
-        if (cudaMemcpyAsync(fin, st[cur], (size_t)L.n_vars, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return AMC_E_CUDA;
+        // start statuses, checked per bucket of ids (every final status and
+        // bitmap word written); gated off when they overflowed
         SortedCheck K;
         K.key[0] = key0;
         K.key[1] = key1;
@@ -699,7 +700,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
         K.scratch = scratch;
         K.err = L.err;
         K.bm = bm;
-        rc = launch_sorted_check(K, s);
+        rc = launch_bucket_check(K, s);
         if (rc) return rc;
         // fallback, gated on by an overflow: the single-pass scan over all the
         // epoch's ops from its start statuses

@@ -150,6 +150,13 @@ struct SortedCheck {
 __host__ __device__ __forceinline__ uint32_t sorted_code_of(uint32_t ks) { return (ks & 7u) | ((ks >> 1) & 8u); }
 size_t sorted_check_scratch_bytes(int64_t cap);
 int launch_sorted_check(const SortedCheck& C, cudaStream_t s);
+// The same outputs for a set whose ops spread over the variable ids (an
+// epoch's candidates; C.pos required): one radix pass groups the pairs into
+// 128 buckets of consecutive ids, one CTA checks each bucket.  Written into
+// C.bm: whole bitmap words (the set's final statuses).  Buckets of at most
+// 2^13 ids (bucket_check_ok).
+bool bucket_check_ok(int32_t n_vars);
+int launch_bucket_check(const SortedCheck& C, cudaStream_t s);
 // The sort alone: stable LSD radix sort of the pairs key[0] / val[0] by key
 // (keys < n_vars), 7-bit digits, key[1] / val[1] as the second buffers; the
 // result is in buffer (*passes & 1).  scratch: sorted_check_scratch_bytes(cap).
