@@ -486,25 +486,31 @@ __global__ void __launch_bounds__(SNT, 4) ss_apply_kernel(const SegParams p)
     }
 }
 
-// (5) A set over many variables whose ops spread evenly over the variable
-// ids (an epoch's candidates), checked per bucket of ids: one stable radix
-// pass on the top seven bits of the id groups the pairs into 128 buckets of
-// 2^shift consecutive ids, each still in position order; then one CTA per
-// bucket does the whole check of its bucket, as a reduce / carry / apply
-// over its warps' stretches (no CTA waits on another):
-//   (a) warp w folds its stretch of the bucket, 32 pairs at a time (lanes with
-//       the same variable grouped by match.any, the group's first lane
-//       composing them in order), into one function per variable of the
-//       bucket (a row of 2^shift bytes in shared memory);
+// (5) A set over many variables whose ops spread over the variable ids (an
+// epoch's candidates), checked per bucket: one stable radix pass on the low
+// seven bits of the id groups the pairs into 128 buckets (bucket b: the ids
+// v with v mod 128 = b, strided over the whole id range, so hot and cold ids
+// mix and the buckets come out about equal), each still in position order;
+// then one CTA per bucket does the whole check of its bucket, as a reduce /
+// carry / apply over its warps' stretches (no CTA waits on another):
+//   (a) warp w folds its stretch of the bucket, 32 pairs at a time, into one
+//       function per variable of the bucket (a row of ceil(n_vars / 128)
+//       bytes in shared memory, indexed by v / 128): when the batch's
+//       variables are distinct (a bit per variable in shared memory tells)
+//       each lane composes its own, else lanes with the same variable are
+//       grouped (match.any) and the group's first lane composes them in order;
 //   (b) a thread per variable carries the entry status through the warps'
-//       functions: every stretch's entry statuses, the final status and the
-//       stuck bitmap's word;
+//       functions: every stretch's entry statuses, and the final status (and
+//       stuck bit) of a variable whose status changed;
 //   (c) each warp re-runs its stretch from those entry statuses, writing the
 //       statuses that are not F (the caller wrote F everywhere) and the first
 //       faults.
 constexpr int BKW = 16;                   // warps of a bucket CTA
-constexpr int BK_MAX_SHIFT = 13;          // buckets of at most 8,192 ids: 128 KB of rows
+constexpr int BK_MAX_W = 8192;            // variables per bucket (n_vars <= 2^20): 128 KB of rows
 constexpr int BKU = 16;                   // batches of 32 pairs loaded at once
+
+// variables per bucket: the ids b, b + 128, ... below n_vars
+__host__ __device__ __forceinline__ int bucket_width(int32_t n_vars) { return (int)(((int64_t)n_vars + SRAD - 1) / SRAD); }
 
 struct BucketParams {
     const uint32_t* key;        // grouped by bucket, position order inside
@@ -513,7 +519,6 @@ struct BucketParams {
     int64_t cap;
     const int* gate;
     const uint32_t* dtot;       // pairs per bucket
-    int shift;                  // bucket b: ids [b << shift, (b + 1) << shift)
     int32_t n_vars;
     const uint32_t* pos;        // set index -> position in the epoch
     const uint8_t* init;        // nullable: all (V,I)
@@ -522,7 +527,7 @@ struct BucketParams {
     int32_t* vff;
     int64_t* ff;
     int64_t offset;
-    uint32_t* bm;               // nullable: stuck bitmap (whole words written per bucket)
+    uint32_t* bm;               // nullable: stuck bitmap, bits set for variables that become F
     Tables tab;
 };
 
@@ -539,7 +544,7 @@ __device__ __forceinline__ void forget(uint32_t* seen, uint32_t lv) { atomicAnd(
 
 __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketParams p)
 {
-    extern __shared__ __align__(16) uint8_t rows[];        // [BKW][1 << shift], then seen bits [BKW][1 << shift >> 5]
+    extern __shared__ __align__(16) uint8_t rows[];        // [BKW][W], then seen bits [BKW][W / 32]
     __shared__ uint8_t comp[MAX_ELEMS * MAX_ELEMS];
     __shared__ uint8_t app[MAX_ELEMS * 8];
     __shared__ uint8_t elem[16];
@@ -561,16 +566,15 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
         if (tid < SRAD) bstart[tid] = (uint32_t)e;
     }
     const uint32_t ID = p.tab.identity;
-    const int W = 1 << p.shift;
+    const int W = bucket_width(p.n_vars);
     const int64_t n = set_count(p.n_dev, p.cap);
     uint32_t* const seen_all = reinterpret_cast<uint32_t*>(rows + (size_t)BKW * W);
-    uint32_t* const seen = seen_all + w * (W >> 5);       // this warp's bits
-    for (int i = tid; i < BKW * (W >> 5); i += BKW * 32) seen_all[i] = 0;
+    const int WS = (W + 31) >> 5;
+    uint32_t* const seen = seen_all + w * WS;             // this warp's bits
+    for (int i = tid; i < BKW * WS; i += BKW * 32) seen_all[i] = 0;
     __syncthreads();
     for (int b = blockIdx.x; b < SRAD; b += gridDim.x) {
-        const int64_t v0 = (int64_t)b << p.shift;
-        if (v0 >= p.n_vars) break;
-        const int nv = (int)min((int64_t)W, (int64_t)p.n_vars - v0);
+        const int nv = (int)(((int64_t)p.n_vars - b + SRAD - 1) / SRAD);   // ids b, b + 128, ... below n_vars
         const int64_t lo_b = bstart[b];
         const int64_t hi_b = min(n, lo_b + (int64_t)p.dtot[b]);
         const int64_t per = (hi_b - lo_b + BKW - 1) / BKW;
@@ -585,7 +589,7 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
 #pragma unroll
             for (int u = 0; u < BKU; ++u) {
                 const int64_t i = g0 + 32 * u + lane;
-                kk[u] = i < hi ? p.key[i] - (uint32_t)v0 : 0xFFFFFFFFu;
+                kk[u] = i < hi ? p.key[i] >> SDIG : 0xFFFFFFFFu;
                 vv[u] = i < hi ? p.val[i] : 0u;
             }
 #pragma unroll
@@ -612,22 +616,22 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
             }
         }
         __syncthreads();
-        // (b) carry: entry statuses of every stretch, final statuses, bitmap words
-        for (int v = tid; v < ((nv + 31) & ~31); v += BKW * 32) {
-            bool stuck = false;
-            if (v < nv) {
-                uint32_t st = p.init ? (uint32_t)(p.init[v0 + v] & 7u) : (uint32_t)AMC_ST_VI;
-                for (int k = 0; k < BKW; ++k) {
-                    uint8_t* r = rows + (size_t)k * W + v;
-                    const uint32_t e = *r;
-                    *r = (uint8_t)st;
-                    st = app[e * 8 + st];
-                }
-                p.fin[v0 + v] = (uint8_t)st;
-                stuck = st == ST_F;
+        // (b) carry: entry statuses of every stretch; final statuses and stuck
+        // bits of the variables whose status changed (the others keep theirs)
+        for (int lv = tid; lv < nv; lv += BKW * 32) {
+            const int64_t v = (int64_t)lv * SRAD + b;
+            const uint32_t s0 = p.init ? (uint32_t)(p.init[v] & 7u) : (uint32_t)AMC_ST_VI;
+            uint32_t st = s0;
+            for (int k = 0; k < BKW; ++k) {
+                uint8_t* r = rows + (size_t)k * W + lv;
+                const uint32_t e = *r;
+                *r = (uint8_t)st;
+                st = app[e * 8 + st];
             }
-            const uint32_t word = __ballot_sync(0xffffffffu, stuck);
-            if (p.bm && lane == 0) p.bm[(v0 + v) >> 5] = word;
+            if (st != s0) {
+                p.fin[v] = (uint8_t)st;
+                if (p.bm && st == ST_F) atomicOr(p.bm + (v >> 5), 1u << (v & 31));
+            }
         }
         __syncthreads();
         // (c) every pair's status from its stretch's entry statuses
@@ -637,7 +641,7 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
 #pragma unroll
             for (int u = 0; u < BKU; ++u) {
                 const int64_t i = g0 + 32 * u + lane;
-                kk[u] = i < hi ? p.key[i] - (uint32_t)v0 : 0xFFFFFFFFu;
+                kk[u] = i < hi ? p.key[i] >> SDIG : 0xFFFFFFFFu;
                 vv[u] = i < hi ? p.val[i] : 0u;
             }
 #pragma unroll
@@ -677,7 +681,7 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
                         p.step[posi] = (uint8_t)post;
                     } else if (pre != ST_F) {
                         const int64_t g = p.offset + (int64_t)posi;
-                        p.vff[v0 + lv] = (int32_t)g;
+                        p.vff[(int64_t)lv * SRAD + b] = (int32_t)g;
                         if ((unsigned long long)g < gmin) gmin = (unsigned long long)g;
                     }
                 }
@@ -824,20 +828,14 @@ int launch_sorted_check(const SortedCheck& C, cudaStream_t s)
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 
-int bucket_check_shift(int32_t n_vars)
-{
-    const int kb = key_bits_of(n_vars);
-    return kb > SDIG ? kb - SDIG : 0;
-}
-
-bool bucket_check_ok(int32_t n_vars) { return bucket_check_shift(n_vars) <= BK_MAX_SHIFT; }
+bool bucket_check_ok(int32_t n_vars) { return n_vars >= 1 && bucket_width(n_vars) <= BK_MAX_W; }
 
 int launch_bucket_check(const SortedCheck& C, cudaStream_t s)
 {
     if (C.cap <= 0) return AMC_OK;
     if (C.cap > ((int64_t)1 << 28) || !C.pos || !bucket_check_ok(C.n_vars)) return AMC_E_INVALID;
-    const int shift = bucket_check_shift(C.n_vars);
-    const size_t smem = ((size_t)BKW << shift) + ((size_t)BKW << shift >> 3);
+    const int W = bucket_width(C.n_vars);
+    const size_t smem = (size_t)BKW * W + (size_t)BKW * 4 * ((W + 31) / 32);
     static size_t attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -853,9 +851,9 @@ int launch_bucket_check(const SortedCheck& C, cudaStream_t s)
     uint8_t* w = static_cast<uint8_t*>(C.scratch);
     uint32_t* hist = reinterpret_cast<uint32_t*>(w);
     uint32_t* dtot = reinterpret_cast<uint32_t*>(w + align_up(4 * SRAD * (size_t)tiles, 256));
-    ss_hist_kernel<<<grid(8), SNT, 0, s>>>(C.key[0], C.n_dev, C.cap, shift, hist, C.gate);
+    ss_hist_kernel<<<grid(8), SNT, 0, s>>>(C.key[0], C.n_dev, C.cap, 0, hist, C.gate);
     ss_hscan_kernel<<<SRAD, 1024, 0, s>>>(hist, dtot, C.n_dev, C.cap, C.gate);
-    ss_scatter_kernel<<<grid(5), SCT, 0, s>>>(C.key[0], C.val[0], C.key[1], C.val[1], C.n_dev, C.cap, shift, hist,
+    ss_scatter_kernel<<<grid(5), SCT, 0, s>>>(C.key[0], C.val[0], C.key[1], C.val[1], C.n_dev, C.cap, 0, hist,
                                               dtot, C.gate);
     BucketParams p;
     p.key = C.key[1];
@@ -864,7 +862,6 @@ int launch_bucket_check(const SortedCheck& C, cudaStream_t s)
     p.cap = C.cap;
     p.gate = C.gate;
     p.dtot = dtot;
-    p.shift = shift;
     p.n_vars = C.n_vars;
     p.pos = C.pos;
     p.init = C.init;
@@ -875,8 +872,7 @@ int launch_bucket_check(const SortedCheck& C, cudaStream_t s)
     p.offset = C.offset;
     p.bm = C.bm;
     p.tab = host_tables();
-    const int buckets = (int)(((int64_t)C.n_vars + ((int64_t)1 << shift) - 1) >> shift);
-    ss_bucket_kernel<<<buckets < SRAD ? buckets : SRAD, BKW * 32, smem, s>>>(p);
+    ss_bucket_kernel<<<C.n_vars < SRAD ? C.n_vars : SRAD, BKW * 32, smem, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 

@@ -679,8 +679,10 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
                                                  ovf);
         if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
         // the candidates, at most C (count on the device), from the epoch's
-        // start statuses, checked per bucket of ids (every final status and
-        // bitmap word written); gated off when they overflowed
+        // start statuses, checked per bucket of ids (final statuses written
+        // where they change); gated off when they overflowed
+        if (cudaMemcpyAsync(fin, st[cur], (size_t)L.n_vars, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return AMC_E_CUDA;
         SortedCheck K;
         K.key[0] = key0;
         K.key[1] = key1;

@@ -152,9 +152,10 @@ size_t sorted_check_scratch_bytes(int64_t cap);
 int launch_sorted_check(const SortedCheck& C, cudaStream_t s);
 // The same outputs for a set whose ops spread over the variable ids (an
 // epoch's candidates; C.pos required): one radix pass groups the pairs into
-// 128 buckets of consecutive ids, one CTA checks each bucket.  Written into
-// C.bm: whole bitmap words (the set's final statuses).  Buckets of at most
-// 2^13 ids (bucket_check_ok).
+// 128 buckets by the low seven bits of the id, one CTA checks each bucket.
+// Final statuses and stuck bits are written only where a status changes, so
+// C.fin must hold the entry statuses.  At most 2^20 variables
+// (bucket_check_ok).
 bool bucket_check_ok(int32_t n_vars);
 int launch_bucket_check(const SortedCheck& C, cudaStream_t s);
 // The sort alone: stable LSD radix sort of the pairs key[0] / val[0] by key
