@@ -508,9 +508,13 @@ __global__ void __launch_bounds__(SNT, 4) ss_apply_kernel(const SegParams p)
 constexpr int BKW = 16;                   // warps of a bucket CTA
 constexpr int BK_MAX_W = 8192;            // variables per bucket (n_vars <= 2^20): 128 KB of rows
 constexpr int BKU = 16;                   // batches of 32 pairs loaded at once
+constexpr uint32_t BK_ABSENT = 0xFF;      // row byte of a variable with no pair in the stretch
 
-// variables per bucket: the ids b, b + 128, ... below n_vars
-__host__ __device__ __forceinline__ int bucket_width(int32_t n_vars) { return (int)(((int64_t)n_vars + SRAD - 1) / SRAD); }
+// row bytes per bucket: one per id b, b + 128, ... below n_vars, padded to 16
+__host__ __device__ __forceinline__ int bucket_width(int32_t n_vars)
+{
+    return (int)((((int64_t)n_vars + SRAD - 1) / SRAD + 15) & ~(int64_t)15);
+}
 
 struct BucketParams {
     const uint32_t* key;        // grouped by bucket, position order inside
@@ -575,20 +579,21 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
     __syncthreads();
     for (int b = blockIdx.x; b < SRAD; b += gridDim.x) {
         const int nv = (int)(((int64_t)p.n_vars - b + SRAD - 1) / SRAD);   // ids b, b + 128, ... below n_vars
-        const int64_t lo_b = bstart[b];
-        const int64_t hi_b = min(n, lo_b + (int64_t)p.dtot[b]);
-        const int64_t per = (hi_b - lo_b + BKW - 1) / BKW;
-        const int64_t lo = min(hi_b, lo_b + w * per), hi = min(hi_b, lo + per);
+        const int lo_b = (int)bstart[b];
+        const int hi_b = (int)min(n, (int64_t)lo_b + (int64_t)p.dtot[b]);
+        const int per = (hi_b - lo_b + BKW - 1) / BKW;
+        const int lo = min(hi_b, lo_b + w * per), hi = min(hi_b, lo + per);
         uint8_t* row = rows + (size_t)w * W;
-        for (int v = lane; v < nv; v += 32) row[v] = (uint8_t)ID;
+        // rows start as "absent" (no pair of the variable in the stretch yet)
+        for (int v = lane; v < W / 16; v += 32) reinterpret_cast<uint4*>(row)[v] = make_uint4(~0u, ~0u, ~0u, ~0u);
         __syncwarp();
         // (a) fold the stretch per variable; BKU batches of 32 pairs are
         // loaded at once (their loads overlap), then folded one by one
-        for (int64_t g0 = lo; g0 < hi; g0 += 32 * BKU) {
+        for (int g0 = lo; g0 < hi; g0 += 32 * BKU) {
             uint32_t kk[BKU], vv[BKU];
 #pragma unroll
             for (int u = 0; u < BKU; ++u) {
-                const int64_t i = g0 + 32 * u + lane;
+                const int i = g0 + 32 * u + lane;
                 kk[u] = i < hi ? p.key[i] >> SDIG : 0xFFFFFFFFu;
                 vv[u] = i < hi ? p.val[i] : 0u;
             }
@@ -600,13 +605,17 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
                 const uint32_t m = ok ? elem[vv[u] & 15u] : ID;
                 if (!__ballot_sync(0xffffffffu, ok && seen_before(seen, lv))) {
                     // every variable once in the batch: each lane composes alone
-                    if (ok) row[lv] = comp[row[lv] * MAX_ELEMS + m];
+                    if (ok) {
+                        const uint32_t r = row[lv];
+                        row[lv] = r == BK_ABSENT ? (uint8_t)m : comp[r * MAX_ELEMS + m];
+                    }
                 } else {
                     mb[w][lane] = (uint8_t)m;
                     const uint32_t peers = __match_any_sync(0xffffffffu, lv);
                     __syncwarp();
                     if (ok && lane == __ffs(peers) - 1) {
                         uint32_t acc = row[lv];
+                        if (acc == BK_ABSENT) acc = ID;
                         for (uint32_t r = peers; r; r &= r - 1) acc = comp[acc * MAX_ELEMS + mb[w][__ffs(r) - 1]];
                         row[lv] = (uint8_t)acc;
                     }
@@ -616,31 +625,46 @@ __global__ void __launch_bounds__(BKW * 32, 1) ss_bucket_kernel(const BucketPara
             }
         }
         __syncthreads();
-        // (b) carry: entry statuses of every stretch; final statuses and stuck
-        // bits of the variables whose status changed (the others keep theirs)
-        for (int lv = tid; lv < nv; lv += BKW * 32) {
-            const int64_t v = (int64_t)lv * SRAD + b;
-            const uint32_t s0 = p.init ? (uint32_t)(p.init[v] & 7u) : (uint32_t)AMC_ST_VI;
-            uint32_t st = s0;
+        // (b) carry, four variables per step: entry statuses of every
+        // stretch; final statuses and stuck bits of the variables whose status
+        // changed (the others keep theirs).  Four variables that no stretch
+        // touches ("absent" in every row) are skipped.
+        for (int l4 = tid; l4 < (nv + 3) / 4; l4 += BKW * 32) {
+            uint32_t e4[BKW];
+            uint32_t all = ~0u;
+#pragma unroll
             for (int k = 0; k < BKW; ++k) {
-                uint8_t* r = rows + (size_t)k * W + lv;
-                const uint32_t e = *r;
-                *r = (uint8_t)st;
-                st = app[e * 8 + st];
+                e4[k] = reinterpret_cast<const uint32_t*>(rows + (size_t)k * W)[l4];
+                all &= e4[k];
             }
-            if (st != s0) {
-                p.fin[v] = (uint8_t)st;
-                if (p.bm && st == ST_F) atomicOr(p.bm + (v >> 5), 1u << (v & 31));
+            if (all == ~0u) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int lv = 4 * l4 + j;
+                if (lv >= nv) break;
+                const int64_t v = (int64_t)lv * SRAD + b;
+                const uint32_t s0 = p.init ? (uint32_t)(p.init[v] & 7u) : (uint32_t)AMC_ST_VI;
+                uint32_t st = s0;
+#pragma unroll
+                for (int k = 0; k < BKW; ++k) {
+                    const uint32_t e = (e4[k] >> (8 * j)) & 0xFFu;
+                    rows[(size_t)k * W + lv] = (uint8_t)st;
+                    if (e != BK_ABSENT) st = app[e * 8 + st];
+                }
+                if (st != s0) {
+                    p.fin[v] = (uint8_t)st;
+                    if (p.bm && st == ST_F) atomicOr(p.bm + (v >> 5), 1u << (v & 31));
+                }
             }
         }
         __syncthreads();
         // (c) every pair's status from its stretch's entry statuses
         unsigned long long gmin = ~0ull;
-        for (int64_t g0 = lo; g0 < hi; g0 += 32 * BKU) {
+        for (int g0 = lo; g0 < hi; g0 += 32 * BKU) {
             uint32_t kk[BKU], vv[BKU], pp[BKU];
 #pragma unroll
             for (int u = 0; u < BKU; ++u) {
-                const int64_t i = g0 + 32 * u + lane;
+                const int i = g0 + 32 * u + lane;
                 kk[u] = i < hi ? p.key[i] >> SDIG : 0xFFFFFFFFu;
                 vv[u] = i < hi ? p.val[i] : 0u;
             }
