@@ -283,7 +283,10 @@ def run_ours(args):
                first_fault=torch.empty(1, dtype=torch.int64, device=dev))
     ws = torch.empty(amc.trace_workspace_bytes(n_ops, n_vars) + 256, dtype=torch.uint8, device=dev)
     ws = ws[(-ws.data_ptr()) % 256:]
-    stream = torch.cuda.current_stream()
+    # a stream of its own: once the size class is tuned, the library replays
+    # the check as a captured graph (the legacy default stream cannot be captured)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
 
     def step():
         amc.check_trace(ks, var, n_vars, out=out, workspace=ws, stream=stream)

@@ -51,6 +51,38 @@ GraphCache& graph_cache()
     return *c;
 }
 
+// Repeated trace checks replay a captured graph unless AMC_TRACE_GRAPH=0 or
+// the stream is the legacy default stream (which cannot be captured) or is
+// being captured by the caller.
+bool trace_graphs_enabled(cudaStream_t s)
+{
+    const char* e = getenv("AMC_TRACE_GRAPH");
+    if (e && e[0] == '0') return false;
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) return false;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone) return false;
+    return true;
+}
+
+// The tuning knobs the launch functions read per call, as part of a graph key
+// (a changed knob captures a new graph).
+void append_knobs(std::vector<uintptr_t>& key)
+{
+    static const char* const knobs[] = {"AMC_SCAN_FB_BITS", "AMC_SCAN_GROUP", "AMC_SCAN_CTAS_PER_SM",
+                                        "AMC_SCAN_DENSE", "AMC_SCAN_DENSE_SORT", "AMC_SCAN_PREFIX",
+                                        "AMC_SCAN_TAIL"};
+    for (const char* k : knobs) {
+        const char* v = getenv(k);
+        uintptr_t h = 1469598103934665603ull;         // FNV-1a of the value (0 when unset)
+        if (!v) {
+            h = 0;
+        } else {
+            for (const char* c = v; *c; ++c) h = (h ^ (uint8_t)*c) * 1099511628211ull;
+        }
+        key.push_back(h);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -153,7 +185,44 @@ int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
         const int i = atoi(e);
         if (i >= 0 && i < 6) return run(i);
     }
-    return autotune_run(shape_key("trace", n_ops, n_vars, init_status ? 1 : 0), 6, 0, s, run);
+    const std::string key = shape_key("trace", n_ops, n_vars, init_status ? 1 : 0);
+    const int pick = autotune_lookup(key);
+    if (pick < 0 || !trace_graphs_enabled(s)) return autotune_run(key, 6, 0, s, run);
+    // the size class is decided: the launch sequence depends only on the
+    // arguments and the tuning knobs, so it is captured once into a CUDA graph
+    // and replayed (one launch instead of one per kernel)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<uintptr_t> gkey = {0x7472616365,        (uintptr_t)dev,           (uintptr_t)s,
+                                  (uintptr_t)kind_side, (uintptr_t)var,           (uintptr_t)n_ops,
+                                  (uintptr_t)n_vars,    (uintptr_t)init_status,   (uintptr_t)step_status,
+                                  (uintptr_t)final_status, (uintptr_t)var_first_fault, (uintptr_t)first_fault,
+                                  (uintptr_t)workspace, (uintptr_t)pick};
+    append_knobs(gkey);
+    GraphCache& gc = graph_cache();
+    std::lock_guard<std::mutex> lock(gc.mu);
+    auto it = gc.execs.find(gkey);
+    if (it == gc.execs.end()) {
+        L.profile = 0;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return AMC_E_CUDA;
+        const int rc = run(pick);
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess) return AMC_E_CUDA;
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return AMC_E_CUDA;
+        it = gc.execs.emplace(gkey, ex).first;
+    }
+    profile_begin(s);
+    const cudaError_t le = cudaGraphLaunch(it->second, s);
+    profile_end(s);
+    return le == cudaSuccess ? AMC_OK : AMC_E_CUDA;
 }
 
 int amc_check_trace_plan(int64_t n_ops, int32_t n_vars, int has_init, int32_t* path, int32_t* launches)

@@ -193,3 +193,37 @@ def test_many_long_lived_variables(amc, oracle_mod, monkeypatch):
         var[pos] = who
         ks[pos] = rng.choice(np.array([0x00, 0x01, 0x04], np.uint8), size=tot)
     check(amc, oracle_mod, ks, var, nv)
+
+
+def test_graph_replay_on_a_side_stream(amc, oracle_mod, monkeypatch):
+    # once a size class is tuned, checks on a non-default stream replay a
+    # captured graph of the launch sequence: repeated calls on the same buffers
+    # with new contents each time (and a changed knob, which captures anew)
+    # must still give the oracle's outputs
+    dev = torch.device("cuda")
+    n, nv = 300_011, 40_000
+    s = torch.cuda.Stream()
+    ks_d = torch.empty(n, dtype=torch.uint8, device=dev)
+    var_d = torch.empty(n, dtype=torch.int32, device=dev)
+    out = dict(step_status=torch.empty(n, dtype=torch.uint8, device=dev),
+               final_status=torch.empty(nv, dtype=torch.uint8, device=dev),
+               var_first_fault=torch.empty(nv, dtype=torch.int32, device=dev),
+               first_fault=torch.empty(1, dtype=torch.int64, device=dev))
+    ws = torch.empty(amc.trace_workspace_bytes(n, nv) + 256, dtype=torch.uint8, device=dev)
+    ws = ws[(-ws.data_ptr()) % 256:]
+    rng = np.random.default_rng(97)
+    for shape in ("14,16", "14,16", "14,16", "15,-2", "15,-2"):
+        monkeypatch.setenv("AMC_SCAN_TAIL", shape)
+        ks, var = workloads.trace_random(rng, n, nv, zipf_s=1.05)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            ks_d.copy_(torch.from_numpy(ks))
+            var_d.copy_(torch.from_numpy(var))
+            amc.check_trace(ks_d, var_d, nv, out=out, workspace=ws, stream=s)
+        s.synchronize()
+        assert amc.sync_status() == 0
+        exp = oracle_mod.check_trace(ks, var, nv)
+        assert np.array_equal(out["step_status"].cpu().numpy(), exp[0]), shape
+        assert np.array_equal(out["final_status"].cpu().numpy(), exp[1]), shape
+        assert np.array_equal(out["var_first_fault"].cpu().numpy(), exp[2]), shape
+        assert int(out["first_fault"].cpu()[0]) == exp[3], shape
