@@ -1,6 +1,7 @@
 // scan_sorted.cu -- a set of ops checked by grouping it by variable: a stable
 // radix sort of (variable, index) pairs, then a segmented scan of the transfer
-// functions over each variable's run.
+// functions over each variable's run; or, for a set whose ops spread over the
+// variable ids, one radix pass into buckets checked one CTA each.
 //
 // It computes what the single-pass scan computes for the same ops in the same
 // order.  An op's status depends only on the earlier ops on its variable (Fig.
@@ -12,14 +13,15 @@
 //   1. pairs: key = variable id, value = index of the op in the set << 4 | its
 //      kind and side (4 bits);
 //   2. LSD radix sort by key, 7-bit digits; per pass a histogram per tile of
-//      4,096 pairs, an exclusive scan of each digit's row over the tiles (one
+//      2,048 pairs, an exclusive scan of each digit's row over the tiles (one
 //      CTA per digit; the digits' totals are scanned by every scatter CTA),
-//      and a stable scatter
-//      (each pair's rank from per-thread digit counters in shared memory over a
-//      blocked arrangement, the tile staged in shared memory in digit order);
-//   3. segmented scan over the sorted pairs in one pass (decoupled look-back
-//      over the tiles' published values gives the carry into each tile's
-//      leading run), every op's prefix applied to its variable's entry status.
+//      and a stable scatter (ranks within each warp from one ballot per digit
+//      bit, per-warp digit counters, the tile staged in shared memory in
+//      digit order);
+//   3. segmented scan over the sorted pairs as reduce / carry / apply over the
+//      tiles, every op's prefix applied to its variable's entry status.
+// The bucket check (5) replaces 2-3 by one radix pass on the low seven bits
+// of the id and one CTA per bucket.
 // Outputs: the status of every op whose status is not F (the caller has
 // written F at every position of the set), the first fault of each variable
 // that faults in the set, the global first fault, and the final statuses.

@@ -1,5 +1,5 @@
 // scan_tail.cu -- long traces checked in epochs: stream filter, compacted
-// candidates, each set checked by sorting it by variable.
+// candidates, each set checked grouped by variable.
 //
 // Section 3.2: F is absorbing, so once a variable's status is F every later
 // op on it yields F (Property Progress: a stuck variable stays stuck).  On a
@@ -12,11 +12,13 @@
 //   2. a streaming kernel writes F at every position and collects the ops on
 //      variables outside the bitmap ("candidates"), in position order;
 //   3. the candidates, a set of ops over the same variables (an op's status
-//      depends only on the earlier ops on its variable), are checked by
-//      sorting them by variable, from the epoch's start statuses, with their
-//      count read from device memory: the statuses that are not F go to their
-//      positions, first faults to trace positions, final statuses start the
-//      next epoch.
+//      depends only on the earlier ops on its variable), are checked from the
+//      epoch's start statuses, with their count read from device memory: one
+//      radix pass groups them into 128 buckets by the low seven bits of the
+//      variable id (position order kept inside a bucket), one CTA checks each
+//      bucket (scan_sorted.cu, bucket check); the statuses that are not F go
+//      to their positions, first faults to trace positions, final statuses
+//      start the next epoch.
 // Outputs are identical to one scan over the whole trace.  An epoch whose
 // candidates overflow their slots is rechecked whole by the single-pass scan.
 #include <cstdio>
@@ -553,7 +555,7 @@ int scan_tail_launches(const ScanLaunch& L)
     for (int64_t e0 = sh.S; e0 < L.n_ops; e0 = epoch_end(sh, e0, L.n_ops)) ++epochs;
     // first part: pairs, its sorted check, the stuck bitmap; per epoch filter,
     // block sums, offsets, gather (which writes the pairs), the candidates'
-    // sorted check, gated set-up / scan / final statuses and the gated merge
+    // bucket check, gated set-up / scan / final statuses and the gated merge
     // with bitmap rebuild
     return 1 + sorted + 1 + epochs * (4 + bucketed + 3 + 1);
 }
@@ -631,7 +633,7 @@ int launch_scan_tail(const ScanLaunch& L, cudaStream_t s)
     rc = launch_sorted_check(A, s);
     if (rc) return rc;
     // the stuck bitmap at the first epoch's start; later epochs add the
-    // variables that become stuck (the sorted checks set their bits, the
+    // variables that become stuck (the bucket checks set their bits, the
     // fallback rebuilds it)
     tail_bitmap_kernel<<<(unsigned)((L.n_vars + 255) / 256), 256, 0, s>>>(st[0], L.n_vars, bm);
 
