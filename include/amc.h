@@ -127,6 +127,11 @@ AMC_API size_t amc_check_trace_workspace(int64_t n_ops, int32_t n_vars);
  *                        time them, each run reading init_status)
  *   step_status [n_ops], final_status [n_vars], var_first_fault [n_vars],
  *   first_fault [1]      outputs (int64)
+ * Once the size class is tuned, a call on a stream other than the legacy
+ * default stream (and not being captured by the caller) captures its launch
+ * sequence into a CUDA graph, kept until exit and keyed by every argument and
+ * the AMC_SCAN_* tuning knobs, and later calls with the same key replay it
+ * (AMC_TRACE_GRAPH=0 turns this off); the results are the same either way.
  * Errors: AMC_E_INVALID for negative sizes, NULL or overlapping buffers,
  * AMC_E_NOMEM when ws_bytes is too small.  Ids out of range or malformed op
  * bytes are reported through amc_sync_status (AMC_E_RANGE / AMC_E_INVALID). */
