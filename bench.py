@@ -1233,7 +1233,7 @@ TRACE_PATH_TEXT = {
     "dense": "dense reduce + carry + apply kernels",
     "prefix": "prefix (dense reduce + carry + apply) + scan_trace_kernel",
     "epochs": ("first part: sorted check (radix sort by variable + segmented scan); epochs to 4x their start: "
-               "tail_filter_kernel + gather + sorted check of the candidates"),
+               "tail_filter_kernel + gather + bucket check of the candidates (one radix pass, a CTA per bucket)"),
     "scan": "scan_trace_kernel",
 }
 

@@ -41,7 +41,7 @@ constexpr int64_t CAND_MAX = (int64_t)1 << 27;   // and at most 2^27 (set index 
 constexpr int TF_PER = 16;                // ops per lane and step
 constexpr int TAIL_MIN_VARS = 16385;      // fewer variables take the reduce / carry / apply path
 constexpr int TAIL_MAX_VARS = 1 << 20;    // bitmap of 128 KB in shared memory
-constexpr int DEFAULT_FIRST_LOG2 = 22;    // first part 2^22 ops,
+constexpr int DEFAULT_FIRST_LOG2 = 21;    // first part 2^21 ops,
 constexpr int DEFAULT_GROW = 2;           // then epochs ending at 4 times their start
 constexpr int64_t DEFAULT_MIN_OPS = (int64_t)1 << 29;
 
@@ -55,7 +55,7 @@ struct TailShape {
 // part 2^s ops, each epoch ending at 2^g times its start; for every trace
 // longer than 2^s ops (test and tuning override); "0" disables.
 // force: -1 by size (from DEFAULT_MIN_OPS ops), 1 for every trace longer than
-// 2^22 ops (first part 2^22 ops from 2^24 ops on, else a quarter of the trace),
+// 2^21 ops (first part 2^21 ops from 2^23 ops on, else a quarter of the trace),
 // 0 never.
 bool tail_shape(int64_t n_ops, int32_t n_vars, bool guarded, TailShape& sh, int force)
 {

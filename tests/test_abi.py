@@ -128,8 +128,8 @@ def test_trace_plan_follows_the_size_rule(monkeypatch):
     # the epoch path from 2^29 ops: pairs + 3 radix passes (3 kernels each) +
     # segmented scan (reduce, carry, apply) + bitmap, then 12 kernels per epoch
     # (filter, block sums, offsets, gather, one radix pass, bucket check,
-    # gated fallback and merge; 2^22 -> 2^24 -> 2^26 -> 2^28 -> 2^30)
-    assert plan(1 << 30, 1 << 20) == ("epochs", 14 + 12 * 4)
+    # gated fallback and merge; 2^21 -> 2^23 -> 2^25 -> 2^27 -> 2^29 -> 2^30)
+    assert plan(1 << 30, 1 << 20) == ("epochs", 14 + 12 * 5)
     assert plan(1 << 29, 1 << 20) == ("epochs", 14 + 12 * 4)
     monkeypatch.setenv("AMC_SCAN_TAIL", "0")
     assert plan(1 << 30, 1 << 20) == ("prefix", 7)

@@ -2,7 +2,7 @@
 its candidates on the first call of a size class: the path by size with the
 single-pass scan's stuck bitmap read through L1, from shared memory or not at
 all, with and without tile groups; the reduce / carry / apply path forced at
-any size; the epoch path forced on every trace longer than 2^22 ops (else the
+any size; the epoch path forced on every trace longer than 2^21 ops (else the
 single-pass scan alone).  AMC_TRACE_CANDIDATE picks one of them untimed.
 Bit-exact against the oracle on every output, with and without initial
 statuses; amc_check_trace_plan names the path each candidate takes."""

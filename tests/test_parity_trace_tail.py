@@ -4,7 +4,7 @@ the compacted candidates checked by sorting them by variable from the epoch's
 start statuses, which also adds the variables that become stuck to the
 bitmap).
 
-Traces over 16,385 to 2^20 variables take it from 2^29 ops on (first part 2^22
+Traces over 16,385 to 2^20 variables take it from 2^29 ops on (first part 2^21
 ops, each epoch ending at four times its start); AMC_SCAN_TAIL="s,e" forces a
 first part of 2^s ops and epochs of 2^e ops, "s,-g" epochs ending at 2^g times
 their start, at any length, so that many epochs, ragged last epochs, epochs
@@ -90,8 +90,8 @@ def test_bad_input_in_the_tail(amc, monkeypatch):
 
 
 def test_default_split_at_2p29(amc, oracle_mod):
-    # 2^29 ops over 2^20 variables: the default first part (2^22 ops) and
-    # epochs ending at 2^24, 2^26, 2^28 and 2^29 ops, against the oracle on
+    # 2^29 ops over 2^20 variables: the default first part (2^21 ops) and
+    # epochs ending at 2^23, 2^25, 2^27 and 2^29 ops, against the oracle on
     # every output
     ks, var = workloads.trace_zipf(1 << 29, 1 << 20, seed=94, device="cuda")
     check(amc, oracle_mod, ks.cpu().numpy(), var.cpu().numpy(), 1 << 20)
