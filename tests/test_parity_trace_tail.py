@@ -227,3 +227,14 @@ def test_graph_replay_on_a_side_stream(amc, oracle_mod, monkeypatch):
         assert np.array_equal(out["final_status"].cpu().numpy(), exp[1]), shape
         assert np.array_equal(out["var_first_fault"].cpu().numpy(), exp[2]), shape
         assert int(out["first_fault"].cpu()[0]) == exp[3], shape
+
+
+@pytest.mark.parametrize("n_vars", [16_385, 100_003])
+def test_bucket_widths(amc, oracle_mod, monkeypatch, n_vars):
+    # the epochs' candidates go to 128 buckets of the ids v with v mod 128 = b:
+    # 129 ids per bucket (rows padded) at the smallest variable count the epoch
+    # path takes, and a count that leaves the last buckets one id short
+    monkeypatch.setenv("AMC_SCAN_TAIL", "14,-2")
+    rng = np.random.default_rng(98)
+    ks, var = workloads.trace_random(rng, 600_001, n_vars, zipf_s=1.05)
+    check(amc, oracle_mod, ks, var, n_vars)
