@@ -17,7 +17,11 @@
 // variable (stable radix sort of (variable, index) pairs, scan_sorted.cu) and
 // runs one segmented scan of the elements over the sorted pairs (decoupled
 // look-back over tiles claimed in order), applying each prefix to its
-// variable's initial status.
+// variable's initial status.  The pairs' keys carry the op byte above the
+// variable id's bits (up to 2^21 variables), so the scan reads its ops in
+// sorted order instead of gathering them; F is written at every position
+// first (F is absorbing: on a long trace nearly every op sees it), and the
+// scan writes only the statuses that are not F.
 #include "amc_internal.cuh"
 #include "kloc.cuh"
 #include "scan_trace.cuh"
@@ -36,6 +40,7 @@ constexpr uint32_t KVAL = (1u << 23) - 1u;
 constexpr uint32_t KIDENT = 0x7Fu << 7;  // G {}, K all, S {}
 constexpr uint32_t KNOKEY = 0xFFFFFFFFu;
 constexpr uint32_t TS_AGG = 1u << 30, TS_INCL = 2u << 30, TS_FLAGS = 3u << 30;
+constexpr int KOP_SHIFT = 21;            // op byte in key bits 21-28 when n_vars <= 2^21
 
 __device__ __forceinline__ uint32_t kcomp(uint32_t f, uint32_t g)
 {
@@ -80,12 +85,13 @@ __device__ __forceinline__ uint32_t kseg(uint32_t x, uint32_t y)
     return (x & KRUN) | kcomp(x & (KRUN - 1u), y & (KRUN - 1u));
 }
 
-// pairs (var, index); every op byte and id checked; initial statuses checked;
-// final statuses and first faults initialised
+// pairs (var | op << KOP_SHIFT when packed, index); every op byte and id
+// checked; F written at every position; initial statuses checked; final
+// statuses and first faults initialised
 __global__ void kl_keys_kernel(const uint8_t* __restrict__ op, const int32_t* __restrict__ var, int64_t n,
-                               int32_t n_vars, int k, uint32_t* __restrict__ key, uint32_t* __restrict__ val,
-                               const uint8_t* __restrict__ init, uint8_t* __restrict__ fin, int32_t* __restrict__ vff,
-                               int64_t* ff, int* err)
+                               int32_t n_vars, int k, int pack, uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                               uint8_t* __restrict__ step, const uint8_t* __restrict__ init, uint8_t* __restrict__ fin,
+                               int32_t* __restrict__ vff, int64_t* ff, int* err)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,8 +104,9 @@ __global__ void kl_keys_kernel(const uint8_t* __restrict__ op, const int32_t* __
             raise_error(err, AMC_E_RANGE);
             uv = 0;
         }
-        key[i] = uv;
+        key[i] = pack ? (uv | o << KOP_SHIFT) : uv;
         val[i] = (uint32_t)i;
+        step[i] = (uint8_t)KL_F;
     }
     for (int64_t v = g; v < n_vars; v += stride) {
         uint8_t s = 1;                                          // valid in location 0 only
@@ -114,6 +121,8 @@ __global__ void kl_keys_kernel(const uint8_t* __restrict__ op, const int32_t* __
 }
 
 struct KSegParams {
+    uint32_t vmask;         // variable bits of a key
+    int pack;               // keys carry the op byte
     const uint32_t* key;
     const uint32_t* val;
     int64_t n;
@@ -150,8 +159,15 @@ __global__ void __launch_bounds__(KNT) kl_seg_kernel(const KSegParams p)
             vv[u] = in ? p.val[b + i0 + u] : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < KE; ++u) el[u] = kk[u] != KNOKEY ? kelem(p.op[vv[u]]) : KIDENT;
-        uint32_t prev = (b + i0 > 0 && b + i0 - 1 < p.n) ? p.key[b + i0 - 1] : KNOKEY;
+        for (int u = 0; u < KE; ++u) {
+            if (kk[u] == KNOKEY) {
+                el[u] = KIDENT;
+                continue;
+            }
+            el[u] = kelem(p.pack ? (kk[u] >> KOP_SHIFT) & 0xFFu : p.op[vv[u]]);
+            kk[u] &= p.vmask;                                   // the variable alone from here on
+        }
+        uint32_t prev = (b + i0 > 0 && b + i0 - 1 < p.n) ? (p.key[b + i0 - 1] & p.vmask) : KNOKEY;
         uint32_t heads = 0, agg = KIDENT;
 #pragma unroll
         for (int u = 0; u < KE; ++u) {
@@ -201,7 +217,7 @@ __global__ void __launch_bounds__(KNT) kl_seg_kernel(const KSegParams p)
                     if ((v & TS_INCL) || (v & KRUN)) break;
                 }
                 st_release(p.tstat + tile, TS_INCL | (kseg(prefix, all) & KVAL));
-                if (p.key[b - 1] == p.key[b]) carry = prefix & (KRUN - 1u);
+                if (((p.key[b - 1] ^ p.key[b]) & p.vmask) == 0) carry = prefix & (KRUN - 1u);
             }
             s_carry = carry;
         }
@@ -209,7 +225,8 @@ __global__ void __launch_bounds__(KNT) kl_seg_kernel(const KSegParams p)
         // the carry reaches this thread's first run only if no run starts
         // before it in the tile
         uint32_t run = (ex & KRUN) ? (ex & (KRUN - 1u)) : kcomp(s_carry, ex & (KRUN - 1u));
-        const uint32_t after = (b + i0 + KE < p.n) ? p.key[b + i0 + KE] : KNOKEY;
+        const uint32_t after = (b + i0 + KE < p.n) ? (p.key[b + i0 + KE] & p.vmask) : KNOKEY;
+        unsigned long long gmin = ~0ull;
 #pragma unroll
         for (int u = 0; u < KE; ++u) {
             const uint32_t kv = kk[u];
@@ -220,16 +237,21 @@ __global__ void __launch_bounds__(KNT) kl_seg_kernel(const KSegParams p)
             const uint32_t s0 = p.init ? p.init[kv] : 1u;
             const uint32_t pre_s = kapply(before, s0);
             const uint32_t post = kapply(run, s0);
-            p.step[vv[u]] = (uint8_t)post;
+            if (post != KL_F) p.step[vv[u]] = (uint8_t)post;    // F is there already
             if (post == KL_F && pre_s != KL_F) {
                 p.vff[kv] = (int32_t)vv[u];
-                const unsigned long long g = vv[u];
-                if (g < *reinterpret_cast<volatile unsigned long long*>(p.ff))
-                    atomicMin(reinterpret_cast<unsigned long long*>(p.ff), g);
+                if ((unsigned long long)vv[u] < gmin) gmin = vv[u];
             }
             const uint32_t next = u + 1 < KE ? kk[u + 1] : after;
             if (next != kv) p.fin[kv] = (uint8_t)post;
         }
+        // the warp's smallest first fault, one atomic per warp
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, gmin, d);
+            if (o < gmin) gmin = o;
+        }
+        if (lane == 0 && gmin != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(p.ff), gmin);
         __syncthreads();
     }
 }
@@ -271,8 +293,9 @@ int launch_kloc(const KlocLaunch& L, cudaStream_t s)
     const int64_t work = L.n_ops > L.n_vars ? L.n_ops : L.n_vars;
     const int64_t blocks = (work + 255) / 256;
     const int kgrid = (int)(blocks < (int64_t)n_sm * 8 ? (blocks > 0 ? blocks : 1) : (int64_t)n_sm * 8);
-    kl_keys_kernel<<<kgrid, 256, 0, s>>>(L.op, L.var, L.n_ops, L.n_vars, L.k, key[0], val[0], L.init, L.final_status,
-                                         L.vff, L.first_fault, L.err);
+    const int pack = L.n_vars <= (1 << KOP_SHIFT) ? 1 : 0;
+    kl_keys_kernel<<<kgrid, 256, 0, s>>>(L.op, L.var, L.n_ops, L.n_vars, L.k, pack, key[0], val[0], L.step, L.init,
+                                         L.final_status, L.vff, L.first_fault, L.err);
     if (cudaGetLastError() != cudaSuccess) return AMC_E_CUDA;
     if (L.n_ops > 0) {
         int passes = 0;
@@ -281,6 +304,8 @@ int launch_kloc(const KlocLaunch& L, cudaStream_t s)
         const int64_t tiles = (L.n_ops + KT - 1) / KT;
         if (cudaMemsetAsync(w + lay.tstat, 0, lay.total - lay.tstat, s) != cudaSuccess) return AMC_E_CUDA;
         KSegParams p;
+        p.vmask = pack ? (1u << KOP_SHIFT) - 1u : 0xFFFFFFFFu;
+        p.pack = pack;
         p.key = key[passes & 1];
         p.val = val[passes & 1];
         p.n = L.n_ops;
