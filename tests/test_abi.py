@@ -131,6 +131,13 @@ def test_trace_plan_follows_the_size_rule(monkeypatch):
     # gated fallback and merge; 2^21 -> 2^23 -> 2^25 -> 2^27 -> 2^29 -> 2^30)
     assert plan(1 << 30, 1 << 20) == ("epochs", 14 + 12 * 5)
     assert plan(1 << 29, 1 << 20) == ("epochs", 14 + 12 * 4)
+    # the epoch path's bounds: from 2^29 ops, 16,385 to 2^20 variables (the
+    # stuck bitmap fills 128 KB of shared memory; fewer variables take the
+    # reduce / carry / apply path)
+    assert plan(1 << 29, 16_385) == ("epochs", 14 + 12 * 4)
+    assert plan((1 << 29) - 1, 16_385)[0] == "prefix"
+    assert plan(1 << 29, 16_384)[0] == "dense"
+    assert plan(1 << 29, (1 << 20) + 1)[0] == "scan"
     monkeypatch.setenv("AMC_SCAN_TAIL", "0")
     assert plan(1 << 30, 1 << 20) == ("prefix", 7)
     monkeypatch.setenv("AMC_SCAN_DENSE", "0")
