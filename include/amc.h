@@ -131,7 +131,8 @@ AMC_API size_t amc_check_trace_workspace(int64_t n_ops, int32_t n_vars);
  * default stream (and not being captured by the caller) captures its launch
  * sequence into a CUDA graph, kept until exit and keyed by every argument and
  * the AMC_SCAN_* tuning knobs, and later calls with the same key replay it
- * (AMC_TRACE_GRAPH=0 turns this off); the results are the same either way.
+ * (AMC_TRACE_GRAPH=0 turns this off; past 256 captured argument sets, new ones
+ * run without a graph); the results are the same either way.
  * Errors: AMC_E_INVALID for negative sizes, NULL or overlapping buffers,
  * AMC_E_NOMEM when ws_bytes is too small.  Ids out of range or malformed op
  * bytes are reported through amc_sync_status (AMC_E_RANGE / AMC_E_INVALID). */

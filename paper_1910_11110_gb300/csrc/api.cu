@@ -51,6 +51,15 @@ GraphCache& graph_cache()
     return *c;
 }
 
+constexpr int MAX_TRACE_GRAPHS = 256;
+
+// Trace-check graphs captured so far (under the graph cache's lock).
+int& trace_graph_count()
+{
+    static int n = 0;
+    return n;
+}
+
 // Repeated trace checks replay a captured graph unless AMC_TRACE_GRAPH=0 or
 // the stream is the legacy default stream (which cannot be captured) or is
 // being captured by the caller.
@@ -203,6 +212,9 @@ int amc_check_trace(const uint8_t* kind_side, const int32_t* var, int64_t n_ops,
     std::lock_guard<std::mutex> lock(gc.mu);
     auto it = gc.execs.find(gkey);
     if (it == gc.execs.end()) {
+        // graphs are kept until exit: past MAX_TRACE_GRAPHS distinct argument
+        // sets, further ones run without a graph
+        if (++trace_graph_count() > MAX_TRACE_GRAPHS) return run(pick);
         L.profile = 0;
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return AMC_E_CUDA;
